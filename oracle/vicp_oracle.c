@@ -31,8 +31,10 @@
  *     its already-labelled neighbours (the label is the root voxel, Sec. 3).
  *   - NNS (Alg. 4): only the root voxel's segment is searched; squared
  *     distance ((dx*dx + dy*dy) + dz*dz) in float; strict minimum, ties to the
- *     smaller target index.  R, t are the float-rounded pose entries and
- *     s_a = ((R_a0*x + R_a1*y) + R_a2*z) + t_a.
+ *     smaller target index, a NaN distance after every number.  R, t are
+ *     the float-rounded pose entries and s_a = ((R_a0*x + R_a1*y) + R_a2*z) + t_a.
+ *   - Grid fit ignores NaN coordinates; a target without any finite
+ *     coordinate on some axis has no grid (status 1).
  *   - Rigid update (Eq. 1): no rejection; centroids and cross-covariance in
  *     double (two passes); SVD by one-sided Jacobi; reflection fixed by
  *     diag(1,1,sign det(V U^T)); pose T <- dT * T; source points are always
@@ -66,17 +68,17 @@ int og_fit_grid(const float *tgt, int32_t n, float voxel_size, int32_t divisions
 {
     if (n < 1)
         return OG_ERR_INVALID;
-    float lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = tgt[a];
-        hi[a] = tgt[a];
-    }
-    for (int32_t j = 1; j < n; ++j)
+    /* NaN coordinates never compare less or greater, so they are left out. */
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int32_t j = 0; j < n; ++j)
         for (int a = 0; a < 3; ++a) {
             float c = tgt[4 * (int64_t)j + a];
             if (c < lo[a]) lo[a] = c;
             if (c > hi[a]) hi[a] = c;
         }
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(lo[a]) || !isfinite(hi[a]))
+            return OG_ERR_INVALID;
     float ext[3];
     float extent = 0.0f;
     for (int a = 0; a < 3; ++a) {
@@ -258,6 +260,19 @@ static void og_transform(const double pose[16], const float *p, float s[3])
     }
 }
 
+/* Candidate order of the nearest-neighbour search: smaller squared distance
+ * first, NaN after every number, equal distances to the smaller index. */
+static int og_better(float d, int32_t j, float bd, int32_t bj)
+{
+    if (bj < 0)
+        return 1;
+    if (isnan(d) != isnan(bd))
+        return isnan(bd);
+    if (!isnan(d) && d != bd)
+        return d < bd;
+    return j < bj;
+}
+
 static float og_dist2(const float s[3], const float *q)
 {
     float dx = s[0] - q[0];
@@ -287,7 +302,7 @@ void og_correspond(const og_grid *g, const uint32_t *off, const int32_t *ids, co
             for (uint32_t k = off[r]; k < off[r + 1]; ++k) {
                 int32_t j = ids[k];
                 float d = og_dist2(s, tgt + 4 * (int64_t)j);
-                if (best < 0 || d < bd || (d == bd && j < best)) {
+                if (og_better(d, j, bd, best)) {
                     best = j;
                     bd = d;
                 }
@@ -297,7 +312,7 @@ void og_correspond(const og_grid *g, const uint32_t *off, const int32_t *ids, co
             /* Global search over the whole target set. */
             for (int32_t j = 0; j < n; ++j) {
                 float d = og_dist2(s, tgt + 4 * (int64_t)j);
-                if (best < 0 || d < bd || (d == bd && j < best)) {
+                if (og_better(d, j, bd, best)) {
                     best = j;
                     bd = d;
                 }

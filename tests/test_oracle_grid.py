@@ -134,3 +134,12 @@ def test_build_grid_matches_steps(pairs):
     assert np.array_equal(b["ids"], oracle.csr(keys, b["off"]))
     root, ring = oracle.dilate(g, b["off"], 10)
     assert np.array_equal(b["root"], root) and np.array_equal(b["ring"], ring)
+
+
+def test_fit_grid_ignores_nan_coordinates():
+    p = np.array([[np.nan, 0, 0, 0], [0.5, 1.0, -2.0, 0], [1.5, 0.0, 0.0, 0]], np.float32)
+    g = oracle.fit_grid(p, 0.25, 0)
+    assert g.origin == (0.5, 0.0, -2.0)
+    assert g.dims == (5, 5, 9)
+    with pytest.raises(ValueError):
+        oracle.fit_grid(np.array([[np.nan, 0, 0, 0]], np.float32), 0.25, 0)

@@ -122,3 +122,14 @@ def test_reduce_matches_two_pass_definition(pairs):
     Hw = (s - s.mean(0)).T @ (q - q.mean(0))
     assert np.allclose(H, Hw, rtol=1e-12, atol=1e-12)
     assert abs(rmse - np.sqrt(((s - q) ** 2).sum(1).mean())) < 1e-13
+
+
+def test_nan_target_never_beats_a_number():
+    """A target point with a NaN coordinate has a NaN distance; the search
+    orders NaN after every number, wherever the NaN point sits in the list."""
+    tgt = np.array([[np.nan, 0, 0, 0], [3, 0, 0, 0], [2, 0, 0, 0], [np.nan, 1, 1, 0]], np.float32)
+    src = np.zeros((1, 4), np.float32)
+    g = oracle.explicit_grid((5, 5, 5), 1.0, (1, 1, 1))      # source outside: global search
+    b = oracle.build_grid(g, tgt, 0)
+    nn, d2, fb = oracle.correspond(g, b, tgt, src, np.eye(4))
+    assert fb[0] and nn[0] == 2 and d2[0] == 4.0
