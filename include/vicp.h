@@ -1,0 +1,259 @@
+/*
+ * vicp.h -- C ABI of the GB300 (sm_103a) dilation-based ICP library.
+ *
+ * The library implements the data-parallel hot path of dilation-based ICP
+ * (VANICP) with per-voxel dynamic memory assignment, arXiv 2512.04996:
+ * voxelise the target and count points per voxel (Alg. 1, GPU part), turn
+ * the counts into segment offsets (Alg. 1, CPU part -- here a parallel
+ * exclusive scan on the GPU), scatter point indices into a compact CSR store
+ * (Alg. 2), dilate root-voxel labels into empty neighbours (Alg. 3), search
+ * each transformed source point's root voxel with a global fallback
+ * (Alg. 4), and solve the rigid update of Eq. 1.
+ *
+ * Conventions shared by every entry point
+ *   - Point clouds are arrays of N x 4 float (x, y, z, w), 16-byte aligned,
+ *     w ignored.  "dev" pointers are CUDA device pointers, "host" pointers
+ *     are host memory (pinned or pageable).
+ *   - Poses are 4x4 row-major double matrices mapping source coordinates
+ *     into the target frame: q = R p + t with R = pose[0..2][0..2],
+ *     t = pose[0..2][3].
+ *   - The caller owns every input and output buffer.  The context owns its
+ *     workspace (grid arrays, scratch), allocated through the allocator given
+ *     to vicp_create and freed by vicp_destroy.
+ *   - Calls are asynchronous on the context's CUDA stream unless stated
+ *     otherwise.  Argument errors are returned immediately and launch
+ *     nothing.  Errors detected on the device (a bounded wait that gave up,
+ *     degenerate geometry in a solve) are recorded in a device status word
+ *     and returned by the next synchronising call (vicp_sync, vicp_register,
+ *     vicp_register_host, vicp_get_grid, vicp_memory_report,
+ *     vicp_profile_read).
+ *   - No entry point aborts, traps or throws across the ABI.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef VICP_H
+#define VICP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VICP_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define VICP_API __attribute__((visibility("default")))
+#else
+#define VICP_API
+#endif
+
+/* Status codes. */
+typedef enum vicp_status {
+    VICP_OK = 0,
+    VICP_ERR_INVALID = 1,         /* bad argument: NULL, misaligned, size or range */
+    VICP_ERR_CUDA = 2,            /* a CUDA runtime call failed (see vicp_last_error) */
+    VICP_ERR_OOM = 3,             /* the allocator returned NULL */
+    VICP_ERR_GRID_TOO_LARGE = 4,  /* nx*ny*nz >= 2^31 voxels */
+    VICP_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    VICP_ERR_STATE = 6,           /* call order: e.g. correspond before build_grid */
+    VICP_ERR_DEGENERATE = 7       /* rank(H) < 2 in the rigid solve; pose left unchanged */
+} vicp_status;
+
+typedef struct vicp_ctx vicp_ctx;
+
+/* Device-memory allocator.  alloc returns a device pointer aligned to at
+ * least 256 bytes, or NULL on failure; free releases it.  `stream` is the
+ * context's stream (stream-ordered allocators may use it).  A NULL allocator
+ * in vicp_create selects cudaMalloc / cudaFree. */
+typedef struct vicp_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} vicp_allocator;
+
+/* Flags for vicp_params.flags. */
+#define VICP_FLAG_KEEP_GRID         (1u << 0) /* auto grid: fit once, reuse for later builds */
+#define VICP_FLAG_REBUILD_EACH_ITER (1u << 1) /* vicp_register: rebuild + dilate every iteration */
+#define VICP_FLAG_TEST_SCAN_TIMEOUT (1u << 31) /* tests only: one scan tile never publishes,
+                                                  so its successor's bounded wait gives up */
+
+/* Run parameters (Sec. 4.1 "Parameter": voxelisation scale, dilation
+ * layers L, maximum iteration count, RMSE-difference threshold). */
+typedef struct vicp_params {
+    float voxel_size;        /* > 0: voxel edge h.  <= 0: h = target extent / grid_divisions */
+    int32_t grid_divisions;  /* used when voxel_size <= 0 (2^N in the paper; any value >= 1) */
+    float origin[3];         /* explicit grid origin, used when dims[0] > 0 */
+    int32_t dims[3];         /* explicit grid dims; dims[0] <= 0: origin = min corner of the
+                                target, dims_a = floor(extent_a / h) + 1 */
+    int32_t dilation_layers; /* L, 0..31 (paper: 10) */
+    int32_t max_iters;       /* ICP iterations of vicp_register (paper: 50) */
+    double rmse_eps;         /* stop once |rmse_k - rmse_(k-1)| < rmse_eps (paper: 1e-5); <= 0: never */
+    uint32_t flags;          /* VICP_FLAG_* */
+} vicp_params;
+
+/* Read-only view of the grid built by the last vicp_build_grid / vicp_dilate.
+ * All pointers are device pointers owned by the context and valid until the
+ * next build or vicp_destroy. */
+typedef struct vicp_grid_view {
+    float origin[3];
+    float voxel_size;
+    float inv_voxel_size;      /* (float)(1.0 / (double)voxel_size) */
+    int32_t dims[3];
+    int64_t n_voxels;          /* V = dims[0]*dims[1]*dims[2] */
+    int32_t n_target;          /* points passed to the last build */
+    int32_t n_stored;          /* points inside the grid = offsets[V] */
+    int32_t dilation_layers;   /* L of the last vicp_dilate, -1 before any */
+    const int32_t *keys;       /* [n_target] voxel key x + nx*(y + ny*z), -1 outside */
+    const uint32_t *offsets;   /* [V+1] exclusive scan of the per-voxel counts */
+    const int32_t *ids;        /* [n_stored] point indices grouped by voxel; the order inside
+                                  one voxel's segment is unspecified */
+    const float *csr_points;   /* [n_stored x 4] x, y, z of ids[k]; w holds the bits of ids[k] */
+    const int32_t *root;       /* [V] root voxel of each voxel, -1 if farther than L */
+    const uint8_t *ring;       /* [V] Manhattan distance to the root, 255 if unlabelled */
+    const uint32_t *occupancy; /* [ceil(V/32)] bit v set iff voxel v holds a point */
+} vicp_grid_view;
+
+/* Device-memory accounting of one context (bytes). */
+typedef struct vicp_memory {
+    uint64_t current_bytes;          /* held now through the allocator */
+    uint64_t peak_bytes;             /* high-water mark since vicp_create */
+    uint64_t static_bytes;           /* per-voxel count + offset arrays (Table 1 note 1's
+                                        "histogram and address offsets") */
+    uint64_t csr_store_bytes;        /* offsets + ids + root + ring: the dynamic store */
+    uint64_t fixed_capacity_bytes;   /* V * C_max * 4 for a fixed-capacity layout with C_max =
+                                        the largest voxel count (the monolithic alternative) */
+    uint64_t paper_static_layout_bytes; /* V * 65536: a 64 KB block per voxel (Sec. 2.2) */
+    uint32_t max_voxel_count;        /* C_max */
+    uint32_t occupied_voxels;
+} vicp_memory;
+
+/* Work counters of the searches since the last reset. */
+typedef struct vicp_stats {
+    uint64_t queries;            /* source points searched */
+    uint64_t fallbacks;          /* of which took the global search (Alg. 4, count == 0) */
+    uint64_t local_candidates;   /* target points examined in root voxels */
+    uint64_t global_candidates;  /* target points examined by global searches */
+} vicp_stats;
+
+/* ---------------------------------------------------------------------- */
+
+VICP_API int32_t vicp_abi_version(void);
+VICP_API const char *vicp_status_string(vicp_status s);
+
+/* Fills *p with the paper's parameters: h = extent/16 (N = 4), L = 10,
+ * 50 iterations, RMSE difference 1e-5 (Sec. 4.1 "Parameter"). */
+VICP_API void vicp_default_params(vicp_params *p);
+
+/* Creates a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `params` is copied.
+ * `alloc` may be NULL (cudaMalloc).  Errors: VICP_ERR_INVALID for NULL
+ * out/params or out-of-range parameters; VICP_ERR_CUDA. */
+VICP_API vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_allocator *alloc,
+                        void *cuda_stream);
+
+/* Synchronises the stream and frees everything the context allocated. */
+VICP_API void vicp_destroy(vicp_ctx *ctx);
+
+/* Rebinds the context to another stream (work already issued stays on the
+ * old one; synchronise first if ordering matters). */
+VICP_API vicp_status vicp_set_stream(vicp_ctx *ctx, void *cuda_stream);
+
+/* Grid build = Alg. 1 + Alg. 2: quantise every target point into its voxel
+ * key (x fastest), count points per voxel with warp-aggregated atomics,
+ * exclusive-scan the counts into segment offsets (the paper's MOC, done on
+ * the GPU by a single-pass decoupled-lookback scan instead of serially on
+ * the host), and scatter point indices into the CSR store.
+ *   target_xyzw: dev, n_target x 4 floats, 16-byte aligned; read only.
+ *   n_target >= 1.
+ * In auto-grid mode (params.dims[0] <= 0) the bounding box is reduced on the
+ * device and read back (this call then synchronises once) unless
+ * VICP_FLAG_KEEP_GRID is set and a grid was already fitted.  Target points
+ * outside an explicit grid are not stored.  Errors: VICP_ERR_INVALID,
+ * VICP_ERR_GRID_TOO_LARGE, VICP_ERR_OOM, VICP_ERR_CUDA. */
+VICP_API vicp_status vicp_build_grid(vicp_ctx *ctx, const float *target_xyzw, int32_t n_target);
+
+/* Dilation = Alg. 3 and Sec. 3's description of it: every empty voxel
+ * within Manhattan distance `layers` of an occupied voxel receives the
+ * occupied root voxel at the smallest distance (ties: smallest voxel index)
+ * and that distance as its ring; the result equals `layers` synchronous
+ * rounds of six-neighbour propagation.  layers < 0 uses
+ * params.dilation_layers; 0 <= layers <= 31.  Errors: VICP_ERR_STATE before
+ * a build, VICP_ERR_INVALID, VICP_ERR_CUDA. */
+VICP_API vicp_status vicp_dilate(vicp_ctx *ctx, int32_t layers);
+
+/* NNS = Alg. 4: transform each source point by the pose (entries rounded to
+ * float), quantise it, follow its voxel's root label and search that root
+ * voxel's points; a point outside the grid or in an unlabelled voxel takes
+ * the global search over all target points (exact nearest neighbour).
+ * Squared distance ((dx*dx + dy*dy) + dz*dz) in float; ties go to the smaller
+ * target index.
+ *   src_xyzw: dev, n_src x 4, 16-byte aligned.  pose_dev: dev, 16 doubles.
+ *   nn_out: dev int32[n_src] target index.  d2_out: dev float[n_src].
+ *   n_fallback_out: dev int32, number of global searches; may be NULL.
+ * Needs vicp_build_grid and vicp_dilate first (VICP_ERR_STATE). */
+VICP_API vicp_status vicp_correspond(vicp_ctx *ctx, const float *src_xyzw, int32_t n_src,
+                            const double *pose_dev, int32_t *nn_out, float *d2_out,
+                            int32_t *n_fallback_out);
+
+/* One ICP iteration on the built grid (Sec. 2.1, Eq. 1): NNS as above, FP64
+ * centroids and cross-covariance reduced deterministically, the optimal
+ * rotation (Horn's quaternion method, FP64) and translation, and
+ * pose <- dT * pose in place.
+ *   pose_dev: dev, 16 doubles, read and written.  rmse_dev: dev double, the
+ *   RMSE of this iteration's correspondences (before the update); may be
+ *   NULL.  Degenerate geometry (rank(H) < 2) leaves the pose unchanged and
+ *   is reported as VICP_ERR_DEGENERATE by the next synchronising call. */
+VICP_API vicp_status vicp_step(vicp_ctx *ctx, const float *src_xyzw, int32_t n_src, double *pose_dev,
+                      double *rmse_dev);
+
+/* Full registration, synchronous: build the grid on the target, dilate,
+ * then up to params.max_iters iterations of vicp_step, stopping early once
+ * |rmse_k - rmse_(k-1)| < params.rmse_eps (Sec. 4.1).  The stopping test
+ * runs on the device; the host reads the result once at the end.
+ *   src_xyzw / tgt_xyzw: dev, 16-byte aligned.
+ *   pose_host: in = initial pose, out = result (left at the last good pose
+ *   on VICP_ERR_DEGENERATE).  iters_out, rmse_out: host, may be NULL
+ *   (iterations applied; RMSE of the last iteration). */
+VICP_API vicp_status vicp_register(vicp_ctx *ctx, const float *src_xyzw, int32_t n_src,
+                          const float *tgt_xyzw, int32_t n_tgt, double pose_host[16],
+                          int32_t *iters_out, double *rmse_out);
+
+/* vicp_register with both clouds in host memory: copies them to
+ * context-owned device buffers on the context's stream first. */
+VICP_API vicp_status vicp_register_host(vicp_ctx *ctx, const float *src_xyzw_host, int32_t n_src,
+                               const float *tgt_xyzw_host, int32_t n_tgt, double pose_host[16],
+                               int32_t *iters_out, double *rmse_out);
+
+/* Synchronous: waits for the stream and fills *out (n_stored is read back). */
+VICP_API vicp_status vicp_get_grid(vicp_ctx *ctx, vicp_grid_view *out);
+
+/* Synchronous: waits for the stream, returns and clears the device status. */
+VICP_API vicp_status vicp_sync(vicp_ctx *ctx);
+
+/* Synchronous: device-memory accounting of the current grid. */
+VICP_API vicp_status vicp_memory_report(vicp_ctx *ctx, vicp_memory *out);
+
+/* Kernel timing: while enabled, every kernel launch is bracketed by CUDA
+ * events on the context's stream.  vicp_profile_read synchronises, writes
+ * per-kernel launch counts and summed milliseconds into arrays of
+ * vicp_kernel_count() entries (either may be NULL) and resets the tallies. */
+VICP_API vicp_status vicp_profile_enable(vicp_ctx *ctx, int32_t enable);
+VICP_API int32_t vicp_kernel_count(void);
+VICP_API const char *vicp_kernel_name(int32_t kernel);
+VICP_API vicp_status vicp_profile_read(vicp_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Synchronous: the search work counters; reset != 0 clears them. */
+VICP_API vicp_status vicp_read_stats(vicp_ctx *ctx, vicp_stats *out, int32_t reset);
+
+/* Kernels this context has launched since vicp_create. */
+VICP_API int64_t vicp_launch_count(const vicp_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). */
+VICP_API const char *vicp_last_error(const vicp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VICP_H */

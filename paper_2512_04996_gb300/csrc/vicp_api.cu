@@ -1,0 +1,835 @@
+// vicp_api.cu -- the C ABI declared in include/vicp.h: context, workspace
+// allocation through the caller's allocator, argument checks, the launch
+// sequence of each entry point, and kernel-level event timing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vicp.h"
+#include "vicp_launch.h"
+
+using namespace vicp;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Timed {
+    int kernel;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace
+
+struct vicp_ctx {
+    vicp_params params{};
+    vicp_allocator alloc{};
+    bool custom_alloc = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string last_error;
+    uint64_t cur_bytes = 0, peak_bytes = 0;
+
+    // grid state
+    bool have_geom = false;
+    GridGeom geom{};
+    bool built = false;
+    int dilated_L = -1;
+    int n_target = 0;
+    const float4 *target = nullptr;   // caller's target of the last build (global search)
+
+    // V-sized
+    Buf counts, off, root, ring, occ, desc, brick_list, brick_box;
+    long long cap_V = -1, cap_bricks = -1;
+    // N-sized
+    Buf keys, ids, csr, outside;
+    long long cap_N = -1;
+    // M-sized
+    Buf nn, d2, fb_list;
+    long long cap_M = -1;
+    // fixed
+    Buf partials, pose, rmse, ctl, bbox;
+    // host-input copies (vicp_register_host)
+    Buf hsrc, htgt;
+
+    // accounting / timing
+    int64_t launches = 0;
+    bool profiling = false;
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t prof_launches[K_COUNT] = {};
+    double prof_ms[K_COUNT] = {};
+};
+
+namespace {
+
+vicp_status fail(vicp_ctx *c, vicp_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return s;
+}
+
+vicp_status cuda_fail(vicp_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, VICP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// --- allocation ------------------------------------------------------------
+vicp_status buf_free(vicp_ctx *c, Buf &b)
+{
+    if (b.p) {
+        if (c->custom_alloc)
+            c->alloc.free(b.p, b.bytes, (void *)c->stream, c->alloc.user);
+        else
+            cudaFree(b.p);
+        c->cur_bytes -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+    return VICP_OK;
+}
+
+vicp_status buf_alloc(vicp_ctx *c, Buf &b, size_t bytes, const char *what)
+{
+    buf_free(c, b);
+    if (bytes == 0)
+        bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->custom_alloc) {
+        p = c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+        if (!p)
+            return fail(c, VICP_ERR_OOM, "allocator returned NULL for %s (%zu bytes)", what, bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, VICP_ERR_OOM, "cudaMalloc of %zu bytes for %s: %s", bytes, what, cudaGetErrorString(e));
+        }
+    }
+    b.p = p;
+    b.bytes = bytes;
+    c->cur_bytes += bytes;
+    if (c->cur_bytes > c->peak_bytes)
+        c->peak_bytes = c->cur_bytes;
+    return VICP_OK;
+}
+
+vicp_status buf_zero(vicp_ctx *c, Buf &b, const char *what)
+{
+    cudaError_t e = cudaMemsetAsync(b.p, 0, b.bytes, c->stream);
+    return e == cudaSuccess ? VICP_OK : cuda_fail(c, e, what);
+}
+
+#define TRY(x)                       \
+    do {                             \
+        vicp_status _s = (x);        \
+        if (_s != VICP_OK)           \
+            return _s;               \
+    } while (0)
+
+// --- timing ----------------------------------------------------------------
+cudaEvent_t take_event(vicp_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <typename F>
+vicp_status launch(vicp_ctx *c, int kernel, F &&f)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) {
+        e0 = take_event(c);
+        cudaEventRecord(e0, c->stream);
+    }
+    cudaError_t e = f();
+    if (c->profiling) {
+        e1 = take_event(c);
+        cudaEventRecord(e1, c->stream);
+        c->pending.push_back({kernel, e0, e1});
+    }
+    c->launches += 1;
+    if (e != cudaSuccess)
+        return fail(c, VICP_ERR_CUDA, "launch of %s: %s", kernel_name(kernel), cudaGetErrorString(e));
+    return VICP_OK;
+}
+
+DevCtl *ctl_of(vicp_ctx *c) { return static_cast<DevCtl *>(c->ctl.p); }
+
+// --- workspace sizing ------------------------------------------------------
+vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
+{
+    if (V > c->cap_V) {
+        TRY(buf_alloc(c, c->counts, (size_t)V * 4, "counts"));
+        TRY(buf_zero(c, c->counts, "zero counts"));   // counts are kept at zero between builds
+        TRY(buf_alloc(c, c->off, (size_t)(V + 1) * 4, "offsets"));
+        TRY(buf_alloc(c, c->root, (size_t)V * 4, "root"));
+        TRY(buf_alloc(c, c->ring, (size_t)V, "ring"));
+        TRY(buf_alloc(c, c->occ, (size_t)occ_words(V) * 4, "occupancy"));
+        TRY(buf_zero(c, c->occ, "zero occupancy"));
+        TRY(buf_alloc(c, c->desc, (size_t)scan_tiles(V) * 8, "scan descriptors"));
+        TRY(buf_zero(c, c->desc, "zero scan descriptors"));
+        c->cap_V = V;
+    }
+    if (n_bricks > c->cap_bricks) {
+        TRY(buf_alloc(c, c->brick_list, (size_t)n_bricks * 4, "brick list"));
+        TRY(buf_alloc(c, c->brick_box, (size_t)n_bricks * 32, "brick boxes"));
+        c->cap_bricks = n_bricks;
+    }
+    return VICP_OK;
+}
+
+vicp_status ensure_point_buffers(vicp_ctx *c, long long n)
+{
+    if (n > c->cap_N) {
+        TRY(buf_alloc(c, c->keys, (size_t)n * 4, "keys"));
+        TRY(buf_alloc(c, c->ids, (size_t)n * 4, "ids"));
+        TRY(buf_alloc(c, c->csr, (size_t)n * 16, "csr points"));
+        TRY(buf_alloc(c, c->outside, (size_t)n * 4, "outside list"));
+        c->cap_N = n;
+    }
+    return VICP_OK;
+}
+
+vicp_status ensure_query_buffers(vicp_ctx *c, long long m)
+{
+    if (m > c->cap_M) {
+        TRY(buf_alloc(c, c->nn, (size_t)m * 4, "nn"));
+        TRY(buf_alloc(c, c->d2, (size_t)m * 4, "d2"));
+        TRY(buf_alloc(c, c->fb_list, (size_t)m * 4, "fallback list"));
+        c->cap_M = m;
+    }
+    return VICP_OK;
+}
+
+// --- geometry (host side of the grid fit) ----------------------------------
+float ordered_to_float(unsigned o)
+{
+    const unsigned b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+vicp_status set_geometry(vicp_ctx *c, const float origin[3], float h, const int dims[3])
+{
+    if (!(h > 0.0f) || !std::isfinite(h))
+        return fail(c, VICP_ERR_INVALID, "voxel size must be finite and > 0 (got %g)", (double)h);
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1)
+            return fail(c, VICP_ERR_INVALID, "grid dims must be >= 1");
+        if (!std::isfinite(origin[a]))
+            return fail(c, VICP_ERR_INVALID, "grid origin must be finite");
+    }
+    const long long V = (long long)dims[0] * dims[1] * dims[2];
+    if (V >= (1ll << 31) - 1)
+        return fail(c, VICP_ERR_GRID_TOO_LARGE, "grid of %d x %d x %d = %lld voxels (limit 2^31 - 2)", dims[0],
+                    dims[1], dims[2], V);
+    GridGeom g{};
+    g.ox = origin[0];
+    g.oy = origin[1];
+    g.oz = origin[2];
+    g.h = h;
+    g.inv_h = (float)(1.0 / (double)h);
+    g.nx = dims[0];
+    g.ny = dims[1];
+    g.nz = dims[2];
+    g.V = V;
+    g.bx = (dims[0] + BRICK - 1) / BRICK;
+    g.by = (dims[1] + BRICK - 1) / BRICK;
+    g.bz = (dims[2] + BRICK - 1) / BRICK;
+    c->geom = g;
+    c->have_geom = true;
+    return VICP_OK;
+}
+
+// Bounding-box grid: origin = minimum corner, h given or extent/divisions,
+// dims_a = floor(extent_a * inv_h) + 1 (one synchronisation to read the box).
+vicp_status fit_geometry(vicp_ctx *c, const float4 *tgt, int n)
+{
+    unsigned *bb = static_cast<unsigned *>(c->bbox.p);
+    TRY(launch(c, K_BBOX, [&] { return launch_bbox(tgt, n, bb, c->stream); }));
+    unsigned hb[6];
+    cudaError_t e = cudaMemcpyAsync(hb, bb, sizeof hb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "bounding box read-back");
+    float lo[3], hi[3], ext[3], extent = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = ordered_to_float(hb[a]);
+        hi[a] = ordered_to_float(hb[3 + a]);
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]))
+            return fail(c, VICP_ERR_INVALID, "target has no finite coordinate on axis %d", a);
+        ext[a] = hi[a] - lo[a];
+        if (ext[a] > extent)
+            extent = ext[a];
+    }
+    float h;
+    if (c->params.voxel_size > 0.0f) {
+        h = c->params.voxel_size;
+    } else {
+        h = extent / (float)c->params.grid_divisions;
+        if (!(h > 0.0f))
+            h = 1.0f;   // all target points coincide: one voxel
+    }
+    const float inv_h = (float)(1.0 / (double)h);
+    int dims[3];
+    for (int a = 0; a < 3; ++a) {
+        const float s = ext[a] * inv_h;
+        if (!(s < 2147483520.0f))
+            return fail(c, VICP_ERR_GRID_TOO_LARGE, "grid axis %d would have %g voxels", a, (double)s);
+        dims[a] = (int)std::floor(s) + 1;
+    }
+    return set_geometry(c, lo, h, dims);
+}
+
+vicp_status check_params(vicp_ctx *c, const vicp_params *p)
+{
+    if (p->dilation_layers < 0 || p->dilation_layers > DILATE_MAX_L)
+        return fail(c, VICP_ERR_INVALID, "dilation_layers must be in [0, %d]", DILATE_MAX_L);
+    if (p->max_iters < 0)
+        return fail(c, VICP_ERR_INVALID, "max_iters must be >= 0");
+    if (p->dims[0] <= 0 && !(p->voxel_size > 0.0f) && p->grid_divisions < 1)
+        return fail(c, VICP_ERR_INVALID, "auto grid needs voxel_size > 0 or grid_divisions >= 1");
+    if (p->dims[0] > 0 && (p->dims[1] < 1 || p->dims[2] < 1 || !(p->voxel_size > 0.0f)))
+        return fail(c, VICP_ERR_INVALID, "explicit grid needs dims >= 1 and voxel_size > 0");
+    return VICP_OK;
+}
+
+double3 grid_center(const GridGeom &g)
+{
+    return make_double3((double)g.ox + 0.5 * (double)g.h * g.nx, (double)g.oy + 0.5 * (double)g.h * g.ny,
+                        (double)g.oz + 0.5 * (double)g.h * g.nz);
+}
+
+vicp_status check_cloud(vicp_ctx *c, const float *p, int32_t n, const char *what)
+{
+    if (!p || n < 1)
+        return fail(c, VICP_ERR_INVALID, "%s: need a non-NULL pointer and n >= 1", what);
+    if (!aligned16(p))
+        return fail(c, VICP_ERR_INVALID, "%s: pointer must be 16-byte aligned", what);
+    return VICP_OK;
+}
+
+vicp_status read_device_status(vicp_ctx *c)
+{
+    unsigned err = 0;
+    DevCtl *d = ctl_of(c);
+    cudaError_t e = cudaMemcpyAsync(&err, &d->err, sizeof err, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "synchronise");
+    if (err) {
+        cudaMemsetAsync(&d->err, 0, sizeof(unsigned), c->stream);
+        if (err & DEVERR_TIMEOUT)
+            return fail(c, VICP_ERR_TIMEOUT, "a device-side wait gave up (device status 0x%x)", err);
+        if (err & DEVERR_BOUNDS)
+            return fail(c, VICP_ERR_CUDA, "a device-side bounds check failed (device status 0x%x)", err);
+        if (err & DEVERR_DEGENERATE)
+            return fail(c, VICP_ERR_DEGENERATE, "rank(H) < 2: degenerate correspondence geometry");
+    }
+    return VICP_OK;
+}
+
+// Correspond + global search into nn/d2 (shared by vicp_correspond and the step).
+vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, int *nn, float *d2, int honor_stop)
+{
+    const GridGeom &g = c->geom;
+    DevCtl *d = ctl_of(c);
+    TRY(launch(c, K_CORRESPOND, [&] {
+        return launch_correspond(src, m, pose, g, (const int *)c->root.p, (const unsigned *)c->off.p,
+                                 (const float4 *)c->csr.p, c->n_target, nn, d2, (int *)c->fb_list.p, d,
+                                 honor_stop, c->stream);
+    }));
+    TRY(launch(c, K_FALLBACK, [&] {
+        return launch_fallback(src, pose, g, (const unsigned *)c->occ.p, (const unsigned *)c->off.p,
+                               (const float4 *)c->csr.p, c->n_target, (const int *)c->brick_list.p,
+                               (const float4 *)c->brick_box.p, c->target, c->n_target,
+                               (const int *)c->outside.p, (const int *)c->fb_list.p, d, nn, d2, m, honor_stop,
+                               c->stream);
+    }));
+    return VICP_OK;
+}
+
+vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double *rmse, int honor_stop)
+{
+    TRY(ensure_query_buffers(c, m));
+    int *nn = (int *)c->nn.p;
+    TRY(run_nns(c, src, m, pose, nn, (float *)c->d2.p, honor_stop));
+    const double3 ctr = grid_center(c->geom);
+    const int nparts = reduce_blocks(m);
+    TRY(launch(c, K_REDUCE, [&] {
+        return launch_reduce(src, m, pose, c->target, c->n_target, nn, ctr, (double *)c->partials.p, ctl_of(c),
+                             honor_stop, c->stream);
+    }));
+    TRY(launch(c, K_SOLVE, [&] {
+        return launch_solve((const double *)c->partials.p, nparts, m, ctr, pose, rmse, ctl_of(c), honor_stop,
+                            c->params.rmse_eps, c->stream);
+    }));
+    return VICP_OK;
+}
+
+vicp_status build(vicp_ctx *c, const float *target, int32_t n)
+{
+    TRY(check_cloud(c, target, n, "target"));
+    const float4 *tgt = reinterpret_cast<const float4 *>(target);
+    const bool auto_grid = c->params.dims[0] <= 0;
+    if (auto_grid) {
+        if (!c->have_geom || !(c->params.flags & VICP_FLAG_KEEP_GRID))
+            TRY(fit_geometry(c, tgt, n));
+    } else if (!c->have_geom) {
+        TRY(set_geometry(c, c->params.origin, c->params.voxel_size, c->params.dims));
+    }
+    const GridGeom &g = c->geom;
+    TRY(ensure_voxel_buffers(c, g.V, (long long)g.bx * g.by * g.bz));
+    TRY(ensure_point_buffers(c, n));
+    DevCtl *d = ctl_of(c);
+    const int skip = (c->params.flags & VICP_FLAG_TEST_SCAN_TIMEOUT) ? 0 : -1;
+    TRY(launch(c, K_HISTOGRAM, [&] {
+        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, d, c->stream);
+    }));
+    TRY(launch(c, K_SCAN, [&] {
+        return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, (unsigned *)c->occ.p,
+                           (unsigned long long *)c->desc.p, d, skip, c->stream);
+    }));
+    TRY(launch(c, K_SCATTER, [&] {
+        return launch_scatter(tgt, (const int *)c->keys.p, n, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
+                              (int *)c->ids.p, (float4 *)c->csr.p, (int *)c->outside.p, d, c->stream);
+    }));
+    TRY(launch(c, K_BRICKS, [&] {
+        return launch_bricks((const unsigned *)c->occ.p, g, (int *)c->brick_list.p, (float4 *)c->brick_box.p, d,
+                             c->stream);
+    }));
+    c->built = true;
+    c->dilated_L = -1;
+    c->n_target = n;
+    c->target = tgt;
+    return VICP_OK;
+}
+
+vicp_status dilate(vicp_ctx *c, int32_t layers)
+{
+    if (!c->built)
+        return fail(c, VICP_ERR_STATE, "vicp_dilate before vicp_build_grid");
+    const int L = layers < 0 ? c->params.dilation_layers : layers;
+    if (L > DILATE_MAX_L)
+        return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
+    TRY(launch(c, K_DILATE, [&] {
+        return launch_dilate((const unsigned *)c->occ.p, c->geom, L, (int *)c->root.p, (unsigned char *)c->ring.p,
+                             c->stream);
+    }));
+    c->dilated_L = L;
+    return VICP_OK;
+}
+
+vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
+                         double pose_host[16], int32_t *iters_out, double *rmse_out)
+{
+    TRY(build(c, tgt, n));
+    TRY(dilate(c, -1));
+    double *pose = (double *)c->pose.p;
+    cudaError_t e = cudaMemcpyAsync(pose, pose_host, 16 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "pose upload");
+    DevCtl *d = ctl_of(c);
+    // reset the loop state: stop, iters, prev_rmse, last_rmse
+    e = cudaMemsetAsync(&d->stop, 0, sizeof(DevCtl) - offsetof(DevCtl, stop), c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "loop state reset");
+    for (int k = 0; k < c->params.max_iters; ++k) {
+        if (k > 0 && (c->params.flags & VICP_FLAG_REBUILD_EACH_ITER)) {
+            TRY(build(c, tgt, n));
+            TRY(dilate(c, -1));
+        }
+        TRY(run_step(c, src, m, pose, nullptr, 1));
+    }
+    struct {
+        int stop, iters;
+        double prev, last;
+    } loop;
+    static_assert(sizeof(loop) == sizeof(DevCtl) - offsetof(DevCtl, stop), "loop state layout");
+    e = cudaMemcpyAsync(pose_host, pose, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&loop, &d->stop, sizeof loop, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "result read-back");
+    vicp_status st = read_device_status(c);   // synchronises
+    if (iters_out)
+        *iters_out = loop.iters;
+    if (rmse_out)
+        *rmse_out = loop.last;
+    return st;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int32_t vicp_abi_version(void) { return VICP_ABI_VERSION; }
+
+const char *vicp_status_string(vicp_status s)
+{
+    switch (s) {
+    case VICP_OK: return "ok";
+    case VICP_ERR_INVALID: return "invalid argument";
+    case VICP_ERR_CUDA: return "CUDA error";
+    case VICP_ERR_OOM: return "out of device memory";
+    case VICP_ERR_GRID_TOO_LARGE: return "grid too large";
+    case VICP_ERR_TIMEOUT: return "device-side wait timed out";
+    case VICP_ERR_STATE: return "call order";
+    case VICP_ERR_DEGENERATE: return "degenerate geometry";
+    }
+    return "unknown status";
+}
+
+void vicp_default_params(vicp_params *p)
+{
+    if (!p)
+        return;
+    std::memset(p, 0, sizeof *p);
+    p->voxel_size = 0.0f;
+    p->grid_divisions = 16;
+    p->dims[0] = p->dims[1] = p->dims[2] = 0;
+    p->dilation_layers = 10;
+    p->max_iters = 50;
+    p->rmse_eps = 1e-5;
+    p->flags = 0u;
+}
+
+vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_allocator *alloc, void *cuda_stream)
+{
+    if (!out || !params)
+        return VICP_ERR_INVALID;
+    *out = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return VICP_ERR_INVALID;
+    vicp_ctx *c = new vicp_ctx();
+    c->params = *params;
+    vicp_status s = check_params(c, params);
+    if (s != VICP_OK) {
+        delete c;
+        return s;
+    }
+    if (alloc) {
+        c->alloc = *alloc;
+        c->custom_alloc = true;
+    }
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&c->device);
+    s = buf_alloc(c, c->ctl, sizeof(DevCtl), "control block");
+    if (s == VICP_OK)
+        s = buf_zero(c, c->ctl, "zero control block");
+    if (s == VICP_OK)
+        s = buf_alloc(c, c->partials, REDUCE_MAX_BLOCKS * REDUCE_VALUES * sizeof(double), "partials");
+    if (s == VICP_OK)
+        s = buf_alloc(c, c->pose, 16 * sizeof(double), "pose");
+    if (s == VICP_OK)
+        s = buf_alloc(c, c->rmse, sizeof(double), "rmse");
+    if (s == VICP_OK)
+        s = buf_alloc(c, c->bbox, 8 * sizeof(unsigned), "bounding box");
+    if (s != VICP_OK) {
+        vicp_destroy(c);
+        return s;
+    }
+    *out = c;
+    return VICP_OK;
+}
+
+void vicp_destroy(vicp_ctx *c)
+{
+    if (!c)
+        return;
+    cudaStreamSynchronize(c->stream);
+    Buf *all[] = {&c->counts, &c->off,     &c->root,     &c->ring,    &c->occ,  &c->desc, &c->brick_list,
+                  &c->brick_box, &c->keys, &c->ids,      &c->csr,     &c->outside, &c->nn, &c->d2,
+                  &c->fb_list, &c->partials, &c->pose,   &c->rmse,    &c->ctl,  &c->bbox, &c->hsrc, &c->htgt};
+    for (Buf *b : all)
+        buf_free(c, *b);
+    for (auto &t : c->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (cudaEvent_t e : c->event_pool)
+        cudaEventDestroy(e);
+    delete c;
+}
+
+vicp_status vicp_set_stream(vicp_ctx *c, void *cuda_stream)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return VICP_OK;
+}
+
+vicp_status vicp_build_grid(vicp_ctx *c, const float *target_xyzw, int32_t n_target)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    return build(c, target_xyzw, n_target);
+}
+
+vicp_status vicp_dilate(vicp_ctx *c, int32_t layers)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    return dilate(c, layers);
+}
+
+vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, const double *pose_dev,
+                            int32_t *nn_out, float *d2_out, int32_t *n_fallback_out)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    TRY(check_cloud(c, src_xyzw, n_src, "source"));
+    if (!pose_dev || !nn_out || !d2_out)
+        return fail(c, VICP_ERR_INVALID, "pose, nn and d2 pointers must be non-NULL");
+    if (!c->built || c->dilated_L < 0)
+        return fail(c, VICP_ERR_STATE, "vicp_correspond needs vicp_build_grid and vicp_dilate first");
+    TRY(ensure_query_buffers(c, n_src));
+    const float4 *src = reinterpret_cast<const float4 *>(src_xyzw);
+    DevCtl *d = ctl_of(c);
+    if (n_fallback_out) {
+        // fb_count is zero between searches; the correspond kernel counts this
+        // search's global queries and the fallback kernel clears it again.
+        TRY(launch(c, K_CORRESPOND, [&] {
+            return launch_correspond(src, n_src, pose_dev, c->geom, (const int *)c->root.p,
+                                     (const unsigned *)c->off.p, (const float4 *)c->csr.p, c->n_target, nn_out,
+                                     d2_out, (int *)c->fb_list.p, d, 0, c->stream);
+        }));
+        cudaError_t e = cudaMemcpyAsync(n_fallback_out, &d->fb_count, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                        c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "fallback count copy");
+        TRY(launch(c, K_FALLBACK, [&] {
+            return launch_fallback(src, pose_dev, c->geom, (const unsigned *)c->occ.p, (const unsigned *)c->off.p,
+                                   (const float4 *)c->csr.p, c->n_target, (const int *)c->brick_list.p,
+                                   (const float4 *)c->brick_box.p, c->target, c->n_target,
+                                   (const int *)c->outside.p, (const int *)c->fb_list.p, d, nn_out, d2_out,
+                                   n_src, 0, c->stream);
+        }));
+        return VICP_OK;
+    }
+    return run_nns(c, src, n_src, pose_dev, nn_out, d2_out, 0);
+}
+
+vicp_status vicp_step(vicp_ctx *c, const float *src_xyzw, int32_t n_src, double *pose_dev, double *rmse_dev)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    TRY(check_cloud(c, src_xyzw, n_src, "source"));
+    if (!pose_dev)
+        return fail(c, VICP_ERR_INVALID, "pose pointer must be non-NULL");
+    if (!c->built || c->dilated_L < 0)
+        return fail(c, VICP_ERR_STATE, "vicp_step needs vicp_build_grid and vicp_dilate first");
+    return run_step(c, reinterpret_cast<const float4 *>(src_xyzw), n_src, pose_dev, rmse_dev, 0);
+}
+
+vicp_status vicp_register(vicp_ctx *c, const float *src_xyzw, int32_t n_src, const float *tgt_xyzw, int32_t n_tgt,
+                          double pose_host[16], int32_t *iters_out, double *rmse_out)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    TRY(check_cloud(c, src_xyzw, n_src, "source"));
+    TRY(check_cloud(c, tgt_xyzw, n_tgt, "target"));
+    if (!pose_host)
+        return fail(c, VICP_ERR_INVALID, "pose_host must be non-NULL");
+    return registration(c, reinterpret_cast<const float4 *>(src_xyzw), n_src, tgt_xyzw, n_tgt, pose_host,
+                        iters_out, rmse_out);
+}
+
+vicp_status vicp_register_host(vicp_ctx *c, const float *src_host, int32_t n_src, const float *tgt_host,
+                               int32_t n_tgt, double pose_host[16], int32_t *iters_out, double *rmse_out)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    if (!src_host || !tgt_host || n_src < 1 || n_tgt < 1 || !pose_host)
+        return fail(c, VICP_ERR_INVALID, "host clouds, sizes >= 1 and pose_host are required");
+    const size_t sb = (size_t)n_src * 16, tb = (size_t)n_tgt * 16;
+    if (c->hsrc.bytes < sb)
+        TRY(buf_alloc(c, c->hsrc, sb, "source copy"));
+    if (c->htgt.bytes < tb)
+        TRY(buf_alloc(c, c->htgt, tb, "target copy"));
+    cudaError_t e = cudaMemcpyAsync(c->hsrc.p, src_host, sb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "host-to-device copy of the clouds");
+    return registration(c, (const float4 *)c->hsrc.p, n_src, (const float *)c->htgt.p, n_tgt, pose_host,
+                        iters_out, rmse_out);
+}
+
+vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
+{
+    if (!c || !out)
+        return VICP_ERR_INVALID;
+    if (!c->built)
+        return fail(c, VICP_ERR_STATE, "no grid built");
+    const GridGeom &g = c->geom;
+    std::memset(out, 0, sizeof *out);
+    out->origin[0] = g.ox;
+    out->origin[1] = g.oy;
+    out->origin[2] = g.oz;
+    out->voxel_size = g.h;
+    out->inv_voxel_size = g.inv_h;
+    out->dims[0] = g.nx;
+    out->dims[1] = g.ny;
+    out->dims[2] = g.nz;
+    out->n_voxels = g.V;
+    out->n_target = c->n_target;
+    out->dilation_layers = c->dilated_L;
+    uint32_t stored = 0;
+    cudaError_t e = cudaMemcpyAsync(&stored, (const unsigned *)c->off.p + g.V, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "read n_stored");
+    vicp_status st = read_device_status(c);
+    out->n_stored = (int32_t)stored;
+    out->keys = (const int32_t *)c->keys.p;
+    out->offsets = (const uint32_t *)c->off.p;
+    out->ids = (const int32_t *)c->ids.p;
+    out->csr_points = (const float *)c->csr.p;
+    out->root = (const int32_t *)c->root.p;
+    out->ring = (const uint8_t *)c->ring.p;
+    out->occupancy = (const uint32_t *)c->occ.p;
+    return st;
+}
+
+vicp_status vicp_sync(vicp_ctx *c)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    return read_device_status(c);
+}
+
+vicp_status vicp_memory_report(vicp_ctx *c, vicp_memory *out)
+{
+    if (!c || !out)
+        return VICP_ERR_INVALID;
+    std::memset(out, 0, sizeof *out);
+    out->current_bytes = c->cur_bytes;
+    out->peak_bytes = c->peak_bytes;
+    if (!c->built)
+        return VICP_OK;
+    const GridGeom &g = c->geom;
+    DevCtl *d = ctl_of(c);
+    cudaError_t e = cudaMemsetAsync(&d->max_count, 0, 2 * sizeof(unsigned), c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "memory report");
+    TRY(launch(c, K_MAXCOUNT, [&] { return launch_maxcount((const unsigned *)c->off.p, g, d, c->stream); }));
+    unsigned mc[2] = {0, 0};
+    uint32_t stored = 0;
+    e = cudaMemcpyAsync(mc, &d->max_count, sizeof mc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&stored, (const unsigned *)c->off.p + g.V, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "memory report read-back");
+    vicp_status st = read_device_status(c);
+    const uint64_t V = (uint64_t)g.V;
+    out->static_bytes = V * 4 + (V + 1) * 4;
+    out->csr_store_bytes = (V + 1) * 4 + (uint64_t)stored * 4 + V * 4 + V;
+    out->max_voxel_count = mc[0];
+    out->occupied_voxels = mc[1];
+    out->fixed_capacity_bytes = V * (uint64_t)mc[0] * 4;
+    out->paper_static_layout_bytes = V * 65536ull;
+    return st;
+}
+
+vicp_status vicp_profile_enable(vicp_ctx *c, int32_t enable)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    c->profiling = enable != 0;
+    return VICP_OK;
+}
+
+int32_t vicp_kernel_count(void) { return K_COUNT; }
+
+const char *vicp_kernel_name(int32_t k) { return kernel_name(k); }
+
+vicp_status vicp_profile_read(vicp_ctx *c, int64_t *launches, double *total_ms)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    vicp_status st = read_device_status(c);   // synchronises
+    for (auto &t : c->pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+            c->prof_ms[t.kernel] += ms;
+            c->prof_launches[t.kernel] += 1;
+        }
+        c->event_pool.push_back(t.start);
+        c->event_pool.push_back(t.stop);
+    }
+    c->pending.clear();
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (launches)
+            launches[k] = c->prof_launches[k];
+        if (total_ms)
+            total_ms[k] = c->prof_ms[k];
+        c->prof_launches[k] = 0;
+        c->prof_ms[k] = 0.0;
+    }
+    return st;
+}
+
+vicp_status vicp_read_stats(vicp_ctx *c, vicp_stats *out, int32_t reset)
+{
+    if (!c || !out)
+        return VICP_ERR_INVALID;
+    DevCtl *d = ctl_of(c);
+    unsigned long long v[4] = {0, 0, 0, 0};
+    static_assert(offsetof(DevCtl, stat_global_cand) - offsetof(DevCtl, stat_queries) == 24, "stats layout");
+    cudaError_t e = cudaMemcpyAsync(v, &d->stat_queries, sizeof v, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && reset)
+        e = cudaMemsetAsync(&d->stat_queries, 0, sizeof v, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "read stats");
+    vicp_status st = read_device_status(c);
+    out->queries = v[0];
+    out->fallbacks = v[1];
+    out->local_candidates = v[2];
+    out->global_candidates = v[3];
+    return st;
+}
+
+int64_t vicp_launch_count(const vicp_ctx *c) { return c ? c->launches : 0; }
+
+const char *vicp_last_error(const vicp_ctx *c) { return c ? c->last_error.c_str() : ""; }
+
+}  // extern "C"
+
+namespace vicp {
+const char *kernel_name(int k)
+{
+    static const char *names[K_COUNT] = {"bbox",     "histogram", "scan",     "scatter", "bricks",  "dilate",
+                                         "correspond", "fallback", "reduce",  "solve",   "maxcount"};
+    return (k >= 0 && k < K_COUNT) ? names[k] : "?";
+}
+}  // namespace vicp

@@ -1,0 +1,166 @@
+// vicp_device.cuh -- types, constants and device helpers shared by the CUDA
+// translation units of the library (not by the host API's callers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vicp {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Voxel grid geometry passed by value to kernels.  Keys are
+// x + nx*(y + ny*z) (x fastest, the neighbour offsets +-1, +-2^N, +-2^2N of
+// Alg. 3); V < 2^31 so keys fit int32.
+struct GridGeom {
+    float ox, oy, oz;   // origin (minimum corner)
+    float inv_h;        // (float)(1.0 / (double)h)
+    float h;
+    int nx, ny, nz;
+    long long V;
+    int bx, by, bz;     // brick grid: ceil(dims / BRICK)
+};
+
+// Brick edge (voxels) of the coarse level used by the exact global search.
+constexpr int BRICK = 8;
+
+// Bits of the device status word.
+constexpr unsigned DEVERR_TIMEOUT = 1u;      // a bounded wait gave up
+constexpr unsigned DEVERR_DEGENERATE = 2u;   // rank(H) < 2 in a solve
+constexpr unsigned DEVERR_BOUNDS = 4u;       // an index failed its bounds check (write skipped)
+
+// Per-context control block in device memory.  Kernels of one stream use it
+// in launch order; the comments say which kernel writes each field.
+struct DevCtl {
+    unsigned scan_ticket;   // scan: dynamic tile index; reset by the histogram kernel
+    unsigned scan_epoch;    // scan: descriptor epoch; bumped by the histogram kernel
+    int n_outside;          // scatter: target points outside the grid; reset by histogram
+    int n_bricks;           // brick list length; reset by histogram
+    int fb_count;           // correspond: fallback queries; reset by the fallback kernel
+    unsigned fb_done;       // fallback: finished blocks (the last one resets fb_count)
+    unsigned err;           // DEVERR_* bits; cleared by the host
+    unsigned max_count;     // memory report: largest voxel count
+    unsigned occupied;      // memory report: occupied voxels
+    int pad0;
+    // Work counters (added by the search kernels, read and cleared by the host).
+    unsigned long long stat_queries;       // source points searched
+    unsigned long long stat_fallbacks;     // of which took the global search
+    unsigned long long stat_local_cand;    // target points examined by local searches
+    unsigned long long stat_global_cand;   // target points examined by global searches
+    // Registration loop state, reset together by the host before a run.
+    int stop;               // 1 once converged or failed
+    int iters;              // iterations applied
+    double prev_rmse;
+    double last_rmse;
+};
+static_assert(sizeof(DevCtl) == 96, "DevCtl layout");
+
+// Rigid transform rounded to float: R row-major, t.
+struct PoseF {
+    float r[9];
+    float t[3];
+};
+
+// Load the 3x4 upper part of a row-major 4x4 double pose, each entry rounded
+// to the nearest float.
+__device__ __forceinline__ void load_pose_f(const double *__restrict__ pose, PoseF &P)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            P.r[3 * a + b] = __double2float_rn(pose[4 * a + b]);
+        P.t[a] = __double2float_rn(pose[4 * a + 3]);
+    }
+}
+
+// s_a = ((R_a0*x + R_a1*y) + R_a2*z) + t_a, every operation rounded to
+// nearest on its own (no contraction into FMA).
+__device__ __forceinline__ float3 transform_pt(const PoseF &P, float4 p)
+{
+    float s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float acc = __fmul_rn(P.r[3 * a + 0], p.x);
+        acc = __fadd_rn(acc, __fmul_rn(P.r[3 * a + 1], p.y));
+        acc = __fadd_rn(acc, __fmul_rn(P.r[3 * a + 2], p.z));
+        s[a] = __fadd_rn(acc, P.t[a]);
+    }
+    return make_float3(s[0], s[1], s[2]);
+}
+
+// Quantize + Concat (Alg. 1/2/4): scaled coordinate s = (p - o) * inv_h per
+// axis; outside when NaN, < 0 or >= dims.
+__device__ __forceinline__ int voxel_key(const GridGeom &g, float x, float y, float z)
+{
+    const float sx = __fmul_rn(__fsub_rn(x, g.ox), g.inv_h);
+    const float sy = __fmul_rn(__fsub_rn(y, g.oy), g.inv_h);
+    const float sz = __fmul_rn(__fsub_rn(z, g.oz), g.inv_h);
+    if (!(sx >= 0.0f) || !(sy >= 0.0f) || !(sz >= 0.0f))
+        return -1;
+    if (sx >= __int2float_rn(g.nx) || sy >= __int2float_rn(g.ny) || sz >= __int2float_rn(g.nz))
+        return -1;
+    const int ix = (int)floorf(sx), iy = (int)floorf(sy), iz = (int)floorf(sz);
+    return ix + g.nx * (iy + g.ny * iz);
+}
+
+// Squared distance ((dx*dx + dy*dy) + dz*dz), each operation rounded once.
+__device__ __forceinline__ float dist2(float3 s, float4 q)
+{
+    const float dx = __fsub_rn(s.x, q.x);
+    const float dy = __fsub_rn(s.y, q.y);
+    const float dz = __fsub_rn(s.z, q.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Candidate key for the nearest-neighbour argmin: squared distance bits
+// above the target index.  A distance is a sum of squares, so it is +0, a
+// positive number, +inf or the canonical NaN 0x7fffffff; the unsigned order
+// of the bits is then the order "numbers ascending, NaN last", and equal
+// distances fall to the smaller index.
+__device__ __forceinline__ unsigned long long nn_key(float d, int id)
+{
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)id;
+}
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b)
+{
+    return a < b ? a : b;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = umin64(v, __shfl_xor_sync(FULL_MASK, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// `width` (1..32) bits of a linear bitmask starting at bit `b`; needs one
+// readable word past the last word touched.
+__device__ __forceinline__ unsigned extract_bits(const unsigned *__restrict__ bits, long long b, int width)
+{
+    const long long w = b >> 5;
+    const int sh = (int)(b & 31);
+    const unsigned lo = __ldg(bits + w);
+    const unsigned hi = (sh + width > 32) ? __ldg(bits + w + 1) : 0u;
+    const unsigned v = __funnelshift_r(lo, hi, sh);
+    return width >= 32 ? v : (v & ((1u << width) - 1u));
+}
+
+}  // namespace vicp

@@ -1,0 +1,222 @@
+// vicp_dilate.cu -- DDMA, dilation of root-voxel labels into empty voxels
+// (Alg. 3 and its description in Sec. 3).
+//
+// What is computed.  L synchronous rounds of six-neighbour propagation, with
+// the smallest root kept where several labelled neighbours meet, label every
+// voxel v within Manhattan distance L of an occupied voxel with
+//     ring[v] = d(v) = min over occupied u of |u - v|_1,
+//     root[v] = the smallest linear index among occupied u at that distance,
+// and leave the rest at root -1 / ring 255.  (On a box grid every monotone
+// lattice path between two voxels stays inside the box, so the rounds reach
+// exactly the voxels at Manhattan distance r in round r.)
+//
+// How.  Instead of L rounds over the dense grid, the kernel evaluates that
+// closed form as a separable lexicographic minimum.  A candidate is packed
+// into one 32-bit word (dist:6 | dz+31:6 | dy+31:6 | dx+31:6), the root's
+// offset from the voxel holding the word.  Because the linear index
+// x + nx*(y + ny*z) orders in-grid voxels as (z, y, x) lexicographically, for
+// a fixed voxel the unsigned order of these words is the order (distance,
+// root index).  Moving a word one voxel along an axis adds one to the
+// distance and shifts one offset field: a single integer add.  Words whose
+// distance reaches L are dropped (they cannot end within L).
+//
+//   pass X: nearest occupied voxel along the row, from the occupancy bitmask
+//           with clz/ffs on a 64-bit window (ties go to the left, the smaller
+//           index);
+//   pass Y: forward and backward running minimum along y;
+//   pass Z: the same along z, then the word is decoded into root and ring.
+//
+// One CTA owns a 32 x 8 x 8 output tile.  It stages the occupancy bits of the
+// tile grown by L in y and z (three 32-bit words per row cover x in
+// [x0-32, x0+64)), runs passes X and Y for eight z-planes at a time into
+// shared memory, then pass Z, and writes root and ring with coalesced
+// stores.  A tile whose grown neighbourhood holds no occupied voxel writes
+// "unlabelled" straight away.  L <= 31.
+#include "vicp_launch.h"
+
+namespace vicp {
+
+namespace {
+constexpr int TX = 32, TY = 8, TZ = 8, ZB = 8, THREADS = 256;
+constexpr unsigned NONE = 0xffffffffu;
+constexpr int SH_D = 18, SH_Z = 12, SH_Y = 6;
+constexpr unsigned CENTER = (31u << SH_Z) | (31u << SH_Y) | 31u;   // zero offsets
+constexpr unsigned STEP_D = 1u << SH_D;
+constexpr unsigned STEP_YF = STEP_D - (1u << SH_Y);   // moved from y-1 to y: dy -= 1
+constexpr unsigned STEP_YB = STEP_D + (1u << SH_Y);   // moved from y+1 to y: dy += 1
+constexpr unsigned STEP_ZF = STEP_D - (1u << SH_Z);
+constexpr unsigned STEP_ZB = STEP_D + (1u << SH_Z);
+
+// Move a word one voxel; words at distance >= L (and NONE) become NONE.
+// `lim` = L << SH_D: a word is >= lim exactly when its distance is >= L.
+__device__ __forceinline__ unsigned step(unsigned v, unsigned inc, unsigned lim)
+{
+    return v >= lim ? NONE : v + inc;
+}
+}  // namespace
+
+size_t dilate_smem_bytes(int L)
+{
+    const size_t HY = TY + 2 * L, HZ = TZ + 2 * L;
+    return sizeof(unsigned) * (HZ * HY * 3 + ZB * HY * TX + HZ * TY * TX);
+}
+
+__global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ, GridGeom g, int L,
+                                                    int tiles_x, int tiles_y, int *__restrict__ root,
+                                                    unsigned char *__restrict__ ring)
+{
+    extern __shared__ unsigned smem[];
+    const int HY = TY + 2 * L, HZ = TZ + 2 * L;
+    unsigned *s_bits = smem;                  // [HZ][HY][3]
+    unsigned *s_a = s_bits + HZ * HY * 3;     // [ZB][HY][TX]  pass X, one z batch
+    unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y, all planes
+    const unsigned lim = (unsigned)L << SH_D;
+
+    const long long t = blockIdx.x;
+    const int x0 = (int)(t % tiles_x) * TX;
+    const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
+    const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // 1. occupancy windows of the grown tile
+    int any = 0;
+    for (int idx = tid; idx < HZ * HY * 3; idx += THREADS) {
+        const int k = idx % 3, row = idx / 3;
+        const int y = y0 - L + row % HY, z = z0 - L + row / HY;
+        unsigned w = 0u;
+        if (y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+            const int xs = x0 - 32 + 32 * k;
+            const int lo = max(xs, 0), hi = min(xs + 32, g.nx);
+            if (lo < hi) {
+                const long long b = (long long)g.nx * (y + (long long)g.ny * z) + lo;
+                w = extract_bits(occ, b, hi - lo) << (lo - xs);
+            }
+        }
+        s_bits[idx] = w;
+        any |= (w != 0u);
+    }
+    any = __syncthreads_or(any);
+
+    unsigned out[TZ];
+    if (!any) {
+#pragma unroll
+        for (int k = 0; k < TZ; ++k)
+            out[k] = NONE;
+    } else {
+        for (int zb = 0; zb < HZ; zb += ZB) {
+            // 2a. pass X: warp per row, lane = x offset in the tile
+            for (int r = warp; r < ZB * HY; r += THREADS / 32) {
+                const int zz = zb + r / HY, yy = r % HY;
+                unsigned lbl = NONE;
+                if (zz < HZ) {
+                    const unsigned *wrow = s_bits + (zz * HY + yy) * 3;
+                    const unsigned a0 = wrow[0], a1 = wrow[1], a2 = wrow[2];
+                    if (a0 | a1 | a2) {
+                        const unsigned left = __funnelshift_r(a0, a1, lane);    // bit i <-> x - 32 + i
+                        const unsigned right = __funnelshift_r(a1, a2, lane);   // bit i <-> x + i
+                        if (right & 1u) {
+                            lbl = CENTER;
+                        } else if (L > 0) {
+                            const unsigned lm = left & (0xffffffffu << (32 - L));
+                            const unsigned rm = (right >> 1) & ((1u << L) - 1u);
+                            const int dl = lm ? __clz(lm) + 1 : 64;
+                            const int dr = rm ? __ffs(rm) : 64;
+                            if (dl <= dr) {
+                                if (dl <= L)
+                                    lbl = ((unsigned)dl << SH_D) | (CENTER - (unsigned)dl);
+                            } else if (dr <= L) {
+                                lbl = ((unsigned)dr << SH_D) | (CENTER + (unsigned)dr);
+                            }
+                        }
+                    }
+                }
+                s_a[r * TX + lane] = lbl;
+            }
+            __syncthreads();
+            // 2b. pass Y: thread per (x, plane of the batch)
+            {
+                const int zz = zb + warp;
+                if (zz < HZ) {
+                    const unsigned *col = s_a + warp * HY * TX + lane;
+                    unsigned *ob = s_b + zz * TY * TX + lane;
+                    unsigned f = NONE;
+                    for (int yy = 0; yy < L; ++yy)
+                        f = min(step(f, STEP_YF, lim), col[yy * TX]);
+#pragma unroll
+                    for (int k = 0; k < TY; ++k) {
+                        f = min(step(f, STEP_YF, lim), col[(L + k) * TX]);
+                        ob[k * TX] = f;
+                    }
+                    unsigned bk = NONE;
+                    for (int yy = HY - 1; yy >= L + TY; --yy)
+                        bk = min(step(bk, STEP_YB, lim), col[yy * TX]);
+#pragma unroll
+                    for (int k = TY - 1; k >= 0; --k) {
+                        bk = min(step(bk, STEP_YB, lim), col[(L + k) * TX]);
+                        ob[k * TX] = min(ob[k * TX], bk);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // 3. pass Z: thread per (x, y) column of the tile
+        const unsigned *col = s_b + warp * TX + lane;
+        unsigned f = NONE;
+        for (int zz = 0; zz < L; ++zz)
+            f = min(step(f, STEP_ZF, lim), col[zz * TY * TX]);
+#pragma unroll
+        for (int k = 0; k < TZ; ++k) {
+            f = min(step(f, STEP_ZF, lim), col[(L + k) * TY * TX]);
+            out[k] = f;
+        }
+        unsigned bk = NONE;
+        for (int zz = HZ - 1; zz >= L + TZ; --zz)
+            bk = min(step(bk, STEP_ZB, lim), col[zz * TY * TX]);
+#pragma unroll
+        for (int k = TZ - 1; k >= 0; --k) {
+            bk = min(step(bk, STEP_ZB, lim), col[(L + k) * TY * TX]);
+            out[k] = min(out[k], bk);
+        }
+    }
+
+    // 4. decode and store
+    const int x = x0 + lane, y = y0 + warp;
+    if (x < g.nx && y < g.ny) {
+#pragma unroll
+        for (int k = 0; k < TZ; ++k) {
+            const int z = z0 + k;
+            if (z < g.nz) {
+                const long long v = x + (long long)g.nx * (y + (long long)g.ny * z);
+                const unsigned w = out[k];
+                int r = -1;
+                unsigned char d = 255;
+                if (w != NONE) {
+                    const int dz = (int)((w >> SH_Z) & 63u) - 31;
+                    const int dy = (int)((w >> SH_Y) & 63u) - 31;
+                    const int dx = (int)(w & 63u) - 31;
+                    r = (int)(v + dx + (long long)g.nx * (dy + (long long)g.ny * dz));
+                    d = (unsigned char)(w >> SH_D);
+                }
+                root[v] = r;
+                ring[v] = d;
+            }
+        }
+    }
+}
+
+cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, int *root, unsigned char *ring,
+                          cudaStream_t st)
+{
+    const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
+    const long long tiles = (long long)tiles_x * tiles_y * tiles_z;
+    const size_t smem = dilate_smem_bytes(L);
+    if (smem > 48 * 1024) {   // opt in above the default limit (a per-device function attribute)
+        cudaError_t e = cudaFuncSetAttribute(k_dilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_dilate<<<(unsigned)tiles, THREADS, smem, st>>>(occ, g, L, tiles_x, tiles_y, root, ring);
+    return cudaGetLastError();
+}
+
+}  // namespace vicp

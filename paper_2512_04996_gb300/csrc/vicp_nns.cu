@@ -1,0 +1,246 @@
+// vicp_nns.cu -- NNS (Alg. 4): localised search in the root voxel, and the
+// global search for source points outside the grid or in unlabelled voxels.
+#include "vicp_launch.h"
+
+namespace vicp {
+
+// ---------------------------------------------------------------------------
+// Localised search: one thread per source point.  The point is transformed
+// by the float-rounded pose, quantised, and its voxel's root label followed
+// once (Alg. 4); the root voxel's CSR segment is scanned with 16-byte loads
+// of (x, y, z, index).  Points that need the global search are compacted
+// into a list with one warp-aggregated atomic per warp.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ src, int m,
+                                                    const double *__restrict__ pose, GridGeom g,
+                                                    const int *__restrict__ root, const unsigned *__restrict__ off,
+                                                    const float4 *__restrict__ csr, int n_cap,
+                                                    int *__restrict__ nn, float *__restrict__ d2,
+                                                    int *__restrict__ fb_list, DevCtl *__restrict__ ctl,
+                                                    int honor_stop)
+{
+    if (honor_stop && *(volatile int *)&ctl->stop)
+        return;
+    __shared__ PoseF sp;
+    if (threadIdx.x == 0)
+        load_pose_f(pose, sp);
+    __syncthreads();
+    const PoseF P = sp;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool fall = false;
+    unsigned cand = 0u;
+    if (i < m) {
+        const float3 s = transform_pt(P, __ldg(src + i));
+        const int v = voxel_key(g, s.x, s.y, s.z);
+        const int r = (v >= 0) ? __ldg(root + v) : -1;
+        if (r >= 0) {
+            const unsigned a = __ldg(off + r);
+            const unsigned b = min(__ldg(off + r + 1), (unsigned)n_cap);
+            cand = b > a ? b - a : 0u;
+            unsigned long long best = ~0ull;
+            for (unsigned k = a; k < b; ++k) {
+                const float4 q = __ldg(csr + k);
+                best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
+            }
+            nn[i] = (int)(unsigned)best;
+            d2[i] = __uint_as_float((unsigned)(best >> 32));
+        } else {
+            fall = true;
+        }
+    }
+    const unsigned long long wc = warp_sum_u64(cand);
+    if ((threadIdx.x & 31) == 0 && wc)
+        atomicAdd(&ctl->stat_local_cand, wc);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(&ctl->stat_queries, (unsigned long long)m);
+    const unsigned fm = __ballot_sync(FULL_MASK, fall);
+    if (fm) {
+        const int lane = threadIdx.x & 31, leader = __ffs(fm) - 1;
+        int base = 0;
+        if (lane == leader)
+            base = atomicAdd(&ctl->fb_count, __popc(fm));
+        base = __shfl_sync(FULL_MASK, base, leader);
+        if (fall) {
+            const int slot = base + __popc(fm & lanemask_lt());
+            if (slot < m)
+                fb_list[slot] = i;
+            else
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+        }
+    }
+}
+
+cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
+                              const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
+                              int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st)
+{
+    k_correspond<<<(m + 255) / 256, 256, 0, st>>>(src, m, pose, g, root, off, csr, n_cap, nn, d2, fb_list, ctl,
+                                                  honor_stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Global search ("Globalsearch" of Alg. 4): the exact nearest target point,
+// found without scanning every point.
+//
+// Each non-empty 8x8x8 brick has a float box that contains all its points.
+// For a query s, the box bound lb = ((ex*ex + ey*ey) + ez*ez), with e the
+// rounded gap between s and the box on each axis, is never larger than the
+// computed squared distance from s to any point in the box: rounding is
+// monotone, so every operation of the bound is <= the same operation of the
+// true distance formula.  A warp per query (1) finds the brick of smallest
+// bound and scans it, which gives a first best distance D, then (2) scans
+// every other brick whose bound is <= D, and (3) scans the target points
+// that lie outside the grid.  The result is the same (distance, index)
+// minimum as a scan of all target points.  A query with a non-finite
+// coordinate scans all target points.
+// ---------------------------------------------------------------------------
+constexpr int FB_THREADS = 256;
+constexpr int FB_WARPS = FB_THREADS / 32;
+
+__device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
+{
+    const float ex = s.x < lo.x ? __fsub_rn(lo.x, s.x) : (s.x > hi.x ? __fsub_rn(s.x, hi.x) : 0.0f);
+    const float ey = s.y < lo.y ? __fsub_rn(lo.y, s.y) : (s.y > hi.y ? __fsub_rn(s.y, hi.y) : 0.0f);
+    const float ez = s.z < lo.z ? __fsub_rn(lo.z, s.z) : (s.z > hi.z ? __fsub_rn(s.z, hi.z) : 0.0f);
+    return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+}
+
+// Scan rows row0, row0+rstep, ... (of the brick's 64 rows) and every point of
+// their occupied voxels.
+__device__ __forceinline__ unsigned long long scan_brick_rows(const GridGeom &g, const unsigned *__restrict__ occ,
+                                                              const unsigned *__restrict__ off,
+                                                              const float4 *__restrict__ csr, unsigned n_cap,
+                                                              int brick, float3 s, int row0, int rstep,
+                                                              unsigned long long best, unsigned &examined)
+{
+    const int bxi = brick % g.bx;
+    const int byi = (brick / g.bx) % g.by;
+    const int bzi = brick / (g.bx * g.by);
+    const int x0 = bxi * BRICK, y0 = byi * BRICK, z0 = bzi * BRICK;
+    const int xw = min(BRICK, g.nx - x0);
+    for (int r = row0; r < BRICK * BRICK; r += rstep) {
+        const int y = y0 + (r % BRICK), z = z0 + (r / BRICK);
+        if (y >= g.ny || z >= g.nz)
+            continue;
+        const long long rowbase = (long long)g.nx * (y + (long long)g.ny * z) + x0;
+        unsigned bits = extract_bits(occ, rowbase, xw);
+        while (bits) {
+            const int xi = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const long long v = rowbase + xi;
+            const unsigned a = __ldg(off + v);
+            const unsigned b = min(__ldg(off + v + 1), n_cap);
+            examined += b > a ? b - a : 0u;
+            for (unsigned k = a; k < b; ++k) {
+                const float4 q = __ldg(csr + k);
+                best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
+            }
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restrict__ src,
+                                                         const double *__restrict__ pose, GridGeom g,
+                                                         const unsigned *__restrict__ occ,
+                                                         const unsigned *__restrict__ off,
+                                                         const float4 *__restrict__ csr, int n_cap,
+                                                         const int *__restrict__ brick_list,
+                                                         const float4 *__restrict__ brick_box,
+                                                         const float4 *__restrict__ tgt, int n_tgt,
+                                                         const int *__restrict__ outside,
+                                                         const int *__restrict__ fb_list,
+                                                         DevCtl *__restrict__ ctl, int *__restrict__ nn,
+                                                         float *__restrict__ d2, int m, int honor_stop)
+{
+    if (honor_stop && *(volatile int *)&ctl->stop)
+        return;   // the correspond kernel appended nothing either
+    __shared__ PoseF sp;
+    if (threadIdx.x == 0)
+        load_pose_f(pose, sp);
+    __syncthreads();
+    const PoseF P = sp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int F = min(*(volatile int *)&ctl->fb_count, m);
+    const int nb = *(volatile int *)&ctl->n_bricks;
+    const int no = *(volatile int *)&ctl->n_outside;
+    const unsigned cap = (unsigned)n_cap;
+    unsigned examined = 0u;
+
+    for (int qi = blockIdx.x * FB_WARPS + warp; qi < F; qi += gridDim.x * FB_WARPS) {
+        const int i = __ldg(fb_list + qi);
+        if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
+            if (lane == 0)
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+            continue;
+        }
+        const float3 s = transform_pt(P, __ldg(src + i));
+        unsigned long long best = ~0ull;
+        if (!(isfinite(s.x) && isfinite(s.y) && isfinite(s.z))) {
+            for (int j = lane; j < n_tgt; j += 32)
+                best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
+            examined += (unsigned)((n_tgt - lane + 31) / 32);
+        } else {
+            if (nb > 0) {
+                // (1) brick of smallest bound (ties: smallest list slot)
+                unsigned long long lbmin = ~0ull;
+                for (int k = lane; k < nb; k += 32) {
+                    const float lb = box_lb2(s, __ldg(brick_box + 2 * k), __ldg(brick_box + 2 * k + 1));
+                    lbmin = umin64(lbmin, ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)k);
+                }
+                lbmin = warp_min_u64(lbmin);
+                const int k0 = (int)(unsigned)lbmin;
+                best = scan_brick_rows(g, occ, off, csr, cap, __ldg(brick_list + k0), s, lane, 32, best, examined);
+                best = warp_min_u64(best);
+                // (2) every other brick that could hold a point at distance <= D
+                for (int k = lane; k < nb; k += 32) {
+                    if (k == k0)
+                        continue;
+                    const float lb = box_lb2(s, __ldg(brick_box + 2 * k), __ldg(brick_box + 2 * k + 1));
+                    if (__float_as_uint(lb) <= (unsigned)(best >> 32))
+                        best = scan_brick_rows(g, occ, off, csr, cap, __ldg(brick_list + k), s, 0, 1, best, examined);
+                }
+            }
+            // (3) target points outside the grid
+            for (int k = lane; k < no; k += 32) {
+                const int j = __ldg(outside + k);
+                best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
+                ++examined;
+            }
+        }
+        best = warp_min_u64(best);
+        if (lane == 0) {
+            nn[i] = (int)(unsigned)best;
+            d2[i] = __uint_as_float((unsigned)(best >> 32));
+        }
+    }
+
+    const unsigned long long we = warp_sum_u64(examined);
+    if (lane == 0 && we)
+        atomicAdd(&ctl->stat_global_cand, we);
+    // The last block to finish clears the fallback counter for the next search.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&ctl->fb_done, 1u);
+        if (done == gridDim.x - 1) {
+            ctl->stat_fallbacks += (unsigned long long)F;
+            ctl->fb_count = 0;
+            ctl->fb_done = 0u;
+        }
+    }
+}
+
+cudaError_t launch_fallback(const float4 *src, const double *pose, const GridGeom &g, const unsigned *occ,
+                            const unsigned *off, const float4 *csr, int n_cap, const int *brick_list,
+                            const float4 *brick_box, const float4 *tgt, int n_tgt, const int *outside,
+                            const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m, int honor_stop,
+                            cudaStream_t st)
+{
+    k_fallback<<<152 * 4, FB_THREADS, 0, st>>>(src, pose, g, occ, off, csr, n_cap, brick_list, brick_box, tgt,
+                                               n_tgt, outside, fb_list, ctl, nn, d2, m, honor_stop);
+    return cudaGetLastError();
+}
+
+}  // namespace vicp

@@ -1,0 +1,367 @@
+"""Python binding of the C ABI in ``include/vicp.h`` -- argument marshalling only.
+
+Every step of the registration runs in the CUDA kernels of ``libvicp.so``;
+this module checks tensor shapes, dtypes and devices, passes raw pointers and
+the current torch CUDA stream, and turns status codes into exceptions.  The
+functions carry the C names (``vicp_create``, ``vicp_build_grid``, ...); the
+``Context`` class bundles them.
+
+Point clouds are CUDA float32 tensors of shape (N, 4) (x, y, z, w; w is
+ignored), contiguous and 16-byte aligned.  Poses are 4x4 float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+VICP_OK = 0
+VICP_ERR_INVALID = 1
+VICP_ERR_CUDA = 2
+VICP_ERR_OOM = 3
+VICP_ERR_GRID_TOO_LARGE = 4
+VICP_ERR_TIMEOUT = 5
+VICP_ERR_STATE = 6
+VICP_ERR_DEGENERATE = 7
+
+VICP_FLAG_KEEP_GRID = 1 << 0
+VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
+VICP_FLAG_TEST_SCAN_TIMEOUT = 1 << 31
+
+
+class VicpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"vicp status {status}: {message}")
+        self.status = status
+
+
+class vicp_params(C.Structure):
+    _fields_ = [("voxel_size", C.c_float), ("grid_divisions", C.c_int32), ("origin", C.c_float * 3),
+                ("dims", C.c_int32 * 3), ("dilation_layers", C.c_int32), ("max_iters", C.c_int32),
+                ("rmse_eps", C.c_double), ("flags", C.c_uint32)]
+
+
+class vicp_grid_view(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("voxel_size", C.c_float), ("inv_voxel_size", C.c_float),
+                ("dims", C.c_int32 * 3), ("n_voxels", C.c_int64), ("n_target", C.c_int32),
+                ("n_stored", C.c_int32), ("dilation_layers", C.c_int32), ("keys", C.c_void_p),
+                ("offsets", C.c_void_p), ("ids", C.c_void_p), ("csr_points", C.c_void_p),
+                ("root", C.c_void_p), ("ring", C.c_void_p), ("occupancy", C.c_void_p)]
+
+
+class vicp_memory(C.Structure):
+    _fields_ = [("current_bytes", C.c_uint64), ("peak_bytes", C.c_uint64), ("static_bytes", C.c_uint64),
+                ("csr_store_bytes", C.c_uint64), ("fixed_capacity_bytes", C.c_uint64),
+                ("paper_static_layout_bytes", C.c_uint64), ("max_voxel_count", C.c_uint32),
+                ("occupied_voxels", C.c_uint32)]
+
+
+class vicp_stats(C.Structure):
+    _fields_ = [("queries", C.c_uint64), ("fallbacks", C.c_uint64), ("local_candidates", C.c_uint64),
+                ("global_candidates", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class vicp_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+# Every exported symbol with its signature (also used by the ABI test).
+_P = C.c_void_p
+SIGNATURES = {
+    "vicp_abi_version": (C.c_int32, []),
+    "vicp_status_string": (C.c_char_p, [C.c_int]),
+    "vicp_default_params": (None, [C.POINTER(vicp_params)]),
+    "vicp_create": (C.c_int, [C.POINTER(_P), C.POINTER(vicp_params), C.POINTER(vicp_allocator), _P]),
+    "vicp_destroy": (None, [_P]),
+    "vicp_set_stream": (C.c_int, [_P, _P]),
+    "vicp_build_grid": (C.c_int, [_P, _P, C.c_int32]),
+    "vicp_dilate": (C.c_int, [_P, C.c_int32]),
+    "vicp_correspond": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
+    "vicp_step": (C.c_int, [_P, _P, C.c_int32, _P, _P]),
+    "vicp_register": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.POINTER(C.c_int32),
+                                C.POINTER(C.c_double)]),
+    "vicp_register_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]),
+    "vicp_get_grid": (C.c_int, [_P, C.POINTER(vicp_grid_view)]),
+    "vicp_sync": (C.c_int, [_P]),
+    "vicp_memory_report": (C.c_int, [_P, C.POINTER(vicp_memory)]),
+    "vicp_profile_enable": (C.c_int, [_P, C.c_int32]),
+    "vicp_kernel_count": (C.c_int32, []),
+    "vicp_kernel_name": (C.c_char_p, [C.c_int32]),
+    "vicp_profile_read": (C.c_int, [_P, _P, _P]),
+    "vicp_read_stats": (C.c_int, [_P, C.POINTER(vicp_stats), C.c_int32]),
+    "vicp_launch_count": (C.c_int64, [_P]),
+    "vicp_last_error": (C.c_char_p, [_P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False) -> C.CDLL:
+    """Load libvicp.so.  Raises if it has not been built: there is no
+    fallback path."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                if not build_if_missing:
+                    raise RuntimeError(f"{_build.LIB} is not built; run __graft_entry__.build() or "
+                                       "python -m paper_2512_04996_gb300.build")
+                _build.build_library()
+            lib = C.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def default_params(**overrides) -> vicp_params:
+    p = vicp_params()
+    load_library().vicp_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if k in ("origin", "dims"):
+            arr = getattr(p, k)
+            for a in range(3):
+                arr[a] = v[a]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _cloud(t: torch.Tensor, what: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{what}: expected a CUDA float32 tensor")
+    if t.dim() != 2 or t.shape[1] != 4 or not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous (N, 4) tensor, got {tuple(t.shape)}")
+    if t.data_ptr() % 16:
+        raise ValueError(f"{what}: data must be 16-byte aligned")
+    return t
+
+
+def _host_cloud(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 4:
+        raise ValueError("host clouds are (N, 4) float32")
+    return a
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of context-owned device memory."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"data": (ptr, True), "shape": tuple(shape), "typestr": typestr,
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, shape, typestr, dtype, device):
+    if not ptr or 0 in shape:
+        return torch.empty(shape, dtype=dtype, device=device)
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device=device)
+
+
+class Context:
+    """One vicp context on the current CUDA device and torch stream."""
+
+    def __init__(self, params: vicp_params | None = None, stream: torch.cuda.Stream | None = None,
+                 allocator: vicp_allocator | None = None, **overrides):
+        self._lib = load_library()
+        self.params = params if params is not None else default_params(**overrides)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._allocator = allocator   # keep the callbacks alive
+        h = C.c_void_p()
+        st = self._lib.vicp_create(C.byref(h), C.byref(self.params),
+                                   C.byref(allocator) if allocator is not None else None,
+                                   C.c_void_p(self.stream.cuda_stream))
+        if st != VICP_OK:
+            raise VicpError(st, "vicp_create failed")
+        self.handle = h
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != VICP_OK:
+            raise VicpError(st, f"{what}: {self._lib.vicp_last_error(self.handle).decode()}")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.vicp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the hot path -----------------------------------------------------
+    def build_grid(self, target: torch.Tensor):
+        t = _cloud(target, "target")
+        self._target = t   # the grid refers to it until the next build
+        self._check(self._lib.vicp_build_grid(self.handle, t.data_ptr(), t.shape[0]), "vicp_build_grid")
+
+    def dilate(self, layers: int = -1):
+        self._check(self._lib.vicp_dilate(self.handle, int(layers)), "vicp_dilate")
+
+    def correspond(self, source: torch.Tensor, pose: torch.Tensor, nn: torch.Tensor | None = None,
+                   d2: torch.Tensor | None = None, n_fallback: torch.Tensor | None = None):
+        s = _cloud(source, "source")
+        m = s.shape[0]
+        if pose.dtype != torch.float64 or not pose.is_cuda or pose.numel() != 16 or not pose.is_contiguous():
+            raise ValueError("pose: contiguous CUDA float64 tensor with 16 entries")
+        nn = torch.empty(m, dtype=torch.int32, device=s.device) if nn is None else nn
+        d2 = torch.empty(m, dtype=torch.float32, device=s.device) if d2 is None else d2
+        if n_fallback is None:
+            n_fallback = torch.zeros(1, dtype=torch.int32, device=s.device)
+        self._check(self._lib.vicp_correspond(self.handle, s.data_ptr(), m, pose.data_ptr(), nn.data_ptr(),
+                                              d2.data_ptr(), n_fallback.data_ptr()), "vicp_correspond")
+        return nn, d2, n_fallback
+
+    def step(self, source: torch.Tensor, pose: torch.Tensor, rmse: torch.Tensor | None = None):
+        s = _cloud(source, "source")
+        if pose.dtype != torch.float64 or not pose.is_cuda or pose.numel() != 16 or not pose.is_contiguous():
+            raise ValueError("pose: contiguous CUDA float64 tensor with 16 entries")
+        rptr = 0 if rmse is None else rmse.data_ptr()
+        self._check(self._lib.vicp_step(self.handle, s.data_ptr(), s.shape[0], pose.data_ptr(), rptr),
+                    "vicp_step")
+        return rmse
+
+    def register(self, source: torch.Tensor, target: torch.Tensor, pose=None):
+        s, t = _cloud(source, "source"), _cloud(target, "target")
+        self._target = t
+        P = np.ascontiguousarray(np.eye(4) if pose is None else pose, dtype=np.float64).copy()
+        it, rm = C.c_int32(0), C.c_double(0.0)
+        st = self._lib.vicp_register(self.handle, s.data_ptr(), s.shape[0], t.data_ptr(), t.shape[0],
+                                     P.ctypes.data_as(C.c_void_p), C.byref(it), C.byref(rm))
+        return st, P, int(it.value), float(rm.value)
+
+    def register_host(self, source, target, pose=None):
+        s, t = _host_cloud(source), _host_cloud(target)
+        P = np.ascontiguousarray(np.eye(4) if pose is None else pose, dtype=np.float64).copy()
+        it, rm = C.c_int32(0), C.c_double(0.0)
+        st = self._lib.vicp_register_host(self.handle, s.ctypes.data_as(C.c_void_p), s.shape[0],
+                                          t.ctypes.data_as(C.c_void_p), t.shape[0],
+                                          P.ctypes.data_as(C.c_void_p), C.byref(it), C.byref(rm))
+        return st, P, int(it.value), float(rm.value)
+
+    # -- inspection -------------------------------------------------------
+    def sync(self) -> int:
+        return int(self._lib.vicp_sync(self.handle))
+
+    def last_error(self) -> str:
+        return self._lib.vicp_last_error(self.handle).decode()
+
+    def grid_view(self) -> vicp_grid_view:
+        v = vicp_grid_view()
+        self._check(self._lib.vicp_get_grid(self.handle, C.byref(v)), "vicp_get_grid")
+        return v
+
+    def get_grid(self) -> dict:
+        """Copies of the grid arrays as torch tensors on the device."""
+        v = self.grid_view()
+        V, n, ns = int(v.n_voxels), int(v.n_target), int(v.n_stored)
+        d = self.device
+        out = {
+            "origin": tuple(float(v.origin[a]) for a in range(3)), "voxel_size": float(v.voxel_size),
+            "inv_voxel_size": float(v.inv_voxel_size), "dims": tuple(int(v.dims[a]) for a in range(3)),
+            "n_voxels": V, "n_target": n, "n_stored": ns, "dilation_layers": int(v.dilation_layers),
+            "keys": _view(v.keys, (n,), "<i4", torch.int32, d).clone(),
+            "offsets": _view(v.offsets, (V + 1,), "<u4", torch.uint32, d).clone(),
+            "ids": _view(v.ids, (ns,), "<i4", torch.int32, d).clone(),
+            "csr_points": _view(v.csr_points, (ns, 4), "<f4", torch.float32, d).clone(),
+            "occupancy": _view(v.occupancy, ((V + 31) // 32,), "<u4", torch.uint32, d).clone(),
+        }
+        if v.dilation_layers >= 0:
+            out["root"] = _view(v.root, (V,), "<i4", torch.int32, d).clone()
+            out["ring"] = _view(v.ring, (V,), "|u1", torch.uint8, d).clone()
+        return out
+
+    def memory_report(self) -> dict:
+        m = vicp_memory()
+        self._check(self._lib.vicp_memory_report(self.handle, C.byref(m)), "vicp_memory_report")
+        return {name: int(getattr(m, name)) for name, _ in vicp_memory._fields_}
+
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.vicp_profile_enable(self.handle, 1 if on else 0), "vicp_profile_enable")
+
+    def profile_read(self) -> dict:
+        k = int(self._lib.vicp_kernel_count())
+        launches = np.zeros(k, np.int64)
+        ms = np.zeros(k, np.float64)
+        self._check(self._lib.vicp_profile_read(self.handle, launches.ctypes.data_as(C.c_void_p),
+                                                ms.ctypes.data_as(C.c_void_p)), "vicp_profile_read")
+        return {self._lib.vicp_kernel_name(i).decode(): (int(launches[i]), float(ms[i])) for i in range(k)}
+
+    def read_stats(self, reset: bool = True) -> dict:
+        st = vicp_stats()
+        self._check(self._lib.vicp_read_stats(self.handle, C.byref(st), 1 if reset else 0), "vicp_read_stats")
+        return {name: int(getattr(st, name)) for name, _ in vicp_stats._fields_}
+
+    def launch_count(self) -> int:
+        return int(self._lib.vicp_launch_count(self.handle))
+
+
+# --- the C names, as plain functions over a Context ------------------------
+def vicp_create(params: vicp_params | None = None, stream=None, allocator=None, **overrides) -> Context:
+    return Context(params, stream, allocator, **overrides)
+
+
+def vicp_destroy(ctx: Context):
+    ctx.close()
+
+
+def vicp_build_grid(ctx: Context, target):
+    ctx.build_grid(target)
+
+
+def vicp_dilate(ctx: Context, layers: int = -1):
+    ctx.dilate(layers)
+
+
+def vicp_correspond(ctx: Context, source, pose, nn=None, d2=None, n_fallback=None):
+    return ctx.correspond(source, pose, nn, d2, n_fallback)
+
+
+def vicp_step(ctx: Context, source, pose, rmse=None):
+    return ctx.step(source, pose, rmse)
+
+
+def vicp_register(ctx: Context, source, target, pose=None):
+    return ctx.register(source, target, pose)
+
+
+def vicp_register_host(ctx: Context, source, target, pose=None):
+    return ctx.register_host(source, target, pose)
+
+
+def vicp_get_grid(ctx: Context) -> dict:
+    return ctx.get_grid()
+
+
+def vicp_sync(ctx: Context) -> int:
+    return ctx.sync()
+
+
+def vicp_memory_report(ctx: Context) -> dict:
+    return ctx.memory_report()

@@ -1,0 +1,116 @@
+"""Failure handling without faulting the GPU: a bounded device-side wait that
+runs out returns VICP_ERR_TIMEOUT and leaves the context usable; an
+allocator that returns NULL gives VICP_ERR_OOM and leaks nothing; calls out
+of order return VICP_ERR_STATE."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import assert_grid_equal, context, gpu_grid, oracle_grid_for, to_np, vicp
+
+pytestmark = pytest.mark.gpu
+
+
+def test_scan_wait_times_out_and_context_recovers(pairs):
+    """One scan tile never publishes its aggregate (test flag): its successor
+    waits 200 ms on the global timer, gives up, records the timeout and
+    publishes anyway; the host sees VICP_ERR_TIMEOUT."""
+    v = vicp()
+    p = pairs(2)                        # ~2M voxels: hundreds of scan tiles
+    ctx = context(L=10, divisions=128, flags=v.VICP_FLAG_TEST_SCAN_TIMEOUT)
+    ctx.build_grid(torch.from_numpy(p.target).cuda())
+    assert ctx.sync() == v.VICP_ERR_TIMEOUT
+    assert ctx.sync() == 0              # the status was cleared
+    # a normal context afterwards is exact, so the device is fine
+    ctx2, g = gpu_grid(p.target, L=10, divisions=128)
+    grid, ref = oracle_grid_for(g, p.target, 10)
+    assert_grid_equal(g, ref, p.target)
+
+
+def test_allocator_failure_is_reported_and_nothing_leaks(pairs):
+    v = vicp()
+    live = {}
+    budget = {"n": 6}
+
+    @v.ALLOC_FN
+    def alloc(nbytes, stream, user):
+        if budget["n"] == 0:
+            return None
+        budget["n"] -= 1
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @v.FREE_FN
+    def free(ptr, nbytes, stream, user):
+        live.pop(ptr)
+
+    a = v.vicp_allocator(alloc, free, None)
+    ctx = v.Context(v.default_params(grid_divisions=64), allocator=a)
+    with pytest.raises(v.VicpError) as e:
+        ctx.build_grid(torch.from_numpy(pairs(1).target).cuda())
+    assert e.value.status == v.VICP_ERR_OOM
+    assert len(live) > 0
+    ctx.close()
+    assert live == {}
+
+
+def test_torch_allocator_path_is_exact(pairs):
+    """The same build with every workspace buffer from torch's allocator."""
+    v = vicp()
+    live = {}
+
+    @v.ALLOC_FN
+    def alloc(nbytes, stream, user):
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @v.FREE_FN
+    def free(ptr, nbytes, stream, user):
+        live.pop(ptr)
+
+    p = pairs(1)
+    a = v.vicp_allocator(alloc, free, None)
+    ctx = v.Context(v.default_params(grid_divisions=64, dilation_layers=10), allocator=a)
+    ctx.build_grid(torch.from_numpy(p.target).cuda())
+    ctx.dilate(10)
+    g = {k: to_np(x) for k, x in ctx.get_grid().items()}
+    grid, ref = oracle_grid_for(g, p.target, 10)
+    assert_grid_equal(g, ref, p.target)
+    rep = ctx.memory_report()
+    assert rep["current_bytes"] == sum(t.numel() for t in live.values())
+    ctx.close()
+    assert live == {}
+
+
+def test_call_order_and_argument_errors(pairs):
+    v = vicp()
+    ctx = context(L=10, divisions=64)
+    src = torch.from_numpy(pairs(1).source).cuda()
+    pose = torch.eye(4, dtype=torch.float64, device="cuda").contiguous()
+    with pytest.raises(v.VicpError) as e:
+        ctx.step(src, pose)
+    assert e.value.status == v.VICP_ERR_STATE
+    with pytest.raises(v.VicpError) as e:
+        ctx.dilate(5)
+    assert e.value.status == v.VICP_ERR_STATE
+    ctx.build_grid(torch.from_numpy(pairs(1).target).cuda())
+    with pytest.raises(v.VicpError) as e:
+        ctx.dilate(32)
+    assert e.value.status == v.VICP_ERR_INVALID
+    lib = v.load_library()
+    misaligned = src.view(-1)[1:].data_ptr()
+    assert lib.vicp_build_grid(ctx.handle, misaligned, 10) == v.VICP_ERR_INVALID
+    assert lib.vicp_build_grid(ctx.handle, src.data_ptr(), 0) == v.VICP_ERR_INVALID
+    assert ctx.sync() == 0
+
+
+def test_grid_too_large_is_rejected():
+    v = vicp()
+    ctx = context(L=10, voxel_size=1.0, origin=(0, 0, 0), dims=(2048, 2048, 1024))
+    with pytest.raises(v.VicpError) as e:
+        ctx.build_grid(torch.zeros((4, 4), dtype=torch.float32, device="cuda"))
+    assert e.value.status == v.VICP_ERR_GRID_TOO_LARGE

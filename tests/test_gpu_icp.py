@@ -1,0 +1,151 @@
+"""GPU ICP iterations (vicp_step / vicp_register) against the oracle: the pose
+within 1e-5 rad and 1e-5 x extent, the same iteration count under the
+paper's stopping rule, deterministic results, and the degenerate case."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import context, gpu_grid, oracle_grid_for, rot_err, to_np
+from paper_2512_04996_gb300.synth import random_rigid
+
+pytestmark = pytest.mark.gpu
+
+ROT_TOL = 1e-5
+
+
+def _extent(target):
+    t = target[:, :3]
+    return float((t.max(0) - t.min(0)).max())
+
+
+def _assert_pose_close(T, R, extent):
+    assert rot_err(T, R) <= ROT_TOL, rot_err(T, R)
+    assert np.linalg.norm(T[:3, 3] - R[:3, 3]) <= 1e-5 * extent
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_single_step(pairs, k):
+    p = pairs(k)
+    ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions)
+    grid, ref = oracle_grid_for(g, p.target, 10)
+    T0 = np.eye(4) if k != 1 else random_rigid(np.random.default_rng(9), 3.0, 0.02)
+    pose = torch.from_numpy(T0.copy()).cuda()
+    rmse = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.step(torch.from_numpy(p.source).cuda(), pose, rmse)
+    assert ctx.sync() == 0
+    st, R, r_rmse, *_ = oracle.iterate(grid, ref, p.target, p.source, T0)
+    assert st == 0
+    _assert_pose_close(to_np(pose), R, _extent(p.target))
+    assert abs(float(to_np(rmse)[0]) - r_rmse) <= 1e-9 * r_rmse
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_register_fixed_iterations(pairs, k):
+    p = pairs(k)
+    ctx = context(L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions, max_iters=p.iters, eps=0.0)
+    st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+    assert st == 0 and it == p.iters
+    grid = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
+    rst, R, rit, hist = oracle.register(grid, 10, p.target, p.source, np.eye(4), max_iters=p.iters, eps=0.0)
+    assert rst == 0 and rit == it
+    _assert_pose_close(T, R, _extent(p.target))
+    assert abs(rm - hist[-1]) <= 1e-7 * hist[-1]
+
+
+def test_register_scene_three_iterations_rebuilding_each(pairs):
+    from paper_2512_04996_gb300 import vicp
+    p = pairs(3)
+    ctx = context(L=10, voxel_size=p.voxel_size, max_iters=3, eps=0.0,
+                  flags=vicp.VICP_FLAG_KEEP_GRID | vicp.VICP_FLAG_REBUILD_EACH_ITER)
+    st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+    assert st == 0 and it == 3
+    grid = oracle.fit_grid(p.target, p.voxel_size, 0)
+    rst, R, rit, hist = oracle.register(grid, 10, p.target, p.source, np.eye(4), max_iters=3, eps=0.0)
+    _assert_pose_close(T, R, _extent(p.target))
+
+
+def test_paper_stopping_rule(pairs):
+    from paper_2512_04996_gb300 import synth
+    p = synth.sphere_plane(seed=77, n=2000)
+    ctx = context(L=10, divisions=64, max_iters=50, eps=1e-5)
+    st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+    grid = oracle.fit_grid(p.target, 0.0, 64)
+    rst, R, rit, hist = oracle.register(grid, 10, p.target, p.source, np.eye(4), max_iters=50, eps=1e-5)
+    assert st == 0 and it == rit and 2 <= it < 50
+    _assert_pose_close(T, R, _extent(p.target))
+
+
+def test_deterministic(pairs):
+    p = pairs(2)
+    out = []
+    for _ in range(2):
+        ctx = context(L=10, divisions=128, max_iters=8, eps=0.0)
+        out.append(ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda()))
+    assert out[0][0] == out[1][0] == 0
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][3] == out[1][3]
+
+
+def test_register_host_equals_register(pairs):
+    p = pairs(1)
+    ctx = context(L=10, divisions=64, max_iters=10, eps=0.0)
+    a = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+    b = ctx.register_host(p.source, p.target)
+    assert a[0] == b[0] == 0 and a[2] == b[2]
+    assert np.array_equal(a[1], b[1])
+
+
+def test_rebuild_each_iteration_equals_build_once(pairs):
+    from paper_2512_04996_gb300 import vicp
+    p = pairs(1)
+    res = []
+    for flags in (0, vicp.VICP_FLAG_KEEP_GRID | vicp.VICP_FLAG_REBUILD_EACH_ITER):
+        ctx = context(L=10, divisions=64, max_iters=12, eps=0.0, flags=flags)
+        res.append(ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda()))
+    assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_steps_equal_register(pairs):
+    p = pairs(1)
+    ctx = context(L=10, divisions=64, max_iters=5, eps=0.0)
+    st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+    ctx2, g = gpu_grid(p.target, L=10, divisions=64)
+    pose = torch.eye(4, dtype=torch.float64, device="cuda").contiguous()
+    src = torch.from_numpy(p.source).cuda()
+    for _ in range(5):
+        ctx2.step(src, pose)
+    assert ctx2.sync() == 0
+    assert np.array_equal(to_np(pose), T)
+
+
+def test_degenerate_geometry_reports_and_keeps_pose():
+    from paper_2512_04996_gb300 import vicp
+    tgt = np.zeros((500, 4), np.float32)
+    tgt[:, 0] = np.linspace(0, 1, 500)
+    ctx = context(L=4, divisions=16, max_iters=5, eps=0.0)
+    st, T, it, rm = ctx.register(torch.from_numpy(tgt).cuda(), torch.from_numpy(tgt).cuda())
+    assert st == vicp.VICP_ERR_DEGENERATE and it == 0
+    assert np.array_equal(T, np.eye(4))
+    grid = oracle.fit_grid(tgt, 0.0, 16)
+    rst, R, rit, hist = oracle.register(grid, 4, tgt, tgt, np.eye(4), max_iters=5, eps=0.0)
+    assert rst == oracle.ERR_DEGENERATE and rit == 0
+    # the context stays usable
+    p = np.zeros((300, 4), np.float32)
+    p[:, :3] = np.random.default_rng(0).standard_normal((300, 3))
+    st, T, it, rm = ctx.register(torch.from_numpy(p).cuda(), torch.from_numpy(p).cuda())
+    assert st == 0 and np.abs(T - np.eye(4)).max() < 1e-12
+
+
+def test_profile_counts_launches(pairs):
+    p = pairs(1)
+    ctx, g = gpu_grid(p.target, L=10, divisions=64)
+    ctx.profile_enable(True)
+    pose = torch.eye(4, dtype=torch.float64, device="cuda").contiguous()
+    src = torch.from_numpy(p.source).cuda()
+    before = ctx.launch_count()
+    for _ in range(3):
+        ctx.step(src, pose)
+    prof = ctx.profile_read()
+    assert ctx.launch_count() - before == 12
+    for name in ("correspond", "fallback", "reduce", "solve"):
+        assert prof[name][0] == 3 and prof[name][1] > 0.0

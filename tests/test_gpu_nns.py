@@ -1,0 +1,114 @@
+"""GPU NNS (Alg. 4) against the oracle: for every source point the same target
+index and the same float squared distance (the tolerance allows another index
+only when its squared distance is within 1e-6 relative), and the same set of
+points taking the global search."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import gpu_grid, oracle_grid_for, to_np, transform_f32
+from paper_2512_04996_gb300.synth import random_rigid
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_correspond(ctx, src, T):
+    s = torch.from_numpy(np.ascontiguousarray(src)).cuda()
+    pose = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float64)).cuda()
+    nn, d2, nf = ctx.correspond(s, pose)
+    torch.cuda.synchronize()
+    return to_np(nn), to_np(d2), int(to_np(nf)[0])
+
+
+def _assert_nn_equal(nn, d2, rnn, rd2, target, src_T=None):
+    same = nn == rnn
+    if not same.all():
+        # allowed only for a different index at a squared distance within 1e-6
+        bad = ~same
+        rel = np.abs(d2[bad].astype(np.float64) - rd2[bad]) / np.maximum(rd2[bad], 1e-30)
+        assert (rel <= 1e-6).all(), (np.flatnonzero(bad)[:5], nn[bad][:5], rnn[bad][:5])
+    both_nan = np.isnan(d2) & np.isnan(rd2)
+    assert np.array_equal(d2[same & ~both_nan], rd2[same & ~both_nan])
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("which", ["identity", "ground_truth", "random"])
+def test_correspond_matches_oracle(pairs, k, which):
+    p = pairs(k)
+    ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions)
+    grid, ref = oracle_grid_for(g, p.target, 10)
+    T = {"identity": np.eye(4), "ground_truth": p.T_gt,
+         "random": random_rigid(np.random.default_rng(k), 25.0, 0.3)}[which]
+    nn, d2, nf = _gpu_correspond(ctx, p.source, T)
+    rnn, rd2, rfb = oracle.correspond(grid, ref, p.target, p.source, T)
+    assert nf == int(rfb.sum())
+    _assert_nn_equal(nn, d2, rnn, rd2, p.target)
+
+
+def test_correspond_scene_sampled(pairs):
+    """Full 226k-point scene on the GPU; the oracle checks a 12k-point sample
+    (each point's search is independent of the others)."""
+    p = pairs(3)
+    ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size)
+    grid, ref = oracle_grid_for(g, p.target, 10)
+    T = p.T_gt
+    nn, d2, nf = _gpu_correspond(ctx, p.source, T)
+    idx = np.random.default_rng(3).choice(p.source.shape[0], 12000, replace=False)
+    rnn, rd2, rfb = oracle.correspond(grid, ref, p.target, p.source[idx], T)
+    _assert_nn_equal(nn[idx], d2[idx], rnn, rd2, p.target)
+    # fallback count of the full cloud: points outside the grid or in an unlabelled voxel
+    keys = oracle.keys(grid, transform_f32(T, p.source))
+    want = int(((keys < 0) | (ref["root"][np.maximum(keys, 0)] < 0)).sum())
+    assert nf == want and 0 < nf < p.source.shape[0]
+
+
+def test_global_search_with_outside_targets_and_odd_sources():
+    """Explicit grid: targets outside it are reachable only by the global
+    search; sources outside, far away, NaN and infinite take it too."""
+    rng = np.random.default_rng(5)
+    tgt = np.zeros((3001, 4), np.float32)
+    tgt[:, :3] = rng.uniform(-0.5, 1.5, (3001, 3))
+    src = np.zeros((1000, 4), np.float32)
+    src[:, :3] = rng.uniform(-1.0, 2.0, (1000, 3))
+    src[0, :3] = [50.0, -40.0, 7.0]
+    src[1, 0] = np.nan
+    src[2, 1] = np.inf
+    ctx, g = gpu_grid(tgt, L=2, voxel_size=0.1, origin=(0.0, 0.0, 0.0), dims=(10, 10, 10))
+    grid, ref = oracle_grid_for(g, tgt, 2)
+    nn, d2, nf = _gpu_correspond(ctx, src, np.eye(4))
+    rnn, rd2, rfb = oracle.correspond(grid, ref, tgt, src, np.eye(4))
+    assert nf == int(rfb.sum())
+    _assert_nn_equal(nn, d2, rnn, rd2, tgt)
+    assert nn[1] == 0 and np.isnan(d2[1])
+
+
+def test_empty_voxels_everywhere_forces_global_search():
+    """L = 0 and a pose far from the target: every point takes the global
+    search, which must still be exact."""
+    rng = np.random.default_rng(6)
+    tgt = np.zeros((20000, 4), np.float32)
+    tgt[:, :3] = rng.standard_normal((20000, 3))
+    src = np.zeros((4000, 4), np.float32)
+    src[:, :3] = rng.standard_normal((4000, 3))
+    ctx, g = gpu_grid(tgt, L=0, divisions=256)
+    grid, ref = oracle_grid_for(g, tgt, 0)
+    T = np.eye(4)
+    T[:3, 3] = [0.003, -0.002, 0.001]
+    nn, d2, nf = _gpu_correspond(ctx, src, T)
+    rnn, rd2, rfb = oracle.correspond(grid, ref, tgt, src, T)
+    assert nf == int(rfb.sum()) and nf > 3000
+    _assert_nn_equal(nn, d2, rnn, rd2, tgt)
+
+
+def test_nn_ties_go_to_smaller_index():
+    tgt = np.zeros((64, 4), np.float32)
+    tgt[:32, 0] = 1.0          # 32 copies of the same point ...
+    tgt[32:, 0] = -1.0         # ... and 32 mirror images, all at distance 1 from 0
+    src = np.zeros((40, 4), np.float32)
+    for L, origin, dims in ((10, (-1.0, -1.0, -1.0), (3, 3, 3)), (0, (5.0, 5.0, 5.0), (2, 2, 2))):
+        ctx, g = gpu_grid(tgt, L=L, voxel_size=1.0, origin=origin, dims=dims)
+        nn, d2, nf = _gpu_correspond(ctx, src, np.eye(4))
+        grid, ref = oracle_grid_for(g, tgt, L)
+        rnn, rd2, rfb = oracle.correspond(grid, ref, tgt, src, np.eye(4))
+        assert np.array_equal(nn, rnn)
