@@ -165,7 +165,7 @@ class _DevArray:
     """__cuda_array_interface__ view of context-owned device memory."""
 
     def __init__(self, ptr: int, shape, typestr: str):
-        self.__cuda_array_interface__ = {"data": (ptr, True), "shape": tuple(shape), "typestr": typestr,
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": tuple(shape), "typestr": typestr,
                                          "version": 3, "strides": None}
 
 
