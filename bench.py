@@ -160,25 +160,27 @@ def algorithmic_bytes(kernel: str, w: dict) -> float:
         return 16 * N + 4 * N + 8 * occ
     if kernel == "scan":           # counts in, offsets + occupancy bits out
         return 4 * V + 4 * (V + 1) + V / 8
-    if kernel == "scatter":        # keys, points, offsets in; ids + csr points out; count RMW
-        return 4 * N + 16 * N + 4 * N + 4 * N + 16 * N + 8 * occ
-    if kernel == "bricks":         # occupancy bits in
-        return V / 8
+    if kernel == "scatter":        # keys, points, offsets in; ids, voxel- and brick-ordered points out; RMW
+        return 4 * N + 16 * N + 4 * N + 4 * N + 16 * N + 16 * N + 8 * occ
+    if kernel == "brick_scan":     # brick counts in, brick offsets + list + ranges out
+        return 4 * w["bricks"] + 4 * (w["bricks"] + 1) + 12 * w["nonempty_bricks"]
+    if kernel == "brick_boxes":    # brick-ordered points in, boxes out
+        return 16 * N + 32 * w["nonempty_bricks"]
     if kernel == "dilate":         # occupancy bits in, root + ring out
         return V / 8 + 5 * V
     if kernel == "correspond":     # per query: point, root, offset pair, nn+d2; candidates 16 B each
         return 36 * w["queries"] + 16 * w["local_cand"] + 4 * w["fallbacks"]
     if kernel == "fallback":       # per fallback: point + list entry + result; candidates 16 B each
         return 28 * w["fallbacks"] + 16 * w["global_cand"]
-    if kernel == "reduce":         # per point: source point, nn, gathered target point
+    if kernel == "reduce_solve":   # per point: source point, nn, gathered target point
         return 36 * M
     return 0.0
 
 
 def _kernel_sha(kernel: str) -> str:
     src = {"histogram": "vicp_grid.cu", "scan": "vicp_grid.cu", "scatter": "vicp_grid.cu",
-           "bricks": "vicp_grid.cu", "dilate": "vicp_dilate.cu", "correspond": "vicp_nns.cu",
-           "fallback": "vicp_nns.cu", "reduce": "vicp_solve.cu", "solve": "vicp_solve.cu"}.get(kernel)
+           "brick_scan": "vicp_grid.cu", "brick_boxes": "vicp_grid.cu", "dilate": "vicp_dilate.cu",
+           "correspond": "vicp_nns.cu", "fallback": "vicp_nns.cu", "reduce_solve": "vicp_solve.cu"}.get(kernel)
     if not src:
         return ""
     h = hashlib.sha256()
@@ -276,7 +278,8 @@ def run_ours(args, rank, ws, local):
     pstats = ctx.read_stats(reset=True)
     mem = ctx.memory_report()
     kernels = {}
-    w = dict(V=V, N=N, M=M, occupied=mem["occupied_voxels"])
+    nbt = int(math.ceil(view.dims[0] / 8) * math.ceil(view.dims[1] / 8) * math.ceil(view.dims[2] / 8))
+    w = dict(V=V, N=N, M=M, occupied=mem["occupied_voxels"], bricks=nbt, nonempty_bricks=mem["nonempty_bricks"])
     per_launch_w = dict(w)
     per_launch_w.update(queries=pstats["queries"] / prof_steps, fallbacks=pstats["fallbacks"] / prof_steps,
                         local_cand=pstats["local_candidates"] / prof_steps,

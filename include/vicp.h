@@ -126,6 +126,8 @@ typedef struct vicp_memory {
     uint64_t paper_static_layout_bytes; /* V * 65536: a 64 KB block per voxel (Sec. 2.2) */
     uint32_t max_voxel_count;        /* C_max */
     uint32_t occupied_voxels;
+    uint32_t nonempty_bricks;        /* 8x8x8-voxel bricks holding a point (global-search index) */
+    uint32_t reserved;
 } vicp_memory;
 
 /* Work counters of the searches since the last reset. */

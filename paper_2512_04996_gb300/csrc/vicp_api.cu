@@ -33,6 +33,7 @@ struct vicp_ctx {
     bool custom_alloc = false;
     cudaStream_t stream = nullptr;
     int device = 0;
+    int sms = 152;
     std::string last_error;
     uint64_t cur_bytes = 0, peak_bytes = 0;
 
@@ -45,10 +46,13 @@ struct vicp_ctx {
     const float4 *target = nullptr;   // caller's target of the last build (global search)
 
     // V-sized
-    Buf counts, off, root, ring, occ, desc, brick_list, brick_box;
-    long long cap_V = -1, cap_bricks = -1;
+    Buf counts, off, root, ring, occ, desc;
+    long long cap_V = -1;
+    // brick level (V / 512)
+    Buf bcounts, boff, brick_list, brick_range, brick_box;
+    long long cap_bricks = -1;
     // N-sized
-    Buf keys, ids, csr, outside;
+    Buf keys, ids, csr, bpts, outside;
     long long cap_N = -1;
     // M-sized
     Buf nn, d2, fb_list;
@@ -194,7 +198,11 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         c->cap_V = V;
     }
     if (n_bricks > c->cap_bricks) {
+        TRY(buf_alloc(c, c->bcounts, (size_t)n_bricks * 4, "brick counts"));
+        TRY(buf_zero(c, c->bcounts, "zero brick counts"));   // kept at zero between builds
+        TRY(buf_alloc(c, c->boff, (size_t)(n_bricks + 1) * 4, "brick offsets"));
         TRY(buf_alloc(c, c->brick_list, (size_t)n_bricks * 4, "brick list"));
+        TRY(buf_alloc(c, c->brick_range, (size_t)n_bricks * 8, "brick ranges"));
         TRY(buf_alloc(c, c->brick_box, (size_t)n_bricks * 32, "brick boxes"));
         c->cap_bricks = n_bricks;
     }
@@ -207,6 +215,7 @@ vicp_status ensure_point_buffers(vicp_ctx *c, long long n)
         TRY(buf_alloc(c, c->keys, (size_t)n * 4, "keys"));
         TRY(buf_alloc(c, c->ids, (size_t)n * 4, "ids"));
         TRY(buf_alloc(c, c->csr, (size_t)n * 16, "csr points"));
+        TRY(buf_alloc(c, c->bpts, (size_t)n * 16, "brick points"));
         TRY(buf_alloc(c, c->outside, (size_t)n * 4, "outside list"));
         c->cap_N = n;
     }
@@ -366,11 +375,9 @@ vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, i
                                  honor_stop, c->stream);
     }));
     TRY(launch(c, K_FALLBACK, [&] {
-        return launch_fallback(src, pose, g, (const unsigned *)c->occ.p, (const unsigned *)c->off.p,
-                               (const float4 *)c->csr.p, c->n_target, (const int *)c->brick_list.p,
-                               (const float4 *)c->brick_box.p, c->target, c->n_target,
-                               (const int *)c->outside.p, (const int *)c->fb_list.p, d, nn, d2, m, honor_stop,
-                               c->stream);
+        return launch_fallback(src, pose, (const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
+                               (const float4 *)c->brick_box.p, c->target, c->n_target, (const int *)c->outside.p,
+                               (const int *)c->fb_list.p, d, nn, d2, m, honor_stop, c->stream);
     }));
     return VICP_OK;
 }
@@ -381,14 +388,10 @@ vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double
     int *nn = (int *)c->nn.p;
     TRY(run_nns(c, src, m, pose, nn, (float *)c->d2.p, honor_stop));
     const double3 ctr = grid_center(c->geom);
-    const int nparts = reduce_blocks(m);
-    TRY(launch(c, K_REDUCE, [&] {
-        return launch_reduce(src, m, pose, c->target, c->n_target, nn, ctr, (double *)c->partials.p, ctl_of(c),
-                             honor_stop, c->stream);
-    }));
-    TRY(launch(c, K_SOLVE, [&] {
-        return launch_solve((const double *)c->partials.p, nparts, m, ctr, pose, rmse, ctl_of(c), honor_stop,
-                            c->params.rmse_eps, c->stream);
+    const int nparts = reduce_blocks(m, c->sms);
+    TRY(launch(c, K_REDUCE_SOLVE, [&] {
+        return launch_reduce_solve(src, m, pose, c->target, c->n_target, nn, ctr, (double *)c->partials.p, nparts,
+                                   rmse, ctl_of(c), honor_stop, c->params.rmse_eps, c->stream);
     }));
     return VICP_OK;
 }
@@ -410,19 +413,25 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     DevCtl *d = ctl_of(c);
     const int skip = (c->params.flags & VICP_FLAG_TEST_SCAN_TIMEOUT) ? 0 : -1;
     TRY(launch(c, K_HISTOGRAM, [&] {
-        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, d, c->stream);
+        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, d,
+                                c->stream);
     }));
     TRY(launch(c, K_SCAN, [&] {
         return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, (unsigned *)c->occ.p,
                            (unsigned long long *)c->desc.p, d, skip, c->stream);
     }));
-    TRY(launch(c, K_SCATTER, [&] {
-        return launch_scatter(tgt, (const int *)c->keys.p, n, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
-                              (int *)c->ids.p, (float4 *)c->csr.p, (int *)c->outside.p, d, c->stream);
+    TRY(launch(c, K_BRICK_SCAN, [&] {
+        return launch_brick_scan((const unsigned *)c->bcounts.p, g, (unsigned *)c->boff.p, (int *)c->brick_list.p,
+                                 (uint2 *)c->brick_range.p, d, c->stream);
     }));
-    TRY(launch(c, K_BRICKS, [&] {
-        return launch_bricks((const unsigned *)c->occ.p, g, (int *)c->brick_list.p, (float4 *)c->brick_box.p, d,
-                             c->stream);
+    TRY(launch(c, K_SCATTER, [&] {
+        return launch_scatter(tgt, (const int *)c->keys.p, n, g, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
+                              (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (int *)c->ids.p,
+                              (float4 *)c->csr.p, (float4 *)c->bpts.p, (int *)c->outside.p, d, c->stream);
+    }));
+    TRY(launch(c, K_BRICK_BOXES, [&] {
+        return launch_brick_boxes((const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
+                                  (float4 *)c->brick_box.p, d, g, c->stream);
     }));
     c->built = true;
     c->dilated_L = -1;
@@ -439,8 +448,8 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     if (L > DILATE_MAX_L)
         return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
     TRY(launch(c, K_DILATE, [&] {
-        return launch_dilate((const unsigned *)c->occ.p, c->geom, L, (int *)c->root.p, (unsigned char *)c->ring.p,
-                             c->stream);
+        return launch_dilate((const unsigned *)c->occ.p, (const unsigned *)c->boff.p, c->geom, L, (int *)c->root.p,
+                             (unsigned char *)c->ring.p, c->stream);
     }));
     c->dilated_L = L;
     return VICP_OK;
@@ -543,6 +552,10 @@ vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_al
     }
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1) {
+        cudaGetLastError();
+        c->sms = 152;
+    }
     s = buf_alloc(c, c->ctl, sizeof(DevCtl), "control block");
     if (s == VICP_OK)
         s = buf_zero(c, c->ctl, "zero control block");
@@ -567,9 +580,11 @@ void vicp_destroy(vicp_ctx *c)
     if (!c)
         return;
     cudaStreamSynchronize(c->stream);
-    Buf *all[] = {&c->counts, &c->off,     &c->root,     &c->ring,    &c->occ,  &c->desc, &c->brick_list,
-                  &c->brick_box, &c->keys, &c->ids,      &c->csr,     &c->outside, &c->nn, &c->d2,
-                  &c->fb_list, &c->partials, &c->pose,   &c->rmse,    &c->ctl,  &c->bbox, &c->hsrc, &c->htgt};
+    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc,
+                  &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->keys,
+                  &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
+                  &c->fb_list, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
+                  &c->hsrc,    &c->htgt};
     for (Buf *b : all)
         buf_free(c, *b);
     for (auto &t : c->pending) {
@@ -629,11 +644,10 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
         if (e != cudaSuccess)
             return cuda_fail(c, e, "fallback count copy");
         TRY(launch(c, K_FALLBACK, [&] {
-            return launch_fallback(src, pose_dev, c->geom, (const unsigned *)c->occ.p, (const unsigned *)c->off.p,
-                                   (const float4 *)c->csr.p, c->n_target, (const int *)c->brick_list.p,
+            return launch_fallback(src, pose_dev, (const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
                                    (const float4 *)c->brick_box.p, c->target, c->n_target,
-                                   (const int *)c->outside.p, (const int *)c->fb_list.p, d, nn_out, d2_out,
-                                   n_src, 0, c->stream);
+                                   (const int *)c->outside.p, (const int *)c->fb_list.p, d, nn_out, d2_out, n_src,
+                                   0, c->stream);
         }));
         return VICP_OK;
     }
@@ -745,7 +759,10 @@ vicp_status vicp_memory_report(vicp_ctx *c, vicp_memory *out)
     TRY(launch(c, K_MAXCOUNT, [&] { return launch_maxcount((const unsigned *)c->off.p, g, d, c->stream); }));
     unsigned mc[2] = {0, 0};
     uint32_t stored = 0;
+    int32_t nbricks = 0;
     e = cudaMemcpyAsync(mc, &d->max_count, sizeof mc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nbricks, &d->n_bricks, sizeof nbricks, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&stored, (const unsigned *)c->off.p + g.V, 4, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess)
@@ -756,6 +773,7 @@ vicp_status vicp_memory_report(vicp_ctx *c, vicp_memory *out)
     out->csr_store_bytes = (V + 1) * 4 + (uint64_t)stored * 4 + V * 4 + V;
     out->max_voxel_count = mc[0];
     out->occupied_voxels = mc[1];
+    out->nonempty_bricks = (uint32_t)nbricks;
     out->fixed_capacity_bytes = V * (uint64_t)mc[0] * 4;
     out->paper_static_layout_bytes = V * 65536ull;
     return st;
@@ -828,8 +846,9 @@ const char *vicp_last_error(const vicp_ctx *c) { return c ? c->last_error.c_str(
 namespace vicp {
 const char *kernel_name(int k)
 {
-    static const char *names[K_COUNT] = {"bbox",     "histogram", "scan",     "scatter", "bricks",  "dilate",
-                                         "correspond", "fallback", "reduce",  "solve",   "maxcount"};
+    static const char *names[K_COUNT] = {"bbox",       "histogram", "scan",     "brick_scan",   "scatter",
+                                         "brick_boxes", "dilate",   "correspond", "fallback", "reduce_solve",
+                                         "maxcount"};
     return (k >= 0 && k < K_COUNT) ? names[k] : "?";
 }
 }  // namespace vicp

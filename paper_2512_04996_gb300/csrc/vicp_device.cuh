@@ -41,7 +41,7 @@ struct DevCtl {
     unsigned err;           // DEVERR_* bits; cleared by the host
     unsigned max_count;     // memory report: largest voxel count
     unsigned occupied;      // memory report: occupied voxels
-    int pad0;
+    unsigned red_done;      // reduction: finished blocks (the last one solves and resets it)
     // Work counters (added by the search kernels, read and cleared by the host).
     unsigned long long stat_queries;       // source points searched
     unsigned long long stat_fallbacks;     // of which took the global search
@@ -89,19 +89,37 @@ __device__ __forceinline__ float3 transform_pt(const PoseF &P, float4 p)
     return make_float3(s[0], s[1], s[2]);
 }
 
-// Quantize + Concat (Alg. 1/2/4): scaled coordinate s = (p - o) * inv_h per
-// axis; outside when NaN, < 0 or >= dims.
-__device__ __forceinline__ int voxel_key(const GridGeom &g, float x, float y, float z)
+// Quantize (Alg. 1/2/4): scaled coordinate s = (p - o) * inv_h per axis,
+// each operation rounded once; the point is outside when a scaled coordinate
+// is NaN, < 0 or >= dims.  Returns false outside.
+__device__ __forceinline__ bool voxel_coords(const GridGeom &g, float x, float y, float z, int &ix, int &iy, int &iz)
 {
     const float sx = __fmul_rn(__fsub_rn(x, g.ox), g.inv_h);
     const float sy = __fmul_rn(__fsub_rn(y, g.oy), g.inv_h);
     const float sz = __fmul_rn(__fsub_rn(z, g.oz), g.inv_h);
     if (!(sx >= 0.0f) || !(sy >= 0.0f) || !(sz >= 0.0f))
-        return -1;
+        return false;
     if (sx >= __int2float_rn(g.nx) || sy >= __int2float_rn(g.ny) || sz >= __int2float_rn(g.nz))
+        return false;
+    ix = (int)floorf(sx);
+    iy = (int)floorf(sy);
+    iz = (int)floorf(sz);
+    return true;
+}
+
+// Concat: key = x + nx*(y + ny*z), or -1 outside the grid.
+__device__ __forceinline__ int voxel_key(const GridGeom &g, float x, float y, float z)
+{
+    int ix, iy, iz;
+    if (!voxel_coords(g, x, y, z, ix, iy, iz))
         return -1;
-    const int ix = (int)floorf(sx), iy = (int)floorf(sy), iz = (int)floorf(sz);
     return ix + g.nx * (iy + g.ny * iz);
+}
+
+// Brick of a voxel (8x8x8 voxels per brick, x fastest).
+__device__ __forceinline__ int brick_key(const GridGeom &g, int ix, int iy, int iz)
+{
+    return (ix / BRICK) + g.bx * ((iy / BRICK) + g.by * (iz / BRICK));
 }
 
 // Squared distance ((dx*dx + dy*dy) + dz*dz), each operation rounded once.

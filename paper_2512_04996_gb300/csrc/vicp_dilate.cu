@@ -30,8 +30,9 @@
 // tile grown by L in y and z (three 32-bit words per row cover x in
 // [x0-32, x0+64)), runs passes X and Y for eight z-planes at a time into
 // shared memory, then pass Z, and writes root and ring with coalesced
-// stores.  A tile whose grown neighbourhood holds no occupied voxel writes
-// "unlabelled" straight away.  L <= 31.
+// stores.  A tile whose grown neighbourhood touches no occupied 8x8x8 brick
+// (checked on the brick offsets before any staging) writes "unlabelled"
+// straight away.  L <= 31.
 #include "vicp_launch.h"
 
 namespace vicp {
@@ -61,7 +62,8 @@ size_t dilate_smem_bytes(int L)
     return sizeof(unsigned) * (HZ * HY * 3 + ZB * HY * TX + HZ * TY * TX);
 }
 
-__global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ, GridGeom g, int L,
+__global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ,
+                                                    const unsigned *__restrict__ boff, GridGeom g, int L,
                                                     int tiles_x, int tiles_y, int *__restrict__ root,
                                                     unsigned char *__restrict__ ring)
 {
@@ -78,9 +80,22 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
     const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // 1. occupancy windows of the grown tile
+    // 0. coarse test: does any 8x8x8 brick touching the grown tile hold a point?
     int any = 0;
-    for (int idx = tid; idx < HZ * HY * 3; idx += THREADS) {
+    {
+        const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
+        const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
+        const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
+        const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nbz = bz1 - bz0 + 1;
+        for (int k = tid; k < nbx * nby * nbz; k += THREADS) {
+            const int b = (bx0 + k % nbx) + g.bx * ((by0 + (k / nbx) % nby) + g.by * (bz0 + k / (nbx * nby)));
+            any |= __ldg(boff + b + 1) > __ldg(boff + b);
+        }
+    }
+    any = __syncthreads_or(any);
+
+    // 1. occupancy windows of the grown tile
+    for (int idx = tid; any && idx < HZ * HY * 3; idx += THREADS) {
         const int k = idx % 3, row = idx / 3;
         const int y = y0 - L + row % HY, z = z0 - L + row / HY;
         unsigned w = 0u;
@@ -93,9 +108,8 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
             }
         }
         s_bits[idx] = w;
-        any |= (w != 0u);
     }
-    any = __syncthreads_or(any);
+    __syncthreads();
 
     unsigned out[TZ];
     if (!any) {
@@ -204,8 +218,8 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
     }
 }
 
-cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, int *root, unsigned char *ring,
-                          cudaStream_t st)
+cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *root,
+                          unsigned char *ring, cudaStream_t st)
 {
     const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
     const long long tiles = (long long)tiles_x * tiles_y * tiles_z;
@@ -215,7 +229,7 @@ cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, int *ro
         if (e != cudaSuccess)
             return e;
     }
-    k_dilate<<<(unsigned)tiles, THREADS, smem, st>>>(occ, g, L, tiles_x, tiles_y, root, ring);
+    k_dilate<<<(unsigned)tiles, THREADS, smem, st>>>(occ, boff, g, L, tiles_x, tiles_y, root, ring);
     return cudaGetLastError();
 }
 

@@ -62,35 +62,129 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // ---------------------------------------------------------------------------
 // VOH: one thread per target point; lanes of a warp holding the same voxel
 // key are grouped with __match_any_sync and their leader adds the group size
-// (warp-aggregated atomics).  Block 0 also resets the scan's ticket, bumps
-// its descriptor epoch and clears the outside/brick counters for this build.
+// (warp-aggregated atomics).  The same is done per 8x8x8 brick for the brick
+// level used by the global search.  Block 0 also resets the scan's ticket,
+// bumps its descriptor epoch and clears the outside counter for this build.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
-                                                   DevCtl *__restrict__ ctl)
+                                                   unsigned *__restrict__ bcounts, DevCtl *__restrict__ ctl)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->scan_ticket = 0u;
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
-        ctl->n_bricks = 0;
     }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int key = -2;   // lanes past the end match only each other and add nothing
+    int key = -2, bk = -2;   // lanes past the end match only each other and add nothing
     if (j < n) {
         const float4 q = __ldg(pts + j);
-        key = voxel_key(g, q.x, q.y, q.z);
+        int ix, iy, iz;
+        if (voxel_coords(g, q.x, q.y, q.z, ix, iy, iz)) {
+            key = ix + g.nx * (iy + g.ny * iz);
+            bk = brick_key(g, ix, iy, iz);
+        } else {
+            key = bk = -1;
+        }
         keys[j] = key;
     }
+    const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(FULL_MASK, key);
-    if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+    if (key >= 0 && lane == __ffs(peers) - 1)
         atomicAdd(counts + key, (unsigned)__popc(peers));
+    const unsigned bpeers = __match_any_sync(FULL_MASK, bk);
+    if (bk >= 0 && lane == __ffs(bpeers) - 1)
+        atomicAdd(bcounts + bk, (unsigned)__popc(bpeers));
 }
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             DevCtl *ctl, cudaStream_t st)
+                             unsigned *bcounts, DevCtl *ctl, cudaStream_t st)
 {
-    k_histogram<<<(n + 255) / 256, 256, 0, st>>>(pts, n, g, keys, counts, ctl);
+    k_histogram<<<(n + 255) / 256, 256, 0, st>>>(pts, n, g, keys, counts, bcounts, ctl);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Brick offsets: one CTA scans the per-brick counts (few: V / 512) into
+// brick offsets, and lists the non-empty bricks in ascending order with their
+// point ranges.  The count and the non-empty flag are scanned together as one
+// 64-bit value (flag count in the high half).
+// ---------------------------------------------------------------------------
+constexpr int BS_THREADS = 1024;
+constexpr int BS_ITEMS = 4;
+
+__global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__restrict__ bcounts, int nbt,
+                                                           unsigned *__restrict__ boff, int *__restrict__ list,
+                                                           uint2 *__restrict__ range, DevCtl *__restrict__ ctl)
+{
+    __shared__ unsigned long long s_w[BS_THREADS / 32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0)
+        s_carry = 0ull;
+    __syncthreads();
+    for (int base = 0; base < nbt; base += BS_THREADS * BS_ITEMS) {
+        unsigned c[BS_ITEMS];
+        unsigned long long sum = 0ull;
+#pragma unroll
+        for (int i = 0; i < BS_ITEMS; ++i) {
+            const int idx = base + tid * BS_ITEMS + i;
+            c[i] = idx < nbt ? bcounts[idx] : 0u;
+            sum += (unsigned long long)c[i] | ((unsigned long long)(c[i] != 0u) << 32);
+        }
+        unsigned long long incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, d);
+            if (lane >= d)
+                incl += y;
+        }
+        if (lane == 31)
+            s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long w = s_w[lane];
+            unsigned long long wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(FULL_MASK, wi, d);
+                if (lane >= d)
+                    wi += y;
+            }
+            s_w[lane] = wi - w;
+        }
+        __syncthreads();
+        unsigned long long run = s_carry + s_w[warp] + (incl - sum);
+#pragma unroll
+        for (int i = 0; i < BS_ITEMS; ++i) {
+            const int idx = base + tid * BS_ITEMS + i;
+            if (idx < nbt) {
+                const unsigned start = (unsigned)run;
+                boff[idx] = start;
+                if (c[i]) {
+                    const int slot = (int)(run >> 32);
+                    list[slot] = idx;
+                    range[slot] = make_uint2(start, start + c[i]);
+                }
+            }
+            run += (unsigned long long)c[i] | ((unsigned long long)(c[i] != 0u) << 32);
+        }
+        __syncthreads();
+        if (tid == BS_THREADS - 1)
+            s_carry = run;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        boff[nbt] = (unsigned)s_carry;
+        ctl->n_bricks = (int)(s_carry >> 32);
+    }
+}
+
+cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
+                              DevCtl *ctl, cudaStream_t st)
+{
+    const int nbt = g.bx * g.by * g.bz;
+    k_brick_scan<<<1, BS_THREADS, 0, st>>>(bcounts, nbt, boff, list, range, ctl);
     return cudaGetLastError();
 }
 
@@ -286,100 +380,125 @@ cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off
 // count), so the counts return to zero for the next build.  Slots fill from
 // the end of each segment; the order inside a segment is unspecified.  The
 // scatter also writes each point's coordinates and index next to its slot
-// (csr), and lists target points outside an explicit grid.
+// (csr), does the same per brick (bpts, brick-ordered), and lists target
+// points outside an explicit grid.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts, const int *__restrict__ keys, int n,
-                                                 const unsigned *__restrict__ off, unsigned *__restrict__ counts,
-                                                 int *__restrict__ ids, float4 *__restrict__ csr,
+                                                 GridGeom g, const unsigned *__restrict__ off,
+                                                 unsigned *__restrict__ counts, const unsigned *__restrict__ boff,
+                                                 unsigned *__restrict__ bcounts, int *__restrict__ ids,
+                                                 float4 *__restrict__ csr, float4 *__restrict__ bpts,
                                                  int *__restrict__ outside, DevCtl *__restrict__ ctl)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int key = (j < n) ? __ldg(keys + j) : -2;
-    const unsigned peers = __match_any_sync(FULL_MASK, key);
-    const int leader = __ffs(peers) - 1;
-    const unsigned rank = __popc(peers & lanemask_lt());
-    const unsigned cnt = __popc(peers);
-    unsigned old = 0u;
-    if ((int)(threadIdx.x & 31) == leader) {
-        if (key >= 0)
-            old = atomicSub(counts + key, cnt);
-        else if (key == -1)
-            old = (unsigned)atomicAdd(&ctl->n_outside, (int)cnt);
-    }
-    old = __shfl_sync(FULL_MASK, old, leader);
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    int bk = key;
     if (key >= 0) {
-        const unsigned pos = __ldg(off + key) + old - 1u - rank;
-        if (pos < (unsigned)n) {
-            const float4 q = __ldg(pts + j);
-            ids[pos] = j;
-            csr[pos] = make_float4(q.x, q.y, q.z, __int_as_float(j));
-        } else {
-            atomicOr(&ctl->err, DEVERR_BOUNDS);
+        q = __ldg(pts + j);
+        int ix, iy, iz;
+        // inside, so the same quantisation as the histogram's gives the brick
+        bk = voxel_coords(g, q.x, q.y, q.z, ix, iy, iz) ? brick_key(g, ix, iy, iz) : -1;
+        q.w = __int_as_float(j);
+    }
+    // voxel segment
+    {
+        const unsigned peers = __match_any_sync(FULL_MASK, key);
+        const int leader = __ffs(peers) - 1;
+        const unsigned rank = __popc(peers & lanemask_lt());
+        const unsigned cnt = __popc(peers);
+        unsigned old = 0u;
+        if (lane == leader) {
+            if (key >= 0)
+                old = atomicSub(counts + key, cnt);
+            else if (key == -1)
+                old = (unsigned)atomicAdd(&ctl->n_outside, (int)cnt);
         }
-    } else if (key == -1) {
-        outside[old + rank] = j;
+        old = __shfl_sync(FULL_MASK, old, leader);
+        if (key >= 0) {
+            const unsigned pos = __ldg(off + key) + old - 1u - rank;
+            if (pos < (unsigned)n) {
+                ids[pos] = j;
+                csr[pos] = q;
+            } else {
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+            }
+        } else if (key == -1) {
+            outside[old + rank] = j;
+        }
+    }
+    // brick segment
+    {
+        const unsigned peers = __match_any_sync(FULL_MASK, bk);
+        const int leader = __ffs(peers) - 1;
+        const unsigned rank = __popc(peers & lanemask_lt());
+        unsigned old = 0u;
+        if (lane == leader && bk >= 0)
+            old = atomicSub(bcounts + bk, (unsigned)__popc(peers));
+        old = __shfl_sync(FULL_MASK, old, leader);
+        if (bk >= 0) {
+            const unsigned pos = __ldg(boff + bk) + old - 1u - rank;
+            if (pos < (unsigned)n)
+                bpts[pos] = q;
+            else
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+        }
     }
 }
 
-cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const unsigned *off, unsigned *counts,
-                           int *ids, float4 *csr, int *outside, DevCtl *ctl, cudaStream_t st)
+cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
+                           unsigned *counts, const unsigned *boff, unsigned *bcounts, int *ids, float4 *csr,
+                           float4 *bpts, int *outside, DevCtl *ctl, cudaStream_t st)
 {
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(pts, keys, n, off, counts, ids, csr, outside, ctl);
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(pts, keys, n, g, off, counts, boff, bcounts, ids, csr, bpts, outside,
+                                               ctl);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Brick list for the exact global search: one warp per 8x8x8 brick reads the
-// brick's 64 occupancy rows; a non-empty brick is appended with its box in
-// float, widened outward so that it contains every point stored in the brick
-// (the widening covers the rounding of the quantisation).
+// Exact bounding box of each non-empty brick's points (a warp per brick):
+// every point of the brick lies inside it as float values, which is what
+// the global search's lower bound needs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bricks(const unsigned *__restrict__ occ, GridGeom g,
-                                                int *__restrict__ list, float4 *__restrict__ box,
-                                                DevCtl *__restrict__ ctl, long long n_bricks)
+__global__ void __launch_bounds__(256) k_brick_boxes(const float4 *__restrict__ bpts, const uint2 *__restrict__ range,
+                                                     float4 *__restrict__ box, const DevCtl *__restrict__ ctl)
 {
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nb = ctl->n_bricks;
     const int lane = threadIdx.x & 31;
-    if (wid >= n_bricks)
-        return;   // whole warp
-    const int bxi = (int)(wid % g.bx);
-    const int byi = (int)((wid / g.bx) % g.by);
-    const int bzi = (int)(wid / ((long long)g.bx * g.by));
-    const int x0 = bxi * BRICK, y0 = byi * BRICK, z0 = bzi * BRICK;
-    const int xw = min(BRICK, g.nx - x0);
-    bool any = false;
-#pragma unroll
-    for (int r = lane; r < BRICK * BRICK; r += 32) {
-        const int y = y0 + (r % BRICK), z = z0 + (r / BRICK);
-        if (y < g.ny && z < g.nz) {
-            const long long b = (long long)g.nx * (y + (long long)g.ny * z) + x0;
-            any |= extract_bits(occ, b, xw) != 0u;
+    const int warps = gridDim.x * (blockDim.x / 32);
+    for (int k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); k < nb; k += warps) {
+        const uint2 r = __ldg(range + k);
+        float lo[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+        float hi[3] = {-lo[0], -lo[1], -lo[2]};
+        for (unsigned i = r.x + lane; i < r.y; i += 32) {
+            const float4 q = __ldg(bpts + i);
+            lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
+            lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
+            lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
         }
-    }
-    if (__any_sync(FULL_MASK, any) && lane == 0) {
-        const int slot = atomicAdd(&ctl->n_bricks, 1);
-        list[slot] = (int)wid;
-        const int x1 = min(x0 + BRICK, g.nx), y1 = min(y0 + BRICK, g.ny), z1 = min(z0 + BRICK, g.nz);
-        // Exact bounds o + i*h in double, widened by 2^-20 of the grid's reach.
-        const double h = (double)g.h;
-        const double reach = fabs((double)g.ox) + fabs((double)g.oy) + fabs((double)g.oz) +
-                             h * (double)(g.nx + g.ny + g.nz);
-        const double m = reach * 0x1p-20;
-        box[2 * slot + 0] = make_float4(__double2float_rd((double)g.ox + x0 * h - m),
-                                        __double2float_rd((double)g.oy + y0 * h - m),
-                                        __double2float_rd((double)g.oz + z0 * h - m), 0.0f);
-        box[2 * slot + 1] = make_float4(__double2float_ru((double)g.ox + x1 * h + m),
-                                        __double2float_ru((double)g.oy + y1 * h + m),
-                                        __double2float_ru((double)g.oz + z1 * h + m), 0.0f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(FULL_MASK, lo[a], o));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(FULL_MASK, hi[a], o));
+            }
+        if (lane == 0) {
+            box[2 * k] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+            box[2 * k + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+        }
     }
 }
 
-cudaError_t launch_bricks(const unsigned *occ, const GridGeom &g, int *brick_list, float4 *brick_box,
-                          DevCtl *ctl, cudaStream_t st)
+cudaError_t launch_brick_boxes(const float4 *bpts, const uint2 *range, float4 *box, const DevCtl *ctl,
+                               const GridGeom &g, cudaStream_t st)
 {
-    const long long nb = (long long)g.bx * g.by * g.bz;
-    const long long blocks = (nb * 32 + 255) / 256;
-    k_bricks<<<(unsigned)blocks, 256, 0, st>>>(occ, g, brick_list, brick_box, ctl, nb);
+    const int nbt = g.bx * g.by * g.bz;
+    int blocks = (nbt + 7) / 8;
+    if (blocks > 152 * 8)
+        blocks = 152 * 8;
+    k_brick_boxes<<<blocks, 256, 0, st>>>(bpts, range, box, ctl);
     return cudaGetLastError();
 }
 

@@ -12,12 +12,12 @@ enum KernelId {
     K_HISTOGRAM,
     K_SCAN,
     K_SCATTER,
-    K_BRICKS,
+    K_BRICK_SCAN,
+    K_BRICK_BOXES,
     K_DILATE,
     K_CORRESPOND,
     K_FALLBACK,
-    K_REDUCE,
-    K_SOLVE,
+    K_REDUCE_SOLVE,
     K_MAXCOUNT,
     K_COUNT
 };
@@ -25,7 +25,7 @@ const char *kernel_name(int k);
 
 // Scan tiling (elements per CTA) -- sizes the descriptor array.
 constexpr int SCAN_TILE = 4096;
-// Reduction blocks of one ICP iteration -- sizes the FP64 partial sums.
+// Reduction blocks of one ICP iteration (two per SM) -- sizes the partial sums.
 constexpr int REDUCE_MAX_BLOCKS = 1024;
 constexpr int REDUCE_VALUES = 16;
 // Largest dilation depth L the tiled kernel supports.
@@ -33,33 +33,38 @@ constexpr int DILATE_MAX_L = 31;
 
 inline long long scan_tiles(long long V) { return (V + SCAN_TILE - 1) / SCAN_TILE; }
 inline long long occ_words(long long V) { return (V + 31) / 32 + 2; }   // +2: window reads
-inline int reduce_blocks(int m) { int b = (m + 255) / 256; return b < 1 ? 1 : (b > REDUCE_MAX_BLOCKS ? REDUCE_MAX_BLOCKS : b); }
+inline int reduce_blocks(int m, int sms)
+{
+    const int cap = 2 * sms < REDUCE_MAX_BLOCKS ? 2 * sms : REDUCE_MAX_BLOCKS;
+    const int b = (m + 255) / 256;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
 size_t dilate_smem_bytes(int L);
 
 cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t st);
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             DevCtl *ctl, cudaStream_t st);
+                             unsigned *bcounts, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, unsigned *occ,
                         unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st);
-cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const unsigned *off, unsigned *counts,
-                           int *ids, float4 *csr, int *outside, DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_bricks(const unsigned *occ, const GridGeom &g, int *brick_list, float4 *brick_box,
-                          DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
+                              DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
+                           unsigned *counts, const unsigned *boff, unsigned *bcounts, int *ids, float4 *csr,
+                           float4 *bpts, int *outside, DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_brick_boxes(const float4 *bpts, const uint2 *range, float4 *box, const DevCtl *ctl,
+                               const GridGeom &g, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, int *root, unsigned char *ring,
-                          cudaStream_t st);
+cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *root,
+                          unsigned char *ring, cudaStream_t st);
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);
-cudaError_t launch_fallback(const float4 *src, const double *pose, const GridGeom &g, const unsigned *occ,
-                            const unsigned *off, const float4 *csr, int n_cap, const int *brick_list,
-                            const float4 *brick_box, const float4 *tgt, int n_tgt, const int *outside,
+cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const uint2 *brange,
+                            const float4 *bbox, const float4 *tgt, int n_tgt, const int *outside,
                             const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m, int honor_stop,
                             cudaStream_t st);
-cudaError_t launch_reduce(const float4 *src, int m, const double *pose, const float4 *tgt, int n_tgt,
-                          const int *nn, double3 center, double *partials, DevCtl *ctl, int honor_stop,
-                          cudaStream_t st);
-cudaError_t launch_solve(const double *partials, int nparts, int m, double3 center, double *pose,
-                         double *rmse_out, DevCtl *ctl, int honor_stop, double eps, cudaStream_t st);
+cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
+                                double3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
+                                int honor_stop, double eps, cudaStream_t st);
 
 }  // namespace vicp

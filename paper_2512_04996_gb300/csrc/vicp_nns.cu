@@ -83,17 +83,20 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
 // Global search ("Globalsearch" of Alg. 4): the exact nearest target point,
 // found without scanning every point.
 //
-// Each non-empty 8x8x8 brick has a float box that contains all its points.
-// For a query s, the box bound lb = ((ex*ex + ey*ey) + ez*ez), with e the
-// rounded gap between s and the box on each axis, is never larger than the
-// computed squared distance from s to any point in the box: rounding is
-// monotone, so every operation of the bound is <= the same operation of the
-// true distance formula.  A warp per query (1) finds the brick of smallest
-// bound and scans it, which gives a first best distance D, then (2) scans
-// every other brick whose bound is <= D, and (3) scans the target points
-// that lie outside the grid.  The result is the same (distance, index)
-// minimum as a scan of all target points.  A query with a non-finite
-// coordinate scans all target points.
+// The grid build groups the stored target points per non-empty 8x8x8 brick
+// (contiguous runs of (x, y, z, index)) and records each brick's exact float
+// bounding box.  For a query s, the box bound lb = ((ex*ex + ey*ey) + ez*ez),
+// with e the rounded gap between s and the box on each axis, is never larger
+// than the computed squared distance from s to any point in the box:
+// rounding is monotone, so every operation of the bound is <= the same
+// operation of the distance formula.  A warp per query
+//   (1) finds the brick of smallest bound and scans its points (lanes split
+//       the run), which gives a first best distance D;
+//   (2) tests every other brick's bound against D and scans, together, each
+//       brick whose bound is still <= D, tightening D as it goes;
+//   (3) scans the target points that lie outside the grid.
+// The result is the same (distance, index) minimum as a scan of all target
+// points.  A query with a non-finite coordinate scans all target points.
 // ---------------------------------------------------------------------------
 constexpr int FB_THREADS = 256;
 constexpr int FB_WARPS = FB_THREADS / 32;
@@ -106,48 +109,24 @@ __device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
     return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
 }
 
-// Scan rows row0, row0+rstep, ... (of the brick's 64 rows) and every point of
-// their occupied voxels.
-__device__ __forceinline__ unsigned long long scan_brick_rows(const GridGeom &g, const unsigned *__restrict__ occ,
-                                                              const unsigned *__restrict__ off,
-                                                              const float4 *__restrict__ csr, unsigned n_cap,
-                                                              int brick, float3 s, int row0, int rstep,
-                                                              unsigned long long best, unsigned &examined)
+// All lanes scan the run [r.x, r.y) of brick-ordered points; returns the
+// warp-wide minimum key (every lane gets it).
+__device__ __forceinline__ unsigned long long scan_run(const float4 *__restrict__ bpts, uint2 r, float3 s, int lane,
+                                                       unsigned long long best, unsigned long long &examined)
 {
-    const int bxi = brick % g.bx;
-    const int byi = (brick / g.bx) % g.by;
-    const int bzi = brick / (g.bx * g.by);
-    const int x0 = bxi * BRICK, y0 = byi * BRICK, z0 = bzi * BRICK;
-    const int xw = min(BRICK, g.nx - x0);
-    for (int r = row0; r < BRICK * BRICK; r += rstep) {
-        const int y = y0 + (r % BRICK), z = z0 + (r / BRICK);
-        if (y >= g.ny || z >= g.nz)
-            continue;
-        const long long rowbase = (long long)g.nx * (y + (long long)g.ny * z) + x0;
-        unsigned bits = extract_bits(occ, rowbase, xw);
-        while (bits) {
-            const int xi = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            const long long v = rowbase + xi;
-            const unsigned a = __ldg(off + v);
-            const unsigned b = min(__ldg(off + v + 1), n_cap);
-            examined += b > a ? b - a : 0u;
-            for (unsigned k = a; k < b; ++k) {
-                const float4 q = __ldg(csr + k);
-                best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
-            }
-        }
+    for (unsigned i = r.x + lane; i < r.y; i += 32) {
+        const float4 q = __ldg(bpts + i);
+        best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
     }
-    return best;
+    examined += r.y - r.x;
+    return warp_min_u64(best);
 }
 
 __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restrict__ src,
-                                                         const double *__restrict__ pose, GridGeom g,
-                                                         const unsigned *__restrict__ occ,
-                                                         const unsigned *__restrict__ off,
-                                                         const float4 *__restrict__ csr, int n_cap,
-                                                         const int *__restrict__ brick_list,
-                                                         const float4 *__restrict__ brick_box,
+                                                         const double *__restrict__ pose,
+                                                         const float4 *__restrict__ bpts,
+                                                         const uint2 *__restrict__ brange,
+                                                         const float4 *__restrict__ bbox,
                                                          const float4 *__restrict__ tgt, int n_tgt,
                                                          const int *__restrict__ outside,
                                                          const int *__restrict__ fb_list,
@@ -165,8 +144,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
     const int F = min(*(volatile int *)&ctl->fb_count, m);
     const int nb = *(volatile int *)&ctl->n_bricks;
     const int no = *(volatile int *)&ctl->n_outside;
-    const unsigned cap = (unsigned)n_cap;
-    unsigned examined = 0u;
+    unsigned long long examined = 0ull;   // every lane counts the same; lane 0 reports
 
     for (int qi = blockIdx.x * FB_WARPS + warp; qi < F; qi += gridDim.x * FB_WARPS) {
         const int i = __ldg(fb_list + qi);
@@ -180,34 +158,42 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
         if (!(isfinite(s.x) && isfinite(s.y) && isfinite(s.z))) {
             for (int j = lane; j < n_tgt; j += 32)
                 best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
-            examined += (unsigned)((n_tgt - lane + 31) / 32);
+            examined += (unsigned long long)n_tgt;
         } else {
             if (nb > 0) {
-                // (1) brick of smallest bound (ties: smallest list slot)
+                // (1) brick of smallest bound (ties: smallest slot)
                 unsigned long long lbmin = ~0ull;
                 for (int k = lane; k < nb; k += 32) {
-                    const float lb = box_lb2(s, __ldg(brick_box + 2 * k), __ldg(brick_box + 2 * k + 1));
+                    const float lb = box_lb2(s, __ldg(bbox + 2 * k), __ldg(bbox + 2 * k + 1));
                     lbmin = umin64(lbmin, ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)k);
                 }
                 lbmin = warp_min_u64(lbmin);
                 const int k0 = (int)(unsigned)lbmin;
-                best = scan_brick_rows(g, occ, off, csr, cap, __ldg(brick_list + k0), s, lane, 32, best, examined);
-                best = warp_min_u64(best);
-                // (2) every other brick that could hold a point at distance <= D
-                for (int k = lane; k < nb; k += 32) {
-                    if (k == k0)
-                        continue;
-                    const float lb = box_lb2(s, __ldg(brick_box + 2 * k), __ldg(brick_box + 2 * k + 1));
-                    if (__float_as_uint(lb) <= (unsigned)(best >> 32))
-                        best = scan_brick_rows(g, occ, off, csr, cap, __ldg(brick_list + k), s, 0, 1, best, examined);
+                best = scan_run(bpts, __ldg(brange + k0), s, lane, best, examined);
+                // (2) every other brick whose bound does not exceed the best distance
+                for (int kb = 0; kb < nb; kb += 32) {
+                    const int k = kb + lane;
+                    unsigned lbb = 0xffffffffu;
+                    if (k < nb && k != k0)
+                        lbb = __float_as_uint(box_lb2(s, __ldg(bbox + 2 * k), __ldg(bbox + 2 * k + 1)));
+                    unsigned cand = __ballot_sync(FULL_MASK, lbb <= (unsigned)(best >> 32));
+                    while (cand) {
+                        const int src_lane = __ffs(cand) - 1;
+                        cand &= cand - 1u;
+                        const unsigned lb = __shfl_sync(FULL_MASK, lbb, src_lane);
+                        if (lb > (unsigned)(best >> 32))
+                            continue;   // the bound was overtaken by a closer point
+                        best = scan_run(bpts, __ldg(brange + kb + src_lane), s, lane, best, examined);
+                    }
                 }
             }
             // (3) target points outside the grid
             for (int k = lane; k < no; k += 32) {
                 const int j = __ldg(outside + k);
                 best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
-                ++examined;
             }
+            examined += (unsigned long long)no;
+            best = warp_min_u64(best);
         }
         best = warp_min_u64(best);
         if (lane == 0) {
@@ -215,10 +201,8 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
             d2[i] = __uint_as_float((unsigned)(best >> 32));
         }
     }
-
-    const unsigned long long we = warp_sum_u64(examined);
-    if (lane == 0 && we)
-        atomicAdd(&ctl->stat_global_cand, we);
+    if (lane == 0 && examined)
+        atomicAdd(&ctl->stat_global_cand, examined);
     // The last block to finish clears the fallback counter for the next search.
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -232,14 +216,13 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
     }
 }
 
-cudaError_t launch_fallback(const float4 *src, const double *pose, const GridGeom &g, const unsigned *occ,
-                            const unsigned *off, const float4 *csr, int n_cap, const int *brick_list,
-                            const float4 *brick_box, const float4 *tgt, int n_tgt, const int *outside,
+cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const uint2 *brange,
+                            const float4 *bbox, const float4 *tgt, int n_tgt, const int *outside,
                             const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m, int honor_stop,
                             cudaStream_t st)
 {
-    k_fallback<<<152 * 4, FB_THREADS, 0, st>>>(src, pose, g, occ, off, csr, n_cap, brick_list, brick_box, tgt,
-                                               n_tgt, outside, fb_list, ctl, nn, d2, m, honor_stop);
+    k_fallback<<<152 * 4, FB_THREADS, 0, st>>>(src, pose, bpts, brange, bbox, tgt, n_tgt, outside, fb_list, ctl, nn,
+                                               d2, m, honor_stop);
     return cudaGetLastError();
 }
 

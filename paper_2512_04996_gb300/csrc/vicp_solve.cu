@@ -1,32 +1,150 @@
 // vicp_solve.cu -- rigid update of Eq. 1: deterministic FP64 reduction of the
-// centroids, cross-covariance and residual, and the FP64 solve.
+// centroids, cross-covariance and residual, and the FP64 solve, in one launch.
 #include "vicp_launch.h"
 
 namespace vicp {
 
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double det3(double a, double b, double c, double d, double e, double f, double g, double h,
+                                       double i)
+{
+    return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+// rank(S) < 2: every 2x2 minor negligible against |S|_F^2 (a definition
+// shared with the oracle, not its code).
+__device__ bool rank_below_two(const double S[9])
+{
+    double s2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        s2 += S[k] * S[k];
+    if (s2 == 0.0)
+        return true;
+    double c2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+            const double cf = S[3 * i1 + j1] * S[3 * i2 + j2] - S[3 * i1 + j2] * S[3 * i2 + j1];
+            c2 += cf * cf;
+        }
+    return sqrt(c2) <= 1e-12 * s2;
+}
+
+// Horn's closed form.  With S the 3x3 cross-covariance sum (s - sbar)(q - qbar)^T,
+// the rotation minimising Eq. 1 is the unit quaternion (w, x, y, z) of the
+// largest eigenvalue of the symmetric, traceless 4x4
+//   [ Sxx+Syy+Szz  Syz-Szy      Szx-Sxz      Sxy-Syx     ]
+//   [ Syz-Szy      Sxx-Syy-Szz  Sxy+Syx      Szx+Sxz     ]
+//   [ Szx-Sxz      Sxy+Syx     -Sxx+Syy-Szz  Syz+Szy     ]
+//   [ Sxy-Syx      Szx+Sxz      Syz+Szy     -Sxx-Syy+Szz ].
+// Its characteristic polynomial is l^4 + c2 l^2 + c1 l + c0 with
+// c2 = -2 |S|_F^2, c1 = -8 det S, c0 = det N.  The largest root is found by
+// Newton's method from the upper bound (Ga + Gb) / 2 = E/2 + tr S (Ga, Gb the
+// centred sums of squares, E the centred residual), which lies just right of
+// it; from the right of the largest root of a real-rooted polynomial Newton
+// decreases monotonically onto it.  The eigenvector is a column of the
+// adjugate of N - l I (rank one at a simple eigenvalue); the column of the
+// largest diagonal cofactor is used.  All in FP64.
+__device__ void horn_rotation(const double S[9], double E, double R[9])
+{
+    const double sxx = S[0], sxy = S[1], sxz = S[2], syx = S[3], syy = S[4], syz = S[5], szx = S[6], szy = S[7],
+                 szz = S[8];
+    double N[4][4] = {{sxx + syy + szz, syz - szy, szx - sxz, sxy - syx},
+                      {syz - szy, sxx - syy - szz, sxy + syx, szx + sxz},
+                      {szx - sxz, sxy + syx, -sxx + syy - szz, syz + szy},
+                      {sxy - syx, szx + sxz, syz + szy, -sxx - syy + szz}};
+    double s2 = 0.0;
+    for (int k = 0; k < 9; ++k)
+        s2 += S[k] * S[k];
+    const double c2 = -2.0 * s2;
+    const double c1 = -8.0 * det3(sxx, sxy, sxz, syx, syy, syz, szx, szy, szz);
+    // det N by Laplace expansion along rows 0 and 1
+    const double a01 = N[0][0] * N[1][1] - N[0][1] * N[1][0], a02 = N[0][0] * N[1][2] - N[0][2] * N[1][0];
+    const double a03 = N[0][0] * N[1][3] - N[0][3] * N[1][0], a12 = N[0][1] * N[1][2] - N[0][2] * N[1][1];
+    const double a13 = N[0][1] * N[1][3] - N[0][3] * N[1][1], a23 = N[0][2] * N[1][3] - N[0][3] * N[1][2];
+    const double b01 = N[2][0] * N[3][1] - N[2][1] * N[3][0], b02 = N[2][0] * N[3][2] - N[2][2] * N[3][0];
+    const double b03 = N[2][0] * N[3][3] - N[2][3] * N[3][0], b12 = N[2][1] * N[3][2] - N[2][2] * N[3][1];
+    const double b13 = N[2][1] * N[3][3] - N[2][3] * N[3][1], b23 = N[2][2] * N[3][3] - N[2][3] * N[3][2];
+    const double c0 = a01 * b23 - a02 * b13 + a03 * b12 + a12 * b03 - a13 * b02 + a23 * b01;
+
+    double l = 0.5 * E + (sxx + syy + szz);
+    l += 1e-12 * fabs(l);
+    const double loose = sqrt(3.0 * s2);   // l_max <= sqrt(3/4 tr N^2) = sqrt(3) |S|_F
+    if (!(l > 0.0) || ((l * l + c2) * l + c1) * l + c0 < 0.0 || l > loose)
+        l = loose;
+    for (int it = 0; it < 64; ++it) {
+        const double P = ((l * l + c2) * l + c1) * l + c0;
+        const double dP = (4.0 * l * l + 2.0 * c2) * l + c1;
+        if (!(dP != 0.0))
+            break;
+        const double step = P / dP;
+        l -= step;
+        if (fabs(step) <= 1e-15 * fabs(l))
+            break;
+    }
+    // adjugate of A = N - l I: cofactor C_ij = (-1)^(i+j) M_ij, M the minor
+    // without row i and column j.
+    double A[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+            A[i][j] = N[i][j] - (i == j ? l : 0.0);
+    auto minor = [&](int r, int c) {
+        int rr[3], cc[3];
+        for (int k = 0, t = 0; k < 4; ++k)
+            if (k != r) rr[t++] = k;
+        for (int k = 0, t = 0; k < 4; ++k)
+            if (k != c) cc[t++] = k;
+        return det3(A[rr[0]][cc[0]], A[rr[0]][cc[1]], A[rr[0]][cc[2]], A[rr[1]][cc[0]], A[rr[1]][cc[1]],
+                    A[rr[1]][cc[2]], A[rr[2]][cc[0]], A[rr[2]][cc[1]], A[rr[2]][cc[2]]);
+    };
+    int best = 0;
+    double bestv = -1.0;
+    for (int i = 0; i < 4; ++i) {
+        const double d = fabs(minor(i, i));
+        if (d > bestv) {
+            bestv = d;
+            best = i;
+        }
+    }
+    double v[4];
+    for (int j = 0; j < 4; ++j)
+        v[j] = (((j + best) & 1) ? -1.0 : 1.0) * minor(best, j);
+    const double inv = 1.0 / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+    const double w = v[0] * inv, x = v[1] * inv, y = v[2] * inv, z = v[3] * inv;
+    R[0] = w * w + x * x - y * y - z * z; R[1] = 2.0 * (x * y - w * z);         R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (y * x + w * z);         R[4] = w * w - x * x + y * y - z * z; R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (z * x - w * y);         R[7] = 2.0 * (z * y + w * x);         R[8] = w * w - x * x - y * y + z * z;
+}
+
 // ---------------------------------------------------------------------------
-// Reduction.  Every block accumulates, in FP64 and relative to a fixed
-// centre c (the grid centre, to keep the single-pass covariance well
-// conditioned):
+// Reduction and solve in one launch.  Every block accumulates, in FP64 and
+// relative to a fixed centre c (the grid centre, to keep the single-pass
+// covariance well conditioned):
 //   [0..2]  sum (s - c)          [3..5]  sum (q - c)
 //   [6..14] sum (s - c)(q - c)^T [15]    sum |s - q|^2
 // over a fixed strided set of points, reduces them with warp shuffles and
-// shared memory in a fixed order, and writes its 16 partials.  The grid size
-// depends only on M, so the sums are bit-identical from run to run.
+// shared memory in a fixed order, and writes its 16 partials.  The last block
+// to finish (atomic ticket) adds all partials in a fixed order and thread 0
+// solves Eq. 1 and updates the pose, so the result is bit-identical from run
+// to run whichever block finishes last.
 // ---------------------------------------------------------------------------
-constexpr int RED_THREADS = 256;
-
-__global__ void __launch_bounds__(RED_THREADS) k_reduce(const float4 *__restrict__ src, int m,
-                                                        const double *__restrict__ pose,
-                                                        const float4 *__restrict__ tgt, int n_tgt,
-                                                        const int *__restrict__ nn, double3 c,
-                                                        double *__restrict__ partials,
-                                                        DevCtl *__restrict__ ctl, int honor_stop)
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__restrict__ src, int m,
+                                                              double *__restrict__ pose,
+                                                              const float4 *__restrict__ tgt, int n_tgt,
+                                                              const int *__restrict__ nn, double3 c,
+                                                              double *__restrict__ partials,
+                                                              double *__restrict__ rmse_out,
+                                                              DevCtl *__restrict__ ctl, int honor_stop, double eps)
 {
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;
     __shared__ PoseF sp;
     __shared__ double s_red[RED_THREADS / 32][REDUCE_VALUES];
+    __shared__ int s_last;
     if (threadIdx.x == 0)
         load_pose_f(pose, sp);
     __syncthreads();
@@ -74,158 +192,35 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const float4 *__restrict
         for (int w = 0; w < RED_THREADS / 32; ++w)
             v += s_red[w][threadIdx.x];
         partials[blockIdx.x * REDUCE_VALUES + threadIdx.x] = v;
+        __threadfence();
     }
-}
-
-cudaError_t launch_reduce(const float4 *src, int m, const double *pose, const float4 *tgt, int n_tgt,
-                          const int *nn, double3 center, double *partials, DevCtl *ctl, int honor_stop,
-                          cudaStream_t st)
-{
-    k_reduce<<<reduce_blocks(m), RED_THREADS, 0, st>>>(src, m, pose, tgt, n_tgt, nn, center, partials, ctl,
-                                                       honor_stop);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Solve.  Horn's closed form: with S the 3x3 cross-covariance
-// sum (s - sbar)(q - qbar)^T, the rotation minimising Eq. 1 is the unit
-// quaternion of the largest eigenvalue of the symmetric 4x4
-//   [ Sxx+Syy+Szz  Syz-Szy      Szx-Sxz      Sxy-Syx     ]
-//   [ Syz-Szy      Sxx-Syy-Szz  Sxy+Syx      Szx+Sxz     ]
-//   [ Szx-Sxz      Sxy+Syx     -Sxx+Syy-Szz  Syz+Szy     ]
-//   [ Sxy-Syx      Szx+Sxz      Syz+Szy     -Sxx-Syy+Szz ]
-// found here by cyclic Jacobi rotations in FP64.  A quaternion is always a
-// proper rotation, so no reflection fix is needed.  t = qbar - R sbar, and
-// pose <- [R t] * pose.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void jacobi_rotate(double A[4][4], double V[4][4], int p, int q)
-{
-    const double apq = A[p][q];
-    if (apq == 0.0)
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(&ctl->red_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last)
         return;
-    const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-    double t;
-    if (fabs(theta) > 1e150)
-        t = 0.5 / theta;
-    else
-        t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-    const double c = 1.0 / sqrt(t * t + 1.0);
-    const double s = t * c;
-    const double tau = s / (1.0 + c);
-    const double h = t * apq;
-    A[p][p] -= h;
-    A[q][q] += h;
-    A[p][q] = A[q][p] = 0.0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        if (r != p && r != q) {
-            const double g = A[r][p], k = A[r][q];
-            A[r][p] = A[p][r] = g - s * (k + g * tau);
-            A[r][q] = A[q][r] = k + s * (g - k * tau);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const double g = V[r][p], k = V[r][q];
-        V[r][p] = g - s * (k + g * tau);
-        V[r][q] = k + s * (g - k * tau);
-    }
-}
+    __threadfence();
 
-__device__ __forceinline__ void horn_rotation(const double S[9], double R[9])
-{
-    const double sxx = S[0], sxy = S[1], sxz = S[2], syx = S[3], syy = S[4], syz = S[5], szx = S[6], szy = S[7],
-                 szz = S[8];
-    double A[4][4] = {{sxx + syy + szz, syz - szy, szx - sxz, sxy - syx},
-                      {syz - szy, sxx - syy - szz, sxy + syx, szx + sxz},
-                      {szx - sxz, sxy + syx, -sxx + syy - szz, syz + szy},
-                      {sxy - syx, szx + sxz, syz + szy, -sxx - syy + szz}};
-    double V[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
-    for (int sweep = 0; sweep < 32; ++sweep) {
-        double off = 0.0, dia = 0.0;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            dia += A[p][p] * A[p][p];
-#pragma unroll
-            for (int q = p + 1; q < 4; ++q)
-                off += A[p][q] * A[p][q];
-        }
-        if (off <= 1e-34 * dia)
-            break;
-        jacobi_rotate(A, V, 0, 1);
-        jacobi_rotate(A, V, 0, 2);
-        jacobi_rotate(A, V, 0, 3);
-        jacobi_rotate(A, V, 1, 2);
-        jacobi_rotate(A, V, 1, 3);
-        jacobi_rotate(A, V, 2, 3);
-    }
-    int k = 0;
-#pragma unroll
-    for (int p = 1; p < 4; ++p)
-        if (A[p][p] > A[k][k])
-            k = p;
-    double w = V[0][k], x = V[1][k], y = V[2][k], z = V[3][k];
-    const double inv = 1.0 / sqrt(w * w + x * x + y * y + z * z);
-    w *= inv; x *= inv; y *= inv; z *= inv;
-    R[0] = w * w + x * x - y * y - z * z; R[1] = 2.0 * (x * y - w * z);         R[2] = 2.0 * (x * z + w * y);
-    R[3] = 2.0 * (y * x + w * z);         R[4] = w * w - x * x + y * y - z * z; R[5] = 2.0 * (y * z - w * x);
-    R[6] = 2.0 * (z * x - w * y);         R[7] = 2.0 * (z * y + w * x);         R[8] = w * w - x * x - y * y + z * z;
-}
-
-// rank(S) < 2: every 2x2 minor negligible against |S|_F^2 (a definition
-// shared with the oracle, not its code).
-__device__ bool rank_below_two(const double S[9])
-{
-    double s2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-        s2 += S[k] * S[k];
-    if (s2 == 0.0)
-        return true;
-    double c2 = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-            const double cf = S[3 * i1 + j1] * S[3 * i2 + j2] - S[3 * i1 + j2] * S[3 * i2 + j1];
-            c2 += cf * cf;
-        }
-    return sqrt(c2) <= 1e-12 * s2;
-}
-
-constexpr int SOLVE_THREADS = 256;
-
-__global__ void __launch_bounds__(SOLVE_THREADS) k_solve(const double *__restrict__ partials, int nparts, int m,
-                                                         double3 c, double *__restrict__ pose,
-                                                         double *__restrict__ rmse_out,
-                                                         DevCtl *__restrict__ ctl, int honor_stop, double eps)
-{
-    if (honor_stop && *(volatile int *)&ctl->stop)
-        return;
-    __shared__ double s_sum[SOLVE_THREADS / 32][REDUCE_VALUES];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // Fixed-order sum of the block partials: thread t adds partials t, t+256, ...
-#pragma unroll 1
-    for (int k = 0; k < REDUCE_VALUES; ++k) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nparts; b += SOLVE_THREADS)
-            v += partials[b * REDUCE_VALUES + k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            v += __shfl_xor_sync(FULL_MASK, v, o);
-        if (lane == 0)
-            s_sum[warp][k] = v;
-    }
+    // Last block: fixed-order sum of all partials.  Thread t adds value t % 16
+    // of partials t/16, t/16 + 16, ...; the 16 groups are then added in order.
+    const int k = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    double v = 0.0;
+    for (int b = grp; b < (int)gridDim.x; b += RED_THREADS / 16)
+        v += __ldcg(partials + b * REDUCE_VALUES + k);
+    v += __shfl_xor_sync(FULL_MASK, v, 16);   // groups 2w and 2w+1 of warp w
+    if (lane < 16)
+        s_red[warp][lane] = v;
     __syncthreads();
     if (threadIdx.x != 0)
         return;
+    ctl->red_done = 0u;
     double S[REDUCE_VALUES];
-    for (int k = 0; k < REDUCE_VALUES; ++k) {
-        double v = 0.0;
-        for (int w = 0; w < SOLVE_THREADS / 32; ++w)
-            v += s_sum[w][k];
-        S[k] = v;
+    for (int q = 0; q < REDUCE_VALUES; ++q) {
+        double t = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w)
+            t += s_red[w][q];
+        S[q] = t;
     }
     const double M = (double)m;
     const double pb[3] = {S[0] / M, S[1] / M, S[2] / M};   // relative to c
@@ -245,8 +240,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(const double *__restric
         }
         return;
     }
+    // centred residual E = sum |s - q|^2 - M |sbar - qbar|^2
+    const double dm[3] = {pb[0] - qb[0], pb[1] - qb[1], pb[2] - qb[2]};
+    const double E = S[15] - M * (dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]);
     double R[9];
-    horn_rotation(H, R);
+    horn_rotation(H, E, R);
     const double pa[3] = {pb[0] + c.x, pb[1] + c.y, pb[2] + c.z};
     const double qa[3] = {qb[0] + c.x, qb[1] + c.y, qb[2] + c.z};
     double dT[12];
@@ -257,28 +255,28 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(const double *__restric
         dT[4 * a + 3] = qa[a] - (R[3 * a] * pa[0] + R[3 * a + 1] * pa[1] + R[3 * a + 2] * pa[2]);
     }
     double T[16];
-    for (int k = 0; k < 16; ++k)
-        T[k] = pose[k];
+    for (int q = 0; q < 16; ++q)
+        T[q] = pose[q];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 4; ++b)
             pose[4 * a + b] = dT[4 * a] * T[b] + dT[4 * a + 1] * T[4 + b] + dT[4 * a + 2] * T[8 + b] +
                               dT[4 * a + 3] * T[12 + b];
-    for (int b = 0; b < 4; ++b)
-        pose[12 + b] = T[12 + b];
     if (honor_stop) {
-        const int k = ctl->iters;
-        ctl->iters = k + 1;
+        const int it = ctl->iters;
+        ctl->iters = it + 1;
         ctl->last_rmse = rmse;
-        if (eps > 0.0 && k >= 1 && fabs(rmse - ctl->prev_rmse) < eps)
+        if (eps > 0.0 && it >= 1 && fabs(rmse - ctl->prev_rmse) < eps)
             ctl->stop = 1;
         ctl->prev_rmse = rmse;
     }
 }
 
-cudaError_t launch_solve(const double *partials, int nparts, int m, double3 center, double *pose,
-                         double *rmse_out, DevCtl *ctl, int honor_stop, double eps, cudaStream_t st)
+cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
+                                double3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
+                                int honor_stop, double eps, cudaStream_t st)
 {
-    k_solve<<<1, SOLVE_THREADS, 0, st>>>(partials, nparts, m, center, pose, rmse_out, ctl, honor_stop, eps);
+    k_reduce_solve<<<nparts, RED_THREADS, 0, st>>>(src, m, pose, tgt, n_tgt, nn, center, partials, rmse_out, ctl,
+                                                   honor_stop, eps);
     return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ class vicp_memory(C.Structure):
     _fields_ = [("current_bytes", C.c_uint64), ("peak_bytes", C.c_uint64), ("static_bytes", C.c_uint64),
                 ("csr_store_bytes", C.c_uint64), ("fixed_capacity_bytes", C.c_uint64),
                 ("paper_static_layout_bytes", C.c_uint64), ("max_voxel_count", C.c_uint32),
-                ("occupied_voxels", C.c_uint32)]
+                ("occupied_voxels", C.c_uint32), ("nonempty_bricks", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class vicp_stats(C.Structure):

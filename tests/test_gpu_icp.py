@@ -146,6 +146,6 @@ def test_profile_counts_launches(pairs):
     for _ in range(3):
         ctx.step(src, pose)
     prof = ctx.profile_read()
-    assert ctx.launch_count() - before == 12
-    for name in ("correspond", "fallback", "reduce", "solve"):
+    assert ctx.launch_count() - before == 9
+    for name in ("correspond", "fallback", "reduce_solve"):
         assert prof[name][0] == 3 and prof[name][1] > 0.0
