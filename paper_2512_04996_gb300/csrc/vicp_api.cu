@@ -46,10 +46,10 @@ struct vicp_ctx {
     const float4 *target = nullptr;   // caller's target of the last build (global search)
 
     // V-sized
-    Buf counts, off, root, ring, occ, desc;
+    Buf counts, off, root, ring, occ, desc, active_tiles;
     long long cap_V = -1;
     // brick level (V / 512)
-    Buf bcounts, boff, brick_list, brick_range, brick_box;
+    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord;
     long long cap_bricks = -1;
     // N-sized
     Buf keys, ids, csr, bpts, outside;
@@ -197,6 +197,9 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_zero(c, c->desc, "zero scan descriptors"));
         c->cap_V = V;
     }
+    if (dilate_tiles(c->geom) * 4 > (long long)c->active_tiles.bytes) {
+        TRY(buf_alloc(c, c->active_tiles, (size_t)dilate_tiles(c->geom) * 4, "active tile list"));
+    }
     if (n_bricks > c->cap_bricks) {
         TRY(buf_alloc(c, c->bcounts, (size_t)n_bricks * 4, "brick counts"));
         TRY(buf_zero(c, c->bcounts, "zero brick counts"));   // kept at zero between builds
@@ -204,6 +207,8 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->brick_list, (size_t)n_bricks * 4, "brick list"));
         TRY(buf_alloc(c, c->brick_range, (size_t)n_bricks * 8, "brick ranges"));
         TRY(buf_alloc(c, c->brick_box, (size_t)n_bricks * 32, "brick boxes"));
+        TRY(buf_alloc(c, c->bslot, (size_t)n_bricks * 4, "brick slots"));
+        TRY(buf_alloc(c, c->boxord, (size_t)n_bricks * 32, "brick box bounds"));
         c->cap_bricks = n_bricks;
     }
     return VICP_OK;
@@ -328,10 +333,10 @@ vicp_status check_params(vicp_ctx *c, const vicp_params *p)
     return VICP_OK;
 }
 
-double3 grid_center(const GridGeom &g)
+float3 grid_center(const GridGeom &g)
 {
-    return make_double3((double)g.ox + 0.5 * (double)g.h * g.nx, (double)g.oy + 0.5 * (double)g.h * g.ny,
-                        (double)g.oz + 0.5 * (double)g.h * g.nz);
+    return make_float3((float)((double)g.ox + 0.5 * (double)g.h * g.nx), (float)((double)g.oy + 0.5 * (double)g.h * g.ny),
+                       (float)((double)g.oz + 0.5 * (double)g.h * g.nz));
 }
 
 vicp_status check_cloud(vicp_ctx *c, const float *p, int32_t n, const char *what)
@@ -387,7 +392,7 @@ vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double
     TRY(ensure_query_buffers(c, m));
     int *nn = (int *)c->nn.p;
     TRY(run_nns(c, src, m, pose, nn, (float *)c->d2.p, honor_stop));
-    const double3 ctr = grid_center(c->geom);
+    const float3 ctr = grid_center(c->geom);
     const int nparts = reduce_blocks(m, c->sms);
     TRY(launch(c, K_REDUCE_SOLVE, [&] {
         return launch_reduce_solve(src, m, pose, c->target, c->n_target, nn, ctr, (double *)c->partials.p, nparts,
@@ -422,16 +427,16 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     }));
     TRY(launch(c, K_BRICK_SCAN, [&] {
         return launch_brick_scan((const unsigned *)c->bcounts.p, g, (unsigned *)c->boff.p, (int *)c->brick_list.p,
-                                 (uint2 *)c->brick_range.p, d, c->stream);
+                                 (uint2 *)c->brick_range.p, (int *)c->bslot.p, (uint4 *)c->boxord.p, d, c->stream);
     }));
     TRY(launch(c, K_SCATTER, [&] {
         return launch_scatter(tgt, (const int *)c->keys.p, n, g, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
-                              (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (int *)c->ids.p,
-                              (float4 *)c->csr.p, (float4 *)c->bpts.p, (int *)c->outside.p, d, c->stream);
+                              (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (const int *)c->bslot.p,
+                              (unsigned *)c->boxord.p, (int *)c->ids.p, (float4 *)c->csr.p, (float4 *)c->bpts.p,
+                              (int *)c->outside.p, d, c->stream);
     }));
     TRY(launch(c, K_BRICK_BOXES, [&] {
-        return launch_brick_boxes((const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
-                                  (float4 *)c->brick_box.p, d, g, c->stream);
+        return launch_brick_boxes((const uint4 *)c->boxord.p, (float4 *)c->brick_box.p, d, g, c->stream);
     }));
     c->built = true;
     c->dilated_L = -1;
@@ -448,8 +453,9 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     if (L > DILATE_MAX_L)
         return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
     TRY(launch(c, K_DILATE, [&] {
-        return launch_dilate((const unsigned *)c->occ.p, (const unsigned *)c->boff.p, c->geom, L, (int *)c->root.p,
-                             (unsigned char *)c->ring.p, c->stream);
+        return launch_dilate((const unsigned *)c->occ.p, (const unsigned *)c->boff.p, c->geom, L,
+                             (int *)c->active_tiles.p, (int *)c->root.p, (unsigned char *)c->ring.p, ctl_of(c), c->sms,
+                             c->stream);
     }));
     c->dilated_L = L;
     return VICP_OK;
@@ -580,8 +586,9 @@ void vicp_destroy(vicp_ctx *c)
     if (!c)
         return;
     cudaStreamSynchronize(c->stream);
-    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc,
-                  &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->keys,
+    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->active_tiles,
+                  &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
+                  &c->boxord,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
                   &c->fb_list, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt};

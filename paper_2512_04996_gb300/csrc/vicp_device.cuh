@@ -42,6 +42,8 @@ struct DevCtl {
     unsigned max_count;     // memory report: largest voxel count
     unsigned occupied;      // memory report: occupied voxels
     unsigned red_done;      // reduction: finished blocks (the last one solves and resets it)
+    int n_active_tiles;     // dilation: tiles listed for the shared-memory kernel (reset by it)
+    unsigned dil_done;      // dilation: finished blocks (the last one resets the list)
     // Work counters (added by the search kernels, read and cleared by the host).
     unsigned long long stat_queries;       // source points searched
     unsigned long long stat_fallbacks;     // of which took the global search
@@ -53,7 +55,7 @@ struct DevCtl {
     double prev_rmse;
     double last_rmse;
 };
-static_assert(sizeof(DevCtl) == 96, "DevCtl layout");
+static_assert(sizeof(DevCtl) == 104, "DevCtl layout");
 
 // Rigid transform rounded to float: R row-major, t.
 struct PoseF {

@@ -26,13 +26,13 @@
 //   pass Y: forward and backward running minimum along y;
 //   pass Z: the same along z, then the word is decoded into root and ring.
 //
-// One CTA owns a 32 x 8 x 8 output tile.  It stages the occupancy bits of the
-// tile grown by L in y and z (three 32-bit words per row cover x in
-// [x0-32, x0+64)), runs passes X and Y for eight z-planes at a time into
-// shared memory, then pass Z, and writes root and ring with coalesced
-// stores.  A tile whose grown neighbourhood touches no occupied 8x8x8 brick
-// (checked on the brick offsets before any staging) writes "unlabelled"
-// straight away.  L <= 31.
+// The grid is cut into 32 x 8 x 8 output tiles.  A tile whose L-grown box
+// touches no occupied 8x8x8 brick is written "unlabelled" by a light
+// classification kernel.  Every other tile is processed by one CTA, which
+// stages the occupancy bits of the tile grown by L in y and z (three 32-bit
+// words per row cover x in [x0-32, x0+64)), runs passes X and Y for eight
+// z-planes at a time into shared memory, then pass Z, and writes root and
+// ring with coalesced stores.  L <= 31.
 #include "vicp_launch.h"
 
 namespace vicp {
@@ -62,10 +62,65 @@ size_t dilate_smem_bytes(int L)
     return sizeof(unsigned) * (HZ * HY * 3 + ZB * HY * TX + HZ * TY * TX);
 }
 
+// ---------------------------------------------------------------------------
+// Tile classification: a warp per 32 x 8 x 8 tile checks the brick offsets of
+// every 8x8x8 brick its L-grown box touches.  A tile with no point in reach
+// writes "unlabelled" (root -1, ring 255) for its voxels at once; any other
+// tile is appended to the list the shared-memory kernel below works through.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L,
+                                                      int tiles_x, int tiles_y, long long n_tiles,
+                                                      int *__restrict__ active, DevCtl *__restrict__ ctl,
+                                                      int *__restrict__ root, unsigned char *__restrict__ ring)
+{
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= n_tiles)
+        return;   // whole warp
+    const int x0 = (int)(t % tiles_x) * TX;
+    const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
+    const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
+    const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
+    const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
+    const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
+    const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nbz = bz1 - bz0 + 1;
+    bool any = false;
+    for (int k = lane; k < nbx * nby * nbz; k += 32) {
+        const int b = (bx0 + k % nbx) + g.bx * ((by0 + (k / nbx) % nby) + g.by * (bz0 + k / (nbx * nby)));
+        any |= __ldg(boff + b + 1) > __ldg(boff + b);
+    }
+    if (__any_sync(FULL_MASK, any)) {
+        if (lane == 0) {
+            const int slot = atomicAdd(&ctl->n_active_tiles, 1);
+            if (slot < n_tiles)
+                active[slot] = (int)t;
+            else
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+        }
+        return;
+    }
+    const int x = x0 + lane;
+    if (x >= g.nx)
+        return;
+    for (int k = 0; k < TY * TZ; ++k) {
+        const int y = y0 + (k % TY), z = z0 + (k / TY);
+        if (y < g.ny && z < g.nz) {
+            const long long v = x + (long long)g.nx * (y + (long long)g.ny * z);
+            root[v] = -1;
+            ring[v] = 255;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Active tiles: a persistent grid works through the list; the last block to
+// finish clears the list length for the next dilation.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ,
-                                                    const unsigned *__restrict__ boff, GridGeom g, int L,
-                                                    int tiles_x, int tiles_y, int *__restrict__ root,
-                                                    unsigned char *__restrict__ ring)
+                                                    const int *__restrict__ active, GridGeom g, int L,
+                                                    int tiles_x, int tiles_y, long long n_tiles,
+                                                    int *__restrict__ root, unsigned char *__restrict__ ring,
+                                                    DevCtl *__restrict__ ctl)
 {
     extern __shared__ unsigned smem[];
     const int HY = TY + 2 * L, HZ = TZ + 2 * L;
@@ -73,50 +128,33 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
     unsigned *s_a = s_bits + HZ * HY * 3;     // [ZB][HY][TX]  pass X, one z batch
     unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y, all planes
     const unsigned lim = (unsigned)L << SH_D;
-
-    const long long t = blockIdx.x;
-    const int x0 = (int)(t % tiles_x) * TX;
-    const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
-    const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_active = (int)min((long long)*(volatile int *)&ctl->n_active_tiles, n_tiles);
 
-    // 0. coarse test: does any 8x8x8 brick touching the grown tile hold a point?
-    int any = 0;
-    {
-        const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
-        const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
-        const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
-        const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nbz = bz1 - bz0 + 1;
-        for (int k = tid; k < nbx * nby * nbz; k += THREADS) {
-            const int b = (bx0 + k % nbx) + g.bx * ((by0 + (k / nbx) % nby) + g.by * (bz0 + k / (nbx * nby)));
-            any |= __ldg(boff + b + 1) > __ldg(boff + b);
-        }
-    }
-    any = __syncthreads_or(any);
+    for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
+        const long long t = __ldg(active + it);
+        const int x0 = (int)(t % tiles_x) * TX;
+        const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
+        const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
 
-    // 1. occupancy windows of the grown tile
-    for (int idx = tid; any && idx < HZ * HY * 3; idx += THREADS) {
-        const int k = idx % 3, row = idx / 3;
-        const int y = y0 - L + row % HY, z = z0 - L + row / HY;
-        unsigned w = 0u;
-        if (y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
-            const int xs = x0 - 32 + 32 * k;
-            const int lo = max(xs, 0), hi = min(xs + 32, g.nx);
-            if (lo < hi) {
-                const long long b = (long long)g.nx * (y + (long long)g.ny * z) + lo;
-                w = extract_bits(occ, b, hi - lo) << (lo - xs);
+        // 1. occupancy windows of the grown tile
+        for (int idx = tid; idx < HZ * HY * 3; idx += THREADS) {
+            const int k = idx % 3, row = idx / 3;
+            const int y = y0 - L + row % HY, z = z0 - L + row / HY;
+            unsigned w = 0u;
+            if (y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+                const int xs = x0 - 32 + 32 * k;
+                const int lo = max(xs, 0), hi = min(xs + 32, g.nx);
+                if (lo < hi) {
+                    const long long b = (long long)g.nx * (y + (long long)g.ny * z) + lo;
+                    w = extract_bits(occ, b, hi - lo) << (lo - xs);
+                }
             }
+            s_bits[idx] = w;
         }
-        s_bits[idx] = w;
-    }
-    __syncthreads();
+        __syncthreads();
 
-    unsigned out[TZ];
-    if (!any) {
-#pragma unroll
-        for (int k = 0; k < TZ; ++k)
-            out[k] = NONE;
-    } else {
+        unsigned out[TZ];
         for (int zb = 0; zb < HZ; zb += ZB) {
             // 2a. pass X: warp per row, lane = x offset in the tile
             for (int r = warp; r < ZB * HY; r += THREADS / 32) {
@@ -174,62 +212,84 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
             __syncthreads();
         }
         // 3. pass Z: thread per (x, y) column of the tile
-        const unsigned *col = s_b + warp * TX + lane;
-        unsigned f = NONE;
-        for (int zz = 0; zz < L; ++zz)
-            f = min(step(f, STEP_ZF, lim), col[zz * TY * TX]);
+        {
+            const unsigned *col = s_b + warp * TX + lane;
+            unsigned f = NONE;
+            for (int zz = 0; zz < L; ++zz)
+                f = min(step(f, STEP_ZF, lim), col[zz * TY * TX]);
 #pragma unroll
-        for (int k = 0; k < TZ; ++k) {
-            f = min(step(f, STEP_ZF, lim), col[(L + k) * TY * TX]);
-            out[k] = f;
-        }
-        unsigned bk = NONE;
-        for (int zz = HZ - 1; zz >= L + TZ; --zz)
-            bk = min(step(bk, STEP_ZB, lim), col[zz * TY * TX]);
+            for (int k = 0; k < TZ; ++k) {
+                f = min(step(f, STEP_ZF, lim), col[(L + k) * TY * TX]);
+                out[k] = f;
+            }
+            unsigned bk = NONE;
+            for (int zz = HZ - 1; zz >= L + TZ; --zz)
+                bk = min(step(bk, STEP_ZB, lim), col[zz * TY * TX]);
 #pragma unroll
-        for (int k = TZ - 1; k >= 0; --k) {
-            bk = min(step(bk, STEP_ZB, lim), col[(L + k) * TY * TX]);
-            out[k] = min(out[k], bk);
+            for (int k = TZ - 1; k >= 0; --k) {
+                bk = min(step(bk, STEP_ZB, lim), col[(L + k) * TY * TX]);
+                out[k] = min(out[k], bk);
+            }
         }
+        // 4. decode and store
+        const int x = x0 + lane, y = y0 + warp;
+        if (x < g.nx && y < g.ny) {
+#pragma unroll
+            for (int k = 0; k < TZ; ++k) {
+                const int z = z0 + k;
+                if (z < g.nz) {
+                    const long long v = x + (long long)g.nx * (y + (long long)g.ny * z);
+                    const unsigned w = out[k];
+                    int r = -1;
+                    unsigned char d = 255;
+                    if (w != NONE) {
+                        const int dz = (int)((w >> SH_Z) & 63u) - 31;
+                        const int dy = (int)((w >> SH_Y) & 63u) - 31;
+                        const int dx = (int)(w & 63u) - 31;
+                        r = (int)(v + dx + (long long)g.nx * (dy + (long long)g.ny * dz));
+                        d = (unsigned char)(w >> SH_D);
+                    }
+                    root[v] = r;
+                    ring[v] = d;
+                }
+            }
+        }
+        __syncthreads();   // shared memory is reused by the next tile
     }
 
-    // 4. decode and store
-    const int x = x0 + lane, y = y0 + warp;
-    if (x < g.nx && y < g.ny) {
-#pragma unroll
-        for (int k = 0; k < TZ; ++k) {
-            const int z = z0 + k;
-            if (z < g.nz) {
-                const long long v = x + (long long)g.nx * (y + (long long)g.ny * z);
-                const unsigned w = out[k];
-                int r = -1;
-                unsigned char d = 255;
-                if (w != NONE) {
-                    const int dz = (int)((w >> SH_Z) & 63u) - 31;
-                    const int dy = (int)((w >> SH_Y) & 63u) - 31;
-                    const int dx = (int)(w & 63u) - 31;
-                    r = (int)(v + dx + (long long)g.nx * (dy + (long long)g.ny * dz));
-                    d = (unsigned char)(w >> SH_D);
-                }
-                root[v] = r;
-                ring[v] = d;
-            }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->dil_done, 1u) == gridDim.x - 1) {
+            ctl->n_active_tiles = 0;
+            ctl->dil_done = 0u;
         }
     }
 }
 
-cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *root,
-                          unsigned char *ring, cudaStream_t st)
+cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
+                          int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
 {
     const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
     const long long tiles = (long long)tiles_x * tiles_y * tiles_z;
+    k_dilate_tiles<<<(unsigned)((tiles * 32 + 255) / 256), 256, 0, st>>>(boff, g, L, tiles_x, tiles_y, tiles, active,
+                                                                         ctl, root, ring);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
     const size_t smem = dilate_smem_bytes(L);
     if (smem > 48 * 1024) {   // opt in above the default limit (a per-device function attribute)
-        cudaError_t e = cudaFuncSetAttribute(k_dilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_dilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
     }
-    k_dilate<<<(unsigned)tiles, THREADS, smem, st>>>(occ, boff, g, L, tiles_x, tiles_y, root, ring);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dilate, THREADS, smem);
+    if (e != cudaSuccess)
+        return e;
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > tiles)
+        grid = tiles;
+    k_dilate<<<(unsigned)grid, THREADS, smem, st>>>(occ, active, g, L, tiles_x, tiles_y, tiles, root, ring, ctl);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,11 @@ __device__ __forceinline__ unsigned float_to_ordered(float f)
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+__device__ __forceinline__ float ordered_to_float(unsigned o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
 __global__ void __launch_bounds__(256) k_bbox(const float4 *__restrict__ pts, int n, unsigned *__restrict__ out)
 {
     float lo[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
@@ -107,84 +112,79 @@ cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *k
 // ---------------------------------------------------------------------------
 // Brick offsets: one CTA scans the per-brick counts (few: V / 512) into
 // brick offsets, and lists the non-empty bricks in ascending order with their
-// point ranges.  The count and the non-empty flag are scanned together as one
-// 64-bit value (flag count in the high half).
+// point ranges and slot numbers; it also resets each listed brick's box.  The
+// count and the non-empty flag are scanned together as one 64-bit value
+// (flag count in the high half): each thread sums a contiguous run of bricks,
+// one block-wide scan offsets the runs, and a second pass writes them.
 // ---------------------------------------------------------------------------
 constexpr int BS_THREADS = 1024;
-constexpr int BS_ITEMS = 4;
+
+__device__ __forceinline__ unsigned long long brick_pair(unsigned c)
+{
+    return (unsigned long long)c | ((unsigned long long)(c != 0u) << 32);
+}
 
 __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__restrict__ bcounts, int nbt,
                                                            unsigned *__restrict__ boff, int *__restrict__ list,
-                                                           uint2 *__restrict__ range, DevCtl *__restrict__ ctl)
+                                                           uint2 *__restrict__ range, int *__restrict__ bslot,
+                                                           uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
 {
     __shared__ unsigned long long s_w[BS_THREADS / 32];
-    __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0)
-        s_carry = 0ull;
-    __syncthreads();
-    for (int base = 0; base < nbt; base += BS_THREADS * BS_ITEMS) {
-        unsigned c[BS_ITEMS];
-        unsigned long long sum = 0ull;
+    // Thread t owns the contiguous bricks [t*per, (t+1)*per).
+    const int per = (nbt + BS_THREADS - 1) / BS_THREADS;
+    const int i0 = min(tid * per, nbt), i1 = min(i0 + per, nbt);
+    unsigned long long sum = 0ull;
+    for (int i = i0; i < i1; ++i)
+        sum += brick_pair(__ldg(bcounts + i));
+    unsigned long long incl = sum;
 #pragma unroll
-        for (int i = 0; i < BS_ITEMS; ++i) {
-            const int idx = base + tid * BS_ITEMS + i;
-            c[i] = idx < nbt ? bcounts[idx] : 0u;
-            sum += (unsigned long long)c[i] | ((unsigned long long)(c[i] != 0u) << 32);
-        }
-        unsigned long long incl = sum;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d)
+            incl += y;
+    }
+    if (lane == 31)
+        s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = s_w[lane];
+        unsigned long long wi = w;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, d);
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, wi, d);
             if (lane >= d)
-                incl += y;
+                wi += y;
         }
-        if (lane == 31)
-            s_w[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const unsigned long long w = s_w[lane];
-            unsigned long long wi = w;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(FULL_MASK, wi, d);
-                if (lane >= d)
-                    wi += y;
-            }
-            s_w[lane] = wi - w;
-        }
-        __syncthreads();
-        unsigned long long run = s_carry + s_w[warp] + (incl - sum);
-#pragma unroll
-        for (int i = 0; i < BS_ITEMS; ++i) {
-            const int idx = base + tid * BS_ITEMS + i;
-            if (idx < nbt) {
-                const unsigned start = (unsigned)run;
-                boff[idx] = start;
-                if (c[i]) {
-                    const int slot = (int)(run >> 32);
-                    list[slot] = idx;
-                    range[slot] = make_uint2(start, start + c[i]);
-                }
-            }
-            run += (unsigned long long)c[i] | ((unsigned long long)(c[i] != 0u) << 32);
-        }
-        __syncthreads();
-        if (tid == BS_THREADS - 1)
-            s_carry = run;
-        __syncthreads();
+        s_w[lane] = wi - w;
     }
-    if (tid == 0) {
-        boff[nbt] = (unsigned)s_carry;
-        ctl->n_bricks = (int)(s_carry >> 32);
+    __syncthreads();
+    unsigned long long run = s_w[warp] + (incl - sum);
+    for (int i = i0; i < i1; ++i) {
+        const unsigned c = __ldg(bcounts + i);
+        const unsigned start = (unsigned)run;
+        boff[i] = start;
+        if (c) {
+            const int slot = (int)(run >> 32);
+            list[slot] = i;
+            range[slot] = make_uint2(start, start + c);
+            bslot[i] = slot;
+            boxord[2 * slot] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);   // min
+            boxord[2 * slot + 1] = make_uint4(0u, 0u, 0u, 0u);                          // max
+        }
+        run += brick_pair(c);
+    }
+    if (tid == BS_THREADS - 1) {
+        boff[nbt] = (unsigned)run;
+        ctl->n_bricks = (int)(run >> 32);
     }
 }
 
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
-                              DevCtl *ctl, cudaStream_t st)
+                              int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st)
 {
     const int nbt = g.bx * g.by * g.bz;
-    k_brick_scan<<<1, BS_THREADS, 0, st>>>(bcounts, nbt, boff, list, range, ctl);
+    k_brick_scan<<<1, BS_THREADS, 0, st>>>(bcounts, nbt, boff, list, range, bslot, boxord, ctl);
     return cudaGetLastError();
 }
 
@@ -193,8 +193,8 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 //
 // Each CTA takes the next tile of 4096 counts from an atomic ticket (so
 // every tile it waits on has already started), scans it, publishes its
-// aggregate, then looks back over its predecessors' descriptors, 32 at a
-// time, until it meets an inclusive prefix.  A descriptor is one 64-bit word
+// aggregate, then looks back over its predecessors' descriptors, 128 at a
+// time (four per lane), until it meets an inclusive prefix.  A descriptor is one 64-bit word
 // [epoch:30 | flag:2 | value:32], so flag and value are read together; the
 // epoch (bumped by the histogram kernel each build) makes the previous
 // build's descriptors invalid without clearing them.  The wait is bounded by
@@ -304,15 +304,21 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
         } else {
             if (lane == 0 && (int)tile != skip_tile)
                 st_relaxed_u64(desc + tile, tag | DESC_AGG | agg);
+            // Lane l inspects the four predecessors look-4l .. look-4l-3, so one
+            // round covers 128 tiles (nearest first).
             long long look = (long long)tile - 1;
             const unsigned long long t0 = global_timer_ns();
             bool gave_up = false;
             for (;;) {
-                const long long idx = look - lane;   // lane 0 is the nearest predecessor
-                unsigned long long d;
+                unsigned long long d[4];
                 for (;;) {
-                    d = (idx >= 0) ? ld_relaxed_u64(desc + idx) : (tag | DESC_PREFIX);
-                    const bool ready = ((d >> 34) == epoch) && ((d & (3ull << 32)) != 0ull);
+                    bool ready = true;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const long long idx = look - 4 * lane - j;
+                        d[j] = (idx >= 0) ? ld_relaxed_u64(desc + idx) : (tag | DESC_PREFIX);
+                        ready &= ((d[j] >> 34) == epoch) && ((d[j] & (3ull << 32)) != 0ull);
+                    }
                     if (__all_sync(FULL_MASK, ready))
                         break;
                     const bool late = (global_timer_ns() - t0 > SCAN_TIMEOUT_NS) ||
@@ -321,19 +327,30 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
                         gave_up = true;
                         break;
                     }
-                    __nanosleep(32);
                 }
                 if (gave_up)
                     break;
-                const unsigned pmask = __ballot_sync(FULL_MASK, (d & DESC_PREFIX) != 0ull);
-                unsigned val = (unsigned)d;
+                int jp = 4;   // first of this lane's four that is an inclusive prefix
+#pragma unroll
+                for (int j = 3; j >= 0; --j)
+                    if (d[j] & DESC_PREFIX)
+                        jp = j;
+                const unsigned pmask = __ballot_sync(FULL_MASK, jp < 4);
                 if (pmask) {
                     const int first = __ffs(pmask) - 1;
-                    excl += warp_sum_u32(lane <= first ? val : 0u);
+                    unsigned v = 0u;
+                    if (lane < first) {
+                        v = (unsigned)d[0] + (unsigned)d[1] + (unsigned)d[2] + (unsigned)d[3];
+                    } else if (lane == first) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            v += (j <= jp) ? (unsigned)d[j] : 0u;
+                    }
+                    excl += warp_sum_u32(v);
                     break;
                 }
-                excl += warp_sum_u32(val);
-                look -= 32;
+                excl += warp_sum_u32((unsigned)d[0] + (unsigned)d[1] + (unsigned)d[2] + (unsigned)d[3]);
+                look -= 128;
             }
             if (lane == 0) {
                 if (gave_up)
@@ -386,7 +403,8 @@ cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off
 __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts, const int *__restrict__ keys, int n,
                                                  GridGeom g, const unsigned *__restrict__ off,
                                                  unsigned *__restrict__ counts, const unsigned *__restrict__ boff,
-                                                 unsigned *__restrict__ bcounts, int *__restrict__ ids,
+                                                 unsigned *__restrict__ bcounts, const int *__restrict__ bslot,
+                                                 unsigned *__restrict__ boxord, int *__restrict__ ids,
                                                  float4 *__restrict__ csr, float4 *__restrict__ bpts,
                                                  int *__restrict__ outside, DevCtl *__restrict__ ctl)
 {
@@ -428,14 +446,29 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
             outside[old + rank] = j;
         }
     }
-    // brick segment
+    // brick segment, and the brick's exact box: the group's min and max of
+    // each coordinate (order-preserving unsigned images of the floats), merged
+    // by the group leader with one atomic per bound
     {
         const unsigned peers = __match_any_sync(FULL_MASK, bk);
         const int leader = __ffs(peers) - 1;
         const unsigned rank = __popc(peers & lanemask_lt());
+        const unsigned ox = float_to_ordered(q.x), oy = float_to_ordered(q.y), oz = float_to_ordered(q.z);
+        const unsigned mnx = __reduce_min_sync(peers, ox), mny = __reduce_min_sync(peers, oy),
+                       mnz = __reduce_min_sync(peers, oz);
+        const unsigned mxx = __reduce_max_sync(peers, ox), mxy = __reduce_max_sync(peers, oy),
+                       mxz = __reduce_max_sync(peers, oz);
         unsigned old = 0u;
-        if (lane == leader && bk >= 0)
+        if (lane == leader && bk >= 0) {
             old = atomicSub(bcounts + bk, (unsigned)__popc(peers));
+            unsigned *b = boxord + 8 * __ldg(bslot + bk);
+            atomicMin(b + 0, mnx);
+            atomicMin(b + 1, mny);
+            atomicMin(b + 2, mnz);
+            atomicMax(b + 4, mxx);
+            atomicMax(b + 5, mxy);
+            atomicMax(b + 6, mxz);
+        }
         old = __shfl_sync(FULL_MASK, old, leader);
         if (bk >= 0) {
             const unsigned pos = __ldg(boff + bk) + old - 1u - rank;
@@ -448,57 +481,40 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
 }
 
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
-                           unsigned *counts, const unsigned *boff, unsigned *bcounts, int *ids, float4 *csr,
-                           float4 *bpts, int *outside, DevCtl *ctl, cudaStream_t st)
+                           unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
+                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, DevCtl *ctl,
+                           cudaStream_t st)
 {
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(pts, keys, n, g, off, counts, boff, bcounts, ids, csr, bpts, outside,
-                                               ctl);
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(pts, keys, n, g, off, counts, boff, bcounts, bslot, boxord, ids, csr,
+                                               bpts, outside, ctl);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Exact bounding box of each non-empty brick's points (a warp per brick):
-// every point of the brick lies inside it as float values, which is what
-// the global search's lower bound needs.
+// Brick boxes as floats: the scatter left each non-empty brick's exact bounds
+// as order-preserving unsigned integers; every stored point of the brick lies
+// inside the box as float values, which is what the global search's lower
+// bound needs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_brick_boxes(const float4 *__restrict__ bpts, const uint2 *__restrict__ range,
-                                                     float4 *__restrict__ box, const DevCtl *__restrict__ ctl)
+__global__ void __launch_bounds__(256) k_brick_boxes(const uint4 *__restrict__ boxord, float4 *__restrict__ box,
+                                                     const DevCtl *__restrict__ ctl)
 {
     const int nb = ctl->n_bricks;
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x / 32);
-    for (int k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); k < nb; k += warps) {
-        const uint2 r = __ldg(range + k);
-        float lo[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
-        float hi[3] = {-lo[0], -lo[1], -lo[2]};
-        for (unsigned i = r.x + lane; i < r.y; i += 32) {
-            const float4 q = __ldg(bpts + i);
-            lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
-            lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
-            lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lo[a] = fminf(lo[a], __shfl_xor_sync(FULL_MASK, lo[a], o));
-                hi[a] = fmaxf(hi[a], __shfl_xor_sync(FULL_MASK, hi[a], o));
-            }
-        if (lane == 0) {
-            box[2 * k] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-            box[2 * k + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
-        }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        const uint4 lo = boxord[2 * k], hi = boxord[2 * k + 1];
+        box[2 * k] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z), 0.0f);
+        box[2 * k + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z), 0.0f);
     }
 }
 
-cudaError_t launch_brick_boxes(const float4 *bpts, const uint2 *range, float4 *box, const DevCtl *ctl,
-                               const GridGeom &g, cudaStream_t st)
+cudaError_t launch_brick_boxes(const uint4 *boxord, float4 *box, const DevCtl *ctl, const GridGeom &g,
+                               cudaStream_t st)
 {
     const int nbt = g.bx * g.by * g.bz;
-    int blocks = (nbt + 7) / 8;
-    if (blocks > 152 * 8)
-        blocks = 152 * 8;
-    k_brick_boxes<<<blocks, 256, 0, st>>>(bpts, range, box, ctl);
+    int blocks = (nbt + 255) / 256;
+    if (blocks > 152 * 2)
+        blocks = 152 * 2;
+    k_brick_boxes<<<blocks, 256, 0, st>>>(boxord, box, ctl);
     return cudaGetLastError();
 }
 

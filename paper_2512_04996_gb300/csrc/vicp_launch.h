@@ -47,15 +47,20 @@ cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *k
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, unsigned *occ,
                         unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st);
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
-                              DevCtl *ctl, cudaStream_t st);
+                              int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
-                           unsigned *counts, const unsigned *boff, unsigned *bcounts, int *ids, float4 *csr,
-                           float4 *bpts, int *outside, DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_brick_boxes(const float4 *bpts, const uint2 *range, float4 *box, const DevCtl *ctl,
-                               const GridGeom &g, cudaStream_t st);
+                           unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
+                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, DevCtl *ctl,
+                           cudaStream_t st);
+cudaError_t launch_brick_boxes(const uint4 *boxord, float4 *box, const DevCtl *ctl, const GridGeom &g,
+                               cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *root,
-                          unsigned char *ring, cudaStream_t st);
+cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
+                          int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st);
+inline long long dilate_tiles(const GridGeom &g)
+{
+    return (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * ((g.nz + 7) / 8);
+}
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);
@@ -64,7 +69,7 @@ cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 
                             const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m, int honor_stop,
                             cudaStream_t st);
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
-                                double3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
+                                float3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);
 
 }  // namespace vicp

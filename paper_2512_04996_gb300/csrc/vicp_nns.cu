@@ -38,7 +38,16 @@ __global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ s
             const unsigned b = min(__ldg(off + r + 1), (unsigned)n_cap);
             cand = b > a ? b - a : 0u;
             unsigned long long best = ~0ull;
-            for (unsigned k = a; k < b; ++k) {
+            unsigned k = a;
+            for (; k + 4 <= b; k += 4) {   // four independent loads in flight
+                const float4 q0 = __ldg(csr + k), q1 = __ldg(csr + k + 1);
+                const float4 q2 = __ldg(csr + k + 2), q3 = __ldg(csr + k + 3);
+                best = umin64(best, nn_key(dist2(s, q0), __float_as_int(q0.w)));
+                best = umin64(best, nn_key(dist2(s, q1), __float_as_int(q1.w)));
+                best = umin64(best, nn_key(dist2(s, q2), __float_as_int(q2.w)));
+                best = umin64(best, nn_key(dist2(s, q3), __float_as_int(q3.w)));
+            }
+            for (; k < b; ++k) {
                 const float4 q = __ldg(csr + k);
                 best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
             }
@@ -100,6 +109,7 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
 // ---------------------------------------------------------------------------
 constexpr int FB_THREADS = 256;
 constexpr int FB_WARPS = FB_THREADS / 32;
+constexpr int FB_CACHE = 32;   // bounds kept per lane: up to 1024 bricks searched from registers
 
 __device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
 {
@@ -160,7 +170,36 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
                 best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
             examined += (unsigned long long)n_tgt;
         } else {
-            if (nb > 0) {
+            if (nb > 0 && nb <= 32 * FB_CACHE) {
+                // Same search with every lane's bounds kept in registers
+                // between the two passes.
+                unsigned lbc[FB_CACHE];
+                unsigned long long lbmin = ~0ull;
+#pragma unroll
+                for (int it = 0; it < FB_CACHE; ++it) {
+                    const int k = it * 32 + lane;
+                    lbc[it] = 0xffffffffu;
+                    if (k < nb)
+                        lbc[it] = __float_as_uint(box_lb2(s, __ldg(bbox + 2 * k), __ldg(bbox + 2 * k + 1)));
+                    lbmin = umin64(lbmin, ((unsigned long long)lbc[it] << 32) | (unsigned)k);
+                }
+                lbmin = warp_min_u64(lbmin);
+                const int k0 = (int)(unsigned)lbmin;
+                best = scan_run(bpts, __ldg(brange + k0), s, lane, best, examined);
+#pragma unroll
+                for (int it = 0; it < FB_CACHE; ++it) {
+                    const int k = it * 32 + lane;
+                    unsigned cand = __ballot_sync(FULL_MASK, k != k0 && lbc[it] <= (unsigned)(best >> 32));
+                    while (cand) {
+                        const int src_lane = __ffs(cand) - 1;
+                        cand &= cand - 1u;
+                        const unsigned lb = __shfl_sync(FULL_MASK, lbc[it], src_lane);
+                        if (lb > (unsigned)(best >> 32))
+                            continue;
+                        best = scan_run(bpts, __ldg(brange + it * 32 + src_lane), s, lane, best, examined);
+                    }
+                }
+            } else if (nb > 0) {
                 // (1) brick of smallest bound (ties: smallest slot)
                 unsigned long long lbmin = ~0ull;
                 for (int k = lane; k < nb; k += 32) {

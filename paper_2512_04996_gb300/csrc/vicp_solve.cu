@@ -121,21 +121,72 @@ __device__ void horn_rotation(const double S[9], double E, double R[9])
 }
 
 // ---------------------------------------------------------------------------
-// Reduction and solve in one launch.  Every block accumulates, in FP64 and
-// relative to a fixed centre c (the grid centre, to keep the single-pass
-// covariance well conditioned):
+// Extended-precision sums on the FP32 pipes.  GB300 executes FP64 at a small
+// fraction of its FP32 rate, so the per-point work of the reduction is done
+// with error-free float transformations ("double-float": a value is the
+// unevaluated sum hi + lo of two floats, about 48 significant bits):
+//   two_sum(a, b)  = (s, e) with s + e == a + b exactly (Knuth),
+//   two_prod(a, b) = (p, e) with p + e == a * b exactly (one FMA).
+// Every per-point term is formed exactly; sums of terms carry a relative
+// error of order 2^-46 of the summed magnitudes, comparable to an FP64
+// accumulation.  Warp partials are converted to FP64 and everything after
+// that -- the sum over warps and blocks and the solve -- is FP64.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ dfl quick_two_sum(float a, float b)   // needs |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_add(dfl x, dfl y)
+{
+    const dfl s = two_sum(x.hi, y.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+// (x.hi + x.lo) * (y.hi + y.lo), the lo * lo term (2^-48 relative) dropped
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl df_shfl_xor(dfl v, int o)
+{
+    return {__shfl_xor_sync(FULL_MASK, v.hi, o), __shfl_xor_sync(FULL_MASK, v.lo, o)};
+}
+
+// ---------------------------------------------------------------------------
+// Reduction and solve in one launch.  Relative to a fixed centre c (the grid
+// centre rounded to float; s - c is then exact as a double-float), every
+// thread accumulates over a fixed strided set of points
 //   [0..2]  sum (s - c)          [3..5]  sum (q - c)
 //   [6..14] sum (s - c)(q - c)^T [15]    sum |s - q|^2
-// over a fixed strided set of points, reduces them with warp shuffles and
-// shared memory in a fixed order, and writes its 16 partials.  The last block
-// to finish (atomic ticket) adds all partials in a fixed order and thread 0
+// in double-float, each warp reduces them with shuffles in a fixed order, and
+// the warps' partials are added in FP64 per block.  The last block to finish
+// (atomic ticket) adds all block partials in a fixed order and thread 0
 // solves Eq. 1 and updates the pose, so the result is bit-identical from run
 // to run whichever block finishes last.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__restrict__ src, int m,
                                                               double *__restrict__ pose,
                                                               const float4 *__restrict__ tgt, int n_tgt,
-                                                              const int *__restrict__ nn, double3 c,
+                                                              const int *__restrict__ nn, float3 cf,
                                                               double *__restrict__ partials,
                                                               double *__restrict__ rmse_out,
                                                               DevCtl *__restrict__ ctl, int honor_stop, double eps)
@@ -149,10 +200,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
         load_pose_f(pose, sp);
     __syncthreads();
     const PoseF P = sp;
-    double acc[REDUCE_VALUES];
+    dfl acc[REDUCE_VALUES];
 #pragma unroll
     for (int k = 0; k < REDUCE_VALUES; ++k)
-        acc[k] = 0.0;
+        acc[k] = {0.0f, 0.0f};
     for (int i = blockIdx.x * RED_THREADS + threadIdx.x; i < m; i += gridDim.x * RED_THREADS) {
         const int j = __ldg(nn + i);
         if ((unsigned)j >= (unsigned)n_tgt) {   // no valid match: report, leave it out
@@ -161,29 +212,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
         }
         const float3 s = transform_pt(P, __ldg(src + i));
         const float4 q = __ldg(tgt + j);
-        const double sv[3] = {(double)s.x - c.x, (double)s.y - c.y, (double)s.z - c.z};
-        const double qv[3] = {(double)q.x - c.x, (double)q.y - c.y, (double)q.z - c.z};
+        const dfl sv[3] = {two_sum(s.x, -cf.x), two_sum(s.y, -cf.y), two_sum(s.z, -cf.z)};
+        const dfl qv[3] = {two_sum(q.x, -cf.x), two_sum(q.y, -cf.y), two_sum(q.z, -cf.z)};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            acc[a] += sv[a];
-            acc[3 + a] += qv[a];
+            acc[a] = df_add(acc[a], sv[a]);
+            acc[3 + a] = df_add(acc[3 + a], qv[a]);
 #pragma unroll
             for (int b = 0; b < 3; ++b)
-                acc[6 + 3 * a + b] = fma(sv[a], qv[b], acc[6 + 3 * a + b]);
+                acc[6 + 3 * a + b] = df_add(acc[6 + 3 * a + b], df_mul(sv[a], qv[b]));
         }
-        const double ex = (double)s.x - (double)q.x, ey = (double)s.y - (double)q.y,
-                     ez = (double)s.z - (double)q.z;
-        acc[15] += ex * ex + ey * ey + ez * ez;
+        const dfl ex = two_sum(s.x, -q.x), ey = two_sum(s.y, -q.y), ez = two_sum(s.z, -q.z);
+        acc[15] = df_add(acc[15], df_add(df_add(df_mul(ex, ex), df_mul(ey, ey)), df_mul(ez, ez)));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < REDUCE_VALUES; ++k) {
-        double v = acc[k];
+        dfl v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
-            v += __shfl_xor_sync(FULL_MASK, v, o);
+            v = df_add(v, df_shfl_xor(v, o));
         if (lane == 0)
-            s_red[warp][k] = v;
+            s_red[warp][k] = (double)v.hi + (double)v.lo;
     }
     __syncthreads();
     if (threadIdx.x < REDUCE_VALUES) {
@@ -245,8 +295,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
     const double E = S[15] - M * (dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]);
     double R[9];
     horn_rotation(H, E, R);
-    const double pa[3] = {pb[0] + c.x, pb[1] + c.y, pb[2] + c.z};
-    const double qa[3] = {qb[0] + c.x, qb[1] + c.y, qb[2] + c.z};
+    const double pa[3] = {pb[0] + (double)cf.x, pb[1] + (double)cf.y, pb[2] + (double)cf.z};
+    const double qa[3] = {qb[0] + (double)cf.x, qb[1] + (double)cf.y, qb[2] + (double)cf.z};
     double dT[12];
     for (int a = 0; a < 3; ++a) {
         dT[4 * a + 0] = R[3 * a + 0];
@@ -272,7 +322,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
 }
 
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
-                                double3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
+                                float3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st)
 {
     k_reduce_solve<<<nparts, RED_THREADS, 0, st>>>(src, m, pose, tgt, n_tgt, nn, center, partials, rmse_out, ctl,
