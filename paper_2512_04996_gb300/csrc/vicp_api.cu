@@ -46,7 +46,7 @@ struct vicp_ctx {
     const float4 *target = nullptr;   // caller's target of the last build (global search)
 
     // V-sized
-    Buf counts, off, root, ring, occ, desc, active_tiles;
+    Buf counts, off, root, ring, occ, desc, tile_sum, active_tiles;
     long long cap_V = -1;
     // brick level (V / 512)
     Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord;
@@ -195,6 +195,8 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_zero(c, c->occ, "zero occupancy"));
         TRY(buf_alloc(c, c->desc, (size_t)scan_tiles(V) * 8, "scan descriptors"));
         TRY(buf_zero(c, c->desc, "zero scan descriptors"));
+        TRY(buf_alloc(c, c->tile_sum, (size_t)scan_tiles(V) * 4, "scan tile sums"));
+        TRY(buf_zero(c, c->tile_sum, "zero scan tile sums"));   // kept at zero between builds
         c->cap_V = V;
     }
     if (dilate_tiles(c->geom) * 4 > (long long)c->active_tiles.bytes) {
@@ -418,12 +420,12 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     DevCtl *d = ctl_of(c);
     const int skip = (c->params.flags & VICP_FLAG_TEST_SCAN_TIMEOUT) ? 0 : -1;
     TRY(launch(c, K_HISTOGRAM, [&] {
-        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, d,
-                                c->stream);
+        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p,
+                                (unsigned *)c->occ.p, (unsigned *)c->tile_sum.p, d, c->stream);
     }));
     TRY(launch(c, K_SCAN, [&] {
-        return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, (unsigned *)c->occ.p,
-                           (unsigned long long *)c->desc.p, d, skip, c->stream);
+        return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, (const unsigned *)c->occ.p,
+                           (unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, skip, c->stream);
     }));
     TRY(launch(c, K_BRICK_SCAN, [&] {
         return launch_brick_scan((const unsigned *)c->bcounts.p, g, (unsigned *)c->boff.p, (int *)c->brick_list.p,
@@ -586,7 +588,8 @@ void vicp_destroy(vicp_ctx *c)
     if (!c)
         return;
     cudaStreamSynchronize(c->stream);
-    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->active_tiles,
+    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->tile_sum,
+                  &c->active_tiles,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
                   &c->boxord,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,

@@ -56,11 +56,17 @@ __device__ __forceinline__ unsigned step(unsigned v, unsigned inc, unsigned lim)
 }
 }  // namespace
 
+// Row-mask words per plane: bit yy of word yy/32 is set when row yy of the
+// grown tile holds an occupied voxel in the staged x window.
+__host__ __device__ constexpr int mask_words(int HY) { return (HY + 31) / 32; }
+
 size_t dilate_smem_bytes(int L)
 {
     const size_t HY = TY + 2 * L, HZ = TZ + 2 * L;
-    return sizeof(unsigned) * (HZ * HY * 3 + ZB * HY * TX + HZ * TY * TX);
+    return sizeof(unsigned) * (HZ * HY * 3 + HZ * mask_words((int)HY) + ZB * HY * TX + HZ * TY * TX);
 }
+
+__device__ __forceinline__ bool row_bit(const unsigned *m, int yy) { return (m[yy >> 5] >> (yy & 31)) & 1u; }
 
 // ---------------------------------------------------------------------------
 // Tile classification: a warp per 32 x 8 x 8 tile checks the brick offsets of
@@ -83,12 +89,15 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
     const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
     const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
     const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
-    const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nbz = bz1 - bz0 + 1;
+    const int nbx = bx1 - bx0 + 1;
     bool any = false;
-    for (int k = lane; k < nbx * nby * nbz; k += 32) {
-        const int b = (bx0 + k % nbx) + g.bx * ((by0 + (k / nbx) % nby) + g.by * (bz0 + k / (nbx * nby)));
-        any |= __ldg(boff + b + 1) > __ldg(boff + b);
-    }
+    for (int bz = bz0; bz <= bz1; ++bz)
+        for (int by = by0; by <= by1; by += 1) {
+            if (lane < nbx) {
+                const int b = bx0 + lane + g.bx * (by + g.by * bz);
+                any |= __ldg(boff + b + 1) > __ldg(boff + b);
+            }
+        }
     if (__any_sync(FULL_MASK, any)) {
         if (lane == 0) {
             const int slot = atomicAdd(&ctl->n_active_tiles, 1);
@@ -102,10 +111,12 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
     const int x = x0 + lane;
     if (x >= g.nx)
         return;
-    for (int k = 0; k < TY * TZ; ++k) {
-        const int y = y0 + (k % TY), z = z0 + (k / TY);
-        if (y < g.ny && z < g.nz) {
-            const long long v = x + (long long)g.nx * (y + (long long)g.ny * z);
+    const long long plane = (long long)g.nx * g.ny;
+    const int ny_t = min(TY, g.ny - y0), nz_t = min(TZ, g.nz - z0);
+    long long vz = x + (long long)g.nx * y0 + plane * z0;
+    for (int zl = 0; zl < nz_t; ++zl, vz += plane) {
+        long long v = vz;
+        for (int yl = 0; yl < ny_t; ++yl, v += g.nx) {
             root[v] = -1;
             ring[v] = 255;
         }
@@ -114,7 +125,10 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
 
 // ---------------------------------------------------------------------------
 // Active tiles: a persistent grid works through the list; the last block to
-// finish clears the list length for the next dilation.
+// finish clears the list length for the next dilation.  Work is proportional
+// to the occupied rows: pass X runs on the rows that hold an occupied voxel
+// in the staged window, pass Y reads pass-X labels only of such rows and
+// skips planes without any.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ,
                                                     const int *__restrict__ active, GridGeom g, int L,
@@ -123,9 +137,10 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
                                                     DevCtl *__restrict__ ctl)
 {
     extern __shared__ unsigned smem[];
-    const int HY = TY + 2 * L, HZ = TZ + 2 * L;
+    const int HY = TY + 2 * L, HZ = TZ + 2 * L, MW = mask_words(HY);
     unsigned *s_bits = smem;                  // [HZ][HY][3]
-    unsigned *s_a = s_bits + HZ * HY * 3;     // [ZB][HY][TX]  pass X, one z batch
+    unsigned *s_mask = s_bits + HZ * HY * 3;  // [HZ][MW]      non-empty rows
+    unsigned *s_a = s_mask + HZ * MW;         // [ZB][HY][TX]  pass X, one z batch (non-empty rows only)
     unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y, all planes
     const unsigned lim = (unsigned)L << SH_D;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -137,75 +152,112 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
         const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
         const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
 
-        // 1. occupancy windows of the grown tile
-        for (int idx = tid; idx < HZ * HY * 3; idx += THREADS) {
-            const int k = idx % 3, row = idx / 3;
-            const int y = y0 - L + row % HY, z = z0 - L + row / HY;
-            unsigned w = 0u;
-            if (y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
-                const int xs = x0 - 32 + 32 * k;
-                const int lo = max(xs, 0), hi = min(xs + 32, g.nx);
-                if (lo < hi) {
-                    const long long b = (long long)g.nx * (y + (long long)g.ny * z) + lo;
-                    w = extract_bits(occ, b, hi - lo) << (lo - xs);
+        // 1. occupancy windows of the grown tile (a lane per row, a warp per
+        //    32 rows of one plane) and the per-plane masks of non-empty rows
+        for (int zz = warp; zz < HZ; zz += THREADS / 32) {
+            const int z = z0 - L + zz;
+            for (int yb = 0; yb < HY; yb += 32) {
+                const int yy = yb + lane, y = y0 - L + yy;
+                unsigned w[3] = {0u, 0u, 0u};
+                if (yy < HY && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+                    const long long rowbase = (long long)g.nx * (y + (long long)g.ny * z);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int xs = x0 - 32 + 32 * k;
+                        const int lo = max(xs, 0), hi = min(xs + 32, g.nx);
+                        if (lo < hi)
+                            w[k] = extract_bits(occ, rowbase + lo, hi - lo) << (lo - xs);
+                    }
                 }
+                if (yy < HY) {
+                    unsigned *dst = s_bits + (zz * HY + yy) * 3;
+                    dst[0] = w[0];
+                    dst[1] = w[1];
+                    dst[2] = w[2];
+                }
+                const unsigned m = __ballot_sync(FULL_MASK, (w[0] | w[1] | w[2]) != 0u);
+                if (lane == 0)
+                    s_mask[zz * MW + (yb >> 5)] = m;
             }
-            s_bits[idx] = w;
         }
         __syncthreads();
 
         unsigned out[TZ];
         for (int zb = 0; zb < HZ; zb += ZB) {
-            // 2a. pass X: warp per row, lane = x offset in the tile
-            for (int r = warp; r < ZB * HY; r += THREADS / 32) {
-                const int zz = zb + r / HY, yy = r % HY;
-                unsigned lbl = NONE;
-                if (zz < HZ) {
-                    const unsigned *wrow = s_bits + (zz * HY + yy) * 3;
-                    const unsigned a0 = wrow[0], a1 = wrow[1], a2 = wrow[2];
-                    if (a0 | a1 | a2) {
-                        const unsigned left = __funnelshift_r(a0, a1, lane);    // bit i <-> x - 32 + i
-                        const unsigned right = __funnelshift_r(a1, a2, lane);   // bit i <-> x + i
-                        if (right & 1u) {
-                            lbl = CENTER;
-                        } else if (L > 0) {
-                            const unsigned lm = left & (0xffffffffu << (32 - L));
-                            const unsigned rm = (right >> 1) & ((1u << L) - 1u);
-                            const int dl = lm ? __clz(lm) + 1 : 64;
-                            const int dr = rm ? __ffs(rm) : 64;
-                            if (dl <= dr) {
-                                if (dl <= L)
-                                    lbl = ((unsigned)dl << SH_D) | (CENTER - (unsigned)dl);
-                            } else if (dr <= L) {
-                                lbl = ((unsigned)dr << SH_D) | (CENTER + (unsigned)dr);
-                            }
-                        }
-                    }
-                }
-                s_a[r * TX + lane] = lbl;
-            }
-            __syncthreads();
-            // 2b. pass Y: thread per (x, plane of the batch)
+            // 2a. pass X on the non-empty rows: warp w takes plane zb + w
             {
                 const int zz = zb + warp;
                 if (zz < HZ) {
-                    const unsigned *col = s_a + warp * HY * TX + lane;
-                    unsigned *ob = s_b + zz * TY * TX + lane;
-                    unsigned f = NONE;
-                    for (int yy = 0; yy < L; ++yy)
-                        f = min(step(f, STEP_YF, lim), col[yy * TX]);
-#pragma unroll
-                    for (int k = 0; k < TY; ++k) {
-                        f = min(step(f, STEP_YF, lim), col[(L + k) * TX]);
-                        ob[k * TX] = f;
+                    for (int mw = 0; mw < MW; ++mw) {
+                        unsigned m = s_mask[zz * MW + mw];
+                        while (m) {
+                            const int yy = 32 * mw + __ffs(m) - 1;
+                            m &= m - 1u;
+                            const unsigned *wrow = s_bits + (zz * HY + yy) * 3;
+                            const unsigned a0 = wrow[0], a1 = wrow[1], a2 = wrow[2];
+                            const unsigned left = __funnelshift_r(a0, a1, lane);    // bit i <-> x - 32 + i
+                            const unsigned right = __funnelshift_r(a1, a2, lane);   // bit i <-> x + i
+                            unsigned lbl = NONE;
+                            if (right & 1u) {
+                                lbl = CENTER;
+                            } else if (L > 0) {
+                                const unsigned lm = left & (0xffffffffu << (32 - L));
+                                const unsigned rm = (right >> 1) & ((1u << L) - 1u);
+                                const int dl = lm ? __clz(lm) + 1 : 64;
+                                const int dr = rm ? __ffs(rm) : 64;
+                                if (dl <= dr) {
+                                    if (dl <= L)
+                                        lbl = ((unsigned)dl << SH_D) | (CENTER - (unsigned)dl);
+                                } else if (dr <= L) {
+                                    lbl = ((unsigned)dr << SH_D) | (CENTER + (unsigned)dr);
+                                }
+                            }
+                            s_a[(warp * HY + yy) * TX + lane] = lbl;
+                        }
                     }
-                    unsigned bk = NONE;
-                    for (int yy = HY - 1; yy >= L + TY; --yy)
-                        bk = min(step(bk, STEP_YB, lim), col[yy * TX]);
+                }
+            }
+            __syncthreads();
+            // 2b. pass Y: thread per (x, plane of the batch); rows without an
+            //     occupied voxel contribute nothing
+            {
+                const int zz = zb + warp;
+                if (zz < HZ) {
+                    const unsigned *mk = s_mask + zz * MW;
+                    int first = HY, last = -1;
+                    for (int mw = 0; mw < MW; ++mw) {
+                        const unsigned m = mk[mw];
+                        if (m) {
+                            first = min(first, 32 * mw + __ffs(m) - 1);
+                            last = max(last, 32 * mw + 31 - __clz(m));
+                        }
+                    }
+                    unsigned *ob = s_b + zz * TY * TX + lane;
+                    // rows farther than L from the tile's y range cannot reach it
+                    if (last < 0) {   // no occupied row in reach: nothing to propagate
 #pragma unroll
-                    for (int k = TY - 1; k >= 0; --k) {
-                        bk = min(step(bk, STEP_YB, lim), col[(L + k) * TX]);
-                        ob[k * TX] = min(ob[k * TX], bk);
+                        for (int k = 0; k < TY; ++k)
+                            ob[k * TX] = NONE;
+                    } else {
+                        const unsigned *col = s_a + warp * HY * TX + lane;
+                        unsigned f = NONE;
+                        for (int yy = first; yy < L; ++yy)
+                            f = min(step(f, STEP_YF, lim), row_bit(mk, yy) ? col[yy * TX] : NONE);
+#pragma unroll
+                        for (int k = 0; k < TY; ++k) {
+                            const int yy = L + k;
+                            f = min(step(f, STEP_YF, lim), (yy >= first && row_bit(mk, yy)) ? col[yy * TX] : NONE);
+                            ob[k * TX] = f;
+                        }
+                        unsigned bk = NONE;
+                        for (int yy = last; yy >= L + TY; --yy)
+                            bk = min(step(bk, STEP_YB, lim), row_bit(mk, yy) ? col[yy * TX] : NONE);
+#pragma unroll
+                        for (int k = TY - 1; k >= 0; --k) {
+                            const int yy = L + k;
+                            bk = min(step(bk, STEP_YB, lim), (yy <= last && row_bit(mk, yy)) ? col[yy * TX] : NONE);
+                            ob[k * TX] = min(ob[k * TX], bk);
+                        }
                     }
                 }
             }

@@ -67,13 +67,16 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // ---------------------------------------------------------------------------
 // VOH: one thread per target point; lanes of a warp holding the same voxel
 // key are grouped with __match_any_sync and their leader adds the group size
-// (warp-aggregated atomics).  The same is done per 8x8x8 brick for the brick
-// level used by the global search.  Block 0 also resets the scan's ticket,
-// bumps its descriptor epoch and clears the outside counter for this build.
+// (warp-aggregated atomics).  The same grouping feeds the per-brick counts
+// (brick level of the global search), the occupancy bitmask (one atomicOr
+// per word) and the per-tile totals the scan starts from.  Block 0 also
+// resets the scan's ticket, bumps its descriptor epoch and clears the
+// outside counter for this build.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
-                                                   unsigned *__restrict__ bcounts, DevCtl *__restrict__ ctl)
+                                                   unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
+                                                   unsigned *__restrict__ tile_sum, DevCtl *__restrict__ ctl)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->scan_ticket = 0u;
@@ -100,12 +103,27 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     const unsigned bpeers = __match_any_sync(FULL_MASK, bk);
     if (bk >= 0 && lane == __ffs(bpeers) - 1)
         atomicAdd(bcounts + bk, (unsigned)__popc(bpeers));
+    // occupancy bit of the voxel (one atomicOr per word and warp)
+    const int word = key >= 0 ? (key >> 5) : -2;
+    const unsigned wpeers = __match_any_sync(FULL_MASK, word);
+    const unsigned wbits = __reduce_or_sync(wpeers, key >= 0 ? 1u << (key & 31) : 0u);
+    if (word >= 0 && lane == __ffs(wpeers) - 1)
+        atomicOr(occ + word, wbits);
+    // per-tile totals for the scan (one atomicAdd per tile and warp)
+    const int tile = key >= 0 ? (key / SCAN_TILE) : -2;
+    const unsigned tpeers = __match_any_sync(FULL_MASK, tile);
+    if (tile >= 0 && lane == __ffs(tpeers) - 1)
+        atomicAdd(tile_sum + tile, (unsigned)__popc(tpeers));
 }
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             unsigned *bcounts, DevCtl *ctl, cudaStream_t st)
+                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st)
 {
-    k_histogram<<<(n + 255) / 256, 256, 0, st>>>(pts, n, g, keys, counts, bcounts, ctl);
+    // the occupancy bits are rebuilt from zero every build
+    cudaError_t e = cudaMemsetAsync(occ, 0, (size_t)occ_words(g.V) * sizeof(unsigned), st);
+    if (e != cudaSuccess)
+        return e;
+    k_histogram<<<(n + 255) / 256, 256, 0, st>>>(pts, n, g, keys, counts, bcounts, occ, tile_sum, ctl);
     return cudaGetLastError();
 }
 
@@ -114,8 +132,9 @@ cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *k
 // brick offsets, and lists the non-empty bricks in ascending order with their
 // point ranges and slot numbers; it also resets each listed brick's box.  The
 // count and the non-empty flag are scanned together as one 64-bit value
-// (flag count in the high half): each thread sums a contiguous run of bricks,
-// one block-wide scan offsets the runs, and a second pass writes them.
+// (flag count in the high half).  The counts are staged in shared memory with
+// coalesced loads; each thread sums a contiguous run of bricks, one
+// block-wide scan offsets the runs, and a second pass writes them.
 // ---------------------------------------------------------------------------
 constexpr int BS_THREADS = 1024;
 
@@ -124,59 +143,76 @@ __device__ __forceinline__ unsigned long long brick_pair(unsigned c)
     return (unsigned long long)c | ((unsigned long long)(c != 0u) << 32);
 }
 
+constexpr int BS_CHUNK = 24576;   // bricks staged in shared memory per pass (96 KB)
+
 __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__restrict__ bcounts, int nbt,
                                                            unsigned *__restrict__ boff, int *__restrict__ list,
                                                            uint2 *__restrict__ range, int *__restrict__ bslot,
                                                            uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
 {
+    extern __shared__ unsigned s_c[];   // [BS_CHUNK]
     __shared__ unsigned long long s_w[BS_THREADS / 32];
+    __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // Thread t owns the contiguous bricks [t*per, (t+1)*per).
-    const int per = (nbt + BS_THREADS - 1) / BS_THREADS;
-    const int i0 = min(tid * per, nbt), i1 = min(i0 + per, nbt);
-    unsigned long long sum = 0ull;
-    for (int i = i0; i < i1; ++i)
-        sum += brick_pair(__ldg(bcounts + i));
-    unsigned long long incl = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, d);
-        if (lane >= d)
-            incl += y;
-    }
-    if (lane == 31)
-        s_w[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned long long w = s_w[lane];
-        unsigned long long wi = w;
+    if (tid == 0)
+        s_carry = 0ull;
+    for (int c0 = 0; c0 < nbt; c0 += BS_CHUNK) {
+        const int cn = min(BS_CHUNK, nbt - c0);
+        for (int i = tid; i < cn; i += BS_THREADS)   // coalesced
+            s_c[i] = __ldg(bcounts + c0 + i);
+        __syncthreads();
+        // thread t owns the contiguous bricks [t*per, (t+1)*per) of the chunk
+        const int per = (cn + BS_THREADS - 1) / BS_THREADS;
+        const int i0 = min(tid * per, cn), i1 = min(i0 + per, cn);
+        unsigned long long sum = 0ull;
+        for (int i = i0; i < i1; ++i)
+            sum += brick_pair(s_c[i]);
+        unsigned long long incl = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(FULL_MASK, wi, d);
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, d);
             if (lane >= d)
-                wi += y;
+                incl += y;
         }
-        s_w[lane] = wi - w;
-    }
-    __syncthreads();
-    unsigned long long run = s_w[warp] + (incl - sum);
-    for (int i = i0; i < i1; ++i) {
-        const unsigned c = __ldg(bcounts + i);
-        const unsigned start = (unsigned)run;
-        boff[i] = start;
-        if (c) {
-            const int slot = (int)(run >> 32);
-            list[slot] = i;
-            range[slot] = make_uint2(start, start + c);
-            bslot[i] = slot;
-            boxord[2 * slot] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);   // min
-            boxord[2 * slot + 1] = make_uint4(0u, 0u, 0u, 0u);                          // max
+        if (lane == 31)
+            s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long w = s_w[lane];
+            unsigned long long wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(FULL_MASK, wi, d);
+                if (lane >= d)
+                    wi += y;
+            }
+            s_w[lane] = wi - w;
         }
-        run += brick_pair(c);
+        __syncthreads();
+        unsigned long long run = s_carry + s_w[warp] + (incl - sum);
+        for (int i = i0; i < i1; ++i) {
+            const unsigned c = s_c[i];
+            const int bi = c0 + i;
+            const unsigned start = (unsigned)run;
+            boff[bi] = start;
+            if (c) {
+                const int slot = (int)(run >> 32);
+                list[slot] = bi;
+                range[slot] = make_uint2(start, start + c);
+                bslot[bi] = slot;
+                boxord[2 * slot] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);   // min
+                boxord[2 * slot + 1] = make_uint4(0u, 0u, 0u, 0u);                          // max
+            }
+            run += brick_pair(c);
+        }
+        __syncthreads();
+        if (tid == BS_THREADS - 1)
+            s_carry = run;
+        __syncthreads();
     }
-    if (tid == BS_THREADS - 1) {
-        boff[nbt] = (unsigned)run;
-        ctl->n_bricks = (int)(run >> 32);
+    if (tid == 0) {
+        boff[nbt] = (unsigned)s_carry;
+        ctl->n_bricks = (int)(s_carry >> 32);
     }
 }
 
@@ -184,27 +220,33 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st)
 {
     const int nbt = g.bx * g.by * g.bz;
-    k_brick_scan<<<1, BS_THREADS, 0, st>>>(bcounts, nbt, boff, list, range, bslot, boxord, ctl);
+    const size_t smem = BS_CHUNK * sizeof(unsigned);
+    cudaError_t e = cudaFuncSetAttribute(k_brick_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_brick_scan<<<1, BS_THREADS, smem, st>>>(bcounts, nbt, boff, list, range, bslot, boxord, ctl);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // MOC as a single-pass exclusive scan with decoupled lookback.
 //
-// Each CTA takes the next tile of 4096 counts from an atomic ticket (so
-// every tile it waits on has already started), scans it, publishes its
-// aggregate, then looks back over its predecessors' descriptors, 128 at a
-// time (four per lane), until it meets an inclusive prefix.  A descriptor is one 64-bit word
+// A tile is 16384 voxels: 512 threads, each owning the 32 voxels of one
+// occupancy word.  Each CTA takes the next tile from an atomic ticket (so
+// every tile it waits on has already started).  The histogram already
+// summed every tile's counts, so the CTA publishes its aggregate at once --
+// no load of the tile's data stands in the chain between tiles -- and resets
+// that sum for the next build.  It then reads its occupancy words, gathers
+// the counts of the occupied voxels only, scans them, and looks back over
+// its predecessors' descriptors, 512 per round (one per thread), down to the
+// nearest inclusive prefix.  A descriptor is one 64-bit word
 // [epoch:30 | flag:2 | value:32], so flag and value are read together; the
-// epoch (bumped by the histogram kernel each build) makes the previous
-// build's descriptors invalid without clearing them.  The wait is bounded by
-// the global timer: on expiry the tile sets DEVERR_TIMEOUT and publishes a
-// prefix anyway, so no successor waits on it.
-//
-// The same pass writes the occupancy bitmask (bit v set iff count[v] > 0).
+// epoch (bumped by the histogram each build) retires the previous build's
+// descriptors without clearing them.  Every wait is bounded by the global
+// timer: on expiry the CTA sets DEVERR_TIMEOUT and publishes a prefix anyway,
+// so no successor waits on it.
 // ---------------------------------------------------------------------------
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = SCAN_TILE / SCAN_THREADS;   // 16
+constexpr int SCAN_THREADS = SCAN_TILE / 32;   // 512
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 constexpr unsigned long long DESC_AGG = 1ull << 32;
 constexpr unsigned long long DESC_PREFIX = 2ull << 32;
@@ -237,44 +279,12 @@ __device__ __forceinline__ unsigned warp_sum_u32(unsigned v)
     return v;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restrict__ counts, long long V,
-                                                       unsigned *__restrict__ off, unsigned *__restrict__ occ,
-                                                       unsigned long long *__restrict__ desc,
-                                                       DevCtl *__restrict__ ctl, int skip_tile)
+// Exclusive block-wide scan of one value per thread; returns the thread's
+// exclusive prefix, *total gets the block total.  Uses s_w[SCAN_WARPS].
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_w, unsigned *total)
 {
-    __shared__ unsigned s_tile, s_excl;
-    __shared__ unsigned s_warp[SCAN_WARPS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0)
-        s_tile = atomicAdd(&ctl->scan_ticket, 1u);
-    __syncthreads();
-    const unsigned tile = s_tile;
-    const unsigned long long epoch = (unsigned long long)(*(volatile unsigned *)&ctl->scan_epoch & 0x3fffffffu);
-    const unsigned long long tag = epoch << 34;
-
-    const long long base = (long long)tile * SCAN_TILE + (long long)tid * SCAN_ITEMS;
-    unsigned c[SCAN_ITEMS];
-    if (base + SCAN_ITEMS <= V) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(counts + base);
-#pragma unroll
-        for (int k = 0; k < SCAN_ITEMS / 4; ++k) {
-            const uint4 u = __ldcs(p + k);
-            c[4 * k + 0] = u.x; c[4 * k + 1] = u.y; c[4 * k + 2] = u.z; c[4 * k + 3] = u.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < SCAN_ITEMS; ++i)
-            c[i] = (base + i < V) ? counts[base + i] : 0u;
-    }
-    unsigned bits = 0u, sum = 0u;
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        bits |= (c[i] != 0u ? 1u : 0u) << i;
-        const unsigned t = c[i];
-        c[i] = sum;   // exclusive within the thread
-        sum += t;
-    }
-    unsigned incl = sum;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const unsigned y = __shfl_up_sync(FULL_MASK, incl, d);
@@ -282,11 +292,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
             incl += y;
     }
     if (lane == 31)
-        s_warp[warp] = incl;
+        s_w[warp] = incl;
     __syncthreads();
-
     if (warp == 0) {
-        const unsigned w = (lane < SCAN_WARPS) ? s_warp[lane] : 0u;
+        const unsigned w = lane < SCAN_WARPS ? s_w[lane] : 0u;
         unsigned wi = w;
 #pragma unroll
         for (int d = 1; d < SCAN_WARPS; d <<= 1) {
@@ -294,100 +303,135 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
             if (lane >= d)
                 wi += y;
         }
-        const unsigned agg = __shfl_sync(FULL_MASK, wi, SCAN_WARPS - 1);
         if (lane < SCAN_WARPS)
-            s_warp[lane] = wi - w;
-        unsigned excl = 0u;
-        if (tile == 0) {
-            if (lane == 0 && skip_tile != 0)
-                st_relaxed_u64(desc, tag | DESC_PREFIX | agg);
-        } else {
-            if (lane == 0 && (int)tile != skip_tile)
-                st_relaxed_u64(desc + tile, tag | DESC_AGG | agg);
-            // Lane l inspects the four predecessors look-4l .. look-4l-3, so one
-            // round covers 128 tiles (nearest first).
-            long long look = (long long)tile - 1;
-            const unsigned long long t0 = global_timer_ns();
-            bool gave_up = false;
-            for (;;) {
-                unsigned long long d[4];
-                for (;;) {
-                    bool ready = true;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const long long idx = look - 4 * lane - j;
-                        d[j] = (idx >= 0) ? ld_relaxed_u64(desc + idx) : (tag | DESC_PREFIX);
-                        ready &= ((d[j] >> 34) == epoch) && ((d[j] & (3ull << 32)) != 0ull);
-                    }
-                    if (__all_sync(FULL_MASK, ready))
-                        break;
-                    const bool late = (global_timer_ns() - t0 > SCAN_TIMEOUT_NS) ||
-                                      (*(volatile unsigned *)&ctl->err != 0u);
-                    if (__any_sync(FULL_MASK, late)) {
-                        gave_up = true;
-                        break;
-                    }
-                }
-                if (gave_up)
-                    break;
-                int jp = 4;   // first of this lane's four that is an inclusive prefix
-#pragma unroll
-                for (int j = 3; j >= 0; --j)
-                    if (d[j] & DESC_PREFIX)
-                        jp = j;
-                const unsigned pmask = __ballot_sync(FULL_MASK, jp < 4);
-                if (pmask) {
-                    const int first = __ffs(pmask) - 1;
-                    unsigned v = 0u;
-                    if (lane < first) {
-                        v = (unsigned)d[0] + (unsigned)d[1] + (unsigned)d[2] + (unsigned)d[3];
-                    } else if (lane == first) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            v += (j <= jp) ? (unsigned)d[j] : 0u;
-                    }
-                    excl += warp_sum_u32(v);
-                    break;
-                }
-                excl += warp_sum_u32((unsigned)d[0] + (unsigned)d[1] + (unsigned)d[2] + (unsigned)d[3]);
-                look -= 128;
-            }
-            if (lane == 0) {
-                if (gave_up)
-                    atomicOr(&ctl->err, DEVERR_TIMEOUT);
-                st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + agg));
-            }
-        }
-        if (lane == 0)
-            s_excl = excl;
+            s_w[lane] = wi - w;
+        if (lane == SCAN_WARPS - 1)
+            s_w[SCAN_WARPS] = wi;
     }
     __syncthreads();
-
-    const unsigned prefix = s_excl + s_warp[warp] + (incl - sum);
-    if (base + SCAN_ITEMS <= V) {
-        uint4 *p = reinterpret_cast<uint4 *>(off + base);
-#pragma unroll
-        for (int k = 0; k < SCAN_ITEMS / 4; ++k)
-            p[k] = make_uint4(prefix + c[4 * k], prefix + c[4 * k + 1], prefix + c[4 * k + 2], prefix + c[4 * k + 3]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < SCAN_ITEMS; ++i)
-            if (base + i < V)
-                off[base + i] = prefix + c[i];
-    }
-    if (base <= V - 1 && V - 1 < base + SCAN_ITEMS)
-        off[V] = prefix + sum;
-    // Occupancy: threads 2k and 2k+1 hold the 32 bits of one word.
-    const unsigned hi_bits = __shfl_down_sync(FULL_MASK, bits, 1);
-    if ((tid & 1) == 0 && base < V)
-        occ[base >> 5] = bits | (hi_bits << 16);
+    *total = s_w[SCAN_WARPS];
+    return s_w[warp] + (incl - v);
 }
 
-cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, unsigned *occ,
-                        unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restrict__ counts, long long V,
+                                                       unsigned *__restrict__ off, const unsigned *__restrict__ occ,
+                                                       unsigned *__restrict__ tile_sum,
+                                                       unsigned long long *__restrict__ desc,
+                                                       DevCtl *__restrict__ ctl, int skip_tile)
+{
+    __shared__ unsigned s_tile, s_agg;
+    __shared__ unsigned s_w[SCAN_WARPS + 1];
+    __shared__ unsigned s_first, s_sum[SCAN_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        const unsigned tile = atomicAdd(&ctl->scan_ticket, 1u);
+        const unsigned long long ep = (unsigned long long)(*(volatile unsigned *)&ctl->scan_epoch & 0x3fffffffu);
+        const unsigned agg = tile_sum[tile];
+        tile_sum[tile] = 0u;   // zero again for the next build
+        if ((int)tile != skip_tile)
+            st_relaxed_u64(desc + tile, (ep << 34) | (tile == 0 ? DESC_PREFIX : DESC_AGG) | agg);
+        s_tile = tile;
+        s_agg = agg;
+    }
+    __syncthreads();
+    const unsigned tile = s_tile;
+    const unsigned long long epoch = (unsigned long long)(*(volatile unsigned *)&ctl->scan_epoch & 0x3fffffffu);
+    const unsigned long long tag = epoch << 34;
+
+    // this thread's 32 voxels: counts of the occupied ones only
+    const long long base = (long long)tile * SCAN_TILE + 32ll * tid;
+    const unsigned bits = base < V ? __ldg(occ + (base >> 5)) : 0u;
+    unsigned sum = 0u;
+    for (unsigned m = bits; m; m &= m - 1u)
+        sum += __ldg(counts + base + __ffs(m) - 1);
+    unsigned tile_total;
+    const unsigned thread_excl = block_excl_scan(sum, s_w, &tile_total);
+
+    // lookback: 512 predecessors per round, nearest first
+    unsigned excl = 0u;
+    if (tile > 0) {
+        long long look = (long long)tile - 1;
+        const unsigned long long t0 = global_timer_ns();
+        for (;;) {
+            const long long idx = look - tid;
+            unsigned long long d = tag | DESC_PREFIX;   // before tile 0: an empty prefix
+            bool late = false;
+            if (idx >= 0) {
+                for (;;) {
+                    d = ld_relaxed_u64(desc + idx);
+                    if (((d >> 34) == epoch) && (d & (3ull << 32)))
+                        break;
+                    if (global_timer_ns() - t0 > SCAN_TIMEOUT_NS || *(volatile unsigned *)&ctl->err != 0u) {
+                        late = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (__syncthreads_or(late)) {
+                if (tid == 0)
+                    atomicOr(&ctl->err, DEVERR_TIMEOUT);
+                break;
+            }
+            // nearest inclusive prefix in this round
+            if (tid == 0)
+                s_first = SCAN_THREADS;
+            __syncthreads();
+            if (d & DESC_PREFIX)
+                atomicMin(&s_first, (unsigned)tid);
+            __syncthreads();
+            const unsigned first = s_first;
+            const unsigned v = (unsigned)tid <= first ? (unsigned)d : 0u;
+            const unsigned ws = warp_sum_u32(v);
+            if (lane == 0)
+                s_sum[warp] = ws;
+            __syncthreads();
+            unsigned round = 0u;
+#pragma unroll
+            for (int w = 0; w < SCAN_WARPS; ++w)
+                round += s_sum[w];
+            excl += round;
+            __syncthreads();
+            if (first < SCAN_THREADS)
+                break;
+            look -= SCAN_THREADS;
+        }
+        if (tid == 0)
+            st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + s_agg));
+    }
+
+    // write the 32 offsets of this thread
+    if (base < V) {
+        unsigned run = excl + thread_excl;
+        unsigned o[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            o[i] = run;
+            if ((bits >> i) & 1u)
+                run += __ldg(counts + base + i);
+        }
+        if (base + 32 <= V) {
+            uint4 *p = reinterpret_cast<uint4 *>(off + base);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                p[k] = make_uint4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (base + i < V)
+                    off[base + i] = o[i];
+        }
+        if (base + 32 >= V)   // the thread holding voxel V-1 closes the array
+            off[V] = run;
+    }
+    (void)tile_total;
+}
+
+cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
+                        unsigned *tile_sum, unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st)
 {
     const long long tiles = scan_tiles(g.V);
-    k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(counts, g.V, off, occ, desc, ctl, skip_tile);
+    k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(counts, g.V, off, occ, tile_sum, desc, ctl, skip_tile);
     return cudaGetLastError();
 }
 

@@ -23,8 +23,9 @@ enum KernelId {
 };
 const char *kernel_name(int k);
 
-// Scan tiling (elements per CTA) -- sizes the descriptor array.
-constexpr int SCAN_TILE = 4096;
+// Scan tiling (voxels per CTA, 32 per thread) -- sizes the descriptor array
+// and the per-tile sums.
+constexpr int SCAN_TILE = 16384;
 // Reduction blocks of one ICP iteration (two per SM) -- sizes the partial sums.
 constexpr int REDUCE_MAX_BLOCKS = 1024;
 constexpr int REDUCE_VALUES = 16;
@@ -43,9 +44,9 @@ size_t dilate_smem_bytes(int L);
 
 cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t st);
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             unsigned *bcounts, DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, unsigned *occ,
-                        unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st);
+                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
+                        unsigned *tile_sum, unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st);
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,

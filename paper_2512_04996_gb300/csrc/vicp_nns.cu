@@ -109,7 +109,6 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
 // ---------------------------------------------------------------------------
 constexpr int FB_THREADS = 256;
 constexpr int FB_WARPS = FB_THREADS / 32;
-constexpr int FB_CACHE = 32;   // bounds kept per lane: up to 1024 bricks searched from registers
 
 __device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
 {
@@ -170,36 +169,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
                 best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
             examined += (unsigned long long)n_tgt;
         } else {
-            if (nb > 0 && nb <= 32 * FB_CACHE) {
-                // Same search with every lane's bounds kept in registers
-                // between the two passes.
-                unsigned lbc[FB_CACHE];
-                unsigned long long lbmin = ~0ull;
-#pragma unroll
-                for (int it = 0; it < FB_CACHE; ++it) {
-                    const int k = it * 32 + lane;
-                    lbc[it] = 0xffffffffu;
-                    if (k < nb)
-                        lbc[it] = __float_as_uint(box_lb2(s, __ldg(bbox + 2 * k), __ldg(bbox + 2 * k + 1)));
-                    lbmin = umin64(lbmin, ((unsigned long long)lbc[it] << 32) | (unsigned)k);
-                }
-                lbmin = warp_min_u64(lbmin);
-                const int k0 = (int)(unsigned)lbmin;
-                best = scan_run(bpts, __ldg(brange + k0), s, lane, best, examined);
-#pragma unroll
-                for (int it = 0; it < FB_CACHE; ++it) {
-                    const int k = it * 32 + lane;
-                    unsigned cand = __ballot_sync(FULL_MASK, k != k0 && lbc[it] <= (unsigned)(best >> 32));
-                    while (cand) {
-                        const int src_lane = __ffs(cand) - 1;
-                        cand &= cand - 1u;
-                        const unsigned lb = __shfl_sync(FULL_MASK, lbc[it], src_lane);
-                        if (lb > (unsigned)(best >> 32))
-                            continue;
-                        best = scan_run(bpts, __ldg(brange + it * 32 + src_lane), s, lane, best, examined);
-                    }
-                }
-            } else if (nb > 0) {
+            if (nb > 0) {
                 // (1) brick of smallest bound (ties: smallest slot)
                 unsigned long long lbmin = ~0ull;
                 for (int k = lane; k < nb; k += 32) {

@@ -62,14 +62,15 @@ __device__ void horn_rotation(const double S[9], double E, double R[9])
         s2 += S[k] * S[k];
     const double c2 = -2.0 * s2;
     const double c1 = -8.0 * det3(sxx, sxy, sxz, syx, syy, syz, szx, szy, szz);
-    // det N by Laplace expansion along rows 0 and 1
-    const double a01 = N[0][0] * N[1][1] - N[0][1] * N[1][0], a02 = N[0][0] * N[1][2] - N[0][2] * N[1][0];
-    const double a03 = N[0][0] * N[1][3] - N[0][3] * N[1][0], a12 = N[0][1] * N[1][2] - N[0][2] * N[1][1];
-    const double a13 = N[0][1] * N[1][3] - N[0][3] * N[1][1], a23 = N[0][2] * N[1][3] - N[0][3] * N[1][2];
-    const double b01 = N[2][0] * N[3][1] - N[2][1] * N[3][0], b02 = N[2][0] * N[3][2] - N[2][2] * N[3][0];
-    const double b03 = N[2][0] * N[3][3] - N[2][3] * N[3][0], b12 = N[2][1] * N[3][2] - N[2][2] * N[3][1];
-    const double b13 = N[2][1] * N[3][3] - N[2][3] * N[3][1], b23 = N[2][2] * N[3][3] - N[2][3] * N[3][2];
-    const double c0 = a01 * b23 - a02 * b13 + a03 * b12 + a12 * b03 - a13 * b02 + a23 * b01;
+    // det N by Laplace expansion along rows 0 and 1 (u: 2x2 minors of rows
+    // 0-1, w: of rows 2-3, over column pairs)
+    const double u01 = N[0][0] * N[1][1] - N[0][1] * N[1][0], u02 = N[0][0] * N[1][2] - N[0][2] * N[1][0];
+    const double u03 = N[0][0] * N[1][3] - N[0][3] * N[1][0], u12 = N[0][1] * N[1][2] - N[0][2] * N[1][1];
+    const double u13 = N[0][1] * N[1][3] - N[0][3] * N[1][1], u23 = N[0][2] * N[1][3] - N[0][3] * N[1][2];
+    const double w01 = N[2][0] * N[3][1] - N[2][1] * N[3][0], w02 = N[2][0] * N[3][2] - N[2][2] * N[3][0];
+    const double w03 = N[2][0] * N[3][3] - N[2][3] * N[3][0], w12 = N[2][1] * N[3][2] - N[2][2] * N[3][1];
+    const double w13 = N[2][1] * N[3][3] - N[2][3] * N[3][1], w23 = N[2][2] * N[3][3] - N[2][3] * N[3][2];
+    const double c0 = u01 * w23 - u02 * w13 + u03 * w12 + u12 * w03 - u13 * w02 + u23 * w01;
 
     double l = 0.5 * E + (sxx + syy + szz);
     l += 1e-12 * fabs(l);
@@ -86,33 +87,43 @@ __device__ void horn_rotation(const double S[9], double E, double R[9])
         if (fabs(step) <= 1e-15 * fabs(l))
             break;
     }
-    // adjugate of A = N - l I: cofactor C_ij = (-1)^(i+j) M_ij, M the minor
-    // without row i and column j.
-    double A[4][4];
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j)
-            A[i][j] = N[i][j] - (i == j ? l : 0.0);
-    auto minor = [&](int r, int c) {
-        int rr[3], cc[3];
-        for (int k = 0, t = 0; k < 4; ++k)
-            if (k != r) rr[t++] = k;
-        for (int k = 0, t = 0; k < 4; ++k)
-            if (k != c) cc[t++] = k;
-        return det3(A[rr[0]][cc[0]], A[rr[0]][cc[1]], A[rr[0]][cc[2]], A[rr[1]][cc[0]], A[rr[1]][cc[1]],
-                    A[rr[1]][cc[2]], A[rr[2]][cc[0]], A[rr[2]][cc[1]], A[rr[2]][cc[2]]);
-    };
-    int best = 0;
-    double bestv = -1.0;
-    for (int i = 0; i < 4; ++i) {
-        const double d = fabs(minor(i, i));
-        if (d > bestv) {
-            bestv = d;
-            best = i;
+    // adjugate of A = N - l I (symmetric): column k is (C_k0, C_k1, C_k2, C_k3)
+    // with C_ij = (-1)^(i+j) det(A without row i and column j).  The column
+    // of the largest diagonal cofactor is the best-conditioned eigenvector.
+    const double a00 = N[0][0] - l, a11 = N[1][1] - l, a22 = N[2][2] - l, a33 = N[3][3] - l;
+    const double a01 = N[0][1], a02 = N[0][2], a03 = N[0][3], a12 = N[1][2], a13 = N[1][3], a23 = N[2][3];
+    const double c00 = det3(a11, a12, a13, a12, a22, a23, a13, a23, a33);
+    const double c11 = det3(a00, a02, a03, a02, a22, a23, a03, a23, a33);
+    const double c22 = det3(a00, a01, a03, a01, a11, a13, a03, a13, a33);
+    const double c33 = det3(a00, a01, a02, a01, a11, a12, a02, a12, a22);
+    double v[4];
+    const double m01 = fabs(c00) >= fabs(c11) ? fabs(c00) : fabs(c11);
+    const double m23 = fabs(c22) >= fabs(c33) ? fabs(c22) : fabs(c33);
+    if (m01 >= m23) {
+        if (fabs(c00) >= fabs(c11)) {   // column 0
+            v[0] = c00;
+            v[1] = -det3(a01, a02, a03, a12, a22, a23, a13, a23, a33);
+            v[2] = det3(a01, a02, a03, a11, a12, a13, a13, a23, a33);
+            v[3] = -det3(a01, a02, a03, a11, a12, a13, a12, a22, a23);
+        } else {                        // column 1
+            v[0] = -det3(a01, a12, a13, a02, a22, a23, a03, a23, a33);
+            v[1] = c11;
+            v[2] = -det3(a00, a01, a03, a02, a12, a23, a03, a13, a33);
+            v[3] = det3(a00, a01, a02, a02, a12, a22, a03, a13, a23);
+        }
+    } else {
+        if (fabs(c22) >= fabs(c33)) {   // column 2
+            v[0] = det3(a01, a02, a03, a11, a12, a13, a13, a23, a33);
+            v[1] = -det3(a00, a02, a03, a01, a12, a13, a03, a23, a33);
+            v[2] = c22;
+            v[3] = -det3(a00, a01, a02, a01, a11, a12, a03, a13, a23);
+        } else {                        // column 3
+            v[0] = -det3(a01, a02, a03, a11, a12, a13, a12, a22, a23);
+            v[1] = det3(a00, a02, a03, a01, a12, a13, a02, a22, a23);
+            v[2] = -det3(a00, a01, a03, a01, a11, a13, a02, a12, a23);
+            v[3] = c33;
         }
     }
-    double v[4];
-    for (int j = 0; j < 4; ++j)
-        v[j] = (((j + best) & 1) ? -1.0 : 1.0) * minor(best, j);
     const double inv = 1.0 / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
     const double w = v[0] * inv, x = v[1] * inv, y = v[2] * inv, z = v[3] * inv;
     R[0] = w * w + x * x - y * y - z * z; R[1] = 2.0 * (x * y - w * z);         R[2] = 2.0 * (x * z + w * y);
