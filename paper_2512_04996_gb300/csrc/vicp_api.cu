@@ -199,8 +199,9 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_zero(c, c->tile_sum, "zero scan tile sums"));   // kept at zero between builds
         c->cap_V = V;
     }
-    if (dilate_tiles(c->geom) * 4 > (long long)c->active_tiles.bytes) {
-        TRY(buf_alloc(c, c->active_tiles, (size_t)dilate_tiles(c->geom) * 4, "active tile list"));
+    // enough for the smallest tiles (any L)
+    if (dilate_tiles(c->geom, DILATE_MAX_L) * 4 > (long long)c->active_tiles.bytes) {
+        TRY(buf_alloc(c, c->active_tiles, (size_t)dilate_tiles(c->geom, DILATE_MAX_L) * 4, "active tile list"));
     }
     if (n_bricks > c->cap_bricks) {
         TRY(buf_alloc(c, c->bcounts, (size_t)n_bricks * 4, "brick counts"));

@@ -26,7 +26,7 @@
 //   pass Y: forward and backward running minimum along y;
 //   pass Z: the same along z, then the word is decoded into root and ring.
 //
-// The grid is cut into 32 x 8 x 8 output tiles.  A tile whose L-grown box
+// The grid is cut into 32 x 8 x 32 output tiles (32 x 8 x 8 for L > 16).  A tile whose L-grown box
 // touches no occupied 8x8x8 brick is written "unlabelled" by a light
 // classification kernel.  Every other tile is processed by one CTA, which
 // stages the occupancy bits of the tile grown by L in y and z (three 32-bit
@@ -38,7 +38,7 @@
 namespace vicp {
 
 namespace {
-constexpr int TX = 32, TY = 8, TZ = 8, ZB = 8, THREADS = 256;
+constexpr int TX = 32, TY = 8, ZB = 8, THREADS = 256;
 constexpr unsigned NONE = 0xffffffffu;
 constexpr int SH_D = 18, SH_Z = 12, SH_Y = 6;
 constexpr unsigned CENTER = (31u << SH_Z) | (31u << SH_Y) | 31u;   // zero offsets
@@ -47,12 +47,16 @@ constexpr unsigned STEP_YF = STEP_D - (1u << SH_Y);   // moved from y-1 to y: dy
 constexpr unsigned STEP_YB = STEP_D + (1u << SH_Y);   // moved from y+1 to y: dy += 1
 constexpr unsigned STEP_ZF = STEP_D - (1u << SH_Z);
 constexpr unsigned STEP_ZB = STEP_D + (1u << SH_Z);
+constexpr int TZ_WIDE = 32, TZ_NARROW = 8, L_WIDE_MAX = 16;   // 32-deep tiles while shared memory allows
 
-// Move a word one voxel; words at distance >= L (and NONE) become NONE.
-// `lim` = L << SH_D: a word is >= lim exactly when its distance is >= L.
-__device__ __forceinline__ unsigned step(unsigned v, unsigned inc, unsigned lim)
+// Move a word n voxels (n >= 0) along one axis: the distance grows by n and
+// one offset field shifts by n (inc = the one-voxel step).  A word whose
+// distance would exceed L becomes NONE (NONE stays NONE).
+__device__ __forceinline__ unsigned stepn(unsigned v, int n, unsigned inc, int L)
 {
-    return v >= lim ? NONE : v + inc;
+    if (n > L)
+        return NONE;
+    return v >= ((unsigned)(L + 1 - n) << SH_D) ? NONE : v + (unsigned)n * inc;
 }
 }  // namespace
 
@@ -60,21 +64,24 @@ __device__ __forceinline__ unsigned step(unsigned v, unsigned inc, unsigned lim)
 // grown tile holds an occupied voxel in the staged x window.
 __host__ __device__ constexpr int mask_words(int HY) { return (HY + 31) / 32; }
 
+static int tile_depth(int L) { return L <= L_WIDE_MAX ? TZ_WIDE : TZ_NARROW; }
+
 size_t dilate_smem_bytes(int L)
 {
-    const size_t HY = TY + 2 * L, HZ = TZ + 2 * L;
-    return sizeof(unsigned) * (HZ * HY * 3 + HZ * mask_words((int)HY) + ZB * HY * TX + HZ * TY * TX);
+    const size_t TZ = tile_depth(L), HY = TY + 2 * L, HZ = TZ + 2 * L;
+    return sizeof(unsigned) * (HZ * HY * 3 + HZ * mask_words((int)HY) + mask_words((int)HZ) + ZB * HY * TX +
+                               HZ * TY * TX);
 }
 
-__device__ __forceinline__ bool row_bit(const unsigned *m, int yy) { return (m[yy >> 5] >> (yy & 31)) & 1u; }
+__device__ __forceinline__ bool bit_of(const unsigned *m, int i) { return (m[i >> 5] >> (i & 31)) & 1u; }
 
 // ---------------------------------------------------------------------------
-// Tile classification: a warp per 32 x 8 x 8 tile checks the brick offsets of
-// every 8x8x8 brick its L-grown box touches.  A tile with no point in reach
-// writes "unlabelled" (root -1, ring 255) for its voxels at once; any other
-// tile is appended to the list the shared-memory kernel below works through.
+// Tile classification: a warp per TX x TY x TZ tile checks the brick offsets
+// of every 8x8x8 brick its L-grown box touches.  A tile with no point in
+// reach writes "unlabelled" (root -1, ring 255) for its voxels at once; any
+// other tile is appended to the list the shared-memory kernel works through.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L,
+__global__ void __launch_bounds__(256, 6) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L, int TZ,
                                                       int tiles_x, int tiles_y, long long n_tiles,
                                                       int *__restrict__ active, DevCtl *__restrict__ ctl,
                                                       int *__restrict__ root, unsigned char *__restrict__ ring)
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
     const int nbx = bx1 - bx0 + 1;
     bool any = false;
     for (int bz = bz0; bz <= bz1; ++bz)
-        for (int by = by0; by <= by1; by += 1) {
+        for (int by = by0; by <= by1; ++by) {
             if (lane < nbx) {
                 const int b = bx0 + lane + g.bx * (by + g.by * bz);
                 any |= __ldg(boff + b + 1) > __ldg(boff + b);
@@ -125,11 +132,12 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
 
 // ---------------------------------------------------------------------------
 // Active tiles: a persistent grid works through the list; the last block to
-// finish clears the list length for the next dilation.  Work is proportional
-// to the occupied rows: pass X runs on the rows that hold an occupied voxel
-// in the staged window, pass Y reads pass-X labels only of such rows and
-// skips planes without any.
+// finish clears the list length for the next dilation.  Work follows the
+// occupied rows: pass X runs on rows holding an occupied voxel in the staged
+// window; passes Y and Z step from one occupied row (plane) to the next with
+// the n-voxel shift and evaluate every output row (plane) of the tile.
 // ---------------------------------------------------------------------------
+template <int TZ>
 __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ,
                                                     const int *__restrict__ active, GridGeom g, int L,
                                                     int tiles_x, int tiles_y, long long n_tiles,
@@ -137,12 +145,12 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
                                                     DevCtl *__restrict__ ctl)
 {
     extern __shared__ unsigned smem[];
-    const int HY = TY + 2 * L, HZ = TZ + 2 * L, MW = mask_words(HY);
+    const int HY = TY + 2 * L, HZ = TZ + 2 * L, MW = mask_words(HY), PW = mask_words(HZ);
     unsigned *s_bits = smem;                  // [HZ][HY][3]
-    unsigned *s_mask = s_bits + HZ * HY * 3;  // [HZ][MW]      non-empty rows
-    unsigned *s_a = s_mask + HZ * MW;         // [ZB][HY][TX]  pass X, one z batch (non-empty rows only)
-    unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y, all planes
-    const unsigned lim = (unsigned)L << SH_D;
+    unsigned *s_mask = s_bits + HZ * HY * 3;  // [HZ][MW]      rows holding an occupied voxel
+    unsigned *s_pmask = s_mask + HZ * MW;     // [PW]          planes whose pass-Y output is not all NONE
+    unsigned *s_a = s_pmask + PW;             // [ZB][HY][TX]  pass X, one z batch (occupied rows only)
+    unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y (flagged planes only)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_active = (int)min((long long)*(volatile int *)&ctl->n_active_tiles, n_tiles);
 
@@ -153,7 +161,9 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
         const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
 
         // 1. occupancy windows of the grown tile (a lane per row, a warp per
-        //    32 rows of one plane) and the per-plane masks of non-empty rows
+        //    32 rows of one plane) and the per-plane masks of occupied rows
+        if (tid < PW)
+            s_pmask[tid] = 0u;
         for (int zz = warp; zz < HZ; zz += THREADS / 32) {
             const int z = z0 - L + zz;
             for (int yb = 0; yb < HY; yb += 32) {
@@ -182,115 +192,164 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
         }
         __syncthreads();
 
-        unsigned out[TZ];
         for (int zb = 0; zb < HZ; zb += ZB) {
-            // 2a. pass X on the non-empty rows: warp w takes plane zb + w
-            {
-                const int zz = zb + warp;
-                if (zz < HZ) {
-                    for (int mw = 0; mw < MW; ++mw) {
-                        unsigned m = s_mask[zz * MW + mw];
-                        while (m) {
-                            const int yy = 32 * mw + __ffs(m) - 1;
-                            m &= m - 1u;
-                            const unsigned *wrow = s_bits + (zz * HY + yy) * 3;
-                            const unsigned a0 = wrow[0], a1 = wrow[1], a2 = wrow[2];
-                            const unsigned left = __funnelshift_r(a0, a1, lane);    // bit i <-> x - 32 + i
-                            const unsigned right = __funnelshift_r(a1, a2, lane);   // bit i <-> x + i
-                            unsigned lbl = NONE;
-                            if (right & 1u) {
-                                lbl = CENTER;
-                            } else if (L > 0) {
-                                const unsigned lm = left & (0xffffffffu << (32 - L));
-                                const unsigned rm = (right >> 1) & ((1u << L) - 1u);
-                                const int dl = lm ? __clz(lm) + 1 : 64;
-                                const int dr = rm ? __ffs(rm) : 64;
-                                if (dl <= dr) {
-                                    if (dl <= L)
-                                        lbl = ((unsigned)dl << SH_D) | (CENTER - (unsigned)dl);
-                                } else if (dr <= L) {
-                                    lbl = ((unsigned)dr << SH_D) | (CENTER + (unsigned)dr);
-                                }
+            // 2a. pass X on the occupied rows: warp w takes plane zb + w
+            const int zz = zb + warp;
+            if (zz < HZ) {
+                for (int mw = 0; mw < MW; ++mw) {
+                    unsigned m = s_mask[zz * MW + mw];
+                    while (m) {
+                        const int yy = 32 * mw + __ffs(m) - 1;
+                        m &= m - 1u;
+                        const unsigned *wrow = s_bits + (zz * HY + yy) * 3;
+                        const unsigned a0 = wrow[0], a1 = wrow[1], a2 = wrow[2];
+                        const unsigned left = __funnelshift_r(a0, a1, lane);    // bit i <-> x - 32 + i
+                        const unsigned right = __funnelshift_r(a1, a2, lane);   // bit i <-> x + i
+                        unsigned lbl = NONE;
+                        if (right & 1u) {
+                            lbl = CENTER;
+                        } else if (L > 0) {
+                            const unsigned lm = left & (0xffffffffu << (32 - L));
+                            const unsigned rm = (right >> 1) & ((1u << L) - 1u);
+                            const int dl = lm ? __clz(lm) + 1 : 64;
+                            const int dr = rm ? __ffs(rm) : 64;
+                            if (dl <= dr) {
+                                if (dl <= L)
+                                    lbl = ((unsigned)dl << SH_D) | (CENTER - (unsigned)dl);
+                            } else if (dr <= L) {
+                                lbl = ((unsigned)dr << SH_D) | (CENTER + (unsigned)dr);
                             }
-                            s_a[(warp * HY + yy) * TX + lane] = lbl;
                         }
+                        s_a[(warp * HY + yy) * TX + lane] = lbl;
                     }
                 }
             }
             __syncthreads();
-            // 2b. pass Y: thread per (x, plane of the batch); rows without an
-            //     occupied voxel contribute nothing
-            {
-                const int zz = zb + warp;
-                if (zz < HZ) {
-                    const unsigned *mk = s_mask + zz * MW;
-                    int first = HY, last = -1;
-                    for (int mw = 0; mw < MW; ++mw) {
-                        const unsigned m = mk[mw];
-                        if (m) {
-                            first = min(first, 32 * mw + __ffs(m) - 1);
-                            last = max(last, 32 * mw + 31 - __clz(m));
+            // 2b. pass Y: thread per (x, plane of the batch), stepping over
+            //     the plane's occupied rows
+            if (zz < HZ) {
+                const unsigned *mk = s_mask + zz * MW;
+                bool any_row = false;
+                for (int mw = 0; mw < MW; ++mw)
+                    any_row |= mk[mw] != 0u;
+                if (any_row) {
+                    if (lane == 0)
+                        atomicOr(s_pmask + (zz >> 5), 1u << (zz & 31));
+                    const unsigned *col = s_a + warp * HY * TX + lane;
+                    unsigned *ob = s_b + zz * TY * TX + lane;
+                    // forward: occupied rows below the tile, then every output row
+                    unsigned f = NONE;
+                    int rp = 0;
+                    for (int mw = 0; mw < MW && 32 * mw < L; ++mw) {
+                        unsigned m = mk[mw];
+                        if (32 * mw + 32 > L)
+                            m &= (1u << (L - 32 * mw)) - 1u;
+                        while (m) {
+                            const int r = 32 * mw + __ffs(m) - 1;
+                            m &= m - 1u;
+                            f = min(stepn(f, r - rp, STEP_YF, L), col[r * TX]);
+                            rp = r;
                         }
                     }
-                    unsigned *ob = s_b + zz * TY * TX + lane;
-                    // rows farther than L from the tile's y range cannot reach it
-                    if (last < 0) {   // no occupied row in reach: nothing to propagate
 #pragma unroll
-                        for (int k = 0; k < TY; ++k)
-                            ob[k * TX] = NONE;
-                    } else {
-                        const unsigned *col = s_a + warp * HY * TX + lane;
-                        unsigned f = NONE;
-                        for (int yy = first; yy < L; ++yy)
-                            f = min(step(f, STEP_YF, lim), row_bit(mk, yy) ? col[yy * TX] : NONE);
-#pragma unroll
-                        for (int k = 0; k < TY; ++k) {
-                            const int yy = L + k;
-                            f = min(step(f, STEP_YF, lim), (yy >= first && row_bit(mk, yy)) ? col[yy * TX] : NONE);
-                            ob[k * TX] = f;
+                    for (int k = 0; k < TY; ++k) {
+                        const int y = L + k;
+                        f = stepn(f, y - rp, STEP_YF, L);
+                        if (bit_of(mk, y))
+                            f = min(f, col[y * TX]);
+                        rp = y;
+                        ob[k * TX] = f;
+                    }
+                    // backward: occupied rows above the tile, then every output row
+                    unsigned bk = NONE;
+                    rp = HY - 1;
+                    for (int mw = MW - 1; mw >= 0; --mw) {
+                        if (32 * mw + 31 < L + TY)
+                            break;
+                        unsigned m = mk[mw];
+                        if (32 * mw < L + TY)
+                            m &= ~((1u << (L + TY - 32 * mw)) - 1u);
+                        while (m) {
+                            const int r = 32 * mw + 31 - __clz(m);
+                            m &= ~(1u << (r - 32 * mw));
+                            bk = min(stepn(bk, rp - r, STEP_YB, L), col[r * TX]);
+                            rp = r;
                         }
-                        unsigned bk = NONE;
-                        for (int yy = last; yy >= L + TY; --yy)
-                            bk = min(step(bk, STEP_YB, lim), row_bit(mk, yy) ? col[yy * TX] : NONE);
+                    }
 #pragma unroll
-                        for (int k = TY - 1; k >= 0; --k) {
-                            const int yy = L + k;
-                            bk = min(step(bk, STEP_YB, lim), (yy <= last && row_bit(mk, yy)) ? col[yy * TX] : NONE);
-                            ob[k * TX] = min(ob[k * TX], bk);
-                        }
+                    for (int k = TY - 1; k >= 0; --k) {
+                        const int y = L + k;
+                        bk = stepn(bk, rp - y, STEP_YB, L);
+                        if (bit_of(mk, y))
+                            bk = min(bk, col[y * TX]);
+                        rp = y;
+                        ob[k * TX] = min(ob[k * TX], bk);
                     }
                 }
             }
             __syncthreads();
         }
-        // 3. pass Z: thread per (x, y) column of the tile
+
+        // 3. pass Z: thread per (x, y) column, stepping over the planes whose
+        //    pass-Y output is not all NONE
+        unsigned out[TZ];
         {
             const unsigned *col = s_b + warp * TX + lane;
             unsigned f = NONE;
-            for (int zz = 0; zz < L; ++zz)
-                f = min(step(f, STEP_ZF, lim), col[zz * TY * TX]);
+            int rp = 0;
+            for (int pw = 0; pw < PW && 32 * pw < L; ++pw) {
+                unsigned m = s_pmask[pw];
+                if (32 * pw + 32 > L)
+                    m &= (1u << (L - 32 * pw)) - 1u;
+                while (m) {
+                    const int r = 32 * pw + __ffs(m) - 1;
+                    m &= m - 1u;
+                    f = min(stepn(f, r - rp, STEP_ZF, L), col[r * TY * TX]);
+                    rp = r;
+                }
+            }
 #pragma unroll
             for (int k = 0; k < TZ; ++k) {
-                f = min(step(f, STEP_ZF, lim), col[(L + k) * TY * TX]);
+                const int z = L + k;
+                f = stepn(f, z - rp, STEP_ZF, L);
+                if (bit_of(s_pmask, z))
+                    f = min(f, col[z * TY * TX]);
+                rp = z;
                 out[k] = f;
             }
             unsigned bk = NONE;
-            for (int zz = HZ - 1; zz >= L + TZ; --zz)
-                bk = min(step(bk, STEP_ZB, lim), col[zz * TY * TX]);
+            rp = HZ - 1;
+            for (int pw = PW - 1; pw >= 0; --pw) {
+                if (32 * pw + 31 < L + TZ)
+                    break;
+                unsigned m = s_pmask[pw];
+                if (32 * pw < L + TZ)
+                    m &= ~((1u << (L + TZ - 32 * pw)) - 1u);
+                while (m) {
+                    const int r = 32 * pw + 31 - __clz(m);
+                    m &= ~(1u << (r - 32 * pw));
+                    bk = min(stepn(bk, rp - r, STEP_ZB, L), col[r * TY * TX]);
+                    rp = r;
+                }
+            }
 #pragma unroll
             for (int k = TZ - 1; k >= 0; --k) {
-                bk = min(step(bk, STEP_ZB, lim), col[(L + k) * TY * TX]);
+                const int z = L + k;
+                bk = stepn(bk, rp - z, STEP_ZB, L);
+                if (bit_of(s_pmask, z))
+                    bk = min(bk, col[z * TY * TX]);
+                rp = z;
                 out[k] = min(out[k], bk);
             }
         }
         // 4. decode and store
         const int x = x0 + lane, y = y0 + warp;
         if (x < g.nx && y < g.ny) {
+            const long long plane = (long long)g.nx * g.ny;
+            long long v = x + (long long)g.nx * y + plane * z0;
 #pragma unroll
-            for (int k = 0; k < TZ; ++k) {
-                const int z = z0 + k;
-                if (z < g.nz) {
-                    const long long v = x + (long long)g.nx * (y + (long long)g.ny * z);
+            for (int k = 0; k < TZ; ++k, v += plane) {
+                if (z0 + k < g.nz) {
                     const unsigned w = out[k];
                     int r = -1;
                     unsigned char d = 255;
@@ -298,7 +357,7 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
                         const int dz = (int)((w >> SH_Z) & 63u) - 31;
                         const int dy = (int)((w >> SH_Y) & 63u) - 31;
                         const int dx = (int)(w & 63u) - 31;
-                        r = (int)(v + dx + (long long)g.nx * (dy + (long long)g.ny * dz));
+                        r = (int)(v + dx + (long long)g.nx * dy + plane * dz);
                         d = (unsigned char)(w >> SH_D);
                     }
                     root[v] = r;
@@ -318,31 +377,44 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
     }
 }
 
-cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
-                          int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
+template <int TZ>
+static cudaError_t run_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
+                              int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
 {
     const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
     const long long tiles = (long long)tiles_x * tiles_y * tiles_z;
-    k_dilate_tiles<<<(unsigned)((tiles * 32 + 255) / 256), 256, 0, st>>>(boff, g, L, tiles_x, tiles_y, tiles, active,
-                                                                         ctl, root, ring);
+    k_dilate_tiles<<<(unsigned)((tiles * 32 + 255) / 256), 256, 0, st>>>(boff, g, L, TZ, tiles_x, tiles_y, tiles,
+                                                                         active, ctl, root, ring);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
     const size_t smem = dilate_smem_bytes(L);
-    if (smem > 48 * 1024) {   // opt in above the default limit (a per-device function attribute)
-        e = cudaFuncSetAttribute(k_dilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-    }
+    e = cudaFuncSetAttribute(k_dilate<TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dilate, THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dilate<TZ>, THREADS, smem);
     if (e != cudaSuccess)
         return e;
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > tiles)
         grid = tiles;
-    k_dilate<<<(unsigned)grid, THREADS, smem, st>>>(occ, active, g, L, tiles_x, tiles_y, tiles, root, ring, ctl);
+    k_dilate<TZ><<<(unsigned)grid, THREADS, smem, st>>>(occ, active, g, L, tiles_x, tiles_y, tiles, root, ring, ctl);
     return cudaGetLastError();
+}
+
+long long dilate_tiles(const GridGeom &g, int L)
+{
+    const int TZ = tile_depth(L);
+    return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * ((g.nz + TZ - 1) / TZ);
+}
+
+cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
+                          int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
+{
+    if (tile_depth(L) == TZ_WIDE)
+        return run_dilate<TZ_WIDE>(occ, boff, g, L, active, root, ring, ctl, sms, st);
+    return run_dilate<TZ_NARROW>(occ, boff, g, L, active, root, ring, ctl, sms, st);
 }
 
 }  // namespace vicp

@@ -158,8 +158,16 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__res
         s_carry = 0ull;
     for (int c0 = 0; c0 < nbt; c0 += BS_CHUNK) {
         const int cn = min(BS_CHUNK, nbt - c0);
-        for (int i = tid; i < cn; i += BS_THREADS)   // coalesced
-            s_c[i] = __ldg(bcounts + c0 + i);
+        for (int i0 = tid; i0 < cn; i0 += 8 * BS_THREADS) {   // coalesced, eight loads in flight
+            unsigned v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                v[k] = (i0 + k * BS_THREADS < cn) ? __ldg(bcounts + c0 + i0 + k * BS_THREADS) : 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (i0 + k * BS_THREADS < cn)
+                    s_c[i0 + k * BS_THREADS] = v[k];
+        }
         __syncthreads();
         // thread t owns the contiguous bricks [t*per, (t+1)*per) of the chunk
         const int per = (cn + BS_THREADS - 1) / BS_THREADS;
@@ -400,29 +408,36 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
             st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + s_agg));
     }
 
-    // write the 32 offsets of this thread
-    if (base < V) {
+    // the 32 offsets of this thread, staged in shared memory (row stride 33
+    // words: conflict-free both ways) and written out with coalesced 16-byte
+    // stores
+    extern __shared__ unsigned s_off[];   // [SCAN_THREADS][33]
+    {
         unsigned run = excl + thread_excl;
-        unsigned o[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-            o[i] = run;
+            s_off[tid * 33 + i] = run;
             if ((bits >> i) & 1u)
                 run += __ldg(counts + base + i);
         }
-        if (base + 32 <= V) {
-            uint4 *p = reinterpret_cast<uint4 *>(off + base);
+        if (base < V && base + 32 >= V)   // the thread holding voxel V-1 closes the array
+            off[V] = run;
+    }
+    __syncthreads();
+    const long long tbase = (long long)tile * SCAN_TILE;
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                p[k] = make_uint4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+    for (int j = 0; j < SCAN_TILE / (4 * SCAN_THREADS); ++j) {
+        const int v = 4 * tid + 4 * SCAN_THREADS * j;   // voxel within the tile
+        const unsigned *r = s_off + (v >> 5) * 33 + (v & 31);
+        const long long gv = tbase + v;
+        if (gv + 4 <= V) {
+            *reinterpret_cast<uint4 *>(off + gv) = make_uint4(r[0], r[1], r[2], r[3]);
         } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (base + i < V)
-                    off[base + i] = o[i];
+            for (int i = 0; i < 4; ++i)
+                if (gv + i < V)
+                    off[gv + i] = r[i];
         }
-        if (base + 32 >= V)   // the thread holding voxel V-1 closes the array
-            off[V] = run;
     }
     (void)tile_total;
 }
@@ -431,7 +446,11 @@ cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off
                         unsigned *tile_sum, unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st)
 {
     const long long tiles = scan_tiles(g.V);
-    k_scan<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(counts, g.V, off, occ, tile_sum, desc, ctl, skip_tile);
+    const size_t smem = (size_t)SCAN_THREADS * 33 * sizeof(unsigned);
+    cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    k_scan<<<(unsigned)tiles, SCAN_THREADS, smem, st>>>(counts, g.V, off, occ, tile_sum, desc, ctl, skip_tile);
     return cudaGetLastError();
 }
 

@@ -58,10 +58,7 @@ cudaError_t launch_brick_boxes(const uint4 *boxord, float4 *box, const DevCtl *c
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
                           int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st);
-inline long long dilate_tiles(const GridGeom &g)
-{
-    return (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * ((g.nz + 7) / 8);
-}
+long long dilate_tiles(const GridGeom &g, int L);   // tiles of the dilation for depth L
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);

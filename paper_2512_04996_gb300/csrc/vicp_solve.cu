@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
         return;
     __shared__ PoseF sp;
     __shared__ double s_red[RED_THREADS / 32][REDUCE_VALUES];
+    __shared__ float s_hi[RED_THREADS / 32][REDUCE_VALUES], s_lo[RED_THREADS / 32][REDUCE_VALUES];
     __shared__ int s_last;
     if (threadIdx.x == 0)
         load_pose_f(pose, sp);
@@ -243,16 +244,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             v = df_add(v, df_shfl_xor(v, o));
-        if (lane == 0)
-            s_red[warp][k] = (double)v.hi + (double)v.lo;
+        if (lane == 0) {
+            s_hi[warp][k] = v.hi;
+            s_lo[warp][k] = v.lo;
+        }
     }
     __syncthreads();
+    // the block's warps in double-float, then one FP64 value per thread 0..15
     if (threadIdx.x < REDUCE_VALUES) {
-        double v = 0.0;
+        dfl v = {s_hi[0][threadIdx.x], s_lo[0][threadIdx.x]};
 #pragma unroll
-        for (int w = 0; w < RED_THREADS / 32; ++w)
-            v += s_red[w][threadIdx.x];
-        partials[blockIdx.x * REDUCE_VALUES + threadIdx.x] = v;
+        for (int w = 1; w < RED_THREADS / 32; ++w)
+            v = df_add(v, dfl{s_hi[w][threadIdx.x], s_lo[w][threadIdx.x]});
+        partials[blockIdx.x * REDUCE_VALUES + threadIdx.x] = (double)v.hi + (double)v.lo;
         __threadfence();
     }
     __syncthreads();
