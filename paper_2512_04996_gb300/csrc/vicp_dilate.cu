@@ -81,24 +81,27 @@ __device__ __forceinline__ bool bit_of(const unsigned *m, int i) { return (m[i >
 // reach writes "unlabelled" (root -1, ring 255) for its voxels at once; any
 // other tile is appended to the list the shared-memory kernel works through.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 6) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L, int TZ,
-                                                      int tiles_x, int tiles_y, long long n_tiles,
+__global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L, int TZ,
+                                                      int tiles_x, int tiles_y, int n_tiles,
                                                       int *__restrict__ active, DevCtl *__restrict__ ctl,
                                                       int *__restrict__ root, unsigned char *__restrict__ ring)
 {
-    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int t = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= n_tiles)
         return;   // whole warp
-    const int x0 = (int)(t % tiles_x) * TX;
-    const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
-    const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
+    const int txy = tiles_x * tiles_y;
+    const int x0 = (t % tiles_x) * TX;
+    const int y0 = ((t / tiles_x) % tiles_y) * TY;
+    const int z0 = (t / txy) * TZ;
     const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
     const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
     const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
     const int nbx = bx1 - bx0 + 1;
     bool any = false;
+#pragma unroll 1
     for (int bz = bz0; bz <= bz1; ++bz)
+#pragma unroll 1
         for (int by = by0; by <= by1; ++by) {
             if (lane < nbx) {
                 const int b = bx0 + lane + g.bx * (by + g.by * bz);
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(256, 6) k_dilate_tiles(const unsigned *__restr
         if (lane == 0) {
             const int slot = atomicAdd(&ctl->n_active_tiles, 1);
             if (slot < n_tiles)
-                active[slot] = (int)t;
+                active[slot] = t;
             else
                 atomicOr(&ctl->err, DEVERR_BOUNDS);
         }
@@ -121,8 +124,10 @@ __global__ void __launch_bounds__(256, 6) k_dilate_tiles(const unsigned *__restr
     const long long plane = (long long)g.nx * g.ny;
     const int ny_t = min(TY, g.ny - y0), nz_t = min(TZ, g.nz - z0);
     long long vz = x + (long long)g.nx * y0 + plane * z0;
+#pragma unroll 1
     for (int zl = 0; zl < nz_t; ++zl, vz += plane) {
         long long v = vz;
+#pragma unroll 2
         for (int yl = 0; yl < ny_t; ++yl, v += g.nx) {
             root[v] = -1;
             ring[v] = 255;
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(256, 6) k_dilate_tiles(const unsigned *__restr
 template <int TZ>
 __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ,
                                                     const int *__restrict__ active, GridGeom g, int L,
-                                                    int tiles_x, int tiles_y, long long n_tiles,
+                                                    int tiles_x, int tiles_y, int n_tiles,
                                                     int *__restrict__ root, unsigned char *__restrict__ ring,
                                                     DevCtl *__restrict__ ctl)
 {
@@ -152,13 +157,14 @@ __global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__
     unsigned *s_a = s_pmask + PW;             // [ZB][HY][TX]  pass X, one z batch (occupied rows only)
     unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y (flagged planes only)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_active = (int)min((long long)*(volatile int *)&ctl->n_active_tiles, n_tiles);
+    const int n_active = min(*(volatile int *)&ctl->n_active_tiles, n_tiles);
+    const int txy = tiles_x * tiles_y;
 
     for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
-        const long long t = __ldg(active + it);
-        const int x0 = (int)(t % tiles_x) * TX;
-        const int y0 = (int)((t / tiles_x) % tiles_y) * TY;
-        const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * TZ;
+        const int t = __ldg(active + it);
+        const int x0 = (t % tiles_x) * TX;
+        const int y0 = ((t / tiles_x) % tiles_y) * TY;
+        const int z0 = (t / txy) * TZ;
 
         // 1. occupancy windows of the grown tile (a lane per row, a warp per
         //    32 rows of one plane) and the per-plane masks of occupied rows
@@ -382,9 +388,9 @@ static cudaError_t run_dilate(const unsigned *occ, const unsigned *boff, const G
                               int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
 {
     const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
-    const long long tiles = (long long)tiles_x * tiles_y * tiles_z;
-    k_dilate_tiles<<<(unsigned)((tiles * 32 + 255) / 256), 256, 0, st>>>(boff, g, L, TZ, tiles_x, tiles_y, tiles,
-                                                                         active, ctl, root, ring);
+    const int tiles = tiles_x * tiles_y * tiles_z;   // < V < 2^31
+    k_dilate_tiles<<<(unsigned)(((long long)tiles * 32 + 255) / 256), 256, 0, st>>>(boff, g, L, TZ, tiles_x, tiles_y,
+                                                                                    tiles, active, ctl, root, ring);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -396,10 +402,10 @@ static cudaError_t run_dilate(const unsigned *occ, const unsigned *boff, const G
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dilate<TZ>, THREADS, smem);
     if (e != cudaSuccess)
         return e;
-    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    int grid = sms * (per_sm > 0 ? per_sm : 1);
     if (grid > tiles)
         grid = tiles;
-    k_dilate<TZ><<<(unsigned)grid, THREADS, smem, st>>>(occ, active, g, L, tiles_x, tiles_y, tiles, root, ring, ctl);
+    k_dilate<TZ><<<grid, THREADS, smem, st>>>(occ, active, g, L, tiles_x, tiles_y, tiles, root, ring, ctl);
     return cudaGetLastError();
 }
 
