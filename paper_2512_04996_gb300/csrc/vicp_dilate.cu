@@ -26,9 +26,9 @@
 //   pass Y: forward and backward running minimum along y;
 //   pass Z: the same along z, then the word is decoded into root and ring.
 //
-// The grid is cut into 32 x 8 x 32 output tiles (32 x 8 x 8 for L > 16).  A tile whose L-grown box
-// touches no occupied 8x8x8 brick is written "unlabelled" by a light
-// classification kernel.  Every other tile is processed by one CTA, which
+// The grid is cut into 32 x 8 x 32 output tiles (32 x 8 x 8 for L > 16).  A
+// tile whose L-grown box touches no occupied 8x8x8 brick is written
+// "unlabelled" by a light classification kernel.  Every other tile is processed by one CTA, which
 // stages the occupancy bits of the tile grown by L in y and z (three 32-bit
 // words per row cover x in [x0-32, x0+64)), runs passes X and Y for eight
 // z-planes at a time into shared memory, then pass Z, and writes root and
@@ -76,20 +76,19 @@ size_t dilate_smem_bytes(int L)
 __device__ __forceinline__ bool bit_of(const unsigned *m, int i) { return (m[i >> 5] >> (i & 31)) & 1u; }
 
 // ---------------------------------------------------------------------------
-// Tile classification: a warp per TX x TY x TZ tile checks the brick offsets
+// Tile classification: a CTA per TX x TY x TZ tile checks the brick offsets
 // of every 8x8x8 brick its L-grown box touches.  A tile with no point in
-// reach writes "unlabelled" (root -1, ring 255) for its voxels at once; any
-// other tile is appended to the list the shared-memory kernel works through.
+// reach writes "unlabelled" (root -1, ring 255) for its voxels at once (a
+// warp per row); any other tile is appended to the list the shared-memory
+// kernel works through.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L, int TZ,
                                                       int tiles_x, int tiles_y, int n_tiles,
                                                       int *__restrict__ active, DevCtl *__restrict__ ctl,
                                                       int *__restrict__ root, unsigned char *__restrict__ ring)
 {
-    const int t = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (t >= n_tiles)
-        return;   // whole warp
+    const int t = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int txy = tiles_x * tiles_y;
     const int x0 = (t % tiles_x) * TX;
     const int y0 = ((t / tiles_x) % tiles_y) * TY;
@@ -97,19 +96,14 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
     const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
     const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
     const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
-    const int nbx = bx1 - bx0 + 1;
-    bool any = false;
-#pragma unroll 1
-    for (int bz = bz0; bz <= bz1; ++bz)
-#pragma unroll 1
-        for (int by = by0; by <= by1; ++by) {
-            if (lane < nbx) {
-                const int b = bx0 + lane + g.bx * (by + g.by * bz);
-                any |= __ldg(boff + b + 1) > __ldg(boff + b);
-            }
-        }
-    if (__any_sync(FULL_MASK, any)) {
-        if (lane == 0) {
+    const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nb = nbx * nby * (bz1 - bz0 + 1);
+    int any = 0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const int b = (bx0 + k % nbx) + g.bx * ((by0 + (k / nbx) % nby) + g.by * (bz0 + k / (nbx * nby)));
+        any |= __ldg(boff + b + 1) > __ldg(boff + b);
+    }
+    if (__syncthreads_or(any)) {
+        if (threadIdx.x == 0) {
             const int slot = atomicAdd(&ctl->n_active_tiles, 1);
             if (slot < n_tiles)
                 active[slot] = t;
@@ -121,17 +115,12 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
     const int x = x0 + lane;
     if (x >= g.nx)
         return;
-    const long long plane = (long long)g.nx * g.ny;
     const int ny_t = min(TY, g.ny - y0), nz_t = min(TZ, g.nz - z0);
-    long long vz = x + (long long)g.nx * y0 + plane * z0;
 #pragma unroll 1
-    for (int zl = 0; zl < nz_t; ++zl, vz += plane) {
-        long long v = vz;
-#pragma unroll 2
-        for (int yl = 0; yl < ny_t; ++yl, v += g.nx) {
-            root[v] = -1;
-            ring[v] = 255;
-        }
+    for (int r = warp; r < ny_t * nz_t; r += blockDim.x / 32) {
+        const long long v = x + (long long)g.nx * (y0 + r % ny_t + (long long)g.ny * (z0 + r / ny_t));
+        root[v] = -1;
+        ring[v] = 255;
     }
 }
 
@@ -389,8 +378,7 @@ static cudaError_t run_dilate(const unsigned *occ, const unsigned *boff, const G
 {
     const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
     const int tiles = tiles_x * tiles_y * tiles_z;   // < V < 2^31
-    k_dilate_tiles<<<(unsigned)(((long long)tiles * 32 + 255) / 256), 256, 0, st>>>(boff, g, L, TZ, tiles_x, tiles_y,
-                                                                                    tiles, active, ctl, root, ring);
+    k_dilate_tiles<<<tiles, 256, 0, st>>>(boff, g, L, TZ, tiles_x, tiles_y, tiles, active, ctl, root, ring);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

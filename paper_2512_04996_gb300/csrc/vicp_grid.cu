@@ -224,10 +224,93 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__res
     }
 }
 
+// Many bricks per CTA in parallel: CTA b owns bricks [1024 b, 1024 b + 1024)
+// and finds its starting offset and slot by summing the counts of all
+// earlier bricks itself (cheap while bricks are few: at most 64 CTAs).
+constexpr int BM_THREADS = 1024;
+constexpr int BM_MAX_BRICKS = 64 * BM_THREADS;
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULL_MASK, v, o);
+    if (lane == 0)
+        s_w[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0ull;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+        t += s_w[w];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned *__restrict__ bcounts, int nbt,
+                                                                 unsigned *__restrict__ boff, int *__restrict__ list,
+                                                                 uint2 *__restrict__ range, int *__restrict__ bslot,
+                                                                 uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
+{
+    __shared__ unsigned long long s_w[BM_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b0 = blockIdx.x * BM_THREADS;
+    unsigned long long before = 0ull;
+    for (int i = tid; i < b0; i += BM_THREADS)
+        before += brick_pair(__ldg(bcounts + i));
+    before = block_sum_u64(before, s_w);
+    const int i = b0 + tid;
+    const unsigned c = i < nbt ? __ldg(bcounts + i) : 0u;
+    const unsigned long long pc = brick_pair(c);
+    unsigned long long incl = pc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d)
+            incl += y;
+    }
+    if (lane == 31)
+        s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = s_w[lane];
+        unsigned long long wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, wi, d);
+            if (lane >= d)
+                wi += y;
+        }
+        s_w[lane] = wi - w;
+    }
+    __syncthreads();
+    const unsigned long long run = before + s_w[warp] + (incl - pc);
+    if (i < nbt) {
+        const unsigned start = (unsigned)run;
+        boff[i] = start;
+        if (c) {
+            const int slot = (int)(run >> 32);
+            list[slot] = i;
+            range[slot] = make_uint2(start, start + c);
+            bslot[i] = slot;
+            boxord[2 * slot] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);   // min
+            boxord[2 * slot + 1] = make_uint4(0u, 0u, 0u, 0u);                          // max
+        }
+        if (i == nbt - 1) {
+            boff[nbt] = (unsigned)(run + pc);
+            ctl->n_bricks = (int)((run + pc) >> 32);
+        }
+    }
+}
+
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st)
 {
     const int nbt = g.bx * g.by * g.bz;
+    if (nbt <= BM_MAX_BRICKS) {
+        k_brick_scan_multi<<<(nbt + BM_THREADS - 1) / BM_THREADS, BM_THREADS, 0, st>>>(bcounts, nbt, boff, list, range,
+                                                                                       bslot, boxord, ctl);
+        return cudaGetLastError();
+    }
     const size_t smem = BS_CHUNK * sizeof(unsigned);
     cudaError_t e = cudaFuncSetAttribute(k_brick_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
