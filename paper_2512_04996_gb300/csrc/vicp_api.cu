@@ -49,7 +49,7 @@ struct vicp_ctx {
     Buf counts, off, root, ring, occ, desc, tile_sum, active_tiles;
     long long cap_V = -1;
     // brick level (V / 512)
-    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord;
+    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_range, sb_box;
     long long cap_bricks = -1;
     // N-sized
     Buf keys, ids, csr, bpts, outside;
@@ -212,6 +212,8 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->brick_box, (size_t)n_bricks * 32, "brick boxes"));
         TRY(buf_alloc(c, c->bslot, (size_t)n_bricks * 4, "brick slots"));
         TRY(buf_alloc(c, c->boxord, (size_t)n_bricks * 32, "brick box bounds"));
+        TRY(buf_alloc(c, c->sb_range, (size_t)(n_bricks / SUPER_BRICKS + 1) * 8, "super-brick ranges"));
+        TRY(buf_alloc(c, c->sb_box, (size_t)(n_bricks / SUPER_BRICKS + 1) * 32, "super-brick boxes"));
         c->cap_bricks = n_bricks;
     }
     return VICP_OK;
@@ -277,6 +279,9 @@ vicp_status set_geometry(vicp_ctx *c, const float origin[3], float h, const int 
     g.bx = (dims[0] + BRICK - 1) / BRICK;
     g.by = (dims[1] + BRICK - 1) / BRICK;
     g.bz = (dims[2] + BRICK - 1) / BRICK;
+    g.sx = (g.bx + SUPER - 1) / SUPER;
+    g.sy = (g.by + SUPER - 1) / SUPER;
+    g.sz = (g.bz + SUPER - 1) / SUPER;
     c->geom = g;
     c->have_geom = true;
     return VICP_OK;
@@ -384,7 +389,8 @@ vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, i
     }));
     TRY(launch(c, K_FALLBACK, [&] {
         return launch_fallback(src, pose, (const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
-                               (const float4 *)c->brick_box.p, c->target, c->n_target, (const int *)c->outside.p,
+                               (const float4 *)c->brick_box.p, (const uint2 *)c->sb_range.p,
+                               (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
                                (const int *)c->fb_list.p, d, nn, d2, m, honor_stop, c->stream);
     }));
     return VICP_OK;
@@ -416,7 +422,7 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
         TRY(set_geometry(c, c->params.origin, c->params.voxel_size, c->params.dims));
     }
     const GridGeom &g = c->geom;
-    TRY(ensure_voxel_buffers(c, g.V, (long long)g.bx * g.by * g.bz));
+    TRY(ensure_voxel_buffers(c, g.V, brick_slots(g)));
     TRY(ensure_point_buffers(c, n));
     DevCtl *d = ctl_of(c);
     const int skip = (c->params.flags & VICP_FLAG_TEST_SCAN_TIMEOUT) ? 0 : -1;
@@ -439,7 +445,9 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
                               (int *)c->outside.p, d, c->stream);
     }));
     TRY(launch(c, K_BRICK_BOXES, [&] {
-        return launch_brick_boxes((const uint4 *)c->boxord.p, (float4 *)c->brick_box.p, d, g, c->stream);
+        return launch_brick_boxes((const uint4 *)c->boxord.p, (const int *)c->brick_list.p,
+                                  (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p, (uint2 *)c->sb_range.p,
+                                  (float4 *)c->sb_box.p, d, g, c->stream);
     }));
     c->built = true;
     c->dilated_L = -1;
@@ -592,7 +600,7 @@ void vicp_destroy(vicp_ctx *c)
     Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->tile_sum,
                   &c->active_tiles,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
-                  &c->boxord,  &c->keys,
+                  &c->boxord,  &c->sb_range, &c->sb_box,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
                   &c->fb_list, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt};
@@ -656,9 +664,9 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
             return cuda_fail(c, e, "fallback count copy");
         TRY(launch(c, K_FALLBACK, [&] {
             return launch_fallback(src, pose_dev, (const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
-                                   (const float4 *)c->brick_box.p, c->target, c->n_target,
-                                   (const int *)c->outside.p, (const int *)c->fb_list.p, d, nn_out, d2_out, n_src,
-                                   0, c->stream);
+                                   (const float4 *)c->brick_box.p, (const uint2 *)c->sb_range.p,
+                                   (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
+                                   (const int *)c->fb_list.p, d, nn_out, d2_out, n_src, 0, c->stream);
         }));
         return VICP_OK;
     }

@@ -19,10 +19,14 @@ struct GridGeom {
     int nx, ny, nz;
     long long V;
     int bx, by, bz;     // brick grid: ceil(dims / BRICK)
+    int sx, sy, sz;     // super-brick grid: ceil(brick dims / SUPER)
 };
 
-// Brick edge (voxels) of the coarse level used by the exact global search.
+// Brick edge (voxels) of the coarse level used by the exact global search,
+// and super-brick edge (bricks) of the level above it.
 constexpr int BRICK = 8;
+constexpr int SUPER = 4;
+constexpr int SUPER_BRICKS = SUPER * SUPER * SUPER;
 
 // Bits of the device status word.
 constexpr unsigned DEVERR_TIMEOUT = 1u;      // a bounded wait gave up
@@ -44,6 +48,8 @@ struct DevCtl {
     unsigned red_done;      // reduction: finished blocks (the last one solves and resets it)
     int n_active_tiles;     // dilation: tiles listed for the shared-memory kernel (reset by it)
     unsigned dil_done;      // dilation: finished blocks (the last one resets the list)
+    int n_super;            // non-empty super-bricks; reset by the histogram
+    int pad1;
     // Work counters (added by the search kernels, read and cleared by the host).
     unsigned long long stat_queries;       // source points searched
     unsigned long long stat_fallbacks;     // of which took the global search
@@ -55,7 +61,7 @@ struct DevCtl {
     double prev_rmse;
     double last_rmse;
 };
-static_assert(sizeof(DevCtl) == 104, "DevCtl layout");
+static_assert(sizeof(DevCtl) == 112, "DevCtl layout");
 
 // Rigid transform rounded to float: R row-major, t.
 struct PoseF {
@@ -118,11 +124,22 @@ __device__ __forceinline__ int voxel_key(const GridGeom &g, float x, float y, fl
     return ix + g.nx * (iy + g.ny * iz);
 }
 
-// Brick of a voxel (8x8x8 voxels per brick, x fastest).
+// Linear index of brick (bx, by, bz): super-brick major (x fastest at both
+// levels), so the bricks of one 4x4x4 super-brick are consecutive.
+__host__ __device__ __forceinline__ int brick_index(const GridGeom &g, int bx, int by, int bz)
+{
+    const int sb = (bx / SUPER) + g.sx * ((by / SUPER) + g.sy * (bz / SUPER));
+    return sb * SUPER_BRICKS + (bx % SUPER) + SUPER * ((by % SUPER) + SUPER * (bz % SUPER));
+}
+
+// Brick of a voxel (8x8x8 voxels per brick).
 __device__ __forceinline__ int brick_key(const GridGeom &g, int ix, int iy, int iz)
 {
-    return (ix / BRICK) + g.bx * ((iy / BRICK) + g.by * (iz / BRICK));
+    return brick_index(g, ix / BRICK, iy / BRICK, iz / BRICK);
 }
+
+// Length of the brick index space (padded to whole super-bricks).
+__host__ __device__ __forceinline__ int brick_slots(const GridGeom &g) { return g.sx * g.sy * g.sz * SUPER_BRICKS; }
 
 // Squared distance ((dx*dx + dy*dy) + dz*dz), each operation rounded once.
 __device__ __forceinline__ float dist2(float3 s, float4 q)

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict
     const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nb = nbx * nby * (bz1 - bz0 + 1);
     int any = 0;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const int b = (bx0 + k % nbx) + g.bx * ((by0 + (k / nbx) % nby) + g.by * (bz0 + k / (nbx * nby)));
+        const int b = brick_index(g, bx0 + k % nbx, by0 + (k / nbx) % nby, bz0 + k / (nbx * nby));
         any |= __ldg(boff + b + 1) > __ldg(boff + b);
     }
     if (__syncthreads_or(any)) {

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
         ctl->scan_ticket = 0u;
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
+        ctl->n_super = 0;
     }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     int key = -2, bk = -2;   // lanes past the end match only each other and add nothing
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned 
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st)
 {
-    const int nbt = g.bx * g.by * g.bz;
+    const int nbt = brick_slots(g);
     if (nbt <= BM_MAX_BRICKS) {
         k_brick_scan_multi<<<(nbt + BM_THREADS - 1) / BM_THREADS, BM_THREADS, 0, st>>>(bcounts, nbt, boff, list, range,
                                                                                        bslot, boxord, ctl);
@@ -640,27 +641,45 @@ cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const Grid
 // Brick boxes as floats: the scatter left each non-empty brick's exact bounds
 // as order-preserving unsigned integers; every stored point of the brick lies
 // inside the box as float values, which is what the global search's lower
-// bound needs.
+// bound needs.  The thread of the first brick of each super-brick (bricks of
+// a super-brick hold consecutive slots) also records the super-brick's slot
+// range and the union of its bricks' boxes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_brick_boxes(const uint4 *__restrict__ boxord, float4 *__restrict__ box,
-                                                     const DevCtl *__restrict__ ctl)
+__global__ void __launch_bounds__(256) k_brick_boxes(const uint4 *__restrict__ boxord, const int *__restrict__ list,
+                                                     float4 *__restrict__ box, uint2 *__restrict__ sb_range,
+                                                     float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
 {
     const int nb = ctl->n_bricks;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
         const uint4 lo = boxord[2 * k], hi = boxord[2 * k + 1];
         box[2 * k] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z), 0.0f);
         box[2 * k + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z), 0.0f);
+        const int sb = __ldg(list + k) / SUPER_BRICKS;
+        if (k == 0 || __ldg(list + k - 1) / SUPER_BRICKS != sb) {
+            uint4 l = lo, h = hi;
+            int e = k + 1;
+            for (; e < nb && __ldg(list + e) / SUPER_BRICKS == sb; ++e) {
+                const uint4 l2 = boxord[2 * e], h2 = boxord[2 * e + 1];
+                l = make_uint4(min(l.x, l2.x), min(l.y, l2.y), min(l.z, l2.z), 0u);
+                h = make_uint4(max(h.x, h2.x), max(h.y, h2.y), max(h.z, h2.z), 0u);
+            }
+            const int slot = atomicAdd(&ctl->n_super, 1);
+            sb_range[slot] = make_uint2((unsigned)k, (unsigned)e);
+            sb_box[2 * slot] = make_float4(ordered_to_float(l.x), ordered_to_float(l.y), ordered_to_float(l.z), 0.f);
+            sb_box[2 * slot + 1] = make_float4(ordered_to_float(h.x), ordered_to_float(h.y), ordered_to_float(h.z), 0.f);
+        }
     }
 }
 
-cudaError_t launch_brick_boxes(const uint4 *boxord, float4 *box, const DevCtl *ctl, const GridGeom &g,
-                               cudaStream_t st)
+cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box,
+                               uint2 *sb_range, float4 *sb_box, DevCtl *ctl, const GridGeom &g, cudaStream_t st)
 {
-    const int nbt = g.bx * g.by * g.bz;
+    (void)range;
+    const int nbt = brick_slots(g);
     int blocks = (nbt + 255) / 256;
     if (blocks > 152 * 2)
         blocks = 152 * 2;
-    k_brick_boxes<<<blocks, 256, 0, st>>>(boxord, box, ctl);
+    k_brick_boxes<<<blocks, 256, 0, st>>>(boxord, list, box, sb_range, sb_box, ctl);
     return cudaGetLastError();
 }
 

@@ -53,8 +53,8 @@ cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const Grid
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
                            unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, DevCtl *ctl,
                            cudaStream_t st);
-cudaError_t launch_brick_boxes(const uint4 *boxord, float4 *box, const DevCtl *ctl, const GridGeom &g,
-                               cudaStream_t st);
+cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box,
+                               uint2 *sb_range, float4 *sb_box, DevCtl *ctl, const GridGeom &g, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
                           int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st);
@@ -63,9 +63,9 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);
 cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const uint2 *brange,
-                            const float4 *bbox, const float4 *tgt, int n_tgt, const int *outside,
-                            const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m, int honor_stop,
-                            cudaStream_t st);
+                            const float4 *bbox, const uint2 *sb_range, const float4 *sb_box, const float4 *tgt,
+                            int n_tgt, const int *outside, const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m,
+                            int honor_stop, cudaStream_t st);
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
                                 float3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);

@@ -93,15 +93,18 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
 // found without scanning every point.
 //
 // The grid build groups the stored target points per non-empty 8x8x8 brick
-// (contiguous runs of (x, y, z, index)) and records each brick's exact float
-// bounding box.  For a query s, the box bound lb = ((ex*ex + ey*ey) + ez*ez),
-// with e the rounded gap between s and the box on each axis, is never larger
-// than the computed squared distance from s to any point in the box:
-// rounding is monotone, so every operation of the bound is <= the same
-// operation of the distance formula.  A warp per query
-//   (1) finds the brick of smallest bound and scans its points (lanes split
-//       the run), which gives a first best distance D;
-//   (2) tests every other brick's bound against D and scans, together, each
+// (contiguous runs of (x, y, z, index)) with each brick's exact float
+// bounding box, and groups the bricks per 4x4x4-brick super-brick (a
+// contiguous range of brick slots) with the union of their boxes.  For a
+// query s, the box bound lb = ((ex*ex + ey*ey) + ez*ez), with e the rounded
+// gap between s and the box on each axis, is never larger than the computed
+// squared distance from s to any point in the box: rounding is monotone, so
+// every operation of the bound is <= the same operation of the distance
+// formula.  A warp per query
+//   (1) takes the super-brick of smallest bound, and in it the brick of
+//       smallest bound, and scans that brick's points (lanes split the run),
+//       which gives a first best distance D;
+//   (2) visits every super-brick whose bound is <= D, and in it scans each
 //       brick whose bound is still <= D, tightening D as it goes;
 //   (3) scans the target points that lie outside the grid.
 // The result is the same (distance, index) minimum as a scan of all target
@@ -116,6 +119,11 @@ __device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
     const float ey = s.y < lo.y ? __fsub_rn(lo.y, s.y) : (s.y > hi.y ? __fsub_rn(s.y, hi.y) : 0.0f);
     const float ez = s.z < lo.z ? __fsub_rn(lo.z, s.z) : (s.z > hi.z ? __fsub_rn(s.z, hi.z) : 0.0f);
     return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+}
+
+__device__ __forceinline__ unsigned lb_bits(float3 s, const float4 *__restrict__ box, int k)
+{
+    return __float_as_uint(box_lb2(s, __ldg(box + 2 * k), __ldg(box + 2 * k + 1)));
 }
 
 // All lanes scan the run [r.x, r.y) of brick-ordered points; returns the
@@ -136,6 +144,8 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
                                                          const float4 *__restrict__ bpts,
                                                          const uint2 *__restrict__ brange,
                                                          const float4 *__restrict__ bbox,
+                                                         const uint2 *__restrict__ sb_range,
+                                                         const float4 *__restrict__ sb_box,
                                                          const float4 *__restrict__ tgt, int n_tgt,
                                                          const int *__restrict__ outside,
                                                          const int *__restrict__ fb_list,
@@ -151,7 +161,7 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
     const PoseF P = sp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int F = min(*(volatile int *)&ctl->fb_count, m);
-    const int nb = *(volatile int *)&ctl->n_bricks;
+    const int ns = *(volatile int *)&ctl->n_super;
     const int no = *(volatile int *)&ctl->n_outside;
     unsigned long long examined = 0ull;   // every lane counts the same; lane 0 reports
 
@@ -169,30 +179,43 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
                 best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
             examined += (unsigned long long)n_tgt;
         } else {
-            if (nb > 0) {
-                // (1) brick of smallest bound (ties: smallest slot)
-                unsigned long long lbmin = ~0ull;
-                for (int k = lane; k < nb; k += 32) {
-                    const float lb = box_lb2(s, __ldg(bbox + 2 * k), __ldg(bbox + 2 * k + 1));
-                    lbmin = umin64(lbmin, ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)k);
-                }
-                lbmin = warp_min_u64(lbmin);
-                const int k0 = (int)(unsigned)lbmin;
+            if (ns > 0) {
+                // (1) nearest super-brick, nearest brick in it, scan it
+                unsigned long long m0 = ~0ull;
+                for (int k = lane; k < ns; k += 32)
+                    m0 = umin64(m0, ((unsigned long long)lb_bits(s, sb_box, k) << 32) | (unsigned)k);
+                m0 = warp_min_u64(m0);
+                const uint2 r0 = __ldg(sb_range + (int)(unsigned)m0);
+                unsigned long long m1 = ~0ull;
+                for (int k = (int)r0.x + lane; k < (int)r0.y; k += 32)
+                    m1 = umin64(m1, ((unsigned long long)lb_bits(s, bbox, k) << 32) | (unsigned)k);
+                m1 = warp_min_u64(m1);
+                const int k0 = (int)(unsigned)m1;
                 best = scan_run(bpts, __ldg(brange + k0), s, lane, best, examined);
-                // (2) every other brick whose bound does not exceed the best distance
-                for (int kb = 0; kb < nb; kb += 32) {
-                    const int k = kb + lane;
-                    unsigned lbb = 0xffffffffu;
-                    if (k < nb && k != k0)
-                        lbb = __float_as_uint(box_lb2(s, __ldg(bbox + 2 * k), __ldg(bbox + 2 * k + 1)));
-                    unsigned cand = __ballot_sync(FULL_MASK, lbb <= (unsigned)(best >> 32));
-                    while (cand) {
-                        const int src_lane = __ffs(cand) - 1;
-                        cand &= cand - 1u;
-                        const unsigned lb = __shfl_sync(FULL_MASK, lbb, src_lane);
-                        if (lb > (unsigned)(best >> 32))
+                // (2) every super-brick, and brick in it, that could hold a point at distance <= D
+                for (int sb0 = 0; sb0 < ns; sb0 += 32) {
+                    const int sbk = sb0 + lane;
+                    const unsigned lbs = sbk < ns ? lb_bits(s, sb_box, sbk) : 0xffffffffu;
+                    unsigned cs = __ballot_sync(FULL_MASK, lbs <= (unsigned)(best >> 32));
+                    while (cs) {
+                        const int sl = __ffs(cs) - 1;
+                        cs &= cs - 1u;
+                        if (__shfl_sync(FULL_MASK, lbs, sl) > (unsigned)(best >> 32))
                             continue;   // the bound was overtaken by a closer point
-                        best = scan_run(bpts, __ldg(brange + kb + src_lane), s, lane, best, examined);
+                        const uint2 r = __ldg(sb_range + sb0 + sl);
+                        for (int kb = (int)r.x; kb < (int)r.y; kb += 32) {
+                            const int k = kb + lane;
+                            const unsigned lbb =
+                                (k < (int)r.y && k != k0) ? lb_bits(s, bbox, k) : 0xffffffffu;
+                            unsigned cb = __ballot_sync(FULL_MASK, lbb <= (unsigned)(best >> 32));
+                            while (cb) {
+                                const int bl = __ffs(cb) - 1;
+                                cb &= cb - 1u;
+                                if (__shfl_sync(FULL_MASK, lbb, bl) > (unsigned)(best >> 32))
+                                    continue;
+                                best = scan_run(bpts, __ldg(brange + kb + bl), s, lane, best, examined);
+                            }
+                        }
                     }
                 }
             }
@@ -202,7 +225,6 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
                 best = umin64(best, nn_key(dist2(s, __ldg(tgt + j)), j));
             }
             examined += (unsigned long long)no;
-            best = warp_min_u64(best);
         }
         best = warp_min_u64(best);
         if (lane == 0) {
@@ -226,12 +248,12 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
 }
 
 cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const uint2 *brange,
-                            const float4 *bbox, const float4 *tgt, int n_tgt, const int *outside,
-                            const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m, int honor_stop,
-                            cudaStream_t st)
+                            const float4 *bbox, const uint2 *sb_range, const float4 *sb_box, const float4 *tgt,
+                            int n_tgt, const int *outside, const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m,
+                            int honor_stop, cudaStream_t st)
 {
-    k_fallback<<<152 * 4, FB_THREADS, 0, st>>>(src, pose, bpts, brange, bbox, tgt, n_tgt, outside, fb_list, ctl, nn,
-                                               d2, m, honor_stop);
+    k_fallback<<<152 * 4, FB_THREADS, 0, st>>>(src, pose, bpts, brange, bbox, sb_range, sb_box, tgt, n_tgt, outside,
+                                               fb_list, ctl, nn, d2, m, honor_stop);
     return cudaGetLastError();
 }
 
