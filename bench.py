@@ -191,17 +191,20 @@ def _kernel_sha(kernel: str) -> str:
 
 
 def _ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu capture of this kernel, if
-    the kernel's source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    """DRAM bytes (read + write) per launch from the committed ncu capture of
+    this kernel, if the kernel's source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         with open(path) as f:
-            rec = json.load(f).get(kernel)
+            for ln in f:
+                if ln.startswith("#") or not ln.strip():
+                    continue
+                name, rd, wr, _t, sha = ln.split()
+                if name == kernel:
+                    return float(rd) + float(wr) if sha == _kernel_sha(kernel) else None
     except Exception:
         return None
-    if not rec or rec.get("source_sha") != _kernel_sha(kernel):
-        return None
-    return float(rec["bytes_per_launch_full"])
+    return None
 
 
 # ----------------------------------------------------------------------------

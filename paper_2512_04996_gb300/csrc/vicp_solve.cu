@@ -277,16 +277,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
     if (lane < 16)
         s_red[warp][lane] = v;
     __syncthreads();
+    __shared__ double s_tot[REDUCE_VALUES];
+    if (threadIdx.x < REDUCE_VALUES) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < RED_THREADS / 32; ++w)
+            t += s_red[w][threadIdx.x];
+        s_tot[threadIdx.x] = t;
+    }
+    __syncthreads();
     if (threadIdx.x != 0)
         return;
     ctl->red_done = 0u;
     double S[REDUCE_VALUES];
-    for (int q = 0; q < REDUCE_VALUES; ++q) {
-        double t = 0.0;
-        for (int w = 0; w < RED_THREADS / 32; ++w)
-            t += s_red[w][q];
-        S[q] = t;
-    }
+#pragma unroll
+    for (int q = 0; q < REDUCE_VALUES; ++q)
+        S[q] = s_tot[q];
     const double M = (double)m;
     const double pb[3] = {S[0] / M, S[1] / M, S[2] / M};   // relative to c
     const double qb[3] = {S[3] / M, S[4] / M, S[5] / M};
