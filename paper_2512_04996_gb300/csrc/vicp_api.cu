@@ -865,7 +865,7 @@ const char *vicp_last_error(const vicp_ctx *c) { return c ? c->last_error.c_str(
 namespace vicp {
 const char *kernel_name(int k)
 {
-    static const char *names[K_COUNT] = {"bbox",       "histogram", "scan",     "brick_scan",   "scatter",
+    static const char *names[K_COUNT] = {"bbox",       "histogram", "scan",     "scatter",      "brick_scan",
                                          "brick_boxes", "dilate",   "correspond", "fallback", "reduce_solve",
                                          "maxcount"};
     return (k >= 0 && k < K_COUNT) ? names[k] : "?";
