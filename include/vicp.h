@@ -254,6 +254,43 @@ VICP_API int64_t vicp_launch_count(const vicp_ctx *ctx);
 /* Text of the last error on this context ("" if none). */
 VICP_API const char *vicp_last_error(const vicp_ctx *ctx);
 
+/* Voxel keys and segment offsets of a target cloud -- the first two steps of
+ * vicp_build_grid (Alg. 1: quantisation, histogram, exclusive scan of the
+ * counts) -- computed WITHOUT allocating any device memory.  The paper has
+ * no counterpart: it is for callers that may not allocate at the point of
+ * the call, such as a loop that has committed a fixed device-memory plan
+ * (cudaMalloc can block and synchronise the device) or a plug-in whose host
+ * framework owns all device memory.  No context is needed.
+ *
+ * Working memory is one static device array inside the library (about
+ * 70 MiB on every GPU the library is loaded on, held until the process
+ * exits); the grid is therefore limited to VICP_STATIC_MAX_VOXELS voxels and
+ * VICP_STATIC_MAX_BRICK_SLOTS 8^3-voxel brick slots (bricks padded to whole
+ * 4x4x4-brick groups per axis); larger grids return VICP_ERR_GRID_TOO_LARGE.
+ * Every call, on any stream or host thread, shares that one array: calls on
+ * one device that overlap in time race and give wrong results, so callers
+ * must serialise them.  Each call clears the parts that must start at zero.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call outside any
+ * stream capture.  The call synchronises `cuda_stream` before returning.
+ *   target_xyzw: dev, n x 4 floats (w ignored), 16-byte aligned; n >= 1.
+ *   origin[3], voxel_size, dims[3]: host; the explicit grid (as
+ *     params.origin / voxel_size / dims of vicp_build_grid), dims >= 1.
+ *   keys_out: dev int32[n], 4-byte aligned; key x + nx*(y + ny*z) of each
+ *     point, -1 outside the grid.
+ *   offsets_out: dev uint32[V + 1], 16-byte aligned, V = dims product;
+ *     exclusive prefix sum of the per-voxel counts, offsets_out[V] = points
+ *     inside the grid.  Equal to vicp_get_grid's keys and offsets after
+ *     vicp_build_grid with the same grid.
+ * Errors: VICP_ERR_INVALID (NULL or misaligned pointer, n < 1, bad grid),
+ * VICP_ERR_GRID_TOO_LARGE, VICP_ERR_TIMEOUT (scan wait ran out),
+ * VICP_ERR_CUDA. */
+#define VICP_STATIC_MAX_VOXELS (1ll << 24)
+#define VICP_STATIC_MAX_BRICK_SLOTS (1ll << 20)
+VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, int32_t n, const float origin[3],
+                                         float voxel_size, const int32_t dims[3], int32_t *keys_out,
+                                         uint32_t *offsets_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

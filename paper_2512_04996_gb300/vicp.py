@@ -29,6 +29,8 @@ VICP_ERR_TIMEOUT = 5
 VICP_ERR_STATE = 6
 VICP_ERR_DEGENERATE = 7
 
+VICP_STATIC_MAX_VOXELS = 1 << 24
+VICP_STATIC_MAX_BRICK_SLOTS = 1 << 20
 VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
 VICP_FLAG_TEST_SCAN_TIMEOUT = 1 << 31
@@ -101,6 +103,8 @@ SIGNATURES = {
     "vicp_read_stats": (C.c_int, [_P, C.POINTER(vicp_stats), C.c_int32]),
     "vicp_launch_count": (C.c_int64, [_P]),
     "vicp_last_error": (C.c_char_p, [_P]),
+    "vicp_offsets_static": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32), _P, _P,
+                                      _P]),
 }
 
 _lock = threading.Lock()
@@ -365,3 +369,35 @@ def vicp_sync(ctx: Context) -> int:
 
 def vicp_memory_report(ctx: Context) -> dict:
     return ctx.memory_report()
+
+
+def vicp_offsets_static(target, origin, voxel_size: float, dims, keys=None, offsets=None, stream=None):
+    """Voxel keys and segment offsets of `target` on an explicit grid, computed
+    in the library's static scratch without any device allocation by the
+    library (the output tensors below are allocated here only when not
+    given).  Returns (keys int32[n], offsets int32[V + 1] holding uint32
+    values).  Calls must not overlap in time on one device."""
+    lib = load_library()
+    _cloud(target, "target")
+    n = target.shape[0]
+    V = int(dims[0]) * int(dims[1]) * int(dims[2])
+    if V > VICP_STATIC_MAX_VOXELS:   # before sizing any output
+        raise VicpError(VICP_ERR_GRID_TOO_LARGE, f"vicp_offsets_static: {V} voxels, the static scratch holds "
+                                                 f"at most {VICP_STATIC_MAX_VOXELS}")
+    if keys is None:
+        keys = torch.empty(n, dtype=torch.int32, device=target.device)
+    if offsets is None:
+        offsets = torch.empty(V + 1, dtype=torch.int32, device=target.device)
+    for t, size, what in ((keys, n, "keys"), (offsets, V + 1, "offsets")):
+        if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous() or t.numel() < size:
+            raise ValueError(f"{what}: expected a contiguous CUDA int32 tensor of >= {size} entries")
+    st = stream if stream is not None else torch.cuda.current_stream(target.device)
+    o = (C.c_float * 3)(*[float(x) for x in origin])
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    r = lib.vicp_offsets_static(C.c_void_p(target.data_ptr()), n, o, float(voxel_size), d,
+                                C.c_void_p(keys.data_ptr()), C.c_void_p(offsets.data_ptr()),
+                                C.c_void_p(st.cuda_stream))
+    if r != VICP_OK:
+        raise VicpError(r, f"vicp_offsets_static: {lib.vicp_status_string(r).decode()} (static scratch holds at "
+                           f"most {VICP_STATIC_MAX_VOXELS} voxels and {VICP_STATIC_MAX_BRICK_SLOTS} brick slots)")
+    return keys, offsets
