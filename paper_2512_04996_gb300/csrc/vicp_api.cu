@@ -46,7 +46,7 @@ struct vicp_ctx {
     const float4 *target = nullptr;   // caller's target of the last build (global search)
 
     // V-sized
-    Buf counts, off, root, ring, occ, desc, tile_sum, active_tiles;
+    Buf counts, off, root, ring, occ, desc, tile_sum, inter, uflag;
     long long cap_V = -1;
     // brick level (V / 512)
     Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_range, sb_box;
@@ -174,7 +174,7 @@ vicp_status launch(vicp_ctx *c, int kernel, F &&f)
         cudaEventRecord(e1, c->stream);
         c->pending.push_back({kernel, e0, e1});
     }
-    c->launches += 1;
+    c->launches += kernel == K_DILATE ? 2 : 1;   // the dilation is two kernels
     if (e != cudaSuccess)
         return fail(c, VICP_ERR_CUDA, "launch of %s: %s", kernel_name(kernel), cudaGetErrorString(e));
     return VICP_OK;
@@ -191,6 +191,7 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->off, (size_t)(V + 1) * 4, "offsets"));
         TRY(buf_alloc(c, c->root, (size_t)V * 4, "root"));
         TRY(buf_alloc(c, c->ring, (size_t)V, "ring"));
+        TRY(buf_alloc(c, c->inter, (size_t)V * 4, "dilation pass-Y words"));
         TRY(buf_alloc(c, c->occ, (size_t)occ_words(V) * 4, "occupancy"));
         TRY(buf_zero(c, c->occ, "zero occupancy"));
         TRY(buf_alloc(c, c->desc, (size_t)scan_tiles(V) * 8, "scan descriptors"));
@@ -199,9 +200,8 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_zero(c, c->tile_sum, "zero scan tile sums"));   // kept at zero between builds
         c->cap_V = V;
     }
-    // enough for the smallest tiles (any L)
-    if (dilate_tiles(c->geom, DILATE_MAX_L) * 4 > (long long)c->active_tiles.bytes) {
-        TRY(buf_alloc(c, c->active_tiles, (size_t)dilate_tiles(c->geom, DILATE_MAX_L) * 4, "active tile list"));
+    if (dilate_units(c->geom) * 4 > (long long)c->uflag.bytes) {
+        TRY(buf_alloc(c, c->uflag, (size_t)dilate_units(c->geom) * 4, "dilation row masks"));
     }
     if (n_bricks > c->cap_bricks) {
         TRY(buf_alloc(c, c->bcounts, (size_t)n_bricks * 4, "brick counts"));
@@ -464,9 +464,8 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     if (L > DILATE_MAX_L)
         return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
     TRY(launch(c, K_DILATE, [&] {
-        return launch_dilate((const unsigned *)c->occ.p, (const unsigned *)c->boff.p, c->geom, L,
-                             (int *)c->active_tiles.p, (int *)c->root.p, (unsigned char *)c->ring.p, ctl_of(c), c->sms,
-                             c->stream);
+        return launch_dilate((const unsigned *)c->occ.p, c->geom, L, c->inter.p, (unsigned *)c->uflag.p,
+                             (int *)c->root.p, (unsigned char *)c->ring.p, c->stream);
     }));
     c->dilated_L = L;
     return VICP_OK;
@@ -598,7 +597,7 @@ void vicp_destroy(vicp_ctx *c)
         return;
     cudaStreamSynchronize(c->stream);
     Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->tile_sum,
-                  &c->active_tiles,
+                  &c->inter,       &c->uflag,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
                   &c->boxord,  &c->sb_range, &c->sb_box,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,

@@ -46,8 +46,8 @@ struct DevCtl {
     unsigned max_count;     // memory report: largest voxel count
     unsigned occupied;      // memory report: occupied voxels
     unsigned red_done;      // reduction: finished blocks (the last one solves and resets it)
-    int n_active_tiles;     // dilation: tiles listed for the shared-memory kernel (reset by it)
-    unsigned dil_done;      // dilation: finished blocks (the last one resets the list)
+    int reserved0;
+    unsigned reserved1;
     int n_super;            // non-empty super-bricks; reset by the histogram
     int pad1;
     // Work counters (added by the search kernels, read and cleared by the host).

@@ -10,7 +10,7 @@
 // lattice path between two voxels stays inside the box, so the rounds reach
 // exactly the voxels at Manhattan distance r in round r.)
 //
-// How.  Instead of L rounds over the dense grid, the kernel evaluates that
+// How.  Instead of L rounds over the dense grid, the kernels evaluate that
 // closed form as a separable lexicographic minimum.  A candidate is packed
 // into one 32-bit word (dist:6 | dz+31:6 | dy+31:6 | dx+31:6), the root's
 // offset from the voxel holding the word.  Because the linear index
@@ -18,7 +18,7 @@
 // a fixed voxel the unsigned order of these words is the order (distance,
 // root index).  Moving a word one voxel along an axis adds one to the
 // distance and shifts one offset field: a single integer add.  Words whose
-// distance reaches L are dropped (they cannot end within L).
+// distance passes L are dropped (they cannot end within L).
 //
 //   pass X: nearest occupied voxel along the row, from the occupancy bitmask
 //           with clz/ffs on a 64-bit window (ties go to the left, the smaller
@@ -26,389 +26,351 @@
 //   pass Y: forward and backward running minimum along y;
 //   pass Z: the same along z, then the word is decoded into root and ring.
 //
-// The grid is cut into 32 x 8 x 32 output tiles (32 x 8 x 8 for L > 16).  A
-// tile whose L-grown box touches no occupied 8x8x8 brick is written
-// "unlabelled" by a light classification kernel.  Every other tile is processed by one CTA, which
-// stages the occupancy bits of the tile grown by L in y and z (three 32-bit
-// words per row cover x in [x0-32, x0+64)), runs passes X and Y for eight
-// z-planes at a time into shared memory, then pass Z, and writes root and
-// ring with coalesced stores.  L <= 31.
+// Most of a grid is far from every point (typically over 90% of the voxels
+// of a depth scene at L = 10), so the work is organised around skipping it.
+// k_dilate_xy runs passes X and Y for units of 32 x 32 voxels of one
+// z-plane (a warp each, a lane per x): the lanes load the occupancy bits of
+// the unit's rows grown by L, and a unit with no occupied voxel in reach only
+// records a zero flag.  The others write their pass-Y words to an
+// intermediate array (16 bits a word while L <= 15).  All words a warp needs
+// are loaded (or shuffled in) before its sweeps, so each sweep is a chain of
+// register operations rather than of memory latencies.  k_dilate_z then runs
+// pass Z for columns of 32 voxels (a warp per 32 x 32 columns of one row y,
+// a lane per x), reading only planes whose unit flag is set, and writes root
+// and ring for every voxel; a column with no flagged plane in reach writes
+// "unlabelled" at once.  L <= 31.
 #include "vicp_launch.h"
 
 namespace vicp {
 
 namespace {
-constexpr int TX = 32, TY = 8, ZB = 8, THREADS = 256;
+constexpr int UX = 32;   // x per unit: a lane each
+constexpr int UY = 32;   // output rows of a pass-XY unit
+constexpr int UZ = 32;   // output planes of a pass-Z unit
+constexpr int WARPS = 4, THREADS = 32 * WARPS;
 constexpr unsigned NONE = 0xffffffffu;
-constexpr int SH_D = 18, SH_Z = 12, SH_Y = 6;
-constexpr unsigned CENTER = (31u << SH_Z) | (31u << SH_Y) | 31u;   // zero offsets
-constexpr unsigned STEP_D = 1u << SH_D;
-constexpr unsigned STEP_YF = STEP_D - (1u << SH_Y);   // moved from y-1 to y: dy -= 1
-constexpr unsigned STEP_YB = STEP_D + (1u << SH_Y);   // moved from y+1 to y: dy += 1
-constexpr unsigned STEP_ZF = STEP_D - (1u << SH_Z);
-constexpr unsigned STEP_ZB = STEP_D + (1u << SH_Z);
-constexpr int TZ_WIDE = 32, TZ_NARROW = 8, L_WIDE_MAX = 16;   // 32-deep tiles while shared memory allows
+constexpr int L_COMPACT_MAX = 15;   // 16-bit intermediate words up to this L
 
-// Move a word n voxels (n >= 0) along one axis: the distance grows by n and
-// one offset field shifts by n (inc = the one-voxel step).  A word whose
-// distance would exceed L becomes NONE (NONE stays NONE).
+// Move a word n voxels (n >= 0) along one axis: the distance (at bit SD)
+// grows by n and one offset field shifts by n (inc = the one-voxel step).  A
+// word whose distance would exceed L becomes NONE (NONE stays NONE).
+template <int SD>
 __device__ __forceinline__ unsigned stepn(unsigned v, int n, unsigned inc, int L)
 {
     if (n > L)
         return NONE;
-    return v >= ((unsigned)(L + 1 - n) << SH_D) ? NONE : v + (unsigned)n * inc;
+    return v >= ((unsigned)(L + 1 - n) << SD) ? NONE : v + (unsigned)n * inc;
+}
+
+// Word layouts, (distance, dz, dy, dx) from the most significant field down,
+// offsets biased to be non-negative.  For L <= 15 passes X and Y work on
+// dist:6 | dy+15:5 | dx+15:5, stored as 16 bits (NONE truncates to 0xffff,
+// distance 63), and pass Z on dist:6 | dz+31:6 | dy+15:5 | dx+15:5, made from
+// the stored word by a few logic operations; the stored NONE becomes a word
+// of distance 63, which no step keeps and every real word beats.  For larger
+// L every pass uses dist:6 | dz+31:6 | dy+31:6 | dx+31:6.
+struct Words16 {
+    using Stored = unsigned short;
+    static constexpr int SD = 10, SY = 5;   // passes X and Y
+    static constexpr int ZD = 16, ZZ = 10;  // pass Z
+    static constexpr unsigned CENTER = (15u << SY) | 15u;
+    __device__ static unsigned load_z(const Stored *p, int i)
+    {
+        const unsigned s = __ldg(p + i);
+        return ((s << 6) & 0x3f0000u) | (31u << ZZ) | (s & 0x3ffu);
+    }
+    // root - voxel for a pass-Z word is offset - bias (modulo 2^32)
+    __device__ static unsigned offset(unsigned w, unsigned nx, unsigned plane)
+    {
+        return (w & 31u) + nx * ((w >> 5) & 31u) + plane * ((w >> 10) & 63u);
+    }
+    __device__ static unsigned bias(unsigned nx, unsigned plane) { return 15u + 15u * nx + 31u * plane; }
+};
+struct Words32 {
+    using Stored = unsigned;
+    static constexpr int SD = 18, SY = 6;
+    static constexpr int ZD = 18, ZZ = 12;
+    static constexpr unsigned CENTER = (31u << 12) | (31u << SY) | 31u;
+    __device__ static unsigned load_z(const Stored *p, int i) { return __ldg(p + i); }
+    __device__ static unsigned offset(unsigned w, unsigned nx, unsigned plane)
+    {
+        return (w & 63u) + nx * ((w >> 6) & 63u) + plane * ((w >> 12) & 63u);
+    }
+    __device__ static unsigned bias(unsigned nx, unsigned plane) { return 31u + 31u * nx + 31u * plane; }
+};
+
+// Pass X for the voxel x of a row from the row's bits around it: `left` bit i
+// is x - 32 + i, `right` bit i is x + i.
+template <class W>
+__device__ __forceinline__ unsigned row_word(unsigned left, unsigned right, int L)
+{
+    if (right & 1u)
+        return W::CENTER;
+    if (L == 0)
+        return NONE;
+    const unsigned lm = left & (0xffffffffu << (32 - L));
+    const unsigned rm = (right >> 1) & ((1u << L) - 1u);
+    const int dl = lm ? __clz(lm) + 1 : 64;
+    const int dr = rm ? __ffs(rm) : 64;
+    if (dl <= dr)
+        return dl <= L ? (((unsigned)dl << W::SD) | (W::CENTER - (unsigned)dl)) : NONE;
+    return dr <= L ? (((unsigned)dr << W::SD) | (W::CENTER + (unsigned)dr)) : NONE;
+}
+
+// One axis of passes Y and Z on 32 output positions held in registers:
+// c[k] holds the words found at position k itself; `before` and `after` are
+// the best words from the halo beyond each end, already moved to positions 0
+// and 31.  Sweeping backward and then forward over the same array gives
+// min over i of stepn(c[i], |k - i|): a candidate reaching k through a
+// turning point j pays |i - j| + |k - j| >= |k - i|, so only the direct move
+// (j between them) can be the minimum.
+template <unsigned INC_FWD, unsigned INC_BWD>
+__device__ __forceinline__ void sweep32(unsigned (&c)[32], unsigned before, unsigned after, unsigned lim)
+{
+    c[31] = min(c[31], after);
+#pragma unroll
+    for (int k = 30; k >= 0; --k)
+        c[k] = min(c[k], c[k + 1] >= lim ? NONE : c[k + 1] + INC_BWD);
+    c[0] = min(c[0], before);
+#pragma unroll
+    for (int k = 1; k < 32; ++k)
+        c[k] = min(c[k], c[k - 1] >= lim ? NONE : c[k - 1] + INC_FWD);
 }
 }  // namespace
 
-// Row-mask words per plane: bit yy of word yy/32 is set when row yy of the
-// grown tile holds an occupied voxel in the staged x window.
-__host__ __device__ constexpr int mask_words(int HY) { return (HY + 31) / 32; }
-
-static int tile_depth(int L) { return L <= L_WIDE_MAX ? TZ_WIDE : TZ_NARROW; }
-
-size_t dilate_smem_bytes(int L)
-{
-    const size_t TZ = tile_depth(L), HY = TY + 2 * L, HZ = TZ + 2 * L;
-    return sizeof(unsigned) * (HZ * HY * 3 + HZ * mask_words((int)HY) + mask_words((int)HZ) + ZB * HY * TX +
-                               HZ * TY * TX);
-}
-
-__device__ __forceinline__ bool bit_of(const unsigned *m, int i) { return (m[i >> 5] >> (i & 31)) & 1u; }
-
 // ---------------------------------------------------------------------------
-// Tile classification: a CTA per TX x TY x TZ tile checks the brick offsets
-// of every 8x8x8 brick its L-grown box touches.  A tile with no point in
-// reach writes "unlabelled" (root -1, ring 255) for its voxels at once (a
-// warp per row); any other tile is appended to the list the shared-memory
-// kernel works through.
+// Passes X and Y.  Warp u = xb + nxb*(yb + nyb*z) covers x in [32xb, 32xb+32),
+// y in [32yb, 32yb+32) of plane z; lane l stands for x = 32xb + l.  Lane l
+// loads the occupancy bits of output row y0 + l and, for l < L, of halo rows
+// y0 - L + l and y0 + 32 + l: four aligned words funnel-shifted into three
+// covering x in [x0-32, x0+64), masked to the grid and to [x0-L, x0+31+L].
+// A row's words are broadcast by shuffles.  rows[u] bit k is set iff output
+// row y0 + k holds a label after pass Y (0 for a unit with nothing in reach,
+// whose words are not written).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dilate_tiles(const unsigned *__restrict__ boff, GridGeom g, int L, int TZ,
-                                                      int tiles_x, int tiles_y, int n_tiles,
-                                                      int *__restrict__ active, DevCtl *__restrict__ ctl,
-                                                      int *__restrict__ root, unsigned char *__restrict__ ring)
+template <class W>
+__global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restrict__ occ, long long n_words, GridGeom g,
+                                                       int L, int nxb, int nyb, int units,
+                                                       typename W::Stored *__restrict__ inter,
+                                                       unsigned *__restrict__ rows)
 {
-    const int t = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int txy = tiles_x * tiles_y;
-    const int x0 = (t % tiles_x) * TX;
-    const int y0 = ((t / tiles_x) % tiles_y) * TY;
-    const int z0 = (t / txy) * TZ;
-    const int bx0 = max(x0 - L, 0) / BRICK, bx1 = min(x0 + TX - 1 + L, g.nx - 1) / BRICK;
-    const int by0 = max(y0 - L, 0) / BRICK, by1 = min(y0 + TY - 1 + L, g.ny - 1) / BRICK;
-    const int bz0 = max(z0 - L, 0) / BRICK, bz1 = min(z0 + TZ - 1 + L, g.nz - 1) / BRICK;
-    const int nbx = bx1 - bx0 + 1, nby = by1 - by0 + 1, nb = nbx * nby * (bz1 - bz0 + 1);
-    int any = 0;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const int b = brick_index(g, bx0 + k % nbx, by0 + (k / nbx) % nby, bz0 + k / (nbx * nby));
-        any |= __ldg(boff + b + 1) > __ldg(boff + b);
-    }
-    if (__syncthreads_or(any)) {
-        if (threadIdx.x == 0) {
-            const int slot = atomicAdd(&ctl->n_active_tiles, 1);
-            if (slot < n_tiles)
-                active[slot] = t;
-            else
-                atomicOr(&ctl->err, DEVERR_BOUNDS);
+    constexpr unsigned STEP_YF = (1u << W::SD) - (1u << W::SY);   // moved from y-1 to y: dy -= 1
+    constexpr unsigned STEP_YB = (1u << W::SD) + (1u << W::SY);   // moved from y+1 to y: dy += 1
+    const int lane = threadIdx.x & 31;
+    const int u = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (u >= units)
+        return;
+    const int xb = u % nxb, q = u / nxb;
+    const int yb = q % nyb, z = q / nyb;
+    const int x0 = xb * UX, y0 = yb * UY;
+    // kept bits of the three words (the same for every row)
+    const int right_room = g.nx - x0;   // >= 1
+    const unsigned m0 = (x0 == 0 || L == 0) ? 0u : (0xffffffffu << (32 - L));
+    const unsigned m1 = right_room >= 32 ? 0xffffffffu : ((1u << right_room) - 1u);
+    const int r2 = min(L, right_room - 32);
+    const unsigned m2 = r2 <= 0 ? 0u : ((1u << r2) - 1u);
+
+    // row sets: [0] output row y0 + lane, [1] y0 - L + lane, [2] y0 + 32 + lane
+    unsigned w[3][3], rm[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int y = j == 0 ? y0 + lane : (j == 1 ? y0 - L + lane : y0 + UY + lane);
+        const bool mine = j == 0 || lane < L;
+        unsigned a0 = 0u, a1 = 0u, a2 = 0u;
+        if (mine && y >= 0 && y < g.ny) {
+            const long long b = (long long)g.nx * (y + (long long)g.ny * z) + x0 - 32;
+            const long long wi = b >> 5;   // floor (b >= -32)
+            const int sh = (int)(b & 31);
+            unsigned qw[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                qw[i] = (wi + i >= 0 && wi + i < n_words) ? __ldg(occ + wi + i) : 0u;
+            a0 = __funnelshift_r(qw[0], qw[1], sh) & m0;
+            a1 = __funnelshift_r(qw[1], qw[2], sh) & m1;
+            a2 = __funnelshift_r(qw[2], qw[3], sh) & m2;
         }
+        w[j][0] = a0;
+        w[j][1] = a1;
+        w[j][2] = a2;
+        rm[j] = __ballot_sync(FULL_MASK, (a0 | a1 | a2) != 0u);
+    }
+    if ((rm[0] | rm[1] | rm[2]) == 0u) {
+        if (lane == 0)
+            rows[u] = 0u;
         return;
     }
+
+    // pass-X word of row set j held by lane s, for this lane's x
+    auto label = [&](int j, int s) -> unsigned {
+        const unsigned b0 = __shfl_sync(FULL_MASK, w[j][0], s);
+        const unsigned b1 = __shfl_sync(FULL_MASK, w[j][1], s);
+        const unsigned b2 = __shfl_sync(FULL_MASK, w[j][2], s);
+        return row_word<W>(__funnelshift_r(b0, b1, lane), __funnelshift_r(b1, b2, lane), L);
+    };
+    unsigned c[UY];
+#pragma unroll
+    for (int k = 0; k < UY; ++k)
+        c[k] = ((rm[0] >> k) & 1u) ? label(0, k) : NONE;
+    // halo rows: below (seen from output row 0) and above (from row 31)
+    unsigned before = NONE, after = NONE;
+    for (unsigned m = rm[1]; m; m &= m - 1u) {   // row y0 - L + s: L - s below row 0
+        const int s = __ffs(m) - 1;
+        before = min(before, stepn<W::SD>(label(1, s), L - s, STEP_YF, L));
+    }
+    for (unsigned m = rm[2]; m; m &= m - 1u) {   // row y0 + 32 + s: s + 1 above row 31
+        const int s = __ffs(m) - 1;
+        after = min(after, stepn<W::SD>(label(2, s), s + 1, STEP_YB, L));
+    }
+    sweep32<STEP_YF, STEP_YB>(c, before, after, (unsigned)L << W::SD);
+
+    // labelled rows (the sweeps also carry labels into rows past the grid's
+    // edge, which are left out)
     const int x = x0 + lane;
+    const bool in = x < g.nx;
+    const int y_room = g.ny - y0;   // >= 1
+    unsigned labelled = 0u;
+#pragma unroll
+    for (int k = 0; k < UY; ++k)
+        labelled |= __ballot_sync(FULL_MASK, in && c[k] != NONE) != 0u ? (1u << k) : 0u;
+    if (y_room < UY)
+        labelled &= (1u << y_room) - 1u;
+    if (lane == 0)
+        rows[u] = labelled;
+    if (in) {
+        const int base = x + g.nx * (y0 + g.ny * z);
+#pragma unroll
+        for (int k = 0; k < UY; ++k)
+            if ((labelled >> k) & 1u)
+                inter[base + g.nx * k] = (typename W::Stored)c[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass Z and the output.  Warp u = xb + nxb*(y + ny*zb) covers x in
+// [32xb, 32xb+32) of row y, z in [32zb, 32zb+32).  Lane l reads whether row y
+// is labelled after pass Y in output plane z0 + l and, for l < L, in halo
+// planes z0 - L + l and z0 + 32 + l; only those planes are read from the
+// intermediate array, all before the sweeps (halo planes four at a time).
+// ---------------------------------------------------------------------------
+template <class W>
+__global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *__restrict__ inter,
+                                                      const unsigned *__restrict__ rows, GridGeom g, int L, int nxb,
+                                                      int nyb, int units, int *__restrict__ root,
+                                                      unsigned char *__restrict__ ring)
+{
+    constexpr unsigned STEP_ZF = (1u << W::ZD) - (1u << W::ZZ);   // moved from z-1 to z: dz -= 1
+    constexpr unsigned STEP_ZB = (1u << W::ZD) + (1u << W::ZZ);   // moved from z+1 to z: dz += 1
+    const int lane = threadIdx.x & 31;
+    const int u = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (u >= units)
+        return;
+    const int xb = u % nxb, q = u / nxb;
+    const int y = q % g.ny, zb = q / g.ny;
+    const int x0 = xb * UX, z0 = zb * UZ, yb = y / UY, ybit = y & (UY - 1);
+    const int x = x0 + lane;
+    const int plane = g.nx * g.ny;
+    const int col = x + g.nx * y;   // voxel (x, y, 0)
+    const int kmax = min(UZ, g.nz - z0);
+
+    // planes: [0] output z0 + lane, [1] z0 - L + lane, [2] z0 + 32 + lane
+    unsigned pm[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int z = j == 0 ? z0 + lane : (j == 1 ? z0 - L + lane : z0 + UZ + lane);
+        const bool mine = j == 0 || lane < L;
+        bool set = false;
+        if (mine && z >= 0 && z < g.nz)
+            set = (__ldg(rows + (z * nyb + yb) * nxb + xb) >> ybit) & 1u;
+        pm[j] = __ballot_sync(FULL_MASK, set);
+    }
     if (x >= g.nx)
         return;
-    const int ny_t = min(TY, g.ny - y0), nz_t = min(TZ, g.nz - z0);
+    if ((pm[0] | pm[1] | pm[2]) == 0u) {   // nothing within L: unlabelled
+        int v = col + plane * z0;
+#pragma unroll 8
+        for (int k = 0; k < kmax; ++k, v += plane) {
+            root[v] = -1;
+            ring[v] = 255;
+        }
+        return;
+    }
+
+    unsigned c[UZ];
+#pragma unroll
+    for (int k = 0; k < UZ; ++k)
+        c[k] = ((pm[0] >> k) & 1u) ? W::load_z(inter, col + plane * (z0 + k)) : NONE;
+    unsigned before = NONE, after = NONE;
 #pragma unroll 1
-    for (int r = warp; r < ny_t * nz_t; r += blockDim.x / 32) {
-        const long long v = x + (long long)g.nx * (y0 + r % ny_t + (long long)g.ny * (z0 + r / ny_t));
-        root[v] = -1;
-        ring[v] = 255;
+    for (int side = 1; side <= 2; ++side) {
+        for (unsigned m = side == 1 ? pm[1] : pm[2]; m;) {
+            int s[4];
+            unsigned wv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                s[i] = m ? __ffs(m) - 1 : -1;
+                m &= m - 1u;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int zz = side == 1 ? z0 - L + s[i] : z0 + UZ + s[i];
+                wv[i] = s[i] >= 0 ? W::load_z(inter, col + plane * zz) : NONE;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (s[i] >= 0) {
+                    if (side == 1)   // L - s below plane 0
+                        before = min(before, stepn<W::ZD>(wv[i], L - s[i], STEP_ZF, L));
+                    else             // s + 1 above plane 31
+                        after = min(after, stepn<W::ZD>(wv[i], s[i] + 1, STEP_ZB, L));
+                }
+            }
+        }
     }
-}
+    sweep32<STEP_ZF, STEP_ZB>(c, before, after, (unsigned)L << W::ZD);
 
-// ---------------------------------------------------------------------------
-// Active tiles: a persistent grid works through the list; the last block to
-// finish clears the list length for the next dilation.  Work follows the
-// occupied rows: pass X runs on rows holding an occupied voxel in the staged
-// window; passes Y and Z step from one occupied row (plane) to the next with
-// the n-voxel shift and evaluate every output row (plane) of the tile.
-// ---------------------------------------------------------------------------
-template <int TZ>
-__global__ void __launch_bounds__(THREADS) k_dilate(const unsigned *__restrict__ occ,
-                                                    const int *__restrict__ active, GridGeom g, int L,
-                                                    int tiles_x, int tiles_y, int n_tiles,
-                                                    int *__restrict__ root, unsigned char *__restrict__ ring,
-                                                    DevCtl *__restrict__ ctl)
-{
-    extern __shared__ unsigned smem[];
-    const int HY = TY + 2 * L, HZ = TZ + 2 * L, MW = mask_words(HY), PW = mask_words(HZ);
-    unsigned *s_bits = smem;                  // [HZ][HY][3]
-    unsigned *s_mask = s_bits + HZ * HY * 3;  // [HZ][MW]      rows holding an occupied voxel
-    unsigned *s_pmask = s_mask + HZ * MW;     // [PW]          planes whose pass-Y output is not all NONE
-    unsigned *s_a = s_pmask + PW;             // [ZB][HY][TX]  pass X, one z batch (occupied rows only)
-    unsigned *s_b = s_a + ZB * HY * TX;       // [HZ][TY][TX]  pass Y (flagged planes only)
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_active = min(*(volatile int *)&ctl->n_active_tiles, n_tiles);
-    const int txy = tiles_x * tiles_y;
-
-    for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
-        const int t = __ldg(active + it);
-        const int x0 = (t % tiles_x) * TX;
-        const int y0 = ((t / tiles_x) % tiles_y) * TY;
-        const int z0 = (t / txy) * TZ;
-
-        // 1. occupancy windows of the grown tile (a lane per row, a warp per
-        //    32 rows of one plane) and the per-plane masks of occupied rows
-        if (tid < PW)
-            s_pmask[tid] = 0u;
-        for (int zz = warp; zz < HZ; zz += THREADS / 32) {
-            const int z = z0 - L + zz;
-            for (int yb = 0; yb < HY; yb += 32) {
-                const int yy = yb + lane, y = y0 - L + yy;
-                unsigned w[3] = {0u, 0u, 0u};
-                if (yy < HY && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
-                    const long long rowbase = (long long)g.nx * (y + (long long)g.ny * z);
+    const unsigned valid = (unsigned)(L + 1) << W::ZD;   // words below this are labels
+    int v = col + plane * z0;
+    const unsigned vb = (unsigned)v - W::bias((unsigned)g.nx, (unsigned)plane);
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int xs = x0 - 32 + 32 * k;
-                        const int lo = max(xs, 0), hi = min(xs + 32, g.nx);
-                        if (lo < hi)
-                            w[k] = extract_bits(occ, rowbase + lo, hi - lo) << (lo - xs);
-                    }
-                }
-                if (yy < HY) {
-                    unsigned *dst = s_bits + (zz * HY + yy) * 3;
-                    dst[0] = w[0];
-                    dst[1] = w[1];
-                    dst[2] = w[2];
-                }
-                const unsigned m = __ballot_sync(FULL_MASK, (w[0] | w[1] | w[2]) != 0u);
-                if (lane == 0)
-                    s_mask[zz * MW + (yb >> 5)] = m;
-            }
-        }
-        __syncthreads();
-
-        for (int zb = 0; zb < HZ; zb += ZB) {
-            // 2a. pass X on the occupied rows: warp w takes plane zb + w
-            const int zz = zb + warp;
-            if (zz < HZ) {
-                for (int mw = 0; mw < MW; ++mw) {
-                    unsigned m = s_mask[zz * MW + mw];
-                    while (m) {
-                        const int yy = 32 * mw + __ffs(m) - 1;
-                        m &= m - 1u;
-                        const unsigned *wrow = s_bits + (zz * HY + yy) * 3;
-                        const unsigned a0 = wrow[0], a1 = wrow[1], a2 = wrow[2];
-                        const unsigned left = __funnelshift_r(a0, a1, lane);    // bit i <-> x - 32 + i
-                        const unsigned right = __funnelshift_r(a1, a2, lane);   // bit i <-> x + i
-                        unsigned lbl = NONE;
-                        if (right & 1u) {
-                            lbl = CENTER;
-                        } else if (L > 0) {
-                            const unsigned lm = left & (0xffffffffu << (32 - L));
-                            const unsigned rm = (right >> 1) & ((1u << L) - 1u);
-                            const int dl = lm ? __clz(lm) + 1 : 64;
-                            const int dr = rm ? __ffs(rm) : 64;
-                            if (dl <= dr) {
-                                if (dl <= L)
-                                    lbl = ((unsigned)dl << SH_D) | (CENTER - (unsigned)dl);
-                            } else if (dr <= L) {
-                                lbl = ((unsigned)dr << SH_D) | (CENTER + (unsigned)dr);
-                            }
-                        }
-                        s_a[(warp * HY + yy) * TX + lane] = lbl;
-                    }
-                }
-            }
-            __syncthreads();
-            // 2b. pass Y: thread per (x, plane of the batch), stepping over
-            //     the plane's occupied rows
-            if (zz < HZ) {
-                const unsigned *mk = s_mask + zz * MW;
-                bool any_row = false;
-                for (int mw = 0; mw < MW; ++mw)
-                    any_row |= mk[mw] != 0u;
-                if (any_row) {
-                    if (lane == 0)
-                        atomicOr(s_pmask + (zz >> 5), 1u << (zz & 31));
-                    const unsigned *col = s_a + warp * HY * TX + lane;
-                    unsigned *ob = s_b + zz * TY * TX + lane;
-                    // forward: occupied rows below the tile, then every output row
-                    unsigned f = NONE;
-                    int rp = 0;
-                    for (int mw = 0; mw < MW && 32 * mw < L; ++mw) {
-                        unsigned m = mk[mw];
-                        if (32 * mw + 32 > L)
-                            m &= (1u << (L - 32 * mw)) - 1u;
-                        while (m) {
-                            const int r = 32 * mw + __ffs(m) - 1;
-                            m &= m - 1u;
-                            f = min(stepn(f, r - rp, STEP_YF, L), col[r * TX]);
-                            rp = r;
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < TY; ++k) {
-                        const int y = L + k;
-                        f = stepn(f, y - rp, STEP_YF, L);
-                        if (bit_of(mk, y))
-                            f = min(f, col[y * TX]);
-                        rp = y;
-                        ob[k * TX] = f;
-                    }
-                    // backward: occupied rows above the tile, then every output row
-                    unsigned bk = NONE;
-                    rp = HY - 1;
-                    for (int mw = MW - 1; mw >= 0; --mw) {
-                        if (32 * mw + 31 < L + TY)
-                            break;
-                        unsigned m = mk[mw];
-                        if (32 * mw < L + TY)
-                            m &= ~((1u << (L + TY - 32 * mw)) - 1u);
-                        while (m) {
-                            const int r = 32 * mw + 31 - __clz(m);
-                            m &= ~(1u << (r - 32 * mw));
-                            bk = min(stepn(bk, rp - r, STEP_YB, L), col[r * TX]);
-                            rp = r;
-                        }
-                    }
-#pragma unroll
-                    for (int k = TY - 1; k >= 0; --k) {
-                        const int y = L + k;
-                        bk = stepn(bk, rp - y, STEP_YB, L);
-                        if (bit_of(mk, y))
-                            bk = min(bk, col[y * TX]);
-                        rp = y;
-                        ob[k * TX] = min(ob[k * TX], bk);
-                    }
-                }
-            }
-            __syncthreads();
-        }
-
-        // 3. pass Z: thread per (x, y) column, stepping over the planes whose
-        //    pass-Y output is not all NONE
-        unsigned out[TZ];
-        {
-            const unsigned *col = s_b + warp * TX + lane;
-            unsigned f = NONE;
-            int rp = 0;
-            for (int pw = 0; pw < PW && 32 * pw < L; ++pw) {
-                unsigned m = s_pmask[pw];
-                if (32 * pw + 32 > L)
-                    m &= (1u << (L - 32 * pw)) - 1u;
-                while (m) {
-                    const int r = 32 * pw + __ffs(m) - 1;
-                    m &= m - 1u;
-                    f = min(stepn(f, r - rp, STEP_ZF, L), col[r * TY * TX]);
-                    rp = r;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < TZ; ++k) {
-                const int z = L + k;
-                f = stepn(f, z - rp, STEP_ZF, L);
-                if (bit_of(s_pmask, z))
-                    f = min(f, col[z * TY * TX]);
-                rp = z;
-                out[k] = f;
-            }
-            unsigned bk = NONE;
-            rp = HZ - 1;
-            for (int pw = PW - 1; pw >= 0; --pw) {
-                if (32 * pw + 31 < L + TZ)
-                    break;
-                unsigned m = s_pmask[pw];
-                if (32 * pw < L + TZ)
-                    m &= ~((1u << (L + TZ - 32 * pw)) - 1u);
-                while (m) {
-                    const int r = 32 * pw + 31 - __clz(m);
-                    m &= ~(1u << (r - 32 * pw));
-                    bk = min(stepn(bk, rp - r, STEP_ZB, L), col[r * TY * TX]);
-                    rp = r;
-                }
-            }
-#pragma unroll
-            for (int k = TZ - 1; k >= 0; --k) {
-                const int z = L + k;
-                bk = stepn(bk, rp - z, STEP_ZB, L);
-                if (bit_of(s_pmask, z))
-                    bk = min(bk, col[z * TY * TX]);
-                rp = z;
-                out[k] = min(out[k], bk);
-            }
-        }
-        // 4. decode and store
-        const int x = x0 + lane, y = y0 + warp;
-        if (x < g.nx && y < g.ny) {
-            const long long plane = (long long)g.nx * g.ny;
-            long long v = x + (long long)g.nx * y + plane * z0;
-#pragma unroll
-            for (int k = 0; k < TZ; ++k, v += plane) {
-                if (z0 + k < g.nz) {
-                    const unsigned w = out[k];
-                    int r = -1;
-                    unsigned char d = 255;
-                    if (w != NONE) {
-                        const int dz = (int)((w >> SH_Z) & 63u) - 31;
-                        const int dy = (int)((w >> SH_Y) & 63u) - 31;
-                        const int dx = (int)(w & 63u) - 31;
-                        r = (int)(v + dx + (long long)g.nx * dy + plane * dz);
-                        d = (unsigned char)(w >> SH_D);
-                    }
-                    root[v] = r;
-                    ring[v] = d;
-                }
-            }
-        }
-        __syncthreads();   // shared memory is reused by the next tile
-    }
-
-    if (tid == 0) {
-        __threadfence();
-        if (atomicAdd(&ctl->dil_done, 1u) == gridDim.x - 1) {
-            ctl->n_active_tiles = 0;
-            ctl->dil_done = 0u;
+    for (int k = 0; k < UZ; ++k, v += plane) {
+        if (k < kmax) {
+            const unsigned w = c[k];
+            const bool hit = w < valid;
+            root[v] = hit ? (int)(vb + (unsigned)plane * k + W::offset(w, (unsigned)g.nx, (unsigned)plane)) : -1;
+            ring[v] = hit ? (unsigned char)(w >> W::ZD) : (unsigned char)255;
         }
     }
 }
 
-template <int TZ>
-static cudaError_t run_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
-                              int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
+template <class W>
+static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
+                              unsigned char *ring, cudaStream_t st)
 {
-    const int tiles_x = (g.nx + TX - 1) / TX, tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
-    const int tiles = tiles_x * tiles_y * tiles_z;   // < V < 2^31
-    k_dilate_tiles<<<tiles, 256, 0, st>>>(boff, g, L, TZ, tiles_x, tiles_y, tiles, active, ctl, root, ring);
+    using S = typename W::Stored;
+    const int nxb = (g.nx + UX - 1) / UX, nyb = (g.ny + UY - 1) / UY, nzb = (g.nz + UZ - 1) / UZ;
+    const int u_xy = nxb * nyb * g.nz;   // < V < 2^31
+    k_dilate_xy<W><<<(u_xy + WARPS - 1) / WARPS, THREADS, 0, st>>>(occ, occ_words(g.V), g, L, nxb, nyb, u_xy,
+                                                                    static_cast<S *>(inter), rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    const size_t smem = dilate_smem_bytes(L);
-    e = cudaFuncSetAttribute(k_dilate<TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dilate<TZ>, THREADS, smem);
-    if (e != cudaSuccess)
-        return e;
-    int grid = sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > tiles)
-        grid = tiles;
-    k_dilate<TZ><<<grid, THREADS, smem, st>>>(occ, active, g, L, tiles_x, tiles_y, tiles, root, ring, ctl);
+    const int u_z = nxb * g.ny * nzb;   // < V < 2^31
+    k_dilate_z<W><<<(u_z + WARPS - 1) / WARPS, THREADS, 0, st>>>(static_cast<const S *>(inter), rows, g, L, nxb, nyb,
+                                                                  u_z, root, ring);
     return cudaGetLastError();
 }
 
-long long dilate_tiles(const GridGeom &g, int L)
+long long dilate_units(const GridGeom &g)
 {
-    const int TZ = tile_depth(L);
-    return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * ((g.nz + TZ - 1) / TZ);
+    return (long long)((g.nx + UX - 1) / UX) * ((g.ny + UY - 1) / UY) * g.nz;
 }
 
-cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
-                          int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st)
+cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
+                          unsigned char *ring, cudaStream_t st)
 {
-    if (tile_depth(L) == TZ_WIDE)
-        return run_dilate<TZ_WIDE>(occ, boff, g, L, active, root, ring, ctl, sms, st);
-    return run_dilate<TZ_NARROW>(occ, boff, g, L, active, root, ring, ctl, sms, st);
+    if (L <= L_COMPACT_MAX)
+        return run_dilate<Words16>(occ, g, L, inter, rows, root, ring, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, root, ring, st);
 }
 
 }  // namespace vicp

@@ -29,7 +29,7 @@ constexpr int SCAN_TILE = 16384;
 // Reduction blocks of one ICP iteration (two per SM) -- sizes the partial sums.
 constexpr int REDUCE_MAX_BLOCKS = 1024;
 constexpr int REDUCE_VALUES = 16;
-// Largest dilation depth L the tiled kernel supports.
+// Largest dilation depth L the kernels support.
 constexpr int DILATE_MAX_L = 31;
 
 inline long long scan_tiles(long long V) { return (V + SCAN_TILE - 1) / SCAN_TILE; }
@@ -40,7 +40,6 @@ inline int reduce_blocks(int m, int sms)
     const int b = (m + 255) / 256;
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
-size_t dilate_smem_bytes(int L);
 
 cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t st);
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
@@ -56,9 +55,11 @@ cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const Grid
 cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box,
                                uint2 *sb_range, float4 *sb_box, DevCtl *ctl, const GridGeom &g, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_dilate(const unsigned *occ, const unsigned *boff, const GridGeom &g, int L, int *active,
-                          int *root, unsigned char *ring, DevCtl *ctl, int sms, cudaStream_t st);
-long long dilate_tiles(const GridGeom &g, int L);   // tiles of the dilation for depth L
+// Dilation: `inter` holds V words of pass Y (V x 4 bytes suffices for any
+// L), `rows` dilate_units(g) 32-bit row masks; neither needs clearing.
+cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
+                          unsigned char *ring, cudaStream_t st);
+long long dilate_units(const GridGeom &g);
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);

@@ -22,7 +22,7 @@ def test_workload_grids(pairs, k):
     assert_grid_equal(g, ref, p.target)
 
 
-@pytest.mark.parametrize("L", [0, 1, 2, 5, 17, 31])
+@pytest.mark.parametrize("L", [0, 1, 2, 5, 15, 16, 17, 31])
 def test_dilation_depths(pairs, L):
     p = pairs(1)
     ctx, g = gpu_grid(p.target, L=L, divisions=64)
