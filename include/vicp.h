@@ -55,7 +55,7 @@ typedef enum vicp_status {
     VICP_ERR_CUDA = 2,            /* a CUDA runtime call failed (see vicp_last_error) */
     VICP_ERR_OOM = 3,             /* the allocator returned NULL */
     VICP_ERR_GRID_TOO_LARGE = 4,  /* nx*ny*nz >= 2^31 voxels */
-    VICP_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    VICP_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up (no current kernel waits) */
     VICP_ERR_STATE = 6,           /* call order: e.g. correspond before build_grid */
     VICP_ERR_DEGENERATE = 7       /* rank(H) < 2 in the rigid solve; pose left unchanged */
 } vicp_status;
@@ -75,8 +75,7 @@ typedef struct vicp_allocator {
 /* Flags for vicp_params.flags. */
 #define VICP_FLAG_KEEP_GRID         (1u << 0) /* auto grid: fit once, reuse for later builds */
 #define VICP_FLAG_REBUILD_EACH_ITER (1u << 1) /* vicp_register: rebuild + dilate every iteration */
-#define VICP_FLAG_TEST_SCAN_TIMEOUT (1u << 31) /* tests only: one scan tile never publishes,
-                                                  so its successor's bounded wait gives up */
+
 
 /* Run parameters (Sec. 4.1 "Parameter": voxelisation scale, dilation
  * layers L, maximum iteration count, RMSE-difference threshold). */
@@ -283,8 +282,7 @@ VICP_API const char *vicp_last_error(const vicp_ctx *ctx);
  *     inside the grid.  Equal to vicp_get_grid's keys and offsets after
  *     vicp_build_grid with the same grid.
  * Errors: VICP_ERR_INVALID (NULL or misaligned pointer, n < 1, bad grid),
- * VICP_ERR_GRID_TOO_LARGE, VICP_ERR_TIMEOUT (scan wait ran out),
- * VICP_ERR_CUDA. */
+ * VICP_ERR_GRID_TOO_LARGE, VICP_ERR_CUDA. */
 #define VICP_STATIC_MAX_VOXELS (1ll << 24)
 #define VICP_STATIC_MAX_BRICK_SLOTS (1ll << 20)
 VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, int32_t n, const float origin[3],

@@ -49,7 +49,7 @@ struct vicp_ctx {
     Buf counts, off, root, ring, occ, desc, tile_sum, inter, uflag;
     long long cap_V = -1;
     // brick level (V / 512)
-    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_range, sb_box;
+    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_box;
     long long cap_bricks = -1;
     // N-sized
     Buf keys, ids, csr, bpts, outside;
@@ -212,7 +212,6 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->brick_box, (size_t)n_bricks * 32, "brick boxes"));
         TRY(buf_alloc(c, c->bslot, (size_t)n_bricks * 4, "brick slots"));
         TRY(buf_alloc(c, c->boxord, (size_t)n_bricks * 32, "brick box bounds"));
-        TRY(buf_alloc(c, c->sb_range, (size_t)(n_bricks / SUPER_BRICKS + 1) * 8, "super-brick ranges"));
         TRY(buf_alloc(c, c->sb_box, (size_t)(n_bricks / SUPER_BRICKS + 1) * 32, "super-brick boxes"));
         c->cap_bricks = n_bricks;
     }
@@ -388,8 +387,7 @@ vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, i
                                  honor_stop, c->stream);
     }));
     TRY(launch(c, K_FALLBACK, [&] {
-        return launch_fallback(src, pose, (const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
-                               (const float4 *)c->brick_box.p, (const uint2 *)c->sb_range.p,
+        return launch_fallback(src, pose, (const float4 *)c->bpts.p, (const float4 *)c->brick_box.p,
                                (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
                                (const int *)c->fb_list.p, d, nn, d2, m, honor_stop, c->stream);
     }));
@@ -425,14 +423,13 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     TRY(ensure_voxel_buffers(c, g.V, brick_slots(g)));
     TRY(ensure_point_buffers(c, n));
     DevCtl *d = ctl_of(c);
-    const int skip = (c->params.flags & VICP_FLAG_TEST_SCAN_TIMEOUT) ? 0 : -1;
     TRY(launch(c, K_HISTOGRAM, [&] {
         return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p,
                                 (unsigned *)c->occ.p, (unsigned *)c->tile_sum.p, d, c->stream);
     }));
     TRY(launch(c, K_SCAN, [&] {
         return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, (const unsigned *)c->occ.p,
-                           (unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, skip, c->stream);
+                           (const unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, c->stream);
     }));
     TRY(launch(c, K_BRICK_SCAN, [&] {
         return launch_brick_scan((const unsigned *)c->bcounts.p, g, (unsigned *)c->boff.p, (int *)c->brick_list.p,
@@ -442,12 +439,12 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
         return launch_scatter(tgt, (const int *)c->keys.p, n, g, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
                               (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (const int *)c->bslot.p,
                               (unsigned *)c->boxord.p, (int *)c->ids.p, (float4 *)c->csr.p, (float4 *)c->bpts.p,
-                              (int *)c->outside.p, d, c->stream);
+                              (int *)c->outside.p, (unsigned *)c->tile_sum.p, d, c->stream);
     }));
     TRY(launch(c, K_BRICK_BOXES, [&] {
         return launch_brick_boxes((const uint4 *)c->boxord.p, (const int *)c->brick_list.p,
-                                  (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p, (uint2 *)c->sb_range.p,
-                                  (float4 *)c->sb_box.p, d, g, c->stream);
+                                  (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p, (float4 *)c->sb_box.p, d,
+                                  g, c->stream);
     }));
     c->built = true;
     c->dilated_L = -1;
@@ -599,7 +596,7 @@ void vicp_destroy(vicp_ctx *c)
     Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->tile_sum,
                   &c->inter,       &c->uflag,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
-                  &c->boxord,  &c->sb_range, &c->sb_box,  &c->keys,
+                  &c->boxord,  &c->sb_box,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
                   &c->fb_list, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt};
@@ -662,8 +659,7 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
         if (e != cudaSuccess)
             return cuda_fail(c, e, "fallback count copy");
         TRY(launch(c, K_FALLBACK, [&] {
-            return launch_fallback(src, pose_dev, (const float4 *)c->bpts.p, (const uint2 *)c->brick_range.p,
-                                   (const float4 *)c->brick_box.p, (const uint2 *)c->sb_range.p,
+            return launch_fallback(src, pose_dev, (const float4 *)c->bpts.p, (const float4 *)c->brick_box.p,
                                    (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
                                    (const int *)c->fb_list.p, d, nn_out, d2_out, n_src, 0, c->stream);
         }));

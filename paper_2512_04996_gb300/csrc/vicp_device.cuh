@@ -36,7 +36,7 @@ constexpr unsigned DEVERR_BOUNDS = 4u;       // an index failed its bounds check
 // Per-context control block in device memory.  Kernels of one stream use it
 // in launch order; the comments say which kernel writes each field.
 struct DevCtl {
-    unsigned scan_ticket;   // scan: dynamic tile index; reset by the histogram kernel
+    unsigned reserved2;
     unsigned scan_epoch;    // scan: descriptor epoch; bumped by the histogram kernel
     int n_outside;          // scatter: target points outside the grid; reset by histogram
     int n_bricks;           // brick list length; reset by histogram
@@ -69,17 +69,22 @@ struct PoseF {
     float t[3];
 };
 
-// Load the 3x4 upper part of a row-major 4x4 double pose, each entry rounded
-// to the nearest float.
-__device__ __forceinline__ void load_pose_f(const double *__restrict__ pose, PoseF &P)
+// The 3x4 upper part of a row-major 4x4 double pose, each entry rounded to
+// the nearest float, loaded into shared memory by threads 0..11 (one entry
+// each: the conversion runs on the FP64 pipe, so twelve lanes of one
+// instruction rather than twelve instructions of one thread).  Contains
+// __syncthreads(); every thread of the block must call it.
+__device__ __forceinline__ void load_pose_f_block(const double *__restrict__ pose, PoseF &sp)
 {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            P.r[3 * a + b] = __double2float_rn(pose[4 * a + b]);
-        P.t[a] = __double2float_rn(pose[4 * a + 3]);
+    if (threadIdx.x < 12) {
+        const int a = threadIdx.x >> 2, b = threadIdx.x & 3;
+        const float v = __double2float_rn(pose[4 * a + b]);
+        if (b < 3)
+            sp.r[3 * a + b] = v;
+        else
+            sp.t[a] = v;
     }
+    __syncthreads();
 }
 
 // s_a = ((R_a0*x + R_a1*y) + R_a2*z) + t_a, every operation rounded to

@@ -70,8 +70,8 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // (warp-aggregated atomics).  The same grouping feeds the per-brick counts
 // (brick level of the global search), the occupancy bitmask (one atomicOr
 // per word) and the per-tile totals the scan starts from.  Block 0 also
-// resets the scan's ticket, bumps its descriptor epoch and clears the
-// outside counter for this build.
+// bumps the scan's descriptor epoch and clears the outside counter for this
+// build.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
@@ -79,7 +79,6 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
                                                    unsigned *__restrict__ tile_sum, DevCtl *__restrict__ ctl)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->scan_ticket = 0u;
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
         ctl->n_super = 0;
@@ -255,9 +254,19 @@ __global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned 
     __shared__ unsigned long long s_w[BM_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b0 = blockIdx.x * BM_THREADS;
+    // the predecessors' counts, eight independent loads per round
     unsigned long long before = 0ull;
-    for (int i = tid; i < b0; i += BM_THREADS)
-        before += brick_pair(__ldg(bcounts + i));
+    for (int i0 = tid; i0 < b0; i0 += 8 * BM_THREADS) {
+        unsigned v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * BM_THREADS;
+            v[u] = i < b0 ? __ldg(bcounts + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            before += brick_pair(v[u]);
+    }
     before = block_sum_u64(before, s_w);
     const int i = b0 + tid;
     const unsigned c = i < nbt ? __ldg(bcounts + i) : 0u;
@@ -321,28 +330,26 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 }
 
 // ---------------------------------------------------------------------------
-// MOC as a single-pass exclusive scan with decoupled lookback.
+// MOC as a single-pass exclusive scan with lookback, without waiting.
 //
 // A tile is 16384 voxels: 512 threads, each owning the 32 voxels of one
-// occupancy word.  Each CTA takes the next tile from an atomic ticket (so
-// every tile it waits on has already started).  The histogram already
-// summed every tile's counts, so the CTA publishes its aggregate at once --
-// no load of the tile's data stands in the chain between tiles -- and resets
-// that sum for the next build.  It then reads its occupancy words, gathers
-// the counts of the occupied voxels only, scans them, and looks back over
-// its predecessors' descriptors, 512 per round (one per thread), down to the
-// nearest inclusive prefix.  A descriptor is one 64-bit word
-// [epoch:30 | flag:2 | value:32], so flag and value are read together; the
-// epoch (bumped by the histogram each build) retires the previous build's
-// descriptors without clearing them.  Every wait is bounded by the global
-// timer: on expiry the CTA sets DEVERR_TIMEOUT and publishes a prefix anyway,
-// so no successor waits on it.
+// occupancy word; CTA t scans tile t.  It reads its occupancy words, gathers
+// the counts of the occupied voxels only (all loads of a thread in flight
+// together) and scans them.  Its exclusive prefix is the sum of every
+// earlier tile's total, and the histogram has already written those totals,
+// so nothing ever has to be waited for: the CTA looks back over its
+// predecessors, 512 per round (one per thread), and adds their totals down
+// to the nearest predecessor that has already published its inclusive
+// prefix (any one that has not is simply summed through).  A published
+// prefix is one 64-bit word [epoch:30 | flag:2 | value:32], so flag and value
+// are read together; the epoch (bumped by the histogram each build) retires
+// the previous build's words without clearing them.  The tile totals stay
+// untouched while the scan runs (predecessors are read throughout); the
+// scatter, which runs next, zeroes them for the following build.
 // ---------------------------------------------------------------------------
 constexpr int SCAN_THREADS = SCAN_TILE / 32;   // 512
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
-constexpr unsigned long long DESC_AGG = 1ull << 32;
 constexpr unsigned long long DESC_PREFIX = 2ull << 32;
-constexpr unsigned long long SCAN_TIMEOUT_NS = 200ull * 1000ull * 1000ull;   // 200 ms
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
@@ -354,13 +361,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_timer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
 }
 
 __device__ __forceinline__ unsigned warp_sum_u32(unsigned v)
@@ -405,92 +405,77 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_w, u
     return s_w[warp] + (incl - v);
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restrict__ counts, long long V,
+__global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__restrict__ counts, long long V,
                                                        unsigned *__restrict__ off, const unsigned *__restrict__ occ,
-                                                       unsigned *__restrict__ tile_sum,
+                                                       const unsigned *__restrict__ tile_sum,
                                                        unsigned long long *__restrict__ desc,
-                                                       DevCtl *__restrict__ ctl, int skip_tile)
+                                                       const DevCtl *__restrict__ ctl)
 {
-    __shared__ unsigned s_tile, s_agg;
-    __shared__ unsigned s_w[SCAN_WARPS + 1];
-    __shared__ unsigned s_first, s_sum[SCAN_WARPS];
+    __shared__ unsigned s_epoch, s_w[SCAN_WARPS + 1], s_first[SCAN_WARPS], s_sum[SCAN_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        const unsigned tile = atomicAdd(&ctl->scan_ticket, 1u);
-        const unsigned long long ep = (unsigned long long)(*(volatile unsigned *)&ctl->scan_epoch & 0x3fffffffu);
-        const unsigned agg = tile_sum[tile];
-        tile_sum[tile] = 0u;   // zero again for the next build
-        if ((int)tile != skip_tile)
-            st_relaxed_u64(desc + tile, (ep << 34) | (tile == 0 ? DESC_PREFIX : DESC_AGG) | agg);
-        s_tile = tile;
-        s_agg = agg;
-    }
-    __syncthreads();
-    const unsigned tile = s_tile;
-    const unsigned long long epoch = (unsigned long long)(*(volatile unsigned *)&ctl->scan_epoch & 0x3fffffffu);
-    const unsigned long long tag = epoch << 34;
+    const unsigned tile = blockIdx.x;
+    if (tid == 0)   // read by one thread per CTA (a hot line otherwise)
+        s_epoch = *(volatile const unsigned *)&ctl->scan_epoch & 0x3fffffffu;
 
-    // this thread's 32 voxels: counts of the occupied ones only
+    // this thread's 32 voxels: counts of the occupied ones only, loaded
+    // together (predicated, one round trip); the first lookback round's
+    // loads go out at the same time (they depend on the tile index only)
     const long long base = (long long)tile * SCAN_TILE + 32ll * tid;
     const unsigned bits = base < V ? __ldg(occ + (base >> 5)) : 0u;
-    unsigned sum = 0u;
-    for (unsigned m = bits; m; m &= m - 1u)
-        sum += __ldg(counts + base + __ffs(m) - 1);
-    unsigned tile_total;
-    const unsigned thread_excl = block_excl_scan(sum, s_w, &tile_total);
-
-    // lookback: 512 predecessors per round, nearest first
-    unsigned excl = 0u;
-    if (tile > 0) {
-        long long look = (long long)tile - 1;
-        const unsigned long long t0 = global_timer_ns();
-        for (;;) {
-            const long long idx = look - tid;
-            unsigned long long d = tag | DESC_PREFIX;   // before tile 0: an empty prefix
-            bool late = false;
-            if (idx >= 0) {
-                for (;;) {
-                    d = ld_relaxed_u64(desc + idx);
-                    if (((d >> 34) == epoch) && (d & (3ull << 32)))
-                        break;
-                    if (global_timer_ns() - t0 > SCAN_TIMEOUT_NS || *(volatile unsigned *)&ctl->err != 0u) {
-                        late = true;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            if (__syncthreads_or(late)) {
-                if (tid == 0)
-                    atomicOr(&ctl->err, DEVERR_TIMEOUT);
-                break;
-            }
-            // nearest inclusive prefix in this round
-            if (tid == 0)
-                s_first = SCAN_THREADS;
-            __syncthreads();
-            if (d & DESC_PREFIX)
-                atomicMin(&s_first, (unsigned)tid);
-            __syncthreads();
-            const unsigned first = s_first;
-            const unsigned v = (unsigned)tid <= first ? (unsigned)d : 0u;
-            const unsigned ws = warp_sum_u32(v);
-            if (lane == 0)
-                s_sum[warp] = ws;
-            __syncthreads();
-            unsigned round = 0u;
-#pragma unroll
-            for (int w = 0; w < SCAN_WARPS; ++w)
-                round += s_sum[w];
-            excl += round;
-            __syncthreads();
-            if (first < SCAN_THREADS)
-                break;
-            look -= SCAN_THREADS;
-        }
-        if (tid == 0)
-            st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + s_agg));
+    unsigned long long d0 = 0ull;
+    unsigned t0 = 0u;
+    if ((long long)tile - 1 - tid >= 0) {
+        d0 = ld_relaxed_u64(desc + (tile - 1 - tid));
+        t0 = __ldg(tile_sum + (tile - 1 - tid));
     }
+    unsigned sum = 0u;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        sum += ((bits >> i) & 1u) ? __ldg(counts + base + i) : 0u;
+    unsigned tile_total;
+    const unsigned thread_excl = block_excl_scan(sum, s_w, &tile_total);   // also orders s_epoch
+    const unsigned long long tag = (unsigned long long)s_epoch << 34;
+
+    // lookback: 512 predecessors per round, nearest first (thread i looks at
+    // tile - 1 - i); sum the totals before the nearest published prefix
+    unsigned excl = 0u;
+    for (long long look = (long long)tile - 1; look >= 0; look -= SCAN_THREADS) {
+        const long long idx = look - tid;
+        bool pre = false;
+        unsigned v = 0u;
+        if (idx >= 0) {
+            unsigned long long d = d0;
+            unsigned t = t0;
+            if (look != (long long)tile - 1) {
+                d = ld_relaxed_u64(desc + idx);
+                t = __ldg(tile_sum + idx);
+            }
+            pre = (d >> 34) == (tag >> 34) && (d & DESC_PREFIX);
+            v = pre ? (unsigned)d : t;
+        }
+        const unsigned pm = __ballot_sync(FULL_MASK, pre);
+        if (lane == 0)
+            s_first[warp] = pm ? (unsigned)(warp * 32 + __ffs(pm) - 1) : (unsigned)SCAN_THREADS;
+        __syncthreads();
+        unsigned first = SCAN_THREADS;
+#pragma unroll
+        for (int w = 0; w < SCAN_WARPS; ++w)
+            first = min(first, s_first[w]);
+        const unsigned ws = warp_sum_u32((unsigned)tid <= first ? v : 0u);
+        if (lane == 0)
+            s_sum[warp] = ws;
+        __syncthreads();
+        unsigned round = 0u;
+#pragma unroll
+        for (int w = 0; w < SCAN_WARPS; ++w)
+            round += s_sum[w];
+        excl += round;
+        __syncthreads();   // s_first / s_sum are reused
+        if (first < SCAN_THREADS)
+            break;
+    }
+    if (tid == 0)
+        st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + tile_total));
 
     // the 32 offsets of this thread, staged in shared memory (row stride 33
     // words: conflict-free both ways) and written out with coalesced 16-byte
@@ -499,10 +484,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
     {
         unsigned run = excl + thread_excl;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 32; ++i) {   // the counts again, from L1
             s_off[tid * 33 + i] = run;
-            if ((bits >> i) & 1u)
-                run += __ldg(counts + base + i);
+            run += ((bits >> i) & 1u) ? __ldg(counts + base + i) : 0u;
         }
         if (base < V && base + 32 >= V)   // the thread holding voxel V-1 closes the array
             off[V] = run;
@@ -527,14 +511,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const unsigned *__restric
 }
 
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
-                        unsigned *tile_sum, unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st)
+                        const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st)
 {
     const long long tiles = scan_tiles(g.V);
     const size_t smem = (size_t)SCAN_THREADS * 33 * sizeof(unsigned);
     cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_scan<<<(unsigned)tiles, SCAN_THREADS, smem, st>>>(counts, g.V, off, occ, tile_sum, desc, ctl, skip_tile);
+    k_scan<<<(unsigned)tiles, SCAN_THREADS, smem, st>>>(counts, g.V, off, occ, tile_sum, desc, ctl);
     return cudaGetLastError();
 }
 
@@ -553,8 +537,12 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
                                                  unsigned *__restrict__ bcounts, const int *__restrict__ bslot,
                                                  unsigned *__restrict__ boxord, int *__restrict__ ids,
                                                  float4 *__restrict__ csr, float4 *__restrict__ bpts,
-                                                 int *__restrict__ outside, DevCtl *__restrict__ ctl)
+                                                 int *__restrict__ outside, unsigned *__restrict__ tile_sum,
+                                                 int n_tiles, DevCtl *__restrict__ ctl)
 {
+    // the scan is done with the tile totals: zero them for the next build
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+        tile_sum[t] = 0u;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int key = (j < n) ? __ldg(keys + j) : -2;
@@ -629,11 +617,11 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
 
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
-                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, DevCtl *ctl,
-                           cudaStream_t st)
+                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
+                           DevCtl *ctl, cudaStream_t st)
 {
     k_scatter<<<(n + 255) / 256, 256, 0, st>>>(pts, keys, n, g, off, counts, boff, bcounts, bslot, boxord, ids, csr,
-                                               bpts, outside, ctl);
+                                               bpts, outside, tile_sum, (int)scan_tiles(g.V), ctl);
     return cudaGetLastError();
 }
 
@@ -641,45 +629,74 @@ cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const Grid
 // Brick boxes as floats: the scatter left each non-empty brick's exact bounds
 // as order-preserving unsigned integers; every stored point of the brick lies
 // inside the box as float values, which is what the global search's lower
-// bound needs.  The thread of the first brick of each super-brick (bricks of
-// a super-brick hold consecutive slots) also records the super-brick's slot
-// range and the union of its bricks' boxes.
+// bound needs.  The w fields carry the brick's point range [lo.w, hi.w) (as
+// integer bits), so one pair of loads gives the search both.  The thread of
+// the first brick of each super-brick (bricks of a super-brick hold
+// consecutive slots) also records the union of its bricks' boxes, with the
+// super-brick's brick-slot range in the w fields.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_brick_boxes(const uint4 *__restrict__ boxord, const int *__restrict__ list,
-                                                     float4 *__restrict__ box, uint2 *__restrict__ sb_range,
+                                                     const uint2 *__restrict__ range, float4 *__restrict__ box,
                                                      float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
 {
     const int nb = ctl->n_bricks;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
         const uint4 lo = boxord[2 * k], hi = boxord[2 * k + 1];
-        box[2 * k] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z), 0.0f);
-        box[2 * k + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z), 0.0f);
+        const uint2 r = range[k];
+        box[2 * k] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z),
+                                 __uint_as_float(r.x));
+        box[2 * k + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z),
+                                     __uint_as_float(r.y));
         const int sb = __ldg(list + k) / SUPER_BRICKS;
         if (k == 0 || __ldg(list + k - 1) / SUPER_BRICKS != sb) {
+            // union over the super-brick's bricks (at most 64, consecutive
+            // slots), eight slots per round with their loads in flight together
             uint4 l = lo, h = hi;
             int e = k + 1;
-            for (; e < nb && __ldg(list + e) / SUPER_BRICKS == sb; ++e) {
-                const uint4 l2 = boxord[2 * e], h2 = boxord[2 * e + 1];
-                l = make_uint4(min(l.x, l2.x), min(l.y, l2.y), min(l.z, l2.z), 0u);
-                h = make_uint4(max(h.x, h2.x), max(h.y, h2.y), max(h.z, h2.z), 0u);
+            bool more = true;
+            while (more) {
+                int key[8];
+                uint4 bl[8], bh[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    key[u] = e + u < nb ? __ldg(list + e + u) : -1;
+                    if (key[u] >= 0 && key[u] / SUPER_BRICKS == sb) {
+                        bl[u] = boxord[2 * (e + u)];
+                        bh[u] = boxord[2 * (e + u) + 1];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (more && key[u] >= 0 && key[u] / SUPER_BRICKS == sb) {
+                        l = make_uint4(min(l.x, bl[u].x), min(l.y, bl[u].y), min(l.z, bl[u].z), 0u);
+                        h = make_uint4(max(h.x, bh[u].x), max(h.y, bh[u].y), max(h.z, bh[u].z), 0u);
+                    } else {
+                        more = false;
+                    }
+                }
+                if (more)
+                    e += 8;
             }
+            // e: the first slot past the super-brick
+            while (e < nb && __ldg(list + e) / SUPER_BRICKS == sb)
+                ++e;
             const int slot = atomicAdd(&ctl->n_super, 1);
-            sb_range[slot] = make_uint2((unsigned)k, (unsigned)e);
-            sb_box[2 * slot] = make_float4(ordered_to_float(l.x), ordered_to_float(l.y), ordered_to_float(l.z), 0.f);
-            sb_box[2 * slot + 1] = make_float4(ordered_to_float(h.x), ordered_to_float(h.y), ordered_to_float(h.z), 0.f);
+            sb_box[2 * slot] = make_float4(ordered_to_float(l.x), ordered_to_float(l.y), ordered_to_float(l.z),
+                                           __uint_as_float((unsigned)k));
+            sb_box[2 * slot + 1] = make_float4(ordered_to_float(h.x), ordered_to_float(h.y), ordered_to_float(h.z),
+                                               __uint_as_float((unsigned)e));
         }
     }
 }
 
-cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box,
-                               uint2 *sb_range, float4 *sb_box, DevCtl *ctl, const GridGeom &g, cudaStream_t st)
+cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box, float4 *sb_box,
+                               DevCtl *ctl, const GridGeom &g, cudaStream_t st)
 {
-    (void)range;
     const int nbt = brick_slots(g);
     int blocks = (nbt + 255) / 256;
     if (blocks > 152 * 2)
         blocks = 152 * 2;
-    k_brick_boxes<<<blocks, 256, 0, st>>>(boxord, list, box, sb_range, sb_box, ctl);
+    k_brick_boxes<<<blocks, 256, 0, st>>>(boxord, list, range, box, sb_box, ctl);
     return cudaGetLastError();
 }
 

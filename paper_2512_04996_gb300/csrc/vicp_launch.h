@@ -45,15 +45,15 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
-                        unsigned *tile_sum, unsigned long long *desc, DevCtl *ctl, int skip_tile, cudaStream_t st);
+                        const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
-                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, DevCtl *ctl,
-                           cudaStream_t st);
-cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box,
-                               uint2 *sb_range, float4 *sb_box, DevCtl *ctl, const GridGeom &g, cudaStream_t st);
+                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
+                           DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box, float4 *sb_box,
+                               DevCtl *ctl, const GridGeom &g, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
 // Dilation: `inter` holds V words of pass Y (V x 4 bytes suffices for any
 // L), `rows` dilate_units(g) 32-bit row masks; neither needs clearing.
@@ -63,10 +63,9 @@ long long dilate_units(const GridGeom &g);
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);
-cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const uint2 *brange,
-                            const float4 *bbox, const uint2 *sb_range, const float4 *sb_box, const float4 *tgt,
-                            int n_tgt, const int *outside, const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m,
-                            int honor_stop, cudaStream_t st);
+cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const float4 *bbox,
+                            const float4 *sb_box, const float4 *tgt, int n_tgt, const int *outside, const int *fb_list,
+                            DevCtl *ctl, int *nn, float *d2, int m, int honor_stop, cudaStream_t st);
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
                                 float3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);

@@ -22,9 +22,13 @@ __global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ s
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;
     __shared__ PoseF sp;
-    if (threadIdx.x == 0)
-        load_pose_f(pose, sp);
-    __syncthreads();
+    __shared__ unsigned long long s_cand;   // block totals: one global atomic each
+    __shared__ int s_fb, s_fb_base;
+    if (threadIdx.x == 0) {
+        s_cand = 0ull;
+        s_fb = 0;
+    }
+    load_pose_f_block(pose, sp);   // also orders the initialisation above
     const PoseF P = sp;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool fall = false;
@@ -57,25 +61,36 @@ __global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ s
             fall = true;
         }
     }
-    const unsigned long long wc = warp_sum_u64(cand);
-    if ((threadIdx.x & 31) == 0 && wc)
-        atomicAdd(&ctl->stat_local_cand, wc);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(&ctl->stat_queries, (unsigned long long)m);
+    // The block's fallback queries and work counts are gathered in shared
+    // memory first: same-address global atomics from every warp would
+    // serialise in one L2 slice.
+    const int lane = threadIdx.x & 31;
     const unsigned fm = __ballot_sync(FULL_MASK, fall);
-    if (fm) {
-        const int lane = threadIdx.x & 31, leader = __ffs(fm) - 1;
-        int base = 0;
-        if (lane == leader)
-            base = atomicAdd(&ctl->fb_count, __popc(fm));
-        base = __shfl_sync(FULL_MASK, base, leader);
-        if (fall) {
-            const int slot = base + __popc(fm & lanemask_lt());
-            if (slot < m)
-                fb_list[slot] = i;
-            else
-                atomicOr(&ctl->err, DEVERR_BOUNDS);
-        }
+    const unsigned long long wc = warp_sum_u64(cand);
+    int wbase = 0;
+    if (lane == 0) {
+        if (wc)
+            atomicAdd(&s_cand, wc);
+        if (fm)
+            wbase = atomicAdd(&s_fb, __popc(fm));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cand)
+            atomicAdd(&ctl->stat_local_cand, s_cand);
+        if (blockIdx.x == 0)
+            atomicAdd(&ctl->stat_queries, (unsigned long long)m);
+        if (s_fb)
+            s_fb_base = atomicAdd(&ctl->fb_count, s_fb);
+    }
+    __syncthreads();
+    wbase = __shfl_sync(FULL_MASK, wbase, 0);
+    if (fall) {
+        const int slot = s_fb_base + wbase + __popc(fm & lanemask_lt());
+        if (slot < m)
+            fb_list[slot] = i;
+        else
+            atomicOr(&ctl->err, DEVERR_BOUNDS);
     }
 }
 
@@ -121,30 +136,65 @@ __device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
     return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
 }
 
-__device__ __forceinline__ unsigned lb_bits(float3 s, const float4 *__restrict__ box, int k)
+// Bound (as order-preserving bits) and index range [a, b) of box record k:
+// the boxes carry their ranges in the w fields.
+__device__ __forceinline__ void load_rec(const float4 *__restrict__ box, int k, float3 s, unsigned &lb, unsigned &a,
+                                         unsigned &b)
 {
-    return __float_as_uint(box_lb2(s, __ldg(box + 2 * k), __ldg(box + 2 * k + 1)));
+    const float4 lo = __ldg(box + 2 * k), hi = __ldg(box + 2 * k + 1);
+    lb = __float_as_uint(box_lb2(s, lo, hi));
+    a = __float_as_uint(lo.w);
+    b = __float_as_uint(hi.w);
 }
 
-// All lanes scan the run [r.x, r.y) of brick-ordered points; returns the
-// warp-wide minimum key (every lane gets it).
-__device__ __forceinline__ unsigned long long scan_run(const float4 *__restrict__ bpts, uint2 r, float3 s, int lane,
-                                                       unsigned long long best, unsigned long long &examined)
+// All lanes scan the run [a, b) of brick-ordered points (four loads in
+// flight per lane); returns the warp-wide minimum key (every lane gets it).
+__device__ __forceinline__ unsigned long long scan_run(const float4 *__restrict__ bpts, unsigned a, unsigned b,
+                                                       float3 s, int lane, unsigned long long best,
+                                                       unsigned long long &examined)
 {
-    for (unsigned i = r.x + lane; i < r.y; i += 32) {
+    unsigned i = a + lane;
+    for (; i + 96 < b; i += 128) {
+        const float4 q0 = __ldg(bpts + i), q1 = __ldg(bpts + i + 32);
+        const float4 q2 = __ldg(bpts + i + 64), q3 = __ldg(bpts + i + 96);
+        best = umin64(best, nn_key(dist2(s, q0), __float_as_int(q0.w)));
+        best = umin64(best, nn_key(dist2(s, q1), __float_as_int(q1.w)));
+        best = umin64(best, nn_key(dist2(s, q2), __float_as_int(q2.w)));
+        best = umin64(best, nn_key(dist2(s, q3), __float_as_int(q3.w)));
+    }
+    for (; i < b; i += 32) {
         const float4 q = __ldg(bpts + i);
         best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
     }
-    examined += r.y - r.x;
+    examined += b - a;
     return warp_min_u64(best);
 }
 
-__global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restrict__ src,
+// Scan, in ascending lane order, the bricks of one 32-record chunk whose bound
+// (lb, per lane) is <= the current best distance; (ra, rb) are the bricks'
+// point ranges.
+__device__ __forceinline__ unsigned long long scan_chunk(const float4 *__restrict__ bpts, unsigned lb, unsigned ra,
+                                                         unsigned rb, float3 s, int lane, unsigned long long best,
+                                                         unsigned long long &examined)
+{
+    unsigned c = __ballot_sync(FULL_MASK, lb <= (unsigned)(best >> 32));
+    while (c) {
+        const int l = __ffs(c) - 1;
+        c &= c - 1u;
+        if (__shfl_sync(FULL_MASK, lb, l) > (unsigned)(best >> 32))
+            continue;   // the bound was overtaken by a closer point
+        const unsigned a = __shfl_sync(FULL_MASK, ra, l), b = __shfl_sync(FULL_MASK, rb, l);
+        best = scan_run(bpts, a, b, s, lane, best, examined);
+    }
+    return best;
+}
+
+constexpr int SB_CACHED = 4;   // super-brick records kept in registers: 32 per chunk
+
+__global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__restrict__ src,
                                                          const double *__restrict__ pose,
                                                          const float4 *__restrict__ bpts,
-                                                         const uint2 *__restrict__ brange,
                                                          const float4 *__restrict__ bbox,
-                                                         const uint2 *__restrict__ sb_range,
                                                          const float4 *__restrict__ sb_box,
                                                          const float4 *__restrict__ tgt, int n_tgt,
                                                          const int *__restrict__ outside,
@@ -155,9 +205,10 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;   // the correspond kernel appended nothing either
     __shared__ PoseF sp;
+    __shared__ unsigned long long s_examined;   // block total: one global atomic
     if (threadIdx.x == 0)
-        load_pose_f(pose, sp);
-    __syncthreads();
+        s_examined = 0ull;
+    load_pose_f_block(pose, sp);   // also orders the initialisation above
     const PoseF P = sp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int F = min(*(volatile int *)&ctl->fb_count, m);
@@ -180,41 +231,97 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
             examined += (unsigned long long)n_tgt;
         } else {
             if (ns > 0) {
-                // (1) nearest super-brick, nearest brick in it, scan it
+                // (1) super-brick records (the first SB_CACHED chunks kept in
+                //     registers), the nearest super-brick S0 ...
+                unsigned sl[SB_CACHED], sa[SB_CACHED], sb[SB_CACHED];
                 unsigned long long m0 = ~0ull;
-                for (int k = lane; k < ns; k += 32)
-                    m0 = umin64(m0, ((unsigned long long)lb_bits(s, sb_box, k) << 32) | (unsigned)k);
+#pragma unroll
+                for (int t = 0; t < SB_CACHED; ++t) {
+                    const int k = 32 * t + lane;
+                    sl[t] = 0xffffffffu;
+                    sa[t] = sb[t] = 0u;
+                    if (k < ns)
+                        load_rec(sb_box, k, s, sl[t], sa[t], sb[t]);
+                    m0 = umin64(m0, ((unsigned long long)sl[t] << 32) | (unsigned)k);
+                }
+                for (int k = 32 * SB_CACHED + lane; k < ns; k += 32) {
+                    unsigned lb, a, b;
+                    load_rec(sb_box, k, s, lb, a, b);
+                    m0 = umin64(m0, ((unsigned long long)lb << 32) | (unsigned)k);
+                }
                 m0 = warp_min_u64(m0);
-                const uint2 r0 = __ldg(sb_range + (int)(unsigned)m0);
+                const int s0 = (int)(unsigned)m0;
+                unsigned r0a, r0b;
+                if (s0 < 32 * SB_CACHED) {
+                    unsigned a = 0u, b = 0u;
+#pragma unroll
+                    for (int t = 0; t < SB_CACHED; ++t)
+                        if (t == (s0 >> 5)) {
+                            a = sa[t];
+                            b = sb[t];
+                        }
+                    r0a = __shfl_sync(FULL_MASK, a, s0 & 31);
+                    r0b = __shfl_sync(FULL_MASK, b, s0 & 31);
+                } else {
+                    r0a = __float_as_uint(__ldg(sb_box + 2 * s0).w);
+                    r0b = __float_as_uint(__ldg(sb_box + 2 * s0 + 1).w);
+                }
+                // ... its brick records (at most 64: two chunks, kept), and the
+                //     nearest brick K0 in it, scanned first for a first distance
+                unsigned bl[2], ba[2], bb[2];
                 unsigned long long m1 = ~0ull;
-                for (int k = (int)r0.x + lane; k < (int)r0.y; k += 32)
-                    m1 = umin64(m1, ((unsigned long long)lb_bits(s, bbox, k) << 32) | (unsigned)k);
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int k = (int)r0a + 32 * t + lane;
+                    bl[t] = 0xffffffffu;
+                    ba[t] = bb[t] = 0u;
+                    if (k < (int)r0b)
+                        load_rec(bbox, k, s, bl[t], ba[t], bb[t]);
+                    m1 = umin64(m1, ((unsigned long long)bl[t] << 32) | (unsigned)k);
+                }
                 m1 = warp_min_u64(m1);
-                const int k0 = (int)(unsigned)m1;
-                best = scan_run(bpts, __ldg(brange + k0), s, lane, best, examined);
-                // (2) every super-brick, and brick in it, that could hold a point at distance <= D
-                for (int sb0 = 0; sb0 < ns; sb0 += 32) {
-                    const int sbk = sb0 + lane;
-                    const unsigned lbs = sbk < ns ? lb_bits(s, sb_box, sbk) : 0xffffffffu;
+                const int k0 = (int)(unsigned)m1 - (int)r0a;   // chunk-relative
+                {
+                    const unsigned a = k0 < 32 ? ba[0] : ba[1], b = k0 < 32 ? bb[0] : bb[1];
+                    best = scan_run(bpts, __shfl_sync(FULL_MASK, a, k0 & 31), __shfl_sync(FULL_MASK, b, k0 & 31), s,
+                                    lane, best, examined);
+                }
+                // (2) every super-brick, and brick in it, that could hold a point
+                //     at distance <= D
+                for (int c0 = 0; c0 < ns; c0 += 32) {
+                    const int t = c0 >> 5;
+                    unsigned lbs = 0xffffffffu, ra = 0u, rb = 0u;
+#pragma unroll
+                    for (int c = 0; c < SB_CACHED; ++c)
+                        if (t == c) {
+                            lbs = sl[c];
+                            ra = sa[c];
+                            rb = sb[c];
+                        }
+                    if (t >= SB_CACHED && c0 + lane < ns)
+                        load_rec(sb_box, c0 + lane, s, lbs, ra, rb);
                     unsigned cs = __ballot_sync(FULL_MASK, lbs <= (unsigned)(best >> 32));
                     while (cs) {
-                        const int sl = __ffs(cs) - 1;
+                        const int l = __ffs(cs) - 1;
                         cs &= cs - 1u;
-                        if (__shfl_sync(FULL_MASK, lbs, sl) > (unsigned)(best >> 32))
+                        if (__shfl_sync(FULL_MASK, lbs, l) > (unsigned)(best >> 32))
                             continue;   // the bound was overtaken by a closer point
-                        const uint2 r = __ldg(sb_range + sb0 + sl);
-                        for (int kb = (int)r.x; kb < (int)r.y; kb += 32) {
-                            const int k = kb + lane;
-                            const unsigned lbb =
-                                (k < (int)r.y && k != k0) ? lb_bits(s, bbox, k) : 0xffffffffu;
-                            unsigned cb = __ballot_sync(FULL_MASK, lbb <= (unsigned)(best >> 32));
-                            while (cb) {
-                                const int bl = __ffs(cb) - 1;
-                                cb &= cb - 1u;
-                                if (__shfl_sync(FULL_MASK, lbb, bl) > (unsigned)(best >> 32))
-                                    continue;
-                                best = scan_run(bpts, __ldg(brange + kb + bl), s, lane, best, examined);
+                        if (c0 + l == s0) {   // S0: its records are in registers; K0 is done
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                const bool k0_here = (k0 >> 5) == u && (k0 & 31) == lane;
+                                best = scan_chunk(bpts, k0_here ? 0xffffffffu : bl[u], ba[u], bb[u], s, lane, best,
+                                                  examined);
                             }
+                            continue;
+                        }
+                        const unsigned a = __shfl_sync(FULL_MASK, ra, l), b = __shfl_sync(FULL_MASK, rb, l);
+                        for (int kb = (int)a; kb < (int)b; kb += 32) {
+                            const int k = kb + lane;
+                            unsigned lbb = 0xffffffffu, pa = 0u, pb = 0u;
+                            if (k < (int)b)
+                                load_rec(bbox, k, s, lbb, pa, pb);
+                            best = scan_chunk(bpts, lbb, pa, pb, s, lane, best, examined);
                         }
                     }
                 }
@@ -232,11 +339,14 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
             d2[i] = __uint_as_float((unsigned)(best >> 32));
         }
     }
+    // work counter: one global atomic per block; the last block to finish
+    // clears the fallback counter for the next search
     if (lane == 0 && examined)
-        atomicAdd(&ctl->stat_global_cand, examined);
-    // The last block to finish clears the fallback counter for the next search.
+        atomicAdd(&s_examined, examined);
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (s_examined)
+            atomicAdd(&ctl->stat_global_cand, s_examined);
         __threadfence();
         const unsigned done = atomicAdd(&ctl->fb_done, 1u);
         if (done == gridDim.x - 1) {
@@ -247,13 +357,22 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(const float4 *__restric
     }
 }
 
-cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const uint2 *brange,
-                            const float4 *bbox, const uint2 *sb_range, const float4 *sb_box, const float4 *tgt,
-                            int n_tgt, const int *outside, const int *fb_list, DevCtl *ctl, int *nn, float *d2, int m,
-                            int honor_stop, cudaStream_t st)
+cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const float4 *bbox,
+                            const float4 *sb_box, const float4 *tgt, int n_tgt, const int *outside, const int *fb_list,
+                            DevCtl *ctl, int *nn, float *d2, int m, int honor_stop, cudaStream_t st)
 {
-    k_fallback<<<152 * 4, FB_THREADS, 0, st>>>(src, pose, bpts, brange, bbox, sb_range, sb_box, tgt, n_tgt, outside,
-                                               fb_list, ctl, nn, d2, m, honor_stop);
+    // as many warps as can be resident: a query per warp at most times
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback, FB_THREADS, 0);
+        if (e != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_fallback<<<sms * per_sm, FB_THREADS, 0, st>>>(src, pose, bpts, bbox, sb_box, tgt, n_tgt, outside, fb_list, ctl,
+                                                    nn, d2, m, honor_stop);
     return cudaGetLastError();
 }
 

@@ -208,9 +208,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
     __shared__ double s_red[RED_THREADS / 32][REDUCE_VALUES];
     __shared__ float s_hi[RED_THREADS / 32][REDUCE_VALUES], s_lo[RED_THREADS / 32][REDUCE_VALUES];
     __shared__ int s_last;
-    if (threadIdx.x == 0)
-        load_pose_f(pose, sp);
-    __syncthreads();
+    load_pose_f_block(pose, sp);
     const PoseF P = sp;
     dfl acc[REDUCE_VALUES];
 #pragma unroll

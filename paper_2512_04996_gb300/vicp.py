@@ -33,7 +33,6 @@ VICP_STATIC_MAX_VOXELS = 1 << 24
 VICP_STATIC_MAX_BRICK_SLOTS = 1 << 20
 VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
-VICP_FLAG_TEST_SCAN_TIMEOUT = 1 << 31
 
 
 class VicpError(RuntimeError):

@@ -1,7 +1,6 @@
-"""Failure handling without faulting the GPU: a bounded device-side wait that
-runs out returns VICP_ERR_TIMEOUT and leaves the context usable; an
-allocator that returns NULL gives VICP_ERR_OOM and leaks nothing; calls out
-of order return VICP_ERR_STATE."""
+"""Failure handling without faulting the GPU: an allocator that returns NULL
+gives VICP_ERR_OOM and leaks nothing; calls out of order return
+VICP_ERR_STATE; an oversized grid is refused before any launch."""
 import ctypes as C
 
 import numpy as np
@@ -11,22 +10,6 @@ import torch
 from gpu_util import assert_grid_equal, context, gpu_grid, oracle_grid_for, to_np, vicp
 
 pytestmark = pytest.mark.gpu
-
-
-def test_scan_wait_times_out_and_context_recovers(pairs):
-    """One scan tile never publishes its aggregate (test flag): its successor
-    waits 200 ms on the global timer, gives up, records the timeout and
-    publishes anyway; the host sees VICP_ERR_TIMEOUT."""
-    v = vicp()
-    p = pairs(2)                        # ~2M voxels: hundreds of scan tiles
-    ctx = context(L=10, divisions=128, flags=v.VICP_FLAG_TEST_SCAN_TIMEOUT)
-    ctx.build_grid(torch.from_numpy(p.target).cuda())
-    assert ctx.sync() == v.VICP_ERR_TIMEOUT
-    assert ctx.sync() == 0              # the status was cleared
-    # a normal context afterwards is exact, so the device is fine
-    ctx2, g = gpu_grid(p.target, L=10, divisions=128)
-    grid, ref = oracle_grid_for(g, p.target, 10)
-    assert_grid_equal(g, ref, p.target)
 
 
 def test_allocator_failure_is_reported_and_nothing_leaks(pairs):
