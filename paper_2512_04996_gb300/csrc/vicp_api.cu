@@ -402,7 +402,7 @@ vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double
     const float3 ctr = grid_center(c->geom);
     const int nparts = reduce_blocks(m, c->sms);
     TRY(launch(c, K_REDUCE_SOLVE, [&] {
-        return launch_reduce_solve(src, m, pose, c->target, c->n_target, nn, ctr, (double *)c->partials.p, nparts,
+        return launch_reduce_solve(src, m, pose, c->target, c->n_target, nn, ctr, (float2 *)c->partials.p, nparts,
                                    rmse, ctl_of(c), honor_stop, c->params.rmse_eps, c->stream);
     }));
     return VICP_OK;
@@ -573,7 +573,7 @@ vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_al
     if (s == VICP_OK)
         s = buf_zero(c, c->ctl, "zero control block");
     if (s == VICP_OK)
-        s = buf_alloc(c, c->partials, REDUCE_MAX_BLOCKS * REDUCE_VALUES * sizeof(double), "partials");
+        s = buf_alloc(c, c->partials, REDUCE_MAX_BLOCKS * REDUCE_VALUES * sizeof(float2), "partials");
     if (s == VICP_OK)
         s = buf_alloc(c, c->pose, 16 * sizeof(double), "pose");
     if (s == VICP_OK)

@@ -67,7 +67,7 @@ cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 
                             const float4 *sb_box, const float4 *tgt, int n_tgt, const int *outside, const int *fb_list,
                             DevCtl *ctl, int *nn, float *d2, int m, int honor_stop, cudaStream_t st);
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
-                                float3 center, double *partials, int nparts, double *rmse_out, DevCtl *ctl,
+                                float3 center, float2 *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);
 
 }  // namespace vicp
