@@ -46,7 +46,9 @@ struct vicp_ctx {
     const float4 *target = nullptr;   // caller's target of the last build (global search)
 
     // V-sized
-    Buf counts, off, root, ring, occ, desc, tile_sum, inter, uflag;
+    Buf counts, off, root, ring, desc, tile_sum, inter, uflag;
+    Buf occ[2];       // occupancy bits: the current build's, and the next build's (kept zeroed)
+    int occ_cur = 0;
     long long cap_V = -1;
     // brick level (V / 512)
     Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_box;
@@ -192,8 +194,10 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->root, (size_t)V * 4, "root"));
         TRY(buf_alloc(c, c->ring, (size_t)V, "ring"));
         TRY(buf_alloc(c, c->inter, (size_t)V * 4, "dilation pass-Y words"));
-        TRY(buf_alloc(c, c->occ, (size_t)occ_words(V) * 4, "occupancy"));
-        TRY(buf_zero(c, c->occ, "zero occupancy"));
+        for (Buf &o : c->occ) {
+            TRY(buf_alloc(c, o, (size_t)occ_words(V) * 4, "occupancy"));
+            TRY(buf_zero(c, o, "zero occupancy"));
+        }
         TRY(buf_alloc(c, c->desc, (size_t)scan_tiles(V) * 8, "scan descriptors"));
         TRY(buf_zero(c, c->desc, "zero scan descriptors"));
         TRY(buf_alloc(c, c->tile_sum, (size_t)scan_tiles(V) * 4, "scan tile sums"));
@@ -423,12 +427,16 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     TRY(ensure_voxel_buffers(c, g.V, brick_slots(g)));
     TRY(ensure_point_buffers(c, n));
     DevCtl *d = ctl_of(c);
+    // this build fills the zeroed occupancy buffer; its scatter clears the other
+    c->occ_cur ^= 1;
+    unsigned *occ = (unsigned *)c->occ[c->occ_cur].p;
+    Buf &occ_next = c->occ[c->occ_cur ^ 1];
     TRY(launch(c, K_HISTOGRAM, [&] {
-        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p,
-                                (unsigned *)c->occ.p, (unsigned *)c->tile_sum.p, d, c->stream);
+        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, occ,
+                                (unsigned *)c->tile_sum.p, d, c->stream);
     }));
     TRY(launch(c, K_SCAN, [&] {
-        return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, (const unsigned *)c->occ.p,
+        return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, occ,
                            (const unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, c->stream);
     }));
     TRY(launch(c, K_BRICK_SCAN, [&] {
@@ -439,7 +447,8 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
         return launch_scatter(tgt, (const int *)c->keys.p, n, g, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
                               (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (const int *)c->bslot.p,
                               (unsigned *)c->boxord.p, (int *)c->ids.p, (float4 *)c->csr.p, (float4 *)c->bpts.p,
-                              (int *)c->outside.p, (unsigned *)c->tile_sum.p, d, c->stream);
+                              (int *)c->outside.p, (unsigned *)c->tile_sum.p, (unsigned *)occ_next.p,
+                              (long long)(occ_next.bytes / 4), d, c->stream);
     }));
     TRY(launch(c, K_BRICK_BOXES, [&] {
         return launch_brick_boxes((const uint4 *)c->boxord.p, (const int *)c->brick_list.p,
@@ -461,7 +470,7 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     if (L > DILATE_MAX_L)
         return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
     TRY(launch(c, K_DILATE, [&] {
-        return launch_dilate((const unsigned *)c->occ.p, c->geom, L, c->inter.p, (unsigned *)c->uflag.p,
+        return launch_dilate((const unsigned *)c->occ[c->occ_cur].p, c->geom, L, c->inter.p, (unsigned *)c->uflag.p,
                              (int *)c->root.p, (unsigned char *)c->ring.p, c->stream);
     }));
     c->dilated_L = L;
@@ -593,7 +602,7 @@ void vicp_destroy(vicp_ctx *c)
     if (!c)
         return;
     cudaStreamSynchronize(c->stream);
-    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ,       &c->desc, &c->tile_sum,
+    Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ[0],    &c->occ[1], &c->desc, &c->tile_sum,
                   &c->inter,       &c->uflag,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
                   &c->boxord,  &c->sb_box,  &c->keys,
@@ -745,7 +754,7 @@ vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
     out->csr_points = (const float *)c->csr.p;
     out->root = (const int32_t *)c->root.p;
     out->ring = (const uint8_t *)c->ring.p;
-    out->occupancy = (const uint32_t *)c->occ.p;
+    out->occupancy = (const uint32_t *)c->occ[c->occ_cur].p;
     return st;
 }
 

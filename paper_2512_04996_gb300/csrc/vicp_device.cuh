@@ -9,6 +9,18 @@ namespace vicp {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_begin(): it waits until the kernel before it in the stream has
+// completed and its writes are visible (so each kernel sees exactly what
+// plain stream order gives it), then lets the next kernel's blocks be
+// scheduled onto the SMs while this one runs, which takes the launch latency
+// out of the gap between the two.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Voxel grid geometry passed by value to kernels.  Keys are
 // x + nx*(y + ny*z) (x fastest, the neighbour offsets +-1, +-2^N, +-2^2N of
 // Alg. 3); V < 2^31 so keys fit int32.

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restric
                                                        typename W::Stored *__restrict__ inter,
                                                        unsigned *__restrict__ rows)
 {
+    pdl_begin();
     constexpr unsigned STEP_YF = (1u << W::SD) - (1u << W::SY);   // moved from y-1 to y: dy -= 1
     constexpr unsigned STEP_YB = (1u << W::SD) + (1u << W::SY);   // moved from y+1 to y: dy += 1
     const int lane = threadIdx.x & 31;
@@ -258,6 +259,7 @@ __global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *
                                                       int nyb, int units, int *__restrict__ root,
                                                       unsigned char *__restrict__ ring)
 {
+    pdl_begin();
     constexpr unsigned STEP_ZF = (1u << W::ZD) - (1u << W::ZZ);   // moved from z-1 to z: dz -= 1
     constexpr unsigned STEP_ZB = (1u << W::ZD) + (1u << W::ZZ);   // moved from z+1 to z: dz += 1
     const int lane = threadIdx.x & 31;
@@ -349,15 +351,13 @@ static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, voi
     using S = typename W::Stored;
     const int nxb = (g.nx + UX - 1) / UX, nyb = (g.ny + UY - 1) / UY, nzb = (g.nz + UZ - 1) / UZ;
     const int u_xy = nxb * nyb * g.nz;   // < V < 2^31
-    k_dilate_xy<W><<<(u_xy + WARPS - 1) / WARPS, THREADS, 0, st>>>(occ, occ_words(g.V), g, L, nxb, nyb, u_xy,
-                                                                    static_cast<S *>(inter), rows);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_kernel(k_dilate_xy<W>, dim3((u_xy + WARPS - 1) / WARPS), dim3(THREADS), 0, st, occ,
+                                  occ_words(g.V), g, L, nxb, nyb, u_xy, static_cast<S *>(inter), rows);
     if (e != cudaSuccess)
         return e;
     const int u_z = nxb * g.ny * nzb;   // < V < 2^31
-    k_dilate_z<W><<<(u_z + WARPS - 1) / WARPS, THREADS, 0, st>>>(static_cast<const S *>(inter), rows, g, L, nxb, nyb,
-                                                                  u_z, root, ring);
-    return cudaGetLastError();
+    return launch_kernel(k_dilate_z<W>, dim3((u_z + WARPS - 1) / WARPS), dim3(THREADS), 0, st,
+                         static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, root, ring);
 }
 
 long long dilate_units(const GridGeom &g)

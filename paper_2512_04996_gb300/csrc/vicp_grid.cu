@@ -25,6 +25,7 @@ __device__ __forceinline__ float ordered_to_float(unsigned o)
 
 __global__ void __launch_bounds__(256) k_bbox(const float4 *__restrict__ pts, int n, unsigned *__restrict__ out)
 {
+    pdl_begin();
     float lo[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
     float hi[3] = {-lo[0], -lo[1], -lo[2]};
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -60,8 +61,7 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
     int blocks = (n + 255) / 256;
     if (blocks > 1216)
         blocks = 1216;
-    k_bbox<<<blocks, 256, 0, st>>>(pts, n, bbox6);
-    return cudaGetLastError();
+    return launch_kernel(k_bbox, dim3(blocks), dim3(256), 0, st, pts, n, bbox6);
 }
 
 // ---------------------------------------------------------------------------
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
                                                    unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
                                                    unsigned *__restrict__ tile_sum, DevCtl *__restrict__ ctl)
 {
+    pdl_begin();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
@@ -119,12 +120,9 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st)
 {
-    // the occupancy bits are rebuilt from zero every build
-    cudaError_t e = cudaMemsetAsync(occ, 0, (size_t)occ_words(g.V) * sizeof(unsigned), st);
-    if (e != cudaSuccess)
-        return e;
-    k_histogram<<<(n + 255) / 256, 256, 0, st>>>(pts, n, g, keys, counts, bcounts, occ, tile_sum, ctl);
-    return cudaGetLastError();
+    // occ must hold zeros: the caller clears it beforehand
+    return launch_kernel(k_histogram, dim3((n + 255) / 256), dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ,
+                         tile_sum, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -150,6 +148,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__res
                                                            uint2 *__restrict__ range, int *__restrict__ bslot,
                                                            uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
 {
+    pdl_begin();
     extern __shared__ unsigned s_c[];   // [BS_CHUNK]
     __shared__ unsigned long long s_w[BS_THREADS / 32];
     __shared__ unsigned long long s_carry;
@@ -251,6 +250,7 @@ __global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned 
                                                                  uint2 *__restrict__ range, int *__restrict__ bslot,
                                                                  uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
 {
+    pdl_begin();
     __shared__ unsigned long long s_w[BM_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b0 = blockIdx.x * BM_THREADS;
@@ -317,16 +317,15 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 {
     const int nbt = brick_slots(g);
     if (nbt <= BM_MAX_BRICKS) {
-        k_brick_scan_multi<<<(nbt + BM_THREADS - 1) / BM_THREADS, BM_THREADS, 0, st>>>(bcounts, nbt, boff, list, range,
-                                                                                       bslot, boxord, ctl);
-        return cudaGetLastError();
+        return launch_kernel(k_brick_scan_multi, dim3((nbt + BM_THREADS - 1) / BM_THREADS), dim3(BM_THREADS), 0, st,
+                             bcounts, nbt, boff, list, range, bslot, boxord, ctl);
     }
     const size_t smem = BS_CHUNK * sizeof(unsigned);
     cudaError_t e = cudaFuncSetAttribute(k_brick_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_brick_scan<<<1, BS_THREADS, smem, st>>>(bcounts, nbt, boff, list, range, bslot, boxord, ctl);
-    return cudaGetLastError();
+    return launch_kernel(k_brick_scan, dim3(1), dim3(BS_THREADS), smem, st, bcounts, nbt, boff, list, range, bslot,
+                         boxord, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,6 +410,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__rest
                                                        unsigned long long *__restrict__ desc,
                                                        const DevCtl *__restrict__ ctl)
 {
+    pdl_begin();
     __shared__ unsigned s_epoch, s_w[SCAN_WARPS + 1], s_first[SCAN_WARPS], s_sum[SCAN_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned tile = blockIdx.x;
@@ -518,8 +518,8 @@ cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off
     cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_scan<<<(unsigned)tiles, SCAN_THREADS, smem, st>>>(counts, g.V, off, occ, tile_sum, desc, ctl);
-    return cudaGetLastError();
+    return launch_kernel(k_scan, dim3((unsigned)tiles), dim3(SCAN_THREADS), smem, st, counts, g.V, off, occ, tile_sum,
+                         desc, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -538,11 +538,16 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
                                                  unsigned *__restrict__ boxord, int *__restrict__ ids,
                                                  float4 *__restrict__ csr, float4 *__restrict__ bpts,
                                                  int *__restrict__ outside, unsigned *__restrict__ tile_sum,
-                                                 int n_tiles, DevCtl *__restrict__ ctl)
+                                                 int n_tiles, unsigned *__restrict__ occ_next,
+                                                 long long occ_next_words, DevCtl *__restrict__ ctl)
 {
-    // the scan is done with the tile totals: zero them for the next build
+    pdl_begin();
+    // the scan is done with the tile totals: zero them for the next build,
+    // and clear the occupancy buffer the next build will fill
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
         tile_sum[t] = 0u;
+    for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < occ_next_words; w += gridDim.x * blockDim.x)
+        occ_next[w] = 0u;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int key = (j < n) ? __ldg(keys + j) : -2;
@@ -618,11 +623,11 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
                            unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
-                           DevCtl *ctl, cudaStream_t st)
+                           unsigned *occ_next, long long occ_next_words, DevCtl *ctl, cudaStream_t st)
 {
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(pts, keys, n, g, off, counts, boff, bcounts, bslot, boxord, ids, csr,
-                                               bpts, outside, tile_sum, (int)scan_tiles(g.V), ctl);
-    return cudaGetLastError();
+    return launch_kernel(k_scatter, dim3((n + 255) / 256), dim3(256), 0, st, pts, keys, n, g, off, counts, boff,
+                         bcounts, bslot, boxord, ids, csr, bpts, outside, tile_sum, (int)scan_tiles(g.V), occ_next,
+                         occ_next_words, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -639,6 +644,7 @@ __global__ void __launch_bounds__(256) k_brick_boxes(const uint4 *__restrict__ b
                                                      const uint2 *__restrict__ range, float4 *__restrict__ box,
                                                      float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
 {
+    pdl_begin();
     const int nb = ctl->n_bricks;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
         const uint4 lo = boxord[2 * k], hi = boxord[2 * k + 1];
@@ -696,8 +702,7 @@ cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2
     int blocks = (nbt + 255) / 256;
     if (blocks > 152 * 2)
         blocks = 152 * 2;
-    k_brick_boxes<<<blocks, 256, 0, st>>>(boxord, list, range, box, sb_box, ctl);
-    return cudaGetLastError();
+    return launch_kernel(k_brick_boxes, dim3(blocks), dim3(256), 0, st, boxord, list, range, box, sb_box, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -706,6 +711,7 @@ cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2
 __global__ void __launch_bounds__(256) k_maxcount(const unsigned *__restrict__ off, long long V,
                                                   DevCtl *__restrict__ ctl)
 {
+    pdl_begin();
     unsigned mx = 0u, occupied = 0u;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V;
          v += (long long)gridDim.x * blockDim.x) {
@@ -729,8 +735,7 @@ cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl,
     long long blocks = (g.V + 255) / 256;
     if (blocks > 2432)
         blocks = 2432;
-    k_maxcount<<<(unsigned)blocks, 256, 0, st>>>(off, g.V, ctl);
-    return cudaGetLastError();
+    return launch_kernel(k_maxcount, dim3((unsigned)blocks), dim3(256), 0, st, off, g.V, ctl);
 }
 
 }  // namespace vicp

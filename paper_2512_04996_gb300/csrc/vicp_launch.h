@@ -2,9 +2,30 @@
 // C ABI runtime (vicp_api.cu).  Each returns the launch's cudaError_t.
 #pragma once
 
+#include <utility>
+
 #include "vicp_device.cuh"
 
 namespace vicp {
+
+// Launch with programmatic stream serialisation allowed (the kernel itself
+// waits for its predecessor in pdl_begin()).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Kernel identifiers for launch accounting and event timing.
 enum KernelId {
@@ -42,16 +63,19 @@ inline int reduce_blocks(int m, int sms)
 }
 
 cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t st);
+// occ must hold zeros (the previous build's scatter clears it).
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
                         const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st);
+// The scatter also zeroes the tile totals and the occupancy buffer of the
+// next build (occ_next, occ_next_words words).
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
                            unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
-                           DevCtl *ctl, cudaStream_t st);
+                           unsigned *occ_next, long long occ_next_words, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box, float4 *sb_box,
                                DevCtl *ctl, const GridGeom &g, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);

@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ s
                                                     int *__restrict__ fb_list, DevCtl *__restrict__ ctl,
                                                     int honor_stop)
 {
+    pdl_begin();
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;
     __shared__ PoseF sp;
@@ -98,9 +99,8 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st)
 {
-    k_correspond<<<(m + 255) / 256, 256, 0, st>>>(src, m, pose, g, root, off, csr, n_cap, nn, d2, fb_list, ctl,
-                                                  honor_stop);
-    return cudaGetLastError();
+    return launch_kernel(k_correspond, dim3((m + 255) / 256), dim3(256), 0, st, src, m, pose, g, root, off, csr, n_cap,
+                         nn, d2, fb_list, ctl, honor_stop);
 }
 
 // ---------------------------------------------------------------------------
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
                                                          DevCtl *__restrict__ ctl, int *__restrict__ nn,
                                                          float *__restrict__ d2, int m, int honor_stop)
 {
+    pdl_begin();
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;   // the correspond kernel appended nothing either
     __shared__ PoseF sp;
@@ -371,9 +372,8 @@ cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_fallback<<<sms * per_sm, FB_THREADS, 0, st>>>(src, pose, bpts, bbox, sb_box, tgt, n_tgt, outside, fb_list, ctl,
-                                                    nn, d2, m, honor_stop);
-    return cudaGetLastError();
+    return launch_kernel(k_fallback, dim3(sms * per_sm), dim3(FB_THREADS), 0, st, src, pose, bpts, bbox, sb_box, tgt,
+                         n_tgt, outside, fb_list, ctl, nn, d2, m, honor_stop);
 }
 
 }  // namespace vicp

@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
                                                               double *__restrict__ rmse_out,
                                                               DevCtl *__restrict__ ctl, int honor_stop, double eps)
 {
+    pdl_begin();
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;
     __shared__ PoseF sp;
@@ -523,9 +524,8 @@ cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const fl
                                 float3 center, float2 *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st)
 {
-    k_reduce_solve<<<nparts, RED_THREADS, 0, st>>>(src, m, pose, tgt, n_tgt, nn, center, partials, rmse_out, ctl,
-                                                   honor_stop, eps);
-    return cudaGetLastError();
+    return launch_kernel(k_reduce_solve, dim3(nparts), dim3(RED_THREADS), 0, st, src, m, pose, tgt, n_tgt, nn, center,
+                         partials, rmse_out, ctl, honor_stop, eps);
 }
 
 }  // namespace vicp

@@ -114,7 +114,7 @@ extern "C" VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, in
     unsigned *bcounts = reinterpret_cast<unsigned *>(base + OFF_BRICKS);
 
     // The scratch keeps the last call's contents: clear everything that must
-    // start at zero (the occupancy bits are cleared by the histogram launch).
+    // start at zero.
     const long long nt = scan_tiles(g.V);
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DevCtl), st);
     if (e == cudaSuccess)
@@ -125,6 +125,8 @@ extern "C" VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, in
         e = cudaMemsetAsync(desc, 0, (size_t)nt * 8, st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(bcounts, 0, (size_t)brick_slots(g) * 4, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(occ, 0, (size_t)occ_words(g.V) * 4, st);
     if (e == cudaSuccess)
         e = launch_histogram(reinterpret_cast<const float4 *>(target_xyzw), n, g, keys_out, counts, bcounts, occ,
                              tiles, ctl, st);
