@@ -57,7 +57,7 @@ struct vicp_ctx {
     Buf keys, ids, csr, bpts, outside;
     long long cap_N = -1;
     // M-sized
-    Buf nn, d2, fb_list;
+    Buf nn, d2, fb_list, hv_list, hv_range;
     long long cap_M = -1;
     // fixed
     Buf partials, pose, rmse, ctl, bbox;
@@ -241,6 +241,8 @@ vicp_status ensure_query_buffers(vicp_ctx *c, long long m)
         TRY(buf_alloc(c, c->nn, (size_t)m * 4, "nn"));
         TRY(buf_alloc(c, c->d2, (size_t)m * 4, "d2"));
         TRY(buf_alloc(c, c->fb_list, (size_t)m * 4, "fallback list"));
+        TRY(buf_alloc(c, c->hv_list, (size_t)m * 4, "dense segment list"));
+        TRY(buf_alloc(c, c->hv_range, (size_t)m * 8, "dense segment ranges"));
         c->cap_M = m;
     }
     return VICP_OK;
@@ -387,13 +389,14 @@ vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, i
     DevCtl *d = ctl_of(c);
     TRY(launch(c, K_CORRESPOND, [&] {
         return launch_correspond(src, m, pose, g, (const int *)c->root.p, (const unsigned *)c->off.p,
-                                 (const float4 *)c->csr.p, c->n_target, nn, d2, (int *)c->fb_list.p, d,
-                                 honor_stop, c->stream);
+                                 (const float4 *)c->csr.p, c->n_target, nn, d2, (int *)c->fb_list.p,
+                                 (int *)c->hv_list.p, (uint2 *)c->hv_range.p, d, honor_stop, c->stream);
     }));
     TRY(launch(c, K_FALLBACK, [&] {
         return launch_fallback(src, pose, (const float4 *)c->bpts.p, (const float4 *)c->brick_box.p,
                                (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
-                               (const int *)c->fb_list.p, d, nn, d2, m, honor_stop, c->stream);
+                               (const int *)c->fb_list.p, (const int *)c->hv_list.p, (const uint2 *)c->hv_range.p,
+                               (const float4 *)c->csr.p, d, nn, d2, m, honor_stop, c->stream);
     }));
     return VICP_OK;
 }
@@ -607,7 +610,7 @@ void vicp_destroy(vicp_ctx *c)
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
                   &c->boxord,  &c->sb_box,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
-                  &c->fb_list, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
+                  &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt};
     for (Buf *b : all)
         buf_free(c, *b);
@@ -661,7 +664,8 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
         TRY(launch(c, K_CORRESPOND, [&] {
             return launch_correspond(src, n_src, pose_dev, c->geom, (const int *)c->root.p,
                                      (const unsigned *)c->off.p, (const float4 *)c->csr.p, c->n_target, nn_out,
-                                     d2_out, (int *)c->fb_list.p, d, 0, c->stream);
+                                     d2_out, (int *)c->fb_list.p, (int *)c->hv_list.p, (uint2 *)c->hv_range.p, d,
+                                     0, c->stream);
         }));
         cudaError_t e = cudaMemcpyAsync(n_fallback_out, &d->fb_count, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                         c->stream);
@@ -670,7 +674,9 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
         TRY(launch(c, K_FALLBACK, [&] {
             return launch_fallback(src, pose_dev, (const float4 *)c->bpts.p, (const float4 *)c->brick_box.p,
                                    (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
-                                   (const int *)c->fb_list.p, d, nn_out, d2_out, n_src, 0, c->stream);
+                                   (const int *)c->fb_list.p, (const int *)c->hv_list.p,
+                                   (const uint2 *)c->hv_range.p, (const float4 *)c->csr.p, d, nn_out, d2_out, n_src, 0,
+                                   c->stream);
         }));
         return VICP_OK;
     }

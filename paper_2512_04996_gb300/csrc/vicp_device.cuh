@@ -58,7 +58,7 @@ struct DevCtl {
     unsigned max_count;     // memory report: largest voxel count
     unsigned occupied;      // memory report: occupied voxels
     unsigned red_done;      // reduction: finished blocks (the last one solves and resets it)
-    int reserved0;
+    int hv_count;           // correspond: dense segments listed; reset by the fallback kernel
     unsigned reserved1;
     int n_super;            // non-empty super-bricks; reset by the histogram
     int pad1;

@@ -84,12 +84,17 @@ cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl,
 cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
                           unsigned char *ring, cudaStream_t st);
 long long dilate_units(const GridGeom &g);
+// The localised search lists queries whose root segment is long (with the
+// segment) in hv_list / hv_range and queries without a root in fb_list; the
+// fallback kernel then answers both lists.
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
-                              int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st);
+                              int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
+                              cudaStream_t st);
 cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const float4 *bbox,
                             const float4 *sb_box, const float4 *tgt, int n_tgt, const int *outside, const int *fb_list,
-                            DevCtl *ctl, int *nn, float *d2, int m, int honor_stop, cudaStream_t st);
+                            const int *hv_list, const uint2 *hv_range, const float4 *csr, DevCtl *ctl, int *nn,
+                            float *d2, int m, int honor_stop, cudaStream_t st);
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
                                 float3 center, float2 *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);

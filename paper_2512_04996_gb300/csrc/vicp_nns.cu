@@ -8,72 +8,84 @@ namespace vicp {
 // Localised search: one thread per source point.  The point is transformed
 // by the float-rounded pose, quantised, and its voxel's root label followed
 // once (Alg. 4); the root voxel's CSR segment is scanned with 16-byte loads
-// of (x, y, z, index).  Points that need the global search are compacted
-// into a list with one warp-aggregated atomic per warp.
+// of (x, y, z, index), eight in flight.  A few dense voxels hold far more
+// points than the rest, and a warp waits for its longest segment: a query
+// whose segment has more than HEAVY points is not scanned here but listed,
+// with its segment, for the next kernel, whose warps take such segments one
+// at a time with all lanes.  Points that need the global search are listed
+// for it.  Both lists get one global atomic per block.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ src, int m,
-                                                    const double *__restrict__ pose, GridGeom g,
-                                                    const int *__restrict__ root, const unsigned *__restrict__ off,
-                                                    const float4 *__restrict__ csr, int n_cap,
-                                                    int *__restrict__ nn, float *__restrict__ d2,
-                                                    int *__restrict__ fb_list, DevCtl *__restrict__ ctl,
-                                                    int honor_stop)
+constexpr unsigned HEAVY = 32;
+constexpr int CORR_THREADS = 512;
+
+__global__ void __launch_bounds__(CORR_THREADS) k_correspond(const float4 *__restrict__ src, int m,
+                                                             const double *__restrict__ pose, GridGeom g,
+                                                             const int *__restrict__ root,
+                                                             const unsigned *__restrict__ off,
+                                                             const float4 *__restrict__ csr, int n_cap,
+                                                             int *__restrict__ nn, float *__restrict__ d2,
+                                                             int *__restrict__ fb_list, int *__restrict__ hv_list,
+                                                             uint2 *__restrict__ hv_range, DevCtl *__restrict__ ctl,
+                                                             int honor_stop)
 {
     pdl_begin();
     if (honor_stop && *(volatile int *)&ctl->stop)
         return;
     __shared__ PoseF sp;
     __shared__ unsigned long long s_cand;   // block totals: one global atomic each
-    __shared__ int s_fb, s_fb_base;
+    __shared__ int s_fb, s_fb_base, s_hv, s_hv_base;
     if (threadIdx.x == 0) {
         s_cand = 0ull;
-        s_fb = 0;
+        s_fb = s_hv = 0;
     }
     load_pose_f_block(pose, sp);   // also orders the initialisation above
     const PoseF P = sp;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool fall = false;
-    unsigned cand = 0u;
+    const int lane = threadIdx.x & 31;
+    bool fall = false, heavy = false;
+    unsigned cand = 0u, a = 0u, b = 0u;
     if (i < m) {
         const float3 s = transform_pt(P, __ldg(src + i));
         const int v = voxel_key(g, s.x, s.y, s.z);
         const int r = (v >= 0) ? __ldg(root + v) : -1;
         if (r >= 0) {
-            const unsigned a = __ldg(off + r);
-            const unsigned b = min(__ldg(off + r + 1), (unsigned)n_cap);
-            cand = b > a ? b - a : 0u;
-            unsigned long long best = ~0ull;
-            unsigned k = a;
-            for (; k + 4 <= b; k += 4) {   // four independent loads in flight
-                const float4 q0 = __ldg(csr + k), q1 = __ldg(csr + k + 1);
-                const float4 q2 = __ldg(csr + k + 2), q3 = __ldg(csr + k + 3);
-                best = umin64(best, nn_key(dist2(s, q0), __float_as_int(q0.w)));
-                best = umin64(best, nn_key(dist2(s, q1), __float_as_int(q1.w)));
-                best = umin64(best, nn_key(dist2(s, q2), __float_as_int(q2.w)));
-                best = umin64(best, nn_key(dist2(s, q3), __float_as_int(q3.w)));
+            a = __ldg(off + r);
+            b = max(a, min(__ldg(off + r + 1), (unsigned)n_cap));
+            cand = b - a;
+            heavy = cand > HEAVY;
+            if (!heavy) {
+                unsigned long long best = ~0ull;
+                unsigned k = a;
+                for (; k + 8 <= b; k += 8) {
+                    float4 q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        q[u] = __ldg(csr + k + u);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        best = umin64(best, nn_key(dist2(s, q[u]), __float_as_int(q[u].w)));
+                }
+                for (; k < b; ++k) {
+                    const float4 q = __ldg(csr + k);
+                    best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
+                }
+                nn[i] = (int)(unsigned)best;
+                d2[i] = __uint_as_float((unsigned)(best >> 32));
             }
-            for (; k < b; ++k) {
-                const float4 q = __ldg(csr + k);
-                best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
-            }
-            nn[i] = (int)(unsigned)best;
-            d2[i] = __uint_as_float((unsigned)(best >> 32));
         } else {
             fall = true;
         }
     }
-    // The block's fallback queries and work counts are gathered in shared
-    // memory first: same-address global atomics from every warp would
-    // serialise in one L2 slice.
-    const int lane = threadIdx.x & 31;
-    const unsigned fm = __ballot_sync(FULL_MASK, fall);
+    const unsigned fm = __ballot_sync(FULL_MASK, fall), hm = __ballot_sync(FULL_MASK, heavy);
     const unsigned long long wc = warp_sum_u64(cand);
-    int wbase = 0;
+    int fb_base = 0, hv_base = 0;
     if (lane == 0) {
         if (wc)
             atomicAdd(&s_cand, wc);
         if (fm)
-            wbase = atomicAdd(&s_fb, __popc(fm));
+            fb_base = atomicAdd(&s_fb, __popc(fm));
+        if (hm)
+            hv_base = atomicAdd(&s_hv, __popc(hm));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -83,24 +95,37 @@ __global__ void __launch_bounds__(256) k_correspond(const float4 *__restrict__ s
             atomicAdd(&ctl->stat_queries, (unsigned long long)m);
         if (s_fb)
             s_fb_base = atomicAdd(&ctl->fb_count, s_fb);
+        if (s_hv)
+            s_hv_base = atomicAdd(&ctl->hv_count, s_hv);
     }
     __syncthreads();
-    wbase = __shfl_sync(FULL_MASK, wbase, 0);
+    fb_base = __shfl_sync(FULL_MASK, fb_base, 0);
+    hv_base = __shfl_sync(FULL_MASK, hv_base, 0);
     if (fall) {
-        const int slot = s_fb_base + wbase + __popc(fm & lanemask_lt());
+        const int slot = s_fb_base + fb_base + __popc(fm & lanemask_lt());
         if (slot < m)
             fb_list[slot] = i;
         else
             atomicOr(&ctl->err, DEVERR_BOUNDS);
     }
+    if (heavy) {
+        const int slot = s_hv_base + hv_base + __popc(hm & lanemask_lt());
+        if (slot < m) {
+            hv_list[slot] = i;
+            hv_range[slot] = make_uint2(a, b);
+        } else {
+            atomicOr(&ctl->err, DEVERR_BOUNDS);
+        }
+    }
 }
 
 cudaError_t launch_correspond(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
-                              int *fb_list, DevCtl *ctl, int honor_stop, cudaStream_t st)
+                              int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
+                              cudaStream_t st)
 {
-    return launch_kernel(k_correspond, dim3((m + 255) / 256), dim3(256), 0, st, src, m, pose, g, root, off, csr, n_cap,
-                         nn, d2, fb_list, ctl, honor_stop);
+    return launch_kernel(k_correspond, dim3((m + CORR_THREADS - 1) / CORR_THREADS), dim3(CORR_THREADS), 0, st, src, m,
+                         pose, g, root, off, csr, n_cap, nn, d2, fb_list, hv_list, hv_range, ctl, honor_stop);
 }
 
 // ---------------------------------------------------------------------------
@@ -128,16 +153,46 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
 constexpr int FB_THREADS = 256;
 constexpr int FB_WARPS = FB_THREADS / 32;
 
+// The gap on an axis is max(lo - s, s - hi, 0): at most one difference is
+// positive, and rounding keeps each difference's sign.
 __device__ __forceinline__ float box_lb2(float3 s, float4 lo, float4 hi)
 {
-    const float ex = s.x < lo.x ? __fsub_rn(lo.x, s.x) : (s.x > hi.x ? __fsub_rn(s.x, hi.x) : 0.0f);
-    const float ey = s.y < lo.y ? __fsub_rn(lo.y, s.y) : (s.y > hi.y ? __fsub_rn(s.y, hi.y) : 0.0f);
-    const float ez = s.z < lo.z ? __fsub_rn(lo.z, s.z) : (s.z > hi.z ? __fsub_rn(s.z, hi.z) : 0.0f);
+    const float ex = fmaxf(fmaxf(__fsub_rn(lo.x, s.x), __fsub_rn(s.x, hi.x)), 0.0f);
+    const float ey = fmaxf(fmaxf(__fsub_rn(lo.y, s.y), __fsub_rn(s.y, hi.y)), 0.0f);
+    const float ez = fmaxf(fmaxf(__fsub_rn(lo.z, s.z), __fsub_rn(s.z, hi.z)), 0.0f);
     return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
 }
 
-// Bound (as order-preserving bits) and index range [a, b) of box record k:
-// the boxes carry their ranges in the w fields.
+// Record index of the smallest bound over the warp (lane values lb, k; any
+// lane holding the minimum may win: the choice only orders the search).
+__device__ __forceinline__ int warp_argmin(unsigned lb, int k)
+{
+    const unsigned mn = __reduce_min_sync(FULL_MASK, lb);
+    return __shfl_sync(FULL_MASK, k, __ffs(__ballot_sync(FULL_MASK, lb == mn)) - 1);
+}
+
+// Warp minimum of (distance bits, index) keys: the smallest distance, then
+// the smallest index at it -- two single-instruction warp reductions.
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v)
+{
+    const unsigned d = __reduce_min_sync(FULL_MASK, (unsigned)(v >> 32));
+    const unsigned i = __reduce_min_sync(FULL_MASK, (unsigned)(v >> 32) == d ? (unsigned)v : 0xffffffffu);
+    return ((unsigned long long)d << 32) | i;
+}
+
+// Bound of box record k (as order-preserving bits), and its index range
+// [a, b) (the boxes carry their ranges in the w fields).
+__device__ __forceinline__ unsigned box_bound(const float4 *__restrict__ box, int k, float3 s)
+{
+    return __float_as_uint(box_lb2(s, __ldg(box + 2 * k), __ldg(box + 2 * k + 1)));
+}
+
+__device__ __forceinline__ uint2 box_range(const float4 *__restrict__ box, int k)
+{
+    return make_uint2(__float_as_uint(__ldg(box + 2 * k).w), __float_as_uint(__ldg(box + 2 * k + 1).w));
+}
+
+// Bound and index range of box record k.
 __device__ __forceinline__ void load_rec(const float4 *__restrict__ box, int k, float3 s, unsigned &lb, unsigned &a,
                                          unsigned &b)
 {
@@ -167,7 +222,7 @@ __device__ __forceinline__ unsigned long long scan_run(const float4 *__restrict_
         best = umin64(best, nn_key(dist2(s, q), __float_as_int(q.w)));
     }
     examined += b - a;
-    return warp_min_u64(best);
+    return warp_min_key(best);
 }
 
 // Scan, in ascending lane order, the bricks of one 32-record chunk whose bound
@@ -199,6 +254,9 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
                                                          const float4 *__restrict__ tgt, int n_tgt,
                                                          const int *__restrict__ outside,
                                                          const int *__restrict__ fb_list,
+                                                         const int *__restrict__ hv_list,
+                                                         const uint2 *__restrict__ hv_range,
+                                                         const float4 *__restrict__ csr,
                                                          DevCtl *__restrict__ ctl, int *__restrict__ nn,
                                                          float *__restrict__ d2, int m, int honor_stop)
 {
@@ -213,11 +271,34 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
     const PoseF P = sp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int F = min(*(volatile int *)&ctl->fb_count, m);
+    const int Hv = min(*(volatile int *)&ctl->hv_count, m);
     const int ns = *(volatile int *)&ctl->n_super;
     const int no = *(volatile int *)&ctl->n_outside;
     unsigned long long examined = 0ull;   // every lane counts the same; lane 0 reports
 
-    for (int qi = blockIdx.x * FB_WARPS + warp; qi < F; qi += gridDim.x * FB_WARPS) {
+    // the dense root segments the localised search left: all lanes scan one.
+    // They go to the warps in reverse order: the global queries below go in
+    // forward order, so the warps left one global query short take the extra
+    // segments.
+    const int n_warps = gridDim.x * FB_WARPS, gw = blockIdx.x * FB_WARPS + warp;
+    for (int qi = n_warps - 1 - gw; qi < Hv; qi += n_warps) {
+        const int i = __ldg(hv_list + qi);
+        const uint2 r = __ldg(hv_range + qi);
+        if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
+            if (lane == 0)
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+            continue;
+        }
+        const float3 s = transform_pt(P, __ldg(src + i));
+        unsigned long long unused = 0ull;
+        const unsigned long long best = scan_run(csr, r.x, r.y, s, lane, ~0ull, unused);
+        if (lane == 0) {
+            nn[i] = (int)(unsigned)best;
+            d2[i] = __uint_as_float((unsigned)(best >> 32));
+        }
+    }
+
+    for (int qi = gw; qi < F; qi += n_warps) {
         const int i = __ldg(fb_list + qi);
         if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
             if (lane == 0)
@@ -232,74 +313,112 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
             examined += (unsigned long long)n_tgt;
         } else {
             if (ns > 0) {
-                // (1) super-brick records (the first SB_CACHED chunks kept in
-                //     registers), the nearest super-brick S0 ...
-                unsigned sl[SB_CACHED], sa[SB_CACHED], sb[SB_CACHED];
-                unsigned long long m0 = ~0ull;
+                // (1) super-brick bounds (the first SB_CACHED chunks kept in
+                //     registers; ranges are fetched from L1 when a record is
+                //     picked), the nearest super-brick S0 ...
+                unsigned sl[SB_CACHED];
+                unsigned lmin = 0xffffffffu;
+                int kmin = lane;
 #pragma unroll
                 for (int t = 0; t < SB_CACHED; ++t) {
                     const int k = 32 * t + lane;
                     sl[t] = 0xffffffffu;
-                    sa[t] = sb[t] = 0u;
                     if (k < ns)
-                        load_rec(sb_box, k, s, sl[t], sa[t], sb[t]);
-                    m0 = umin64(m0, ((unsigned long long)sl[t] << 32) | (unsigned)k);
+                        sl[t] = box_bound(sb_box, k, s);
+                    if (sl[t] < lmin) {
+                        lmin = sl[t];
+                        kmin = k;
+                    }
                 }
                 for (int k = 32 * SB_CACHED + lane; k < ns; k += 32) {
-                    unsigned lb, a, b;
-                    load_rec(sb_box, k, s, lb, a, b);
-                    m0 = umin64(m0, ((unsigned long long)lb << 32) | (unsigned)k);
+                    const unsigned lb = box_bound(sb_box, k, s);
+                    if (lb < lmin) {
+                        lmin = lb;
+                        kmin = k;
+                    }
                 }
-                m0 = warp_min_u64(m0);
-                const int s0 = (int)(unsigned)m0;
-                unsigned r0a, r0b;
-                if (s0 < 32 * SB_CACHED) {
-                    unsigned a = 0u, b = 0u;
-#pragma unroll
-                    for (int t = 0; t < SB_CACHED; ++t)
-                        if (t == (s0 >> 5)) {
-                            a = sa[t];
-                            b = sb[t];
-                        }
-                    r0a = __shfl_sync(FULL_MASK, a, s0 & 31);
-                    r0b = __shfl_sync(FULL_MASK, b, s0 & 31);
-                } else {
-                    r0a = __float_as_uint(__ldg(sb_box + 2 * s0).w);
-                    r0b = __float_as_uint(__ldg(sb_box + 2 * s0 + 1).w);
-                }
-                // ... its brick records (at most 64: two chunks, kept), and the
+                const int s0 = min(warp_argmin(lmin, kmin), ns - 1);
+                uint2 r0 = box_range(sb_box, s0);
+                // ... its bricks' bounds (at most 64: two chunks, kept), and the
                 //     nearest brick K0 in it, scanned first for a first distance
-                unsigned bl[2], ba[2], bb[2];
-                unsigned long long m1 = ~0ull;
+                unsigned bl[2];
+                unsigned bmin = 0xffffffffu;
+                int bk = lane;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const int k = (int)r0a + 32 * t + lane;
-                    bl[t] = 0xffffffffu;
-                    ba[t] = bb[t] = 0u;
-                    if (k < (int)r0b)
-                        load_rec(bbox, k, s, bl[t], ba[t], bb[t]);
-                    m1 = umin64(m1, ((unsigned long long)bl[t] << 32) | (unsigned)k);
+                    const int k = 32 * t + lane;   // relative to the super-brick's first brick
+                    bl[t] = (int)r0.x + k < (int)r0.y ? box_bound(bbox, (int)r0.x + k, s) : 0xffffffffu;
+                    if (bl[t] < bmin) {
+                        bmin = bl[t];
+                        bk = k;
+                    }
                 }
-                m1 = warp_min_u64(m1);
-                const int k0 = (int)(unsigned)m1 - (int)r0a;   // chunk-relative
+                int k0 = min(warp_argmin(bmin, bk), (int)(r0.y - r0.x) - 1);
                 {
-                    const unsigned a = k0 < 32 ? ba[0] : ba[1], b = k0 < 32 ? bb[0] : bb[1];
-                    best = scan_run(bpts, __shfl_sync(FULL_MASK, a, k0 & 31), __shfl_sync(FULL_MASK, b, k0 & 31), s,
-                                    lane, best, examined);
+                    const uint2 pr = box_range(bbox, (int)r0.x + k0);
+                    best = scan_run(bpts, pr.x, pr.y, s, lane, best, examined);
                 }
-                // (2) every super-brick, and brick in it, that could hold a point
-                //     at distance <= D
-                for (int c0 = 0; c0 < ns; c0 += 32) {
-                    const int t = c0 >> 5;
-                    unsigned lbs = 0xffffffffu, ra = 0u, rb = 0u;
+                // (2) best first: the unvisited super-brick of smallest bound
+                //     while that bound is <= D, and in it the unvisited brick
+                //     of smallest bound while that bound is <= D
 #pragma unroll
-                    for (int c = 0; c < SB_CACHED; ++c)
-                        if (t == c) {
-                            lbs = sl[c];
-                            ra = sa[c];
-                            rb = sb[c];
+                for (int t = 0; t < SB_CACHED; ++t)
+                    if (32 * t + lane == s0)
+                        sl[t] = 0xffffffffu;
+                if ((k0 & 31) == lane) {   // K0 is done
+                    if (k0 < 32)
+                        bl[0] = 0xffffffffu;
+                    else
+                        bl[1] = 0xffffffffu;
+                }
+                for (;;) {
+                    // bricks of the current super-brick (first r0.x), nearest first
+                    for (;;) {
+                        const bool first = bl[0] <= bl[1];
+                        const unsigned v = first ? bl[0] : bl[1];
+                        const unsigned mn = __reduce_min_sync(FULL_MASK, v);
+                        if (mn > (unsigned)(best >> 32))
+                            break;
+                        const int w = __ffs(__ballot_sync(FULL_MASK, v == mn)) - 1;
+                        const int rel = __shfl_sync(FULL_MASK, first ? lane : 32 + lane, w);
+                        if (lane == w) {
+                            if (first)
+                                bl[0] = 0xffffffffu;
+                            else
+                                bl[1] = 0xffffffffu;
                         }
-                    if (t >= SB_CACHED && c0 + lane < ns)
+                        const uint2 pr = box_range(bbox, (int)r0.x + rel);
+                        best = scan_run(bpts, pr.x, pr.y, s, lane, best, examined);
+                    }
+                    // the next super-brick
+                    unsigned v = 0xffffffffu;
+                    int vk = lane;
+#pragma unroll
+                    for (int t = 0; t < SB_CACHED; ++t)
+                        if (sl[t] < v) {
+                            v = sl[t];
+                            vk = 32 * t + lane;
+                        }
+                    const unsigned mn = __reduce_min_sync(FULL_MASK, v);
+                    if (mn > (unsigned)(best >> 32))
+                        break;
+                    const int w = __ffs(__ballot_sync(FULL_MASK, v == mn)) - 1;
+                    const int sk = __shfl_sync(FULL_MASK, vk, w);
+#pragma unroll
+                    for (int t = 0; t < SB_CACHED; ++t)
+                        if (lane == w && 32 * t + lane == sk)
+                            sl[t] = 0xffffffffu;
+                    r0 = box_range(sb_box, sk);
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {   // at most 64 bricks in a super-brick
+                        const int k = (int)r0.x + 32 * t + lane;
+                        bl[t] = k < (int)r0.y ? box_bound(bbox, k, s) : 0xffffffffu;
+                    }
+                }
+                // super-bricks past the cached chunks, in index order
+                for (int c0 = 32 * SB_CACHED; c0 < ns; c0 += 32) {
+                    unsigned lbs = 0xffffffffu, ra = 0u, rb = 0u;
+                    if (c0 + lane < ns)
                         load_rec(sb_box, c0 + lane, s, lbs, ra, rb);
                     unsigned cs = __ballot_sync(FULL_MASK, lbs <= (unsigned)(best >> 32));
                     while (cs) {
@@ -307,20 +426,11 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
                         cs &= cs - 1u;
                         if (__shfl_sync(FULL_MASK, lbs, l) > (unsigned)(best >> 32))
                             continue;   // the bound was overtaken by a closer point
-                        if (c0 + l == s0) {   // S0: its records are in registers; K0 is done
-#pragma unroll
-                            for (int u = 0; u < 2; ++u) {
-                                const bool k0_here = (k0 >> 5) == u && (k0 & 31) == lane;
-                                best = scan_chunk(bpts, k0_here ? 0xffffffffu : bl[u], ba[u], bb[u], s, lane, best,
-                                                  examined);
-                            }
-                            continue;
-                        }
-                        const unsigned a = __shfl_sync(FULL_MASK, ra, l), b = __shfl_sync(FULL_MASK, rb, l);
-                        for (int kb = (int)a; kb < (int)b; kb += 32) {
+                        const unsigned xa = __shfl_sync(FULL_MASK, ra, l), xb = __shfl_sync(FULL_MASK, rb, l);
+                        for (int kb = (int)xa; kb < (int)xb; kb += 32) {
                             const int k = kb + lane;
                             unsigned lbb = 0xffffffffu, pa = 0u, pb = 0u;
-                            if (k < (int)b)
+                            if (k < (int)xb)
                                 load_rec(bbox, k, s, lbb, pa, pb);
                             best = scan_chunk(bpts, lbb, pa, pb, s, lane, best, examined);
                         }
@@ -334,7 +444,7 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
             }
             examined += (unsigned long long)no;
         }
-        best = warp_min_u64(best);
+        best = warp_min_key(best);
         if (lane == 0) {
             nn[i] = (int)(unsigned)best;
             d2[i] = __uint_as_float((unsigned)(best >> 32));
@@ -353,6 +463,7 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
         if (done == gridDim.x - 1) {
             ctl->stat_fallbacks += (unsigned long long)F;
             ctl->fb_count = 0;
+            ctl->hv_count = 0;
             ctl->fb_done = 0u;
         }
     }
@@ -360,9 +471,10 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
 
 cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const float4 *bbox,
                             const float4 *sb_box, const float4 *tgt, int n_tgt, const int *outside, const int *fb_list,
-                            DevCtl *ctl, int *nn, float *d2, int m, int honor_stop, cudaStream_t st)
+                            const int *hv_list, const uint2 *hv_range, const float4 *csr, DevCtl *ctl, int *nn,
+                            float *d2, int m, int honor_stop, cudaStream_t st)
 {
-    // as many warps as can be resident: a query per warp at most times
+    // as many warps as can be resident
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback, FB_THREADS, 0);
@@ -373,7 +485,7 @@ cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return launch_kernel(k_fallback, dim3(sms * per_sm), dim3(FB_THREADS), 0, st, src, pose, bpts, bbox, sb_box, tgt,
-                         n_tgt, outside, fb_list, ctl, nn, d2, m, honor_stop);
+                         n_tgt, outside, fb_list, hv_list, hv_range, csr, ctl, nn, d2, m, honor_stop);
 }
 
 }  // namespace vicp
