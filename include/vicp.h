@@ -157,7 +157,8 @@ VICP_API vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, cons
 VICP_API void vicp_destroy(vicp_ctx *ctx);
 
 /* Rebinds the context to another stream (work already issued stays on the
- * old one; synchronise first if ordering matters). */
+ * old one, and the internal dilation stream's ordering refers to it:
+ * synchronise first). */
 VICP_API vicp_status vicp_set_stream(vicp_ctx *ctx, void *cuda_stream);
 
 /* Grid build = Alg. 1 + Alg. 2: quantise every target point into its voxel
@@ -179,8 +180,11 @@ VICP_API vicp_status vicp_build_grid(vicp_ctx *ctx, const float *target_xyzw, in
  * occupied root voxel at the smallest distance (ties: smallest voxel index)
  * and that distance as its ring; the result equals `layers` synchronous
  * rounds of six-neighbour propagation.  layers < 0 uses
- * params.dilation_layers; 0 <= layers <= 31.  Errors: VICP_ERR_STATE before
- * a build, VICP_ERR_INVALID, VICP_ERR_CUDA. */
+ * params.dilation_layers; 0 <= layers <= 31.  The dilation depends only on
+ * the build's first kernel, so it runs on a second, internal stream,
+ * concurrently with the rest of the build; the context's stream then waits
+ * for it, so work issued on that stream after this call sees its results.
+ * Errors: VICP_ERR_STATE before a build, VICP_ERR_INVALID, VICP_ERR_CUDA. */
 VICP_API vicp_status vicp_dilate(vicp_ctx *ctx, int32_t layers);
 
 /* NNS = Alg. 4: transform each source point by the pose (entries rounded to

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "vicp.h"
@@ -32,6 +33,13 @@ struct vicp_ctx {
     vicp_allocator alloc{};
     bool custom_alloc = false;
     cudaStream_t stream = nullptr;
+    // The dilation needs only the histogram's occupancy bits, so it runs on a
+    // second stream, concurrently with the rest of the build: `side` waits
+    // for ev_hist (after the histogram) and ev_nns (after the last search,
+    // which reads root/ring); the context's stream waits for ev_dil (after
+    // the dilation), so everything issued later sees its results.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_hist = nullptr, ev_nns = nullptr, ev_dil = nullptr;
     int device = 0;
     int sms = 152;
     std::string last_error;
@@ -46,7 +54,9 @@ struct vicp_ctx {
     const float4 *target = nullptr;   // caller's target of the last build (global search)
 
     // V-sized
-    Buf counts, off, root, ring, desc, tile_sum, inter, uflag;
+    Buf counts, off, root, ring, desc, tile_sum, inter, uflag, zdirty;
+    bool labels_clean = false;   // root/ring "unlabelled" except where zdirty marks labels
+    int lab_dims[3] = {0, 0, 0};   // grid dimensions that state belongs to
     Buf occ[2];       // occupancy bits: the current build's, and the next build's (kept zeroed)
     int occ_cur = 0;
     long long cap_V = -1;
@@ -163,23 +173,29 @@ cudaEvent_t take_event(vicp_ctx *c)
 }
 
 template <typename F>
-vicp_status launch(vicp_ctx *c, int kernel, F &&f)
+vicp_status launch_on(vicp_ctx *c, int kernel, cudaStream_t st, F &&f)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->profiling) {
         e0 = take_event(c);
-        cudaEventRecord(e0, c->stream);
+        cudaEventRecord(e0, st);
     }
     cudaError_t e = f();
     if (c->profiling) {
         e1 = take_event(c);
-        cudaEventRecord(e1, c->stream);
+        cudaEventRecord(e1, st);
         c->pending.push_back({kernel, e0, e1});
     }
     c->launches += kernel == K_DILATE ? 2 : 1;   // the dilation is two kernels
     if (e != cudaSuccess)
         return fail(c, VICP_ERR_CUDA, "launch of %s: %s", kernel_name(kernel), cudaGetErrorString(e));
     return VICP_OK;
+}
+
+template <typename F>
+vicp_status launch(vicp_ctx *c, int kernel, F &&f)
+{
+    return launch_on(c, kernel, c->stream, std::forward<F>(f));
 }
 
 DevCtl *ctl_of(vicp_ctx *c) { return static_cast<DevCtl *>(c->ctl.p); }
@@ -193,6 +209,7 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->off, (size_t)(V + 1) * 4, "offsets"));
         TRY(buf_alloc(c, c->root, (size_t)V * 4, "root"));
         TRY(buf_alloc(c, c->ring, (size_t)V, "ring"));
+        c->labels_clean = false;
         TRY(buf_alloc(c, c->inter, (size_t)V * 4, "dilation pass-Y words"));
         for (Buf &o : c->occ) {
             TRY(buf_alloc(c, o, (size_t)occ_words(V) * 4, "occupancy"));
@@ -206,6 +223,10 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
     }
     if (dilate_units(c->geom) * 4 > (long long)c->uflag.bytes) {
         TRY(buf_alloc(c, c->uflag, (size_t)dilate_units(c->geom) * 4, "dilation row masks"));
+    }
+    if (dilate_column_units(c->geom) > (long long)c->zdirty.bytes) {
+        TRY(buf_alloc(c, c->zdirty, (size_t)dilate_column_units(c->geom), "dilation label flags"));
+        c->labels_clean = false;
     }
     if (n_bricks > c->cap_bricks) {
         TRY(buf_alloc(c, c->bcounts, (size_t)n_bricks * 4, "brick counts"));
@@ -398,7 +419,8 @@ vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, i
                                (const int *)c->fb_list.p, (const int *)c->hv_list.p, (const uint2 *)c->hv_range.p,
                                (const float4 *)c->csr.p, d, nn, d2, m, honor_stop, c->stream);
     }));
-    return VICP_OK;
+    cudaError_t e = cudaEventRecord(c->ev_nns, c->stream);   // a later dilation waits for this search
+    return e == cudaSuccess ? VICP_OK : cuda_fail(c, e, "event record");
 }
 
 vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double *rmse, int honor_stop)
@@ -438,6 +460,9 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
         return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, occ,
                                 (unsigned *)c->tile_sum.p, d, c->stream);
     }));
+    cudaError_t ev = cudaEventRecord(c->ev_hist, c->stream);   // the dilation may start from here
+    if (ev != cudaSuccess)
+        return cuda_fail(c, ev, "event record");
     TRY(launch(c, K_SCAN, [&] {
         return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, occ,
                            (const unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, c->stream);
@@ -472,10 +497,36 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     const int L = layers < 0 ? c->params.dilation_layers : layers;
     if (L > DILATE_MAX_L)
         return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
-    TRY(launch(c, K_DILATE, [&] {
-        return launch_dilate((const unsigned *)c->occ[c->occ_cur].p, c->geom, L, c->inter.p, (unsigned *)c->uflag.p,
-                             (int *)c->root.p, (unsigned char *)c->ring.p, c->stream);
+    const GridGeom &g = c->geom;
+    // on the side stream, after the histogram and after the last search
+    cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_hist, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->side, c->ev_nns, 0);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream wait");
+    if (!c->labels_clean || c->lab_dims[0] != g.nx || c->lab_dims[1] != g.ny || c->lab_dims[2] != g.nz) {
+        // new arrays or new dimensions: every voxel "unlabelled" (all bytes 0xff), no labels recorded
+        e = cudaMemsetAsync(c->root.p, 0xff, (size_t)g.V * 4, c->side);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->ring.p, 0xff, (size_t)g.V, c->side);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->zdirty.p, 0, (size_t)dilate_column_units(g), c->side);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "clear root/ring");
+        c->labels_clean = true;
+        c->lab_dims[0] = g.nx;
+        c->lab_dims[1] = g.ny;
+        c->lab_dims[2] = g.nz;
+    }
+    TRY(launch_on(c, K_DILATE, c->side, [&] {
+        return launch_dilate((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p, (unsigned *)c->uflag.p,
+                             (unsigned char *)c->zdirty.p, (int *)c->root.p, (unsigned char *)c->ring.p, c->side);
     }));
+    e = cudaEventRecord(c->ev_dil, c->side);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->stream, c->ev_dil, 0);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream wait");
     c->dilated_L = L;
     return VICP_OK;
 }
@@ -577,6 +628,14 @@ vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_al
     }
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&c->device);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_hist, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_nns, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_dil, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        vicp_destroy(c);
+        return VICP_ERR_CUDA;
+    }
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1) {
         cudaGetLastError();
         c->sms = 152;
@@ -605,8 +664,10 @@ void vicp_destroy(vicp_ctx *c)
     if (!c)
         return;
     cudaStreamSynchronize(c->stream);
+    if (c->side)
+        cudaStreamSynchronize(c->side);
     Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ[0],    &c->occ[1], &c->desc, &c->tile_sum,
-                  &c->inter,       &c->uflag,
+                  &c->inter,       &c->uflag,      &c->zdirty,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
                   &c->boxord,  &c->sb_box,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
@@ -620,6 +681,11 @@ void vicp_destroy(vicp_ctx *c)
     }
     for (cudaEvent_t e : c->event_pool)
         cudaEventDestroy(e);
+    for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil})
+        if (e)
+            cudaEventDestroy(e);
+    if (c->side)
+        cudaStreamDestroy(c->side);
     delete c;
 }
 
@@ -678,7 +744,8 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
                                    (const uint2 *)c->hv_range.p, (const float4 *)c->csr.p, d, nn_out, d2_out, n_src, 0,
                                    c->stream);
         }));
-        return VICP_OK;
+        e = cudaEventRecord(c->ev_nns, c->stream);   // a later dilation waits for this search
+        return e == cudaSuccess ? VICP_OK : cuda_fail(c, e, "event record");
     }
     return run_nns(c, src, n_src, pose_dev, nn_out, d2_out, 0);
 }

@@ -31,14 +31,17 @@
 // k_dilate_xy runs passes X and Y for units of 32 x 32 voxels of one
 // z-plane (a warp each, a lane per x): the lanes load the occupancy bits of
 // the unit's rows grown by L, and a unit with no occupied voxel in reach only
-// records a zero flag.  The others write their pass-Y words to an
+// records a zero row mask.  The others write their pass-Y words to an
 // intermediate array (16 bits a word while L <= 15).  All words a warp needs
 // are loaded (or shuffled in) before its sweeps, so each sweep is a chain of
 // register operations rather than of memory latencies.  k_dilate_z then runs
 // pass Z for columns of 32 voxels (a warp per 32 x 32 columns of one row y,
-// a lane per x), reading only planes whose unit flag is set, and writes root
-// and ring for every voxel; a column with no flagged plane in reach writes
-// "unlabelled" at once.  L <= 31.
+// a lane per x), reading only planes whose row mask is set, and writes root
+// and ring.  root and ring keep "unlabelled" between dilations everywhere
+// but where the last dilation wrote labels (a flag per column unit), so a
+// column unit with nothing in reach now and no labels before writes nothing;
+// the host clears both arrays in full only when they are new or the grid's
+// dimensions change.  L <= 31.
 #include "vicp_launch.h"
 
 namespace vicp {
@@ -149,18 +152,13 @@ __device__ __forceinline__ void sweep32(unsigned (&c)[32], unsigned before, unsi
 // whose words are not written).
 // ---------------------------------------------------------------------------
 template <class W>
-__global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restrict__ occ, long long n_words, GridGeom g,
-                                                       int L, int nxb, int nyb, int units,
-                                                       typename W::Stored *__restrict__ inter,
-                                                       unsigned *__restrict__ rows)
+__device__ __forceinline__ void dilate_xy_unit(int u, const unsigned *__restrict__ occ, long long n_words,
+                                               const GridGeom &g, int L, int nxb, int nyb,
+                                               typename W::Stored *__restrict__ inter, unsigned *__restrict__ rows)
 {
-    pdl_begin();
     constexpr unsigned STEP_YF = (1u << W::SD) - (1u << W::SY);   // moved from y-1 to y: dy -= 1
     constexpr unsigned STEP_YB = (1u << W::SD) + (1u << W::SY);   // moved from y+1 to y: dy += 1
     const int lane = threadIdx.x & 31;
-    const int u = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (u >= units)
-        return;
     const int xb = u % nxb, q = u / nxb;
     const int yb = q % nyb, z = q / nyb;
     const int x0 = xb * UX, y0 = yb * UY;
@@ -246,6 +244,17 @@ __global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restric
     }
 }
 
+template <class W>
+__global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restrict__ occ, long long n_words, GridGeom g,
+                                                       int L, int nxb, int nyb, int units,
+                                                       typename W::Stored *__restrict__ inter,
+                                                       unsigned *__restrict__ rows)
+{
+    pdl_begin();
+    for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
+        dilate_xy_unit<W>(u, occ, n_words, g, L, nxb, nyb, inter, rows);
+}
+
 // ---------------------------------------------------------------------------
 // Pass Z and the output.  Warp u = xb + nxb*(y + ny*zb) covers x in
 // [32xb, 32xb+32) of row y, z in [32zb, 32zb+32).  Lane l reads whether row y
@@ -254,18 +263,14 @@ __global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restric
 // intermediate array, all before the sweeps (halo planes four at a time).
 // ---------------------------------------------------------------------------
 template <class W>
-__global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *__restrict__ inter,
-                                                      const unsigned *__restrict__ rows, GridGeom g, int L, int nxb,
-                                                      int nyb, int units, int *__restrict__ root,
-                                                      unsigned char *__restrict__ ring)
+__device__ __forceinline__ void dilate_z_unit(int u, const typename W::Stored *__restrict__ inter,
+                                              const unsigned *__restrict__ rows, unsigned char *__restrict__ dirty,
+                                              const GridGeom &g, int L, int nxb, int nyb, int *__restrict__ root,
+                                              unsigned char *__restrict__ ring)
 {
-    pdl_begin();
     constexpr unsigned STEP_ZF = (1u << W::ZD) - (1u << W::ZZ);   // moved from z-1 to z: dz -= 1
     constexpr unsigned STEP_ZB = (1u << W::ZD) + (1u << W::ZZ);   // moved from z+1 to z: dz += 1
     const int lane = threadIdx.x & 31;
-    const int u = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (u >= units)
-        return;
     const int xb = u % nxb, q = u / nxb;
     const int y = q % g.ny, zb = q / g.ny;
     const int x0 = xb * UX, z0 = zb * UZ, yb = y / UY, ybit = y & (UY - 1);
@@ -285,9 +290,15 @@ __global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *
             set = (__ldg(rows + (z * nyb + yb) * nxb + xb) >> ybit) & 1u;
         pm[j] = __ballot_sync(FULL_MASK, set);
     }
-    if (x >= g.nx)
+    // A unit with nothing within L keeps "unlabelled" unless the previous
+    // dilation labelled some of its voxels; those are reset here.
+    const bool labels = (pm[0] | pm[1] | pm[2]) != 0u;
+    const bool was = __ldg(dirty + u) != 0;
+    if (lane == 0 && labels != was)
+        dirty[u] = labels ? 1 : 0;
+    if (x >= g.nx || !(labels || was))
         return;
-    if ((pm[0] | pm[1] | pm[2]) == 0u) {   // nothing within L: unlabelled
+    if (!labels) {
         int v = col + plane * z0;
 #pragma unroll 8
         for (int k = 0; k < kmax; ++k, v += plane) {
@@ -345,19 +356,44 @@ __global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *
 }
 
 template <class W>
-static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
-                              unsigned char *ring, cudaStream_t st)
+__global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *__restrict__ inter,
+                                                      const unsigned *__restrict__ rows,
+                                                      unsigned char *__restrict__ dirty, GridGeom g, int L, int nxb,
+                                                      int nyb, int units, int *__restrict__ root,
+                                                      unsigned char *__restrict__ ring)
+{
+    pdl_begin();
+    for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
+        dilate_z_unit<W>(u, inter, rows, dirty, g, L, nxb, nyb, root, ring);
+}
+
+// Blocks that can be resident at once (the kernels loop over their units).
+template <typename K>
+static int resident_blocks(K kernel)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, THREADS, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return sms * per_sm;
+}
+
+template <class W>
+static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
+                              unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st)
 {
     using S = typename W::Stored;
+    static const int xy_blocks = resident_blocks(k_dilate_xy<W>), z_blocks = resident_blocks(k_dilate_z<W>);
     const int nxb = (g.nx + UX - 1) / UX, nyb = (g.ny + UY - 1) / UY, nzb = (g.nz + UZ - 1) / UZ;
     const int u_xy = nxb * nyb * g.nz;   // < V < 2^31
-    cudaError_t e = launch_kernel(k_dilate_xy<W>, dim3((u_xy + WARPS - 1) / WARPS), dim3(THREADS), 0, st, occ,
-                                  occ_words(g.V), g, L, nxb, nyb, u_xy, static_cast<S *>(inter), rows);
+    cudaError_t e = launch_kernel(k_dilate_xy<W>, dim3(min(xy_blocks, (u_xy + WARPS - 1) / WARPS)), dim3(THREADS), 0,
+                                  st, occ, occ_words(g.V), g, L, nxb, nyb, u_xy, static_cast<S *>(inter), rows);
     if (e != cudaSuccess)
         return e;
     const int u_z = nxb * g.ny * nzb;   // < V < 2^31
-    return launch_kernel(k_dilate_z<W>, dim3((u_z + WARPS - 1) / WARPS), dim3(THREADS), 0, st,
-                         static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, root, ring);
+    return launch_kernel(k_dilate_z<W>, dim3(min(z_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0, st,
+                         static_cast<const S *>(inter), rows, dirty, g, L, nxb, nyb, u_z, root, ring);
 }
 
 long long dilate_units(const GridGeom &g)
@@ -365,12 +401,17 @@ long long dilate_units(const GridGeom &g)
     return (long long)((g.nx + UX - 1) / UX) * ((g.ny + UY - 1) / UY) * g.nz;
 }
 
-cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
-                          unsigned char *ring, cudaStream_t st)
+long long dilate_column_units(const GridGeom &g)
+{
+    return (long long)((g.nx + UX - 1) / UX) * g.ny * ((g.nz + UZ - 1) / UZ);
+}
+
+cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
+                          unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st)
 {
     if (L <= L_COMPACT_MAX)
-        return run_dilate<Words16>(occ, g, L, inter, rows, root, ring, st);
-    return run_dilate<Words32>(occ, g, L, inter, rows, root, ring, st);
+        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, st);
 }
 
 }  // namespace vicp

@@ -80,10 +80,14 @@ cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2
                                DevCtl *ctl, const GridGeom &g, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
 // Dilation: `inter` holds V words of pass Y (V x 4 bytes suffices for any
-// L), `rows` dilate_units(g) 32-bit row masks; neither needs clearing.
-cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows, int *root,
-                          unsigned char *ring, cudaStream_t st);
+// L), `rows` dilate_units(g) 32-bit row masks (neither needs clearing),
+// `dirty` dilate_column_units(g) bytes marking the column units whose voxels
+// hold labels.  root/ring must hold "unlabelled" (all bytes 0xff) wherever
+// `dirty` is 0: clear all three when they are new or the dimensions change.
+cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
+                          unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st);
 long long dilate_units(const GridGeom &g);
+long long dilate_column_units(const GridGeom &g);
 // The localised search lists queries whose root segment is long (with the
 // segment) in hv_list / hv_range and queries without a root in fb_list; the
 // fallback kernel then answers both lists.

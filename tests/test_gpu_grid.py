@@ -73,8 +73,11 @@ def test_large_sparse_grid_more_than_2_24_voxels():
     assert_grid_equal(g, ref, p)
 
 
-@pytest.mark.parametrize("dims", [(1, 40, 37), (45, 1, 33), (70, 29, 1), (1, 1, 300), (33, 9, 9)])
+@pytest.mark.parametrize("dims", [(1, 40, 37), (45, 1, 33), (70, 29, 1), (1, 1, 300), (33, 9, 9),
+                                  (36, 20, 25), (100, 12, 10), (64, 33, 5), (40, 70, 8)])
 def test_thin_and_ragged_grids(dims):
+    """Grids thin in one axis, ragged against the 32-voxel units, and with row
+    lengths that select each store width of the dilation's fill."""
     rng = np.random.default_rng(sum(dims))
     n = 777
     q = rng.uniform(0, 1, (n, 3)) * np.array(dims) * 0.1
@@ -97,6 +100,24 @@ def test_rebuild_reuses_buffers_and_stays_exact(pairs):
         ctx.dilate(10)
         g = {k: to_np(v) for k, v in ctx.get_grid().items()}
         grid, ref = oracle_grid_for(g, p.target, 10)
+        assert_grid_equal(g, ref, p.target)
+
+
+def test_labels_follow_each_dilation_on_a_fixed_grid(pairs):
+    """root/ring are rewritten only where labels were or are: a different
+    cloud on the same explicit grid, and a smaller L on the same build, must
+    leave no stale label behind."""
+    import torch
+    from gpu_util import context, to_np
+    p1, p2 = pairs(1), pairs(2)
+    lo = np.minimum(p1.target[:, :3].min(0), p2.target[:, :3].min(0)) - 0.05
+    ctx = context(L=10, voxel_size=0.02, origin=tuple(lo), dims=(120, 110, 100))
+    for p, L in ((p1, 10), (p2, 10), (p2, 3), (p1, 12), (p1, 0)):
+        if L != 3:   # (p2, 3): dilate the same build again with a smaller L
+            ctx.build_grid(torch.from_numpy(p.target).cuda())
+        ctx.dilate(L)
+        g = {k: to_np(v) for k, v in ctx.get_grid().items()}
+        grid, ref = oracle_grid_for(g, p.target, L)
         assert_grid_equal(g, ref, p.target)
 
 
