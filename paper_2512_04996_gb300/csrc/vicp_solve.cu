@@ -333,35 +333,64 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
 #pragma unroll
     for (int k = 0; k < REDUCE_VALUES; ++k)
         acc[k] = {0.0f, 0.0f};
-    for (int i = blockIdx.x * RED_THREADS + threadIdx.x; i < m; i += gridDim.x * RED_THREADS) {
-        const int j = __ldg(nn + i);
-        if ((unsigned)j >= (unsigned)n_tgt) {   // no valid match: report, leave it out
-            atomicOr(&ctl->err, DEVERR_BOUNDS);
-            continue;
-        }
-        const float3 s = transform_pt(P, __ldg(src + i));
-        const float4 q = __ldg(tgt + j);
-        const dfl sv[3] = {two_sum(s.x, -cf.x), two_sum(s.y, -cf.y), two_sum(s.z, -cf.z)};
-        const dfl qv[3] = {two_sum(q.x, -cf.x), two_sum(q.y, -cf.y), two_sum(q.z, -cf.z)};
+    // this thread's points, four per round with all their loads issued first
+    const int stride = gridDim.x * RED_THREADS;
+    for (int i0 = blockIdx.x * RED_THREADS + threadIdx.x; i0 < m; i0 += 4 * stride) {
+        int j[4];
+        float4 p[4], q[4];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            acc[a] = df_acc(acc[a], sv[a]);
-            acc[3 + a] = df_acc(acc[3 + a], qv[a]);
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                acc[6 + 3 * a + b] = df_acc(acc[6 + 3 * a + b], df_mul(sv[a], qv[b]));
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * stride;
+            j[u] = -1;
+            if (i < m) {
+                j[u] = __ldg(nn + i);
+                p[u] = __ldg(src + i);
+            }
         }
-        const dfl ex = two_sum(s.x, -q.x), ey = two_sum(s.y, -q.y), ez = two_sum(s.z, -q.z);
-        acc[15] = df_acc(acc[15], df_acc(df_acc(df_mul(ex, ex), df_mul(ey, ey)), df_mul(ez, ez)));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if ((unsigned)j[u] < (unsigned)n_tgt)
+                q[u] = __ldg(tgt + j[u]);
+            else if (i0 + u * stride < m)   // no valid match: report, leave it out
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if ((unsigned)j[u] >= (unsigned)n_tgt)
+                continue;
+            const float3 sp3 = transform_pt(P, p[u]);
+            const dfl sv[3] = {two_sum(sp3.x, -cf.x), two_sum(sp3.y, -cf.y), two_sum(sp3.z, -cf.z)};
+            const dfl qv[3] = {two_sum(q[u].x, -cf.x), two_sum(q[u].y, -cf.y), two_sum(q[u].z, -cf.z)};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                acc[a] = df_acc(acc[a], sv[a]);
+                acc[3 + a] = df_acc(acc[3 + a], qv[a]);
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    acc[6 + 3 * a + b] = df_acc(acc[6 + 3 * a + b], df_mul(sv[a], qv[b]));
+            }
+            const dfl ex = two_sum(sp3.x, -q[u].x), ey = two_sum(sp3.y, -q[u].y), ez = two_sum(sp3.z, -q[u].z);
+            acc[15] = df_acc(acc[15], df_acc(df_acc(df_mul(ex, ex), df_mul(ey, ey)), df_mul(ez, ez)));
+        }
     }
+    // warp sums through shared memory: lane l adds value l % 16 over lanes
+    // 16 (l / 16) .. 16 (l / 16) + 15 in order, and the two halves are added
+    __shared__ float s_thi[RED_THREADS / 32][REDUCE_VALUES][33], s_tlo[RED_THREADS / 32][REDUCE_VALUES][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < REDUCE_VALUES; ++k) {
-        dfl v = acc[k];
+        s_thi[warp][k][lane] = acc[k].hi;
+        s_tlo[warp][k][lane] = acc[k].lo;
+    }
+    __syncwarp();
+    {
+        const int k = lane & 15, h = (lane >> 4) * 16;
+        dfl v = {s_thi[warp][k][h], s_tlo[warp][k][h]};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            v = df_acc(v, df_shfl_xor(v, o));
-        if (lane == 0) {
+        for (int t = 1; t < 16; ++t)
+            v = df_acc(v, dfl{s_thi[warp][k][h + t], s_tlo[warp][k][h + t]});
+        v = df_acc(v, df_shfl_xor(v, 16));
+        if (lane < 16) {
             s_hi[warp][k] = v.hi;
             s_lo[warp][k] = v.lo;
         }
@@ -391,9 +420,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
     {
         const int k = threadIdx.x & 15, grp = threadIdx.x >> 4;
         dfl v = {0.0f, 0.0f};
-        for (int b = grp; b < (int)gridDim.x; b += RED_THREADS / 16) {
-            const float2 q = __ldcg(partials + b * REDUCE_VALUES + k);
-            v = df_acc(v, dfl{q.x, q.y});
+        for (int b0 = grp; b0 < (int)gridDim.x; b0 += 8 * (RED_THREADS / 16)) {   // eight loads in flight
+            float2 q[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + u * (RED_THREADS / 16);
+                q[u] = b < (int)gridDim.x ? __ldcg(partials + b * REDUCE_VALUES + k) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (b0 + u * (RED_THREADS / 16) < (int)gridDim.x)
+                    v = df_acc(v, dfl{q[u].x, q[u].y});
         }
         v = df_acc(v, df_shfl_xor(v, 16));   // groups 2w and 2w+1 of warp w
         if (lane < 16) {
