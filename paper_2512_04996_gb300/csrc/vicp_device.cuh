@@ -21,6 +21,15 @@ __device__ __forceinline__ void pdl_begin()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The start of a kernel that does not wait for the kernel before it: only
+// for a kernel that reads nothing that kernel writes and writes nothing it
+// reads.  It starts once every block of the kernel before it has passed that
+// kernel's own wait, so everything older has completed.
+__device__ __forceinline__ void pdl_begin_nowait()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Voxel grid geometry passed by value to kernels.  Keys are
 // x + nx*(y + ny*z) (x fastest, the neighbour offsets +-1, +-2^N, +-2^2N of
 // Alg. 3); V < 2^31 so keys fit int32.

@@ -78,7 +78,15 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
                                                    unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
                                                    unsigned *__restrict__ tile_sum, DevCtl *__restrict__ ctl)
 {
-    pdl_begin();
+    // A build follows the previous iteration's reduction and solve, whose
+    // single-block tail leaves the GPU idle; the histogram touches none of
+    // the arrays (nor control words) that the solve reads or writes, so it
+    // does not wait for it and the next build overlaps that tail.  Every
+    // reader of the solve's pose is still ordered after it: the event
+    // recorded after the histogram completes only after all earlier work of
+    // the stream, the dilation waits for that event, and the search waits
+    // for the dilation.
+    pdl_begin_nowait();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
