@@ -14,6 +14,13 @@ independent replica of the workload (no collective on the data path);
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
+The line also carries `batched`: the 256-pair batched workload (sizes
+log-uniform in 2k..64k points, 4.6M points per side, 40 iterations) in pairs/s
+through the batched registration (one persistent launch per iteration,
+replayed from a CUDA graph, kernel shape from the autotuner) against the same
+256 pairs registered one at a time through the single-pair path, with the
+pose agreement between the two.
+
 `--impl reference` times the CPU oracle (the plain C restatement of the
 paper) on this host's cores on a bounded sample of the same workload.
 """
@@ -208,6 +215,147 @@ def _ncu_traffic(kernel: str):
 
 
 # ----------------------------------------------------------------------------
+# batched registration (256 uneven pairs) against one pair at a time
+# ----------------------------------------------------------------------------
+BATCH_ITERS = 40
+
+
+def _rot_deg(Ta, Tb) -> float:
+    E = Ta[:3, :3] @ Tb[:3, :3].T
+    return math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(E) - 1.0) / 2.0))))
+
+
+def run_batched(dev, flush, reps: int = 5) -> dict:
+    import torch
+
+    from paper_2512_04996_gb300 import synth, vicp
+
+    ps = synth.batched_pairs()
+    P = len(ps)
+    stream = torch.cuda.current_stream(dev)
+    tgt_np = np.ascontiguousarray(np.concatenate([p.target for p in ps]))
+    src_np = np.ascontiguousarray(np.concatenate([p.source for p in ps]))
+    n_tgt = np.array([p.target.shape[0] for p in ps], np.int32)
+    n_src = np.array([p.source.shape[0] for p in ps], np.int32)
+    vs = np.array([p.voxel_size for p in ps], np.float32)
+    dv = np.array([p.grid_divisions for p in ps], np.int32)
+    tgt = torch.from_numpy(tgt_np).to(dev)
+    src = torch.from_numpy(src_np).to(dev)
+    b = vicp.Batch(dilation_layers=L_LAYERS, max_iters=BATCH_ITERS, rmse_eps=0.0)
+    b.build(tgt, n_tgt, vs, dv)
+    shape, tune_ms = b.tune(src, n_src, iters=4, trials=2)
+    threads, ppt, blocks = vicp.vicp_batch_shape_info(shape)
+    for _ in range(2):   # warm-up: captures the iteration graph
+        st, T, it, rm, pst = b.register(src, n_src)
+        if st != 0:
+            raise RuntimeError("batched warm-up failed: " + b._lib.vicp_batch_last_error(b.handle).decode())
+    b.report(reset=True)
+
+    # build + 40 iterations of all pairs, per repetition (device time)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    reg_ms, launches0 = [], b.launch_count()
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        e0, e1 = ev[k]
+        e0.record(stream)
+        b.build(tgt, n_tgt, vs, dv)
+        e1.record(stream)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        st, T, it, rm, pst = b.register(src, n_src)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise RuntimeError("batched run failed")
+        reg_ms.append((e0.elapsed_time(e1), r0.elapsed_time(r1)))
+    gpu_launches = b.launch_count() - launches0
+    stats = b.report(reset=True)
+    build_ms = statistics.median(x[0] for x in reg_ms)
+    iter_ms = statistics.median(x[1] for x in reg_ms)
+    batched_pps = P / ((build_ms + iter_ms) / 1e3)
+
+    # the iteration kernel alone: one launch's average device time
+    ctx_it = vicp.Batch(dilation_layers=L_LAYERS, max_iters=1, rmse_eps=0.0, shape=shape,
+                        flags=vicp.VICP_BATCH_FLAG_NO_GRAPH)
+    ctx_it.build(tgt, n_tgt, vs, dv)
+    T_cur = np.ascontiguousarray(np.tile(np.eye(4), (P, 1, 1)))
+    k_ms = []
+    for k in range(BATCH_ITERS):
+        flush.fill_(k & 0xff)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        st, T_cur, *_ = ctx_it.register(src, n_src, T_cur)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        k_ms.append(a0.elapsed_time(a1))
+    it_stats = ctx_it.report(reset=True)
+
+    # end to end: host clouds in, poses out, through vicp_batch_register_host
+    bh = vicp.Batch(dilation_layers=L_LAYERS, max_iters=BATCH_ITERS, rmse_eps=0.0, shape=shape)
+    src_pin = torch.from_numpy(src_np).pin_memory().numpy()
+    tgt_pin = torch.from_numpy(tgt_np).pin_memory().numpy()
+    bh.register_host(src_pin, n_src, tgt_pin, n_tgt, vs, dv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        st, Th, *_ = bh.register_host(src_pin, n_src, tgt_pin, n_tgt, vs, dv)
+    e2e_s = (time.perf_counter() - t0) / reps
+
+    # one pair at a time through the single-pair path (vicp_register)
+    src_t = [torch.from_numpy(p.source).to(dev) for p in ps]
+    tgt_t = [torch.from_numpy(p.target).to(dev) for p in ps]
+    ctxs = {d: vicp.Context(dilation_layers=L_LAYERS, max_iters=BATCH_ITERS, rmse_eps=0.0, grid_divisions=int(d))
+            for d in sorted(set(int(x) for x in dv))}
+    for d, c in ctxs.items():   # size every context's buffers once
+        k = int(np.flatnonzero(dv == d)[np.argmax(n_tgt[dv == d])])
+        c.register(src_t[k], tgt_t[k])
+    torch.cuda.synchronize()
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for k, p in enumerate(ps):
+        st, S, it1, rm1 = ctxs[int(dv[k])].register(src_t[k], tgt_t[k])
+        plain.append(S)
+    plain_s = time.perf_counter() - t0
+    plain_pps = P / plain_s
+
+    rot_diff = max(_rot_deg(T[k], plain[k]) for k in range(P))
+    ext = [float((p.target[:, :3].max(0) - p.target[:, :3].min(0)).max()) for p in ps]
+    tr_diff = max(float(np.linalg.norm(T[k][:3, 3] - plain[k][:3, 3])) / ext[k] for k in range(P))
+    err_b = [_rot_deg(T[k], p.T_gt) for k, p in enumerate(ps)]
+    err_p = [_rot_deg(plain[k], p.T_gt) for k, p in enumerate(ps)]
+    rep = b.report()
+    M, N = int(n_src.sum()), int(n_tgt.sum())
+    return {
+        "metric": "batched pairs/s (256 pairs, 40 iterations each, grids built per batch)",
+        "value": round(batched_pps, 1), "unit": "pairs/s",
+        "plain_one_at_a_time": {"value": round(plain_pps, 1), "unit": "pairs/s",
+                                "what": "the same 256 pairs through vicp_register one after another "
+                                        "(host wall clock, each call synchronises)"},
+        "speedup_vs_plain": round(batched_pps / plain_pps, 2),
+        "build_ms": round(build_ms, 3), "iterations_ms": round(iter_ms, 3),
+        "iteration_kernel_us": round(1e3 * statistics.median(k_ms), 1),
+        "e2e": {"value": round(P / e2e_s, 1), "unit": "pairs/s", "h2d_bytes_per_step": int(16 * (M + N)),
+                "d2h_bytes_per_step": int(P * (16 * 8 + 48)),
+                "what": "vicp_batch_register_host: H2D of all pooled clouds from pinned memory, build, "
+                        "40 iterations, poses and states read back (host wall clock)"},
+        "gpu_launches_per_batch": int(gpu_launches // reps),
+        "shape": {"index": shape, "threads": threads, "points_per_thread": ppt, "resident_blocks": blocks,
+                  "tune_ms": [round(float(x), 3) for x in tune_ms]},
+        "accuracy": {"max_rot_diff_vs_plain_deg": rot_diff, "max_trans_diff_vs_plain_rel_extent": tr_diff,
+                     "median_rot_err_vs_truth_deg": round(statistics.median(err_b), 6),
+                     "median_rot_err_vs_truth_deg_plain": round(statistics.median(err_p), 6)},
+        "search": {"fallbacks_per_batch": stats["fallbacks"] // reps,
+                   "queries_per_batch": stats["queries"] // reps,
+                   "iteration_kernel_fallbacks": it_stats["fallbacks"]},
+        "workload": f"{P} pairs (even: sphere+plane, odd: bumpy object), sizes log-uniform in 2k..64k, "
+                    f"{M} source / {N} target points, L={L_LAYERS}, {BATCH_ITERS} iterations from identity",
+        "peak_device_bytes": rep["peak_bytes"],
+    }
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args, rank, ws, local):
@@ -343,6 +491,8 @@ def run_ours(args, rank, ws, local):
     E = T @ np.linalg.inv(pair.T_gt)
     rot_err_deg = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(E[:3, :3]) - 1) / 2))))
 
+    batched = run_batched(dev, flush)
+
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * total_s / args.steps, 4),
@@ -376,6 +526,7 @@ def run_ours(args, rank, ws, local):
                    "max_voxel_count": mem["max_voxel_count"], "occupied_voxels": mem["occupied_voxels"]},
         "registration": {"status": st, "iters": it, "rmse": rm, "rot_err_vs_truth_deg": round(rot_err_deg, 5),
                          "trans_err_vs_truth_m": float(np.linalg.norm(E[:3, 3]))},
+        "batched": batched,
     }
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(pair)

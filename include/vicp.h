@@ -293,6 +293,126 @@ VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, int32_t n, co
                                          float voxel_size, const int32_t dims[3], int32_t *keys_out,
                                          uint32_t *offsets_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------------- */
+/* Batched registration: many independent (source, target) pairs of uneven
+ * sizes registered together.  The pairs' clouds are pooled (concatenated in
+ * pair order: pair k's points follow pair k-1's), every pair gets its own
+ * grid fitted to its target exactly as vicp_build_grid fits one, and all
+ * pairs' grids are built by a few launches over the pooled store (one
+ * exclusive scan over all pairs' counts gives every pair's segments).  Each
+ * ICP iteration of all pairs is ONE persistent cooperative launch: the
+ * localised search of Alg. 4 for every (pair, tile) item, the global
+ * searches and dense segments shared out over all warps, and per pair the
+ * deterministic reduction and the update of Eq. 1.  The paper registers one
+ * pair at a time; this extends its kernels (Algs. 1-4) to many pairs.  The
+ * result of each pair is that of vicp_register on the pair alone up to the
+ * rounding order of the reduction (the sums are split differently).  */
+
+typedef struct vicp_batch vicp_batch;
+
+#define VICP_BATCH_MAX_PAIRS 65536
+#define VICP_BATCH_SHAPES 5                     /* iteration kernel shapes (see vicp_batch_shape_info) */
+#define VICP_BATCH_FLAG_NO_GRAPH (1u << 0)      /* launch the iterations one by one instead of
+                                                   replaying them as a captured CUDA graph */
+
+typedef struct vicp_batch_params {
+    int32_t dilation_layers;  /* L of every pair, 0..31 */
+    int32_t max_iters;        /* iterations of vicp_batch_register */
+    double rmse_eps;          /* a pair stops once |rmse_k - rmse_(k-1)| < rmse_eps; <= 0: never */
+    int32_t shape;            /* iteration kernel shape 0..VICP_BATCH_SHAPES-1; < 0: the one
+                                 vicp_batch_tune chose, else shape 0 */
+    uint32_t flags;           /* VICP_BATCH_FLAG_* */
+} vicp_batch_params;
+
+/* Fills *p: L = 10, 40 iterations, rmse_eps = 0 (fixed iteration count),
+ * shape -1, flags 0. */
+VICP_API void vicp_batch_default_params(vicp_batch_params *p);
+
+/* Threads per block, source points per thread and resident blocks (on the
+ * current device) of iteration kernel shape `shape`.  Errors:
+ * VICP_ERR_INVALID. */
+VICP_API vicp_status vicp_batch_shape_info(int32_t shape, int32_t *threads, int32_t *points_per_thread,
+                                           int32_t *resident_blocks);
+
+/* Creates a batch context on the current device and `cuda_stream`
+ * (NULL = legacy default stream); `alloc` as for vicp_create. */
+VICP_API vicp_status vicp_batch_create(vicp_batch **out, const vicp_batch_params *params,
+                                       const vicp_allocator *alloc, void *cuda_stream);
+VICP_API void vicp_batch_destroy(vicp_batch *b);
+
+/* Builds and dilates the grids of n_pairs targets (Alg. 1-3 per pair).
+ *   tgt_xyzw: dev, pooled targets, sum(n_tgt) x 4 floats, 16-byte aligned;
+ *     must stay valid and unchanged until the next build (the searches read it).
+ *   n_tgt: host int32[n_pairs], each >= 1; sum < 2^31.
+ *   voxel_size: host float[n_pairs] or NULL; where > 0 it is the pair's
+ *     voxel edge, else h = target extent / grid_divisions[k].
+ *   grid_divisions: host int32[n_pairs] (>= 1 where used) or NULL.
+ * Synchronises once (the bounding boxes are read back).  Errors:
+ * VICP_ERR_INVALID, VICP_ERR_GRID_TOO_LARGE (a pair's grid, or all pairs'
+ * voxels together, reach 2^31 - 1), VICP_ERR_OOM, VICP_ERR_CUDA. */
+VICP_API vicp_status vicp_batch_build(vicp_batch *b, int32_t n_pairs, const float *tgt_xyzw, const int32_t *n_tgt,
+                                      const float *voxel_size, const int32_t *grid_divisions);
+
+/* Registers every pair on the built grids, synchronously: up to
+ * params.max_iters iterations, each pair stopping on its own RMSE test.
+ *   src_xyzw: dev, pooled sources (pair order), 16-byte aligned.
+ *   n_src: host int32[n_pairs], each >= 1.
+ *   poses: host double[n_pairs * 16], row-major 4x4 each; in = initial,
+ *     out = result (a degenerate pair keeps its last good pose).
+ *   iters_out (int32[n_pairs]), rmse_out (double[n_pairs], RMSE of the last
+ *   iteration), status_out (int32[n_pairs]: VICP_OK or VICP_ERR_DEGENERATE):
+ *   host, each may be NULL.
+ * Errors: VICP_ERR_STATE before a build, VICP_ERR_INVALID, VICP_ERR_OOM,
+ * VICP_ERR_TIMEOUT (a grid barrier gave up), VICP_ERR_CUDA; with status_out
+ * NULL, VICP_ERR_DEGENERATE if any pair was degenerate. */
+VICP_API vicp_status vicp_batch_register(vicp_batch *b, const float *src_xyzw, const int32_t *n_src, double *poses,
+                                         int32_t *iters_out, double *rmse_out, int32_t *status_out);
+
+/* Build + register with every cloud in host memory (copied to
+ * context-owned device buffers on the context's stream first). */
+VICP_API vicp_status vicp_batch_register_host(vicp_batch *b, int32_t n_pairs, const float *src_xyzw_host,
+                                              const int32_t *n_src, const float *tgt_xyzw_host,
+                                              const int32_t *n_tgt, const float *voxel_size,
+                                              const int32_t *grid_divisions, double *poses, int32_t *iters_out,
+                                              double *rmse_out, int32_t *status_out);
+
+/* NNS of every pair (Alg. 4, as vicp_correspond per pair) at the given
+ * poses, without an update.
+ *   src_xyzw, n_src: as for vicp_batch_register.  poses_dev: dev,
+ *   double[n_pairs * 16].  nn_out: dev int32[sum n_src], the pair's own
+ *   target index of each source point; d2_out: dev float[sum n_src]. */
+VICP_API vicp_status vicp_batch_correspond(vicp_batch *b, const float *src_xyzw, const int32_t *n_src,
+                                           const double *poses_dev, int32_t *nn_out, float *d2_out);
+
+/* Autotuner: runs `iters` iterations of every pair from `poses` (host, as
+ * for vicp_batch_register; left unchanged) with each iteration kernel shape,
+ * timing each with CUDA events (best of `trials`), and keeps the fastest for
+ * later registrations whose params.shape < 0.  shape_out (host int32) and
+ * ms_out (host float[VICP_BATCH_SHAPES], -1 for a shape that cannot run)
+ * may be NULL. */
+VICP_API vicp_status vicp_batch_tune(vicp_batch *b, const float *src_xyzw, const int32_t *n_src,
+                                     const double *poses, int32_t iters, int32_t trials, int32_t *shape_out,
+                                     float *ms_out);
+
+/* Pair k's grid after vicp_batch_build, as vicp_get_grid gives a single
+ * grid, with one difference: offsets hold positions in the POOLED store, so
+ * offsets[0] is the pair's first position (not 0) and ids / csr_points point
+ * at the start of the pooled store; ids and the csr w fields hold the pair's
+ * own target indices.  Synchronous.  Errors: VICP_ERR_STATE, VICP_ERR_INVALID. */
+VICP_API vicp_status vicp_batch_pair_grid(vicp_batch *b, int32_t pair, vicp_grid_view *out);
+
+/* Synchronous: device bytes held by the batch context now and at peak,
+ * and the search work counters (reset != 0 clears them); either may be NULL. */
+VICP_API vicp_status vicp_batch_report(vicp_batch *b, uint64_t *current_bytes, uint64_t *peak_bytes,
+                                       vicp_stats *stats, int32_t reset);
+
+/* Kernels the batch context has launched since vicp_batch_create (a graph
+ * replay counts its kernels). */
+VICP_API int64_t vicp_batch_launch_count(const vicp_batch *b);
+
+/* Text of the last error on this batch context ("" if none). */
+VICP_API const char *vicp_batch_last_error(const vicp_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "vicp.h"
+#include "vicp_geom.h"
 #include "vicp_launch.h"
 
 using namespace vicp;
@@ -270,14 +271,6 @@ vicp_status ensure_query_buffers(vicp_ctx *c, long long m)
 }
 
 // --- geometry (host side of the grid fit) ----------------------------------
-float ordered_to_float(unsigned o)
-{
-    const unsigned b = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
-    float f;
-    std::memcpy(&f, &b, 4);
-    return f;
-}
-
 vicp_status set_geometry(vicp_ctx *c, const float origin[3], float h, const int dims[3])
 {
     if (!(h > 0.0f) || !std::isfinite(h))
@@ -292,22 +285,7 @@ vicp_status set_geometry(vicp_ctx *c, const float origin[3], float h, const int 
     if (V >= (1ll << 31) - 1)
         return fail(c, VICP_ERR_GRID_TOO_LARGE, "grid of %d x %d x %d = %lld voxels (limit 2^31 - 2)", dims[0],
                     dims[1], dims[2], V);
-    GridGeom g{};
-    g.ox = origin[0];
-    g.oy = origin[1];
-    g.oz = origin[2];
-    g.h = h;
-    g.inv_h = (float)(1.0 / (double)h);
-    g.nx = dims[0];
-    g.ny = dims[1];
-    g.nz = dims[2];
-    g.V = V;
-    g.bx = (dims[0] + BRICK - 1) / BRICK;
-    g.by = (dims[1] + BRICK - 1) / BRICK;
-    g.bz = (dims[2] + BRICK - 1) / BRICK;
-    g.sx = (g.bx + SUPER - 1) / SUPER;
-    g.sy = (g.by + SUPER - 1) / SUPER;
-    g.sz = (g.bz + SUPER - 1) / SUPER;
+    const GridGeom g = make_geom(origin, h, dims);
     c->geom = g;
     c->have_geom = true;
     return VICP_OK;
@@ -325,32 +303,17 @@ vicp_status fit_geometry(vicp_ctx *c, const float4 *tgt, int n)
         e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "bounding box read-back");
-    float lo[3], hi[3], ext[3], extent = 0.0f;
+    float lo[3], hi[3], h = 0.0f;
     for (int a = 0; a < 3; ++a) {
-        lo[a] = ordered_to_float(hb[a]);
-        hi[a] = ordered_to_float(hb[3 + a]);
-        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]))
-            return fail(c, VICP_ERR_INVALID, "target has no finite coordinate on axis %d", a);
-        ext[a] = hi[a] - lo[a];
-        if (ext[a] > extent)
-            extent = ext[a];
+        lo[a] = ordered_to_float_host(hb[a]);
+        hi[a] = ordered_to_float_host(hb[3 + a]);
     }
-    float h;
-    if (c->params.voxel_size > 0.0f) {
-        h = c->params.voxel_size;
-    } else {
-        h = extent / (float)c->params.grid_divisions;
-        if (!(h > 0.0f))
-            h = 1.0f;   // all target points coincide: one voxel
-    }
-    const float inv_h = (float)(1.0 / (double)h);
-    int dims[3];
-    for (int a = 0; a < 3; ++a) {
-        const float s = ext[a] * inv_h;
-        if (!(s < 2147483520.0f))
-            return fail(c, VICP_ERR_GRID_TOO_LARGE, "grid axis %d would have %g voxels", a, (double)s);
-        dims[a] = (int)std::floor(s) + 1;
-    }
+    int dims[3], axis = 0;
+    const GeomResult r = fit_box(lo, hi, c->params.voxel_size, c->params.grid_divisions, &h, dims, &axis);
+    if (r == GEOM_NONFINITE)
+        return fail(c, VICP_ERR_INVALID, "target has no finite coordinate on axis %d", axis);
+    if (r == GEOM_TOO_LARGE)
+        return fail(c, VICP_ERR_GRID_TOO_LARGE, "grid axis %d would be too long", axis);
     return set_geometry(c, lo, h, dims);
 }
 
@@ -365,12 +328,6 @@ vicp_status check_params(vicp_ctx *c, const vicp_params *p)
     if (p->dims[0] > 0 && (p->dims[1] < 1 || p->dims[2] < 1 || !(p->voxel_size > 0.0f)))
         return fail(c, VICP_ERR_INVALID, "explicit grid needs dims >= 1 and voxel_size > 0");
     return VICP_OK;
-}
-
-float3 grid_center(const GridGeom &g)
-{
-    return make_float3((float)((double)g.ox + 0.5 * (double)g.h * g.nx), (float)((double)g.oy + 0.5 * (double)g.h * g.ny),
-                       (float)((double)g.oz + 0.5 * (double)g.h * g.nz));
 }
 
 vicp_status check_cloud(vicp_ctx *c, const float *p, int32_t n, const char *what)

@@ -57,7 +57,7 @@ constexpr unsigned DEVERR_BOUNDS = 4u;       // an index failed its bounds check
 // Per-context control block in device memory.  Kernels of one stream use it
 // in launch order; the comments say which kernel writes each field.
 struct DevCtl {
-    unsigned reserved2;
+    unsigned bar_count;     // batched iteration: blocks arrived at the grid barrier
     unsigned scan_epoch;    // scan: descriptor epoch; bumped by the histogram kernel
     int n_outside;          // scatter: target points outside the grid; reset by histogram
     int n_bricks;           // brick list length; reset by histogram
@@ -68,7 +68,7 @@ struct DevCtl {
     unsigned occupied;      // memory report: occupied voxels
     unsigned red_done;      // reduction: finished blocks (the last one solves and resets it)
     int hv_count;           // correspond: dense segments listed; reset by the fallback kernel
-    unsigned reserved1;
+    unsigned bar_gen;       // batched iteration: grid barrier generation
     int n_super;            // non-empty super-bricks; reset by the histogram
     int pad1;
     // Work counters (added by the search kernels, read and cleared by the host).
@@ -166,6 +166,19 @@ __device__ __forceinline__ int brick_key(const GridGeom &g, int ix, int iy, int 
 
 // Length of the brick index space (padded to whole super-bricks).
 __host__ __device__ __forceinline__ int brick_slots(const GridGeom &g) { return g.sx * g.sy * g.sz * SUPER_BRICKS; }
+
+// Floats mapped to unsigned integers whose order matches the float order, so
+// atomicMin/atomicMax reduce them (and back).
+__device__ __forceinline__ unsigned float_to_ordered(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float ordered_to_float(unsigned o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
 
 // Squared distance ((dx*dx + dy*dy) + dz*dz), each operation rounded once.
 __device__ __forceinline__ float dist2(float3 s, float4 q)

@@ -8,21 +8,10 @@
 namespace vicp {
 
 // ---------------------------------------------------------------------------
-// Bounding box of the target (auto grid).  Floats are mapped to unsigned
-// integers whose order matches the float order, so atomicMin/atomicMax
-// reduce them; NaN coordinates are skipped by fminf/fmaxf.
+// Bounding box of the target (auto grid): per-axis atomicMin/atomicMax on the
+// order-preserving unsigned images of the coordinates; NaN coordinates are
+// skipped by fminf/fmaxf.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned float_to_ordered(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-__device__ __forceinline__ float ordered_to_float(unsigned o)
-{
-    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
-}
-
 __global__ void __launch_bounds__(256) k_bbox(const float4 *__restrict__ pts, int n, unsigned *__restrict__ out)
 {
     pdl_begin();

@@ -33,6 +33,9 @@ VICP_STATIC_MAX_VOXELS = 1 << 24
 VICP_STATIC_MAX_BRICK_SLOTS = 1 << 20
 VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
+VICP_BATCH_MAX_PAIRS = 65536
+VICP_BATCH_SHAPES = 5
+VICP_BATCH_FLAG_NO_GRAPH = 1 << 0
 
 
 class VicpError(RuntimeError):
@@ -60,6 +63,11 @@ class vicp_memory(C.Structure):
                 ("csr_store_bytes", C.c_uint64), ("fixed_capacity_bytes", C.c_uint64),
                 ("paper_static_layout_bytes", C.c_uint64), ("max_voxel_count", C.c_uint32),
                 ("occupied_voxels", C.c_uint32), ("nonempty_bricks", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class vicp_batch_params(C.Structure):
+    _fields_ = [("dilation_layers", C.c_int32), ("max_iters", C.c_int32), ("rmse_eps", C.c_double),
+                ("shape", C.c_int32), ("flags", C.c_uint32)]
 
 
 class vicp_stats(C.Structure):
@@ -104,6 +112,21 @@ SIGNATURES = {
     "vicp_last_error": (C.c_char_p, [_P]),
     "vicp_offsets_static": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32), _P, _P,
                                       _P]),
+    "vicp_batch_default_params": (None, [C.POINTER(vicp_batch_params)]),
+    "vicp_batch_shape_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32)]),
+    "vicp_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(vicp_batch_params), C.POINTER(vicp_allocator), _P]),
+    "vicp_batch_destroy": (None, [_P]),
+    "vicp_batch_build": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "vicp_batch_register": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "vicp_batch_register_host": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "vicp_batch_correspond": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "vicp_batch_tune": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int32), _P]),
+    "vicp_batch_pair_grid": (C.c_int, [_P, C.c_int32, C.POINTER(vicp_grid_view)]),
+    "vicp_batch_report": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(vicp_stats),
+                                    C.c_int32]),
+    "vicp_batch_launch_count": (C.c_int64, [_P]),
+    "vicp_batch_last_error": (C.c_char_p, [_P]),
 }
 
 _lock = threading.Lock()
@@ -400,3 +423,220 @@ def vicp_offsets_static(target, origin, voxel_size: float, dims, keys=None, offs
         raise VicpError(r, f"vicp_offsets_static: {lib.vicp_status_string(r).decode()} (static scratch holds at "
                            f"most {VICP_STATIC_MAX_VOXELS} voxels and {VICP_STATIC_MAX_BRICK_SLOTS} brick slots)")
     return keys, offsets
+
+
+# --- batched registration ---------------------------------------------------
+def batch_default_params(**overrides) -> vicp_batch_params:
+    p = vicp_batch_params()
+    load_library().vicp_batch_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _sizes(n, P=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    if a.ndim != 1 or (P is not None and a.shape[0] != P):
+        raise ValueError("per-pair sizes: expected a 1-D int32 array with one entry per pair")
+    return a
+
+
+class Batch:
+    """A batched-registration context (vicp_batch_*) on the current CUDA
+    device and torch stream.  Clouds are pooled: one (sum n, 4) float32
+    tensor per side, pair k's rows following pair k-1's."""
+
+    def __init__(self, params: vicp_batch_params | None = None, stream: torch.cuda.Stream | None = None,
+                 allocator: vicp_allocator | None = None, **overrides):
+        self._lib = load_library()
+        self.params = params if params is not None else batch_default_params(**overrides)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._allocator = allocator
+        h = C.c_void_p()
+        st = self._lib.vicp_batch_create(C.byref(h), C.byref(self.params),
+                                         C.byref(allocator) if allocator is not None else None,
+                                         C.c_void_p(self.stream.cuda_stream))
+        if st != VICP_OK:
+            raise VicpError(st, "vicp_batch_create failed")
+        self.handle = h
+        self.n_pairs = 0
+
+    def _check(self, st: int, what: str):
+        if st != VICP_OK:
+            raise VicpError(st, f"{what}: {self._lib.vicp_batch_last_error(self.handle).decode()}")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.vicp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def build(self, target: torch.Tensor, n_tgt, voxel_size=None, grid_divisions=None):
+        t = _cloud(target, "target")
+        n = _sizes(n_tgt)
+        P = n.shape[0]
+        if int(n.sum()) != t.shape[0]:
+            raise ValueError("target rows must equal the sum of n_tgt")
+        vs = None if voxel_size is None else np.ascontiguousarray(np.asarray(voxel_size, np.float32))
+        dv = None if grid_divisions is None else _sizes(grid_divisions, P)
+        for a in (vs, dv):
+            if a is not None and a.shape != (P,):
+                raise ValueError("per-pair parameters need one entry per pair")
+        self._target = t   # the grids refer to it until the next build
+        self._check(self._lib.vicp_batch_build(self.handle, P, t.data_ptr(), _ptr(n),
+                                               None if vs is None else _ptr(vs),
+                                               None if dv is None else _ptr(dv)), "vicp_batch_build")
+        self.n_pairs = P
+
+    def register(self, source: torch.Tensor, n_src, poses=None):
+        """Returns (status, poses (P, 4, 4) float64, iters (P,), rmse (P,), per-pair status (P,))."""
+        s = _cloud(source, "source")
+        n = _sizes(n_src, self.n_pairs or None)   # before a build the library reports the call order
+        if int(n.sum()) != s.shape[0]:
+            raise ValueError("source rows must equal the sum of n_src")
+        P = n.shape[0]
+        T = np.ascontiguousarray(np.tile(np.eye(4), (P, 1, 1)) if poses is None else poses,
+                                 dtype=np.float64).copy()
+        it = np.zeros(P, np.int32)
+        rm = np.zeros(P, np.float64)
+        ps = np.zeros(P, np.int32)
+        st = self._lib.vicp_batch_register(self.handle, s.data_ptr(), _ptr(n), _ptr(T), _ptr(it), _ptr(rm), _ptr(ps))
+        return st, T, it, rm, ps
+
+    def register_host(self, source, n_src, target, n_tgt, voxel_size=None, grid_divisions=None, poses=None):
+        s, t = _host_cloud(source), _host_cloud(target)
+        ns, nt = _sizes(n_src), _sizes(n_tgt)
+        P = ns.shape[0]
+        vs = None if voxel_size is None else np.ascontiguousarray(np.asarray(voxel_size, np.float32))
+        dv = None if grid_divisions is None else _sizes(grid_divisions, P)
+        T = np.ascontiguousarray(np.tile(np.eye(4), (P, 1, 1)) if poses is None else poses,
+                                 dtype=np.float64).copy()
+        it = np.zeros(P, np.int32)
+        rm = np.zeros(P, np.float64)
+        ps = np.zeros(P, np.int32)
+        st = self._lib.vicp_batch_register_host(self.handle, P, _ptr(s), _ptr(ns), _ptr(t), _ptr(nt),
+                                                None if vs is None else _ptr(vs), None if dv is None else _ptr(dv),
+                                                _ptr(T), _ptr(it), _ptr(rm), _ptr(ps))
+        if st == VICP_OK:
+            self.n_pairs = P
+        return st, T, it, rm, ps
+
+    def correspond(self, source: torch.Tensor, n_src, poses: torch.Tensor):
+        s = _cloud(source, "source")
+        n = _sizes(n_src, self.n_pairs)
+        if (poses.dtype != torch.float64 or not poses.is_cuda or poses.numel() != 16 * self.n_pairs
+                or not poses.is_contiguous()):
+            raise ValueError("poses: contiguous CUDA float64 tensor with 16 entries per pair")
+        m = s.shape[0]
+        nn = torch.empty(m, dtype=torch.int32, device=s.device)
+        d2 = torch.empty(m, dtype=torch.float32, device=s.device)
+        self._check(self._lib.vicp_batch_correspond(self.handle, s.data_ptr(), _ptr(n), poses.data_ptr(),
+                                                    nn.data_ptr(), d2.data_ptr()), "vicp_batch_correspond")
+        return nn, d2
+
+    def tune(self, source: torch.Tensor, n_src, poses=None, iters: int = 4, trials: int = 2):
+        s = _cloud(source, "source")
+        n = _sizes(n_src, self.n_pairs)
+        P = self.n_pairs
+        T = np.ascontiguousarray(np.tile(np.eye(4), (P, 1, 1)) if poses is None else poses, dtype=np.float64)
+        shape = C.c_int32(-1)
+        ms = np.zeros(VICP_BATCH_SHAPES, np.float32)
+        self._check(self._lib.vicp_batch_tune(self.handle, s.data_ptr(), _ptr(n), _ptr(T), int(iters), int(trials),
+                                              C.byref(shape), _ptr(ms)), "vicp_batch_tune")
+        return int(shape.value), ms
+
+    def pair_grid(self, pair: int) -> dict:
+        """Copies of pair `pair`'s grid arrays (offsets are pooled positions;
+        ids / csr_points are the pair's own segment of the pooled store)."""
+        v = vicp_grid_view()
+        self._check(self._lib.vicp_batch_pair_grid(self.handle, int(pair), C.byref(v)), "vicp_batch_pair_grid")
+        V, n, ns = int(v.n_voxels), int(v.n_target), int(v.n_stored)
+        d = self.device
+        off = _view(v.offsets, (V + 1,), "<u4", torch.uint32, d).clone()
+        base = int(off[0].item()) if V >= 0 else 0
+        ids_all = _view(v.ids, (base + ns,), "<i4", torch.int32, d)
+        pts_all = _view(v.csr_points, (base + ns, 4), "<f4", torch.float32, d)
+        return {
+            "origin": tuple(float(v.origin[a]) for a in range(3)), "voxel_size": float(v.voxel_size),
+            "inv_voxel_size": float(v.inv_voxel_size), "dims": tuple(int(v.dims[a]) for a in range(3)),
+            "n_voxels": V, "n_target": n, "n_stored": ns, "dilation_layers": int(v.dilation_layers),
+            "base": base,
+            "keys": _view(v.keys, (n,), "<i4", torch.int32, d).clone(),
+            "offsets": off,
+            "ids": ids_all[base:].clone(),
+            "csr_points": pts_all[base:].clone(),
+            "occupancy": _view(v.occupancy, ((V + 31) // 32,), "<u4", torch.uint32, d).clone(),
+            "root": _view(v.root, (V,), "<i4", torch.int32, d).clone(),
+            "ring": _view(v.ring, (V,), "|u1", torch.uint8, d).clone(),
+        }
+
+    def report(self, reset: bool = False) -> dict:
+        cur, peak = C.c_uint64(0), C.c_uint64(0)
+        st = vicp_stats()
+        self._check(self._lib.vicp_batch_report(self.handle, C.byref(cur), C.byref(peak), C.byref(st),
+                                                1 if reset else 0), "vicp_batch_report")
+        out = {name: int(getattr(st, name)) for name, _ in vicp_stats._fields_}
+        out.update(current_bytes=int(cur.value), peak_bytes=int(peak.value))
+        return out
+
+    def launch_count(self) -> int:
+        return int(self._lib.vicp_batch_launch_count(self.handle))
+
+
+def vicp_batch_shape_info(shape: int):
+    """(threads per block, source points per thread, resident blocks) of an
+    iteration kernel shape."""
+    th, ppt, rb = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    st = load_library().vicp_batch_shape_info(int(shape), C.byref(th), C.byref(ppt), C.byref(rb))
+    if st != VICP_OK:
+        raise VicpError(st, f"vicp_batch_shape_info: no shape {shape}")
+    return int(th.value), int(ppt.value), int(rb.value)
+
+
+def vicp_batch_create(params: vicp_batch_params | None = None, stream=None, allocator=None, **overrides) -> Batch:
+    return Batch(params, stream, allocator, **overrides)
+
+
+def vicp_batch_destroy(b: Batch):
+    b.close()
+
+
+def vicp_batch_build(b: Batch, target, n_tgt, voxel_size=None, grid_divisions=None):
+    b.build(target, n_tgt, voxel_size, grid_divisions)
+
+
+def vicp_batch_register(b: Batch, source, n_src, poses=None):
+    return b.register(source, n_src, poses)
+
+
+def vicp_batch_register_host(b: Batch, source, n_src, target, n_tgt, voxel_size=None, grid_divisions=None,
+                             poses=None):
+    return b.register_host(source, n_src, target, n_tgt, voxel_size, grid_divisions, poses)
+
+
+def vicp_batch_correspond(b: Batch, source, n_src, poses):
+    return b.correspond(source, n_src, poses)
+
+
+def vicp_batch_tune(b: Batch, source, n_src, poses=None, iters: int = 4, trials: int = 2):
+    return b.tune(source, n_src, poses, iters, trials)
+
+
+def vicp_batch_pair_grid(b: Batch, pair: int) -> dict:
+    return b.pair_grid(pair)
