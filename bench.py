@@ -14,7 +14,8 @@ independent replica of the workload (no collective on the data path);
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
-The line also carries `batched`: the 256-pair batched workload (sizes
+The line also carries `differentiable` (forward + backward of the
+point-to-point loss over 64 pairs of 20k points) and `batched`: the 256-pair batched workload (sizes
 log-uniform in 2k..64k points, 4.6M points per side, 40 iterations) in pairs/s
 through the batched registration (one persistent launch per iteration,
 replayed from a CUDA graph, kernel shape from the autotuner) against the same
@@ -356,6 +357,64 @@ def run_batched(dev, flush, reps: int = 5) -> dict:
 
 
 # ----------------------------------------------------------------------------
+# differentiable loss: 64 pairs x 20k points, forward + backward
+# ----------------------------------------------------------------------------
+def run_loss(dev, flush, steps: int = 50) -> dict:
+    import torch
+
+    from paper_2512_04996_gb300 import synth, vicp
+
+    ps = synth.loss_pairs(workers=max(1, min(16, os.cpu_count() or 1)))
+    P = len(ps)
+    stream = torch.cuda.current_stream(dev)
+    tgt = torch.from_numpy(np.ascontiguousarray(np.concatenate([p.target for p in ps]))).to(dev)
+    src = torch.from_numpy(np.ascontiguousarray(np.concatenate([p.source for p in ps]))).to(dev)
+    n_tgt = np.array([p.target.shape[0] for p in ps], np.int32)
+    n_src = np.array([p.source.shape[0] for p in ps], np.int32)
+    b = vicp.Batch(dilation_layers=L_LAYERS)
+    b.build(tgt, n_tgt, None, np.array([p.grid_divisions for p in ps], np.int32))
+    T0 = torch.from_numpy(np.ascontiguousarray(np.stack([p.T_gt for p in ps]))).to(dev)
+    src_g = src.clone().requires_grad_(True)
+
+    def step(recompute=False):
+        xi = torch.zeros((P, 6), dtype=torch.float32, device=dev, requires_grad=True)
+        loss = vicp.point_to_point_loss(xi, src_g, b, n_src, T0, recompute)
+        loss.sum().backward()
+        return loss, xi
+
+    out = {}
+    for recompute in (False, True):
+        for _ in range(3):
+            step(recompute)
+        torch.cuda.synchronize()
+        l0 = b.launch_count()
+        ms = []
+        for k in range(steps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            loss, xi = step(recompute)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            src_g.grad = None
+        med = statistics.median(ms)
+        out["recompute" if recompute else "stored"] = {
+            "ms_per_forward_backward": round(med, 4), "pairs_per_s": round(P / (med / 1e3), 1),
+            "points_per_s": round(int(n_src.sum()) / (med / 1e3), 1),
+            # the batch context counts its own launches; Exp and the Jacobian transpose are two more
+            "library_launches_per_step": int((b.launch_count() - l0) / steps) + 2}
+    return {
+        "workload": f"{P} pairs x {int(n_src[0])} points (bumpy-object generator, voxel = extent/128), "
+                    "loss of Eq. 1 at the true poses, gradients in 6 float32 se(3) parameters per pair "
+                    "and in every source point",
+        "what": "one forward (Exp, batched NNS, loss) + backward (loss gradients, left-Jacobian transpose) "
+                "through torch.autograd, CUDA events on the stream",
+        **out,
+    }
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args, rank, ws, local):
@@ -492,6 +551,7 @@ def run_ours(args, rank, ws, local):
     rot_err_deg = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(E[:3, :3]) - 1) / 2))))
 
     batched = run_batched(dev, flush)
+    differentiable = run_loss(dev, flush)
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -527,6 +587,7 @@ def run_ours(args, rank, ws, local):
         "registration": {"status": st, "iters": it, "rmse": rm, "rot_err_vs_truth_deg": round(rot_err_deg, 5),
                          "trans_err_vs_truth_m": float(np.linalg.norm(E[:3, 3]))},
         "batched": batched,
+        "differentiable": differentiable,
     }
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(pair)

@@ -413,6 +413,48 @@ VICP_API int64_t vicp_batch_launch_count(const vicp_batch *b);
 /* Text of the last error on this batch context ("" if none). */
 VICP_API const char *vicp_batch_last_error(const vicp_batch *b);
 
+/* ---------------------------------------------------------------------- */
+/* Differentiable loss.  The point-to-point objective of Eq. 1 as a loss per
+ * pair, L_k = (1/M) sum_i |T p_i - q_nn(i)|^2, at pose T with the
+ * correspondences nn of the localised NNS held fixed (they carry no
+ * gradient).  Poses are parameterised in se(3) with a left perturbation:
+ * T = Exp(xi) T0, xi = (rho, phi), translation part first.  The paper
+ * minimises Eq. 1 by the closed-form update only; the gradients serve
+ * callers that put the loss into a larger differentiable objective. */
+
+/* T = Exp(xi) T0 for n poses (FP64, on the device, stream-ordered).
+ *   xi_dev: dev double[n * 6]; T0_dev, T_dev: dev double[n * 16] row-major.
+ * Errors: VICP_ERR_INVALID, VICP_ERR_CUDA. */
+VICP_API vicp_status vicp_se3_exp(int32_t n, const double *xi_dev, const double *T0_dev, double *T_dev,
+                                  void *cuda_stream);
+
+/* out = J(xi)^T g for n poses, J the 6x6 left Jacobian of SE(3)
+ * (Exp(xi + e) = Exp(J(xi) e) Exp(xi) to first order): turns the
+ * left-perturbation gradient at Exp(xi) T0 into the gradient in xi.
+ *   xi_dev, g_dev, out_dev: dev double[n * 6]. */
+VICP_API vicp_status vicp_se3_left_jacobian_t(int32_t n, const double *xi_dev, const double *g_dev, double *out_dev,
+                                              void *cuda_stream);
+
+/* Loss and gradients of every pair of a built batch (stream-ordered, no
+ * synchronisation).
+ *   src_xyzw, n_src: the pooled sources (as for vicp_batch_register).
+ *   poses_dev: dev double[n_pairs * 16], the poses T.
+ *   nn_dev: dev int32[sum n_src], each source point's target index within
+ *     its pair (vicp_batch_correspond at the same poses).
+ *   dloss_dev: dev double[n_pairs], weights of the pairs' losses in the
+ *     gradients (the incoming gradient); NULL = all 1.
+ *   loss_out: dev double[n_pairs].
+ *   grad_pose_out: dev double[n_pairs * 6] or NULL: dloss_k * dL_k/dd at
+ *     d = 0 for T <- Exp(d) T: (2/M) (sum r_i, sum s_i x r_i) with
+ *     s_i = T p_i, r_i = s_i - q_nn(i).
+ *   grad_src_out: dev float[sum n_src * 4], 16-byte aligned, or NULL:
+ *     dloss_k (2/M) R^T r_i in x, y, z and 0 in w.
+ * s_i and r_i are formed in double-float arithmetic from the FP64 pose; the
+ * sums are double-float and deterministic. */
+VICP_API vicp_status vicp_batch_loss(vicp_batch *b, const float *src_xyzw, const int32_t *n_src,
+                                     const double *poses_dev, const int32_t *nn_dev, const double *dloss_dev,
+                                     double *loss_out, double *grad_pose_out, float *grad_src_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,4 +119,14 @@ int batch_iter_blocks(int shape);
 // persistent launch of `blocks` blocks (<= batch_iter_blocks(shape)).
 cudaError_t launch_batch_iter(int shape, int blocks, const BatchIterArgs &a, cudaStream_t st);
 
+// Differentiable loss (vicp_diff.cu): SE(3) exponential T = Exp(xi) T0 and
+// J(xi)^T g (J the left Jacobian), one thread per pose; the loss of Eq. 1
+// per pair with its left-perturbation and per-point gradients.
+cudaError_t launch_se3_exp(int n, const double *xi, const double *T0, double *T, cudaStream_t st);
+cudaError_t launch_se3_jlt(int n, const double *xi, const double *g, double *out, cudaStream_t st);
+cudaError_t launch_batch_loss(const float4 *src, const float4 *tgt, const BatchPair *pairs, BatchState *state,
+                              const BatchItem *items, int n_items, const double *pose, const int *nn,
+                              const double *dloss, float2 *partials, double *loss_out, double *grad_pose,
+                              float4 *grad_src, DevCtl *ctl, cudaStream_t st);
+
 }  // namespace vicp

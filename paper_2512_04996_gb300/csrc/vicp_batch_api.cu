@@ -877,6 +877,49 @@ vicp_status vicp_batch_report(vicp_batch *b, uint64_t *current_bytes, uint64_t *
     return VICP_OK;
 }
 
+vicp_status vicp_se3_exp(int32_t n, const double *xi_dev, const double *T0_dev, double *T_dev, void *cuda_stream)
+{
+    if (n < 1 || !xi_dev || !T0_dev || !T_dev)
+        return VICP_ERR_INVALID;
+    const cudaError_t e = launch_se3_exp(n, xi_dev, T0_dev, T_dev, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? VICP_OK : VICP_ERR_CUDA;
+}
+
+vicp_status vicp_se3_left_jacobian_t(int32_t n, const double *xi_dev, const double *g_dev, double *out_dev,
+                                     void *cuda_stream)
+{
+    if (n < 1 || !xi_dev || !g_dev || !out_dev)
+        return VICP_ERR_INVALID;
+    const cudaError_t e = launch_se3_jlt(n, xi_dev, g_dev, out_dev, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? VICP_OK : VICP_ERR_CUDA;
+}
+
+vicp_status vicp_batch_loss(vicp_batch *b, const float *src_xyzw, const int32_t *n_src, const double *poses_dev,
+                            const int32_t *nn_dev, const double *dloss_dev, double *loss_out, double *grad_pose_out,
+                            float *grad_src_out)
+{
+    if (!b)
+        return VICP_ERR_INVALID;
+    if (!b->built)
+        return bfail(b, VICP_ERR_STATE, "vicp_batch_loss before vicp_batch_build");
+    if (!src_xyzw || !aligned16(src_xyzw) || !poses_dev || !nn_dev || !loss_out ||
+        (grad_src_out && !aligned16(grad_src_out)))
+        return bfail(b, VICP_ERR_INVALID, "vicp_batch_loss: NULL or misaligned pointer");
+    BTRY(prepare_items(b, n_src, pick_shape(b)));
+    BCUDA(b,
+          cudaMemset2DAsync((char *)b->state.p + offsetof(BatchState, items_done), sizeof(BatchState), 0,
+                            sizeof(unsigned), b->P, b->stream),
+          "ticket reset");
+    BCUDA(b,
+          launch_batch_loss(reinterpret_cast<const float4 *>(src_xyzw), b->target, (const BatchPair *)b->pairs_d.p,
+                            (BatchState *)b->state.p, (const BatchItem *)b->sitems.p, b->n_items, poses_dev, nn_dev,
+                            dloss_dev, (float2 *)b->partials.p, loss_out, grad_pose_out,
+                            reinterpret_cast<float4 *>(grad_src_out), bctl(b), b->stream),
+          "launch of the batched loss");
+    b->launches += 1;
+    return VICP_OK;
+}
+
 int64_t vicp_batch_launch_count(const vicp_batch *b) { return b ? b->launches : 0; }
 
 const char *vicp_batch_last_error(const vicp_batch *b) { return b ? b->last_error.c_str() : ""; }

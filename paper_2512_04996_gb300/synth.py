@@ -322,6 +322,28 @@ def batched_pairs(seed: int = CONFIG_SEEDS[4], n_pairs: int = 256, n_min: int = 
     return out
 
 
+def _loss_pair(args):
+    k, seed, n = args
+    p = bumpy_object(seed=seed, n=n)
+    p.name = f"loss{k:02d}_{n}"
+    return p
+
+
+def loss_pairs(seed: int = CONFIG_SEEDS[5], n_pairs: int = 64, n: int = 20_000, workers: int = 1) -> list[Pair]:
+    """The differentiable-loss workload: pairs of n points from the
+    bumpy-object generator (voxel = extent / 128).  Each pair's seed is drawn
+    first, so `workers` > 1 (processes, started by spawning) gives the same
+    pairs."""
+    rng = np.random.default_rng(seed)
+    jobs = [(k, int(rng.integers(0, 2**31 - 1)), n) for k in range(n_pairs)]
+    if workers <= 1:
+        return [_loss_pair(j) for j in jobs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_loss_pair, jobs))
+
+
 def make_config(k: int) -> Pair:
     """The single-pair workloads by number: 1 sphere+plane 4k, 2 bumpy object
     40k, 3 depth scene 226k."""

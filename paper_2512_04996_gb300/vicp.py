@@ -126,6 +126,9 @@ SIGNATURES = {
     "vicp_batch_report": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(vicp_stats),
                                     C.c_int32]),
     "vicp_batch_launch_count": (C.c_int64, [_P]),
+    "vicp_se3_exp": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
+    "vicp_se3_left_jacobian_t": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
+    "vicp_batch_loss": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "vicp_batch_last_error": (C.c_char_p, [_P]),
 }
 
@@ -598,6 +601,32 @@ class Batch:
     def launch_count(self) -> int:
         return int(self._lib.vicp_batch_launch_count(self.handle))
 
+    def loss(self, source: torch.Tensor, n_src, poses: torch.Tensor, nn: torch.Tensor, dloss=None,
+             grad_pose: bool = False, grad_src: bool = False):
+        """Per-pair loss (P,) float64 of Eq. 1 at `poses` with the fixed
+        correspondences `nn`; with grad_pose the left-perturbation gradients
+        (P, 6) float64, with grad_src the per-point gradients (M, 4) float32,
+        each weighted by dloss (P,) float64 when given."""
+        s = _cloud(source, "source")
+        n = _sizes(n_src, self.n_pairs)
+        P = self.n_pairs
+        if (poses.dtype != torch.float64 or not poses.is_cuda or poses.numel() != 16 * P
+                or not poses.is_contiguous()):
+            raise ValueError("poses: contiguous CUDA float64 tensor with 16 entries per pair")
+        if nn.dtype != torch.int32 or not nn.is_cuda or nn.numel() != s.shape[0] or not nn.is_contiguous():
+            raise ValueError("nn: contiguous CUDA int32 tensor with one entry per source point")
+        if dloss is not None and (dloss.dtype != torch.float64 or not dloss.is_cuda or dloss.numel() != P
+                                  or not dloss.is_contiguous()):
+            raise ValueError("dloss: contiguous CUDA float64 tensor with one entry per pair")
+        out = torch.empty(P, dtype=torch.float64, device=s.device)
+        gp = torch.empty((P, 6), dtype=torch.float64, device=s.device) if grad_pose else None
+        gs = torch.empty((s.shape[0], 4), dtype=torch.float32, device=s.device) if grad_src else None
+        self._check(self._lib.vicp_batch_loss(self.handle, s.data_ptr(), _ptr(n), poses.data_ptr(), nn.data_ptr(),
+                                              None if dloss is None else dloss.data_ptr(), out.data_ptr(),
+                                              None if gp is None else gp.data_ptr(),
+                                              None if gs is None else gs.data_ptr()), "vicp_batch_loss")
+        return out, gp, gs
+
 
 def vicp_batch_shape_info(shape: int):
     """(threads per block, source points per thread, resident blocks) of an
@@ -640,3 +669,78 @@ def vicp_batch_tune(b: Batch, source, n_src, poses=None, iters: int = 4, trials:
 
 def vicp_batch_pair_grid(b: Batch, pair: int) -> dict:
     return b.pair_grid(pair)
+
+
+# --- differentiable loss -----------------------------------------------------
+def _f64_dev(t: torch.Tensor, n: int, what: str):
+    if t.dtype != torch.float64 or not t.is_cuda or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{what}: contiguous CUDA float64 tensor with {n} entries")
+    return t
+
+
+def vicp_se3_exp(xi: torch.Tensor, T0: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """T = Exp(xi) T0 for (n, 6) xi and (n, 4, 4) T0 (float64, CUDA)."""
+    n = xi.shape[0]
+    _f64_dev(xi, 6 * n, "xi")
+    _f64_dev(T0, 16 * n, "T0")
+    out = torch.empty_like(T0) if out is None else _f64_dev(out, 16 * n, "out")
+    st = torch.cuda.current_stream(xi.device).cuda_stream
+    r = load_library().vicp_se3_exp(n, xi.data_ptr(), T0.data_ptr(), out.data_ptr(), C.c_void_p(st))
+    if r != VICP_OK:
+        raise VicpError(r, "vicp_se3_exp")
+    return out
+
+
+def vicp_se3_left_jacobian_t(xi: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+    """J(xi)^T g per row, J the left Jacobian of SE(3)."""
+    n = xi.shape[0]
+    _f64_dev(xi, 6 * n, "xi")
+    _f64_dev(g, 6 * n, "g")
+    out = torch.empty_like(g)
+    st = torch.cuda.current_stream(xi.device).cuda_stream
+    r = load_library().vicp_se3_left_jacobian_t(n, xi.data_ptr(), g.data_ptr(), out.data_ptr(), C.c_void_p(st))
+    if r != VICP_OK:
+        raise VicpError(r, "vicp_se3_left_jacobian_t")
+    return out
+
+
+class PointToPointLoss(torch.autograd.Function):
+    """Per-pair loss L_k = (1/M) sum |T p_i - q_nn(i)|^2 (Eq. 1) of a built
+    batch at T = Exp(xi) T0, the correspondences from the localised NNS at T
+    held fixed.  Differentiable in xi ((P, 6), translation part first) and
+    in the source points ((M, 4); the w column gets no gradient).  With
+    recompute=True the correspondences are not kept between forward and
+    backward but searched again (same poses, the same result)."""
+
+    @staticmethod
+    def forward(ctx, xi, source, batch, n_src, T0, recompute=False):
+        xi64 = xi.detach().to(torch.float64).contiguous()
+        T = vicp_se3_exp(xi64, T0)
+        src = source.detach()
+        nn, _ = batch.correspond(src, n_src, T)
+        loss, _, _ = batch.loss(src, n_src, T, nn)
+        ctx.batch, ctx.n_src, ctx.recompute = batch, n_src, recompute
+        ctx.xi_dtype = xi.dtype
+        if recompute:
+            del nn
+            ctx.save_for_backward(xi64, T, src)
+        else:
+            ctx.save_for_backward(xi64, T, src, nn)
+        return loss
+
+    @staticmethod
+    def backward(ctx, dloss):
+        if ctx.recompute:
+            xi64, T, src = ctx.saved_tensors
+            nn, _ = ctx.batch.correspond(src, ctx.n_src, T)
+        else:
+            xi64, T, src, nn = ctx.saved_tensors
+        dl = dloss.detach().to(torch.float64).contiguous()
+        _, g_left, g_src = ctx.batch.loss(src, ctx.n_src, T, nn, dloss=dl, grad_pose=ctx.needs_input_grad[0],
+                                          grad_src=ctx.needs_input_grad[1])
+        g_xi = vicp_se3_left_jacobian_t(xi64, g_left).to(ctx.xi_dtype) if g_left is not None else None
+        return g_xi, g_src, None, None, None, None
+
+
+def point_to_point_loss(xi, source, batch: Batch, n_src, T0, recompute: bool = False):
+    return PointToPointLoss.apply(xi, source, batch, n_src, T0, recompute)
