@@ -314,6 +314,10 @@ typedef struct vicp_batch vicp_batch;
 #define VICP_BATCH_SHAPES 5                     /* iteration kernel shapes (see vicp_batch_shape_info) */
 #define VICP_BATCH_FLAG_NO_GRAPH (1u << 0)      /* launch the iterations one by one instead of
                                                    replaying them as a captured CUDA graph */
+#define VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT (1u << 1) /* test hook: block 0 of the iteration kernel
+                                                   leaves before the first grid barrier, so the
+                                                   other blocks' bounded wait (1 s) runs out and
+                                                   the call returns VICP_ERR_TIMEOUT */
 
 typedef struct vicp_batch_params {
     int32_t dilation_layers;  /* L of every pair, 0..31 */
@@ -405,6 +409,10 @@ VICP_API vicp_status vicp_batch_pair_grid(vicp_batch *b, int32_t pair, vicp_grid
  * and the search work counters (reset != 0 clears them); either may be NULL. */
 VICP_API vicp_status vicp_batch_report(vicp_batch *b, uint64_t *current_bytes, uint64_t *peak_bytes,
                                        vicp_stats *stats, int32_t reset);
+
+/* Replaces params.flags of the context (for example to clear a test hook);
+ * takes effect at the next call. */
+VICP_API vicp_status vicp_batch_set_flags(vicp_batch *b, uint32_t flags);
 
 /* Kernels the batch context has launched since vicp_batch_create (a graph
  * replay counts its kernels). */

@@ -617,6 +617,13 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
     extern __shared__ float s_dyn[];   // [2][WARPS][N_SUMS][33]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     DevCtl *const ctl = a.ctl;
+    // After a barrier gave up, the arrival count no longer matches the
+    // blocks in the barrier: the remaining launches of the registration do
+    // nothing (the host clears the status and the count).
+    if (*(volatile const unsigned *)&ctl->err & DEVERR_TIMEOUT)
+        return;
+    if (a.test_leave_early && blockIdx.x == 0)
+        return;   // the others' first barrier runs out of time (test of the time limit)
 
     // ---- phase 1: localised search, item by item --------------------------
     for (int itx = blockIdx.x; itx < a.n_items; itx += gridDim.x) {
@@ -728,6 +735,12 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
         unsigned long long examined = 0ull;
         for (int qi = n_warps - 1 - gw; qi < Hv; qi += n_warps) {
             const int4 e = a.hv_list[qi];
+            if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap || e.z > e.w ||
+                (unsigned)e.w > (unsigned)a.n_stored) {   // a stale entry: skip it, report it
+                if (lane == 0)
+                    atomicOr(&ctl->err, DEVERR_BOUNDS);
+                continue;
+            }
             const PoseF P = pose_f_warp(a.pose + 16 * e.x);
             const float3 s = transform_pt(P, __ldg(a.src + e.y));
             unsigned long long unused = 0ull;
@@ -739,6 +752,11 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
         }
         for (int qi = gw; qi < F; qi += n_warps) {
             const int2 e = a.fb_list[qi];
+            if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap) {
+                if (lane == 0)   // a stale entry: skip it, report it
+                    atomicOr(&ctl->err, DEVERR_BOUNDS);
+                continue;
+            }
             const BatchPair *bp = a.pairs + e.x;
             const PoseF P = pose_f_warp(a.pose + 16 * e.x);
             const float3 s = transform_pt(P, __ldg(a.src + e.y));

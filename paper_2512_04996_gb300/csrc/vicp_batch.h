@@ -74,6 +74,7 @@ struct BatchIterArgs {
     double *pose;               // [P][16] row-major 4x4, FP64
     const BatchItem *items;     // source tiles, grouped by pair
     int n_items;
+    int n_pairs;
     int n_stored;               // points in the pooled CSR store
     const int *root;            // pooled, pair-local voxel labels
     const unsigned *off;        // pooled offsets (positions in the CSR store)
@@ -91,6 +92,7 @@ struct BatchIterArgs {
     DevCtl *ctl;                // fb_count, hv_count, barrier, stats, err
     double eps;                 // stopping threshold on the RMSE difference (<= 0: never)
     int search_only;            // 1: phases 1-2 only (nn, d2), no reduction or update
+    int test_leave_early;       // test hook: block 0 leaves before the first barrier
 };
 
 cudaError_t launch_batch_bbox(const float4 *pts, const BatchItem *items, int n_items, int P, unsigned *bbox,

@@ -480,6 +480,7 @@ BatchIterArgs iter_args(vicp_batch *b, const float4 *src, double *pose, int *nn,
     a.pose = pose;
     a.items = (const BatchItem *)b->sitems.p;
     a.n_items = b->n_items;
+    a.n_pairs = b->P;
     a.n_stored = b->N;
     a.root = (const int *)b->root.p;
     a.off = (const unsigned *)b->off.p;
@@ -497,6 +498,7 @@ BatchIterArgs iter_args(vicp_batch *b, const float4 *src, double *pose, int *nn,
     a.ctl = bctl(b);
     a.eps = b->params.rmse_eps;
     a.search_only = search_only;
+    a.test_leave_early = (b->params.flags & VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT) ? 1 : 0;
     return a;
 }
 
@@ -917,6 +919,15 @@ vicp_status vicp_batch_loss(vicp_batch *b, const float *src_xyzw, const int32_t 
                             reinterpret_cast<float4 *>(grad_src_out), bctl(b), b->stream),
           "launch of the batched loss");
     b->launches += 1;
+    return VICP_OK;
+}
+
+vicp_status vicp_batch_set_flags(vicp_batch *b, uint32_t flags)
+{
+    if (!b)
+        return VICP_ERR_INVALID;
+    b->params.flags = flags;
+    drop_graph(b);   // the captured launches hold the old flags' arguments
     return VICP_OK;
 }
 

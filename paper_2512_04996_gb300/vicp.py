@@ -36,6 +36,7 @@ VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
 VICP_BATCH_MAX_PAIRS = 65536
 VICP_BATCH_SHAPES = 5
 VICP_BATCH_FLAG_NO_GRAPH = 1 << 0
+VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT = 1 << 1
 
 
 class VicpError(RuntimeError):
@@ -126,6 +127,7 @@ SIGNATURES = {
     "vicp_batch_report": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(vicp_stats),
                                     C.c_int32]),
     "vicp_batch_launch_count": (C.c_int64, [_P]),
+    "vicp_batch_set_flags": (C.c_int, [_P, C.c_uint32]),
     "vicp_se3_exp": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
     "vicp_se3_left_jacobian_t": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
     "vicp_batch_loss": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -600,6 +602,10 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(self._lib.vicp_batch_launch_count(self.handle))
+
+    def set_flags(self, flags: int):
+        self._check(self._lib.vicp_batch_set_flags(self.handle, int(flags)), "vicp_batch_set_flags")
+        self.params.flags = int(flags)
 
     def loss(self, source: torch.Tensor, n_src, poses: torch.Tensor, nn: torch.Tensor, dloss=None,
              grad_pose: bool = False, grad_src: bool = False):

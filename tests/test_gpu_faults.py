@@ -1,6 +1,9 @@
 """Failure handling without faulting the GPU: an allocator that returns NULL
 gives VICP_ERR_OOM and leaks nothing; calls out of order return
-VICP_ERR_STATE; an oversized grid is refused before any launch."""
+VICP_ERR_STATE; an oversized grid is refused before any launch; the batched
+iteration kernel's grid barrier (the library's only device-side wait) gives
+up after its time limit with VICP_ERR_TIMEOUT when a block never arrives, and
+the context works normally afterwards."""
 import ctypes as C
 
 import numpy as np
@@ -97,3 +100,33 @@ def test_grid_too_large_is_rejected():
     with pytest.raises(v.VicpError) as e:
         ctx.build_grid(torch.zeros((4, 4), dtype=torch.float32, device="cuda"))
     assert e.value.status == v.VICP_ERR_GRID_TOO_LARGE
+
+
+def test_batch_barrier_time_limit_and_recovery():
+    """A test hook makes block 0 of the iteration kernel leave before the
+    first grid barrier (nothing else ever arrives for it): the other blocks'
+    wait runs out after one second, the call reports VICP_ERR_TIMEOUT, and
+    the same context then registers exactly like a fresh one."""
+    import time
+
+    from paper_2512_04996_gb300 import synth
+    v = vicp()
+    ps = synth.batched_pairs(seed=61, n_pairs=3, n_min=800, n_max=2500)
+    tgt = torch.from_numpy(np.concatenate([p.target for p in ps])).cuda()
+    src = torch.from_numpy(np.concatenate([p.source for p in ps])).cuda()
+    n_tgt = np.array([p.target.shape[0] for p in ps], np.int32)
+    n_src = np.array([p.source.shape[0] for p in ps], np.int32)
+    dv = np.array([p.grid_divisions for p in ps], np.int32)
+    b = v.Batch(dilation_layers=10, max_iters=3, flags=v.VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT)
+    b.build(tgt, n_tgt, None, dv)
+    t0 = time.perf_counter()
+    st = b.register(src, n_src)[0]
+    assert st == v.VICP_ERR_TIMEOUT
+    assert 0.9 < time.perf_counter() - t0 < 30.0
+    b.set_flags(0)
+    st, T, it, rm, _ = b.register(src, n_src)
+    fresh = v.Batch(dilation_layers=10, max_iters=3)
+    fresh.build(tgt, n_tgt, None, dv)
+    st2, T2, it2, rm2, _ = fresh.register(src, n_src)
+    assert st == 0 and st2 == 0
+    assert np.array_equal(T, T2) and np.array_equal(it, it2) and np.array_equal(rm, rm2)
