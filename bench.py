@@ -357,6 +357,121 @@ def run_batched(dev, flush, reps: int = 5) -> dict:
 
 
 # ----------------------------------------------------------------------------
+# fixed-capacity store (direct addressing) against the CSR store
+# ----------------------------------------------------------------------------
+def run_fixed(dev, pair, flush, reps: int = 100) -> dict:
+    import torch
+
+    from paper_2512_04996_gb300 import vicp
+
+    stream = torch.cuda.current_stream(dev)
+    src = torch.from_numpy(pair.source).to(dev)
+    tgt = torch.from_numpy(pair.target).to(dev)
+    ctx = vicp.Context(voxel_size=pair.voxel_size, dilation_layers=L_LAYERS, max_iters=1, rmse_eps=0.0)
+    ctx.build_grid(tgt)
+    ctx.dilate(L_LAYERS)
+    mem = ctx.memory_report()
+    C = int(mem["max_voxel_count"])
+    view = ctx.grid_view()
+    V, N = int(view.n_voxels), tgt.shape[0]
+    over, nbytes = ctx.fixed_build(tgt, C)
+
+    def timed(fn):
+        ms = []
+        for k in range(reps + 3):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                ms.append(e0.elapsed_time(e1))
+        return 1e3 * statistics.median(ms)
+
+    # builds: the CSR store's kernels (histogram, scan, scatter) by the
+    # library's per-kernel timing; the fixed store's reset + scatter by events
+    ctx.profile_enable(True)
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        ctx.build_grid(tgt)
+    prof = ctx.profile_read()
+    csr_build_us = sum(1e3 * prof[k][1] / max(1, prof[k][0]) for k in ("histogram", "scan", "scatter"))
+    ctx.profile_enable(False)
+    ctx.dilate(L_LAYERS)
+    ctx.profile_enable(True)
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        ctx.fixed_build(tgt, C)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    fixed_scatter_us = 1e3 * prof["fixed_scatter"][1] / max(1, prof["fixed_scatter"][0])
+    reset = torch.empty(V, dtype=torch.int32, device=dev)   # the fill counts' reset, timed as a plain memset
+    fixed_reset_us = timed(lambda: reset.zero_())
+    del reset
+    # searches at the true pose, each layout's localised search kernel alone
+    pose = torch.from_numpy(np.ascontiguousarray(pair.T_gt)).to(dev)
+    nn = torch.empty(src.shape[0], dtype=torch.int32, device=dev)
+    d2 = torch.empty(src.shape[0], dtype=torch.float32, device=dev)
+    ctx.profile_enable(True)
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        ctx.correspond(src, pose, nn, d2)
+        flush.fill_(k & 0xff)
+        ctx.fixed_correspond(src, pose, nn, d2)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    us = {k: 1e3 * prof[k][1] / max(1, prof[k][0]) for k in ("correspond", "fixed_correspond")}
+    ctx.close()
+    return {
+        "capacity": C, "dropped_points": over,
+        "store_bytes": {"fixed": nbytes, "csr_offsets_ids_points": 4 * (V + 1) + 4 * N + 16 * N},
+        "build_us": {"csr_histogram_scan_scatter": round(csr_build_us, 2),
+                     "fixed_scatter": round(fixed_scatter_us, 2), "fixed_count_reset": round(fixed_reset_us, 2),
+                     "fixed_total": round(fixed_scatter_us + fixed_reset_us, 2)},
+        "localised_search_us": {"csr": round(us["correspond"], 2), "fixed": round(us["fixed_correspond"], 2)},
+        "workload": f"226k scene, {V} voxels, capacity = the largest voxel count (nothing dropped), "
+                    f"search at the true pose; L2 flushed between launches",
+    }
+
+
+# ----------------------------------------------------------------------------
+# histogram ablation: warp-aggregated vs the paper's shared-memory hash
+# ----------------------------------------------------------------------------
+def run_hist_ablation(dev, tgt, view, occupied: int, flush, reps: int = 200) -> dict:
+    import torch
+
+    from paper_2512_04996_gb300 import vicp
+
+    stream = torch.cuda.current_stream(dev)
+    N = tgt.shape[0]
+    dims = [int(view.dims[a]) for a in range(3)]
+    origin = [float(view.origin[a]) for a in range(3)]
+    V = int(view.n_voxels)
+    keys = torch.empty(N, dtype=torch.int32, device=dev)
+    counts = torch.zeros(V, dtype=torch.int32, device=dev)
+    alg = 16 * N + 4 * N + 8 * occupied
+    out = {}
+    for method, name in ((vicp.VICP_HIST_WARP_AGGREGATED, "warp_aggregated"),
+                         (vicp.VICP_HIST_SHARED_HASH, "shared_hash")):
+        ms = []
+        for k in range(reps + 3):
+            counts.zero_()
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vicp.vicp_voxel_histogram(tgt, origin, float(view.voxel_size), dims, method, keys, counts)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        out[name] = {"us": round(1e3 * med, 3), "gbs": round(alg / (med * 1e-3) / 1e9, 1)}
+    out["workload"] = f"keys + counts of the {N}-point scene target on its {V}-voxel grid (L2 flushed)"
+    return out
+
+
+# ----------------------------------------------------------------------------
 # differentiable loss: 64 pairs x 20k points, forward + backward
 # ----------------------------------------------------------------------------
 def run_loss(dev, flush, steps: int = 50) -> dict:
@@ -550,6 +665,8 @@ def run_ours(args, rank, ws, local):
     E = T @ np.linalg.inv(pair.T_gt)
     rot_err_deg = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(E[:3, :3]) - 1) / 2))))
 
+    hist_ablation = run_hist_ablation(dev, tgt, view, mem["occupied_voxels"], flush)
+    fixed_capacity = run_fixed(dev, pair, flush)
     batched = run_batched(dev, flush)
     differentiable = run_loss(dev, flush)
 
@@ -586,6 +703,8 @@ def run_ours(args, rank, ws, local):
                    "max_voxel_count": mem["max_voxel_count"], "occupied_voxels": mem["occupied_voxels"]},
         "registration": {"status": st, "iters": it, "rmse": rm, "rot_err_vs_truth_deg": round(rot_err_deg, 5),
                          "trans_err_vs_truth_m": float(np.linalg.norm(E[:3, 3]))},
+        "histogram_ablation": hist_ablation,
+        "fixed_capacity_layout": fixed_capacity,
         "batched": batched,
         "differentiable": differentiable,
     }

@@ -257,6 +257,29 @@ VICP_API int64_t vicp_launch_count(const vicp_ctx *ctx);
 /* Text of the last error on this context ("" if none). */
 VICP_API const char *vicp_last_error(const vicp_ctx *ctx);
 
+/* Fixed-capacity voxel store, a measured alternative to the CSR store: each
+ * voxel owns `capacity` slots at v * capacity (direct addressing, the
+ * monolithic layout whose memory cost the paper's dynamic assignment
+ * removes, Sec. 2.2 and Sec. 3), filled by one scatter with no histogram and
+ * no scan; points past a voxel's capacity are dropped and counted.  It
+ * replaces the voxel store only: the geometry, the dilation labels and the
+ * global search's brick level are those of the context's CSR build.
+ *   vicp_fixed_build: target_xyzw / n must be the last vicp_build_grid's
+ *     target (else VICP_ERR_STATE); capacity >= 1 and V * capacity < 2^32;
+ *     allocates V * capacity * 16 + 4V bytes (slots of x, y, z, index and
+ *     fill counts).  Synchronous: overflow_out (host, may be NULL) = points
+ *     dropped; store_bytes_out (host, may be NULL) = bytes of the store.
+ *   vicp_fixed_correspond: as vicp_correspond, with the localised search
+ *     reading the fixed store; with capacity >= the largest voxel count the
+ *     results equal vicp_correspond's.  Needs vicp_dilate after the CSR build.
+ * Errors: VICP_ERR_INVALID, VICP_ERR_STATE, VICP_ERR_GRID_TOO_LARGE,
+ * VICP_ERR_OOM, VICP_ERR_CUDA. */
+VICP_API vicp_status vicp_fixed_build(vicp_ctx *ctx, const float *target_xyzw, int32_t n, int32_t capacity,
+                                      uint32_t *overflow_out, uint64_t *store_bytes_out);
+VICP_API vicp_status vicp_fixed_correspond(vicp_ctx *ctx, const float *src_xyzw, int32_t n_src,
+                                           const double *pose_dev, int32_t *nn_out, float *d2_out,
+                                           int32_t *n_fallback_out);
+
 /* Voxel keys and segment offsets of a target cloud -- the first two steps of
  * vicp_build_grid (Alg. 1: quantisation, histogram, exclusive scan of the
  * counts) -- computed WITHOUT allocating any device memory.  The paper has
@@ -462,6 +485,28 @@ VICP_API vicp_status vicp_se3_left_jacobian_t(int32_t n, const double *xi_dev, c
 VICP_API vicp_status vicp_batch_loss(vicp_batch *b, const float *src_xyzw, const int32_t *n_src,
                                      const double *poses_dev, const int32_t *nn_dev, const double *dloss_dev,
                                      double *loss_out, double *grad_pose_out, float *grad_src_out);
+
+/* Voxel occupancy histogram (VOH, Alg. 1 GPU part) as a standalone
+ * ablation of two designs; no allocation, stream-ordered (no
+ * synchronisation).  method VICP_HIST_WARP_AGGREGATED: lanes of a warp with
+ * the same voxel add their group size with one atomic (the design the grid
+ * build uses).  method VICP_HIST_SHARED_HASH: the paper's per-block
+ * shared-memory hash table (one slot per thread, slot = key modulo the
+ * block size, linear probing by atomicCAS, count by atomicAdd on the same
+ * packed word, one global atomicAdd per used slot), with the word widened to
+ * [key + 1 : 32 | count : 32] so that voxel 0 is not the empty word and any
+ * grid size fits (the paper's 16-bit key field limits grids to 2^16 voxels).
+ *   target_xyzw: dev, n x 4 floats, 16-byte aligned; n >= 1.
+ *   origin[3], voxel_size, dims[3]: host, the explicit grid, V < 2^31 - 1.
+ *   keys_out: dev int32[n], key x + nx*(y + ny*z) of each point, -1 outside.
+ *   counts_out: dev uint32[V]; the call ADDS the counts (pass zeros for a
+ *     histogram).
+ * Errors: VICP_ERR_INVALID, VICP_ERR_GRID_TOO_LARGE, VICP_ERR_CUDA. */
+#define VICP_HIST_WARP_AGGREGATED 0
+#define VICP_HIST_SHARED_HASH 1
+VICP_API vicp_status vicp_voxel_histogram(const float *target_xyzw, int32_t n, const float origin[3],
+                                          float voxel_size, const int32_t dims[3], int32_t method,
+                                          int32_t *keys_out, uint32_t *counts_out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -74,6 +74,10 @@ struct vicp_ctx {
     Buf partials, pose, rmse, ctl, bbox;
     // host-input copies (vicp_register_host)
     Buf hsrc, htgt;
+    // fixed-capacity store (vicp_fixed_build): C slots per voxel
+    Buf fslots, fcount, fover;
+    unsigned fixed_C = 0;
+    bool fixed_built = false;
 
     // accounting / timing
     int64_t launches = 0;
@@ -629,7 +633,7 @@ void vicp_destroy(vicp_ctx *c)
                   &c->boxord,  &c->sb_box,  &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
                   &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
-                  &c->hsrc,    &c->htgt};
+                  &c->hsrc,    &c->htgt,    &c->fslots,   &c->fcount,   &c->fover};
     for (Buf *b : all)
         buf_free(c, *b);
     for (auto &t : c->pending) {
@@ -840,6 +844,87 @@ vicp_status vicp_profile_enable(vicp_ctx *c, int32_t enable)
     return VICP_OK;
 }
 
+vicp_status vicp_fixed_build(vicp_ctx *c, const float *target_xyzw, int32_t n, int32_t capacity,
+                             uint32_t *overflow_out, uint64_t *store_bytes_out)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    TRY(check_cloud(c, target_xyzw, n, "target"));
+    if (capacity < 1)
+        return fail(c, VICP_ERR_INVALID, "capacity must be >= 1");
+    if (!c->built || reinterpret_cast<const float4 *>(target_xyzw) != c->target || n != c->n_target)
+        return fail(c, VICP_ERR_STATE, "vicp_fixed_build needs vicp_build_grid on the same target first");
+    const GridGeom &g = c->geom;
+    if ((unsigned long long)g.V * (unsigned long long)capacity >= (1ull << 32))
+        return fail(c, VICP_ERR_GRID_TOO_LARGE, "%lld voxels x %d slots exceed 2^32 slots", g.V, capacity);
+    const size_t slot_bytes = (size_t)g.V * (size_t)capacity * 16;
+    if (c->fslots.bytes < slot_bytes)
+        TRY(buf_alloc(c, c->fslots, slot_bytes, "fixed-capacity slots"));
+    if (c->fcount.bytes < (size_t)g.V * 4)
+        TRY(buf_alloc(c, c->fcount, (size_t)g.V * 4, "fixed-capacity counts"));
+    if (!c->fover.p)
+        TRY(buf_alloc(c, c->fover, 4, "overflow counter"));
+    cudaError_t e = cudaMemsetAsync(c->fcount.p, 0, (size_t)g.V * 4, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->fover.p, 0, 4, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "fixed-capacity reset");
+    c->fixed_C = (unsigned)capacity;
+    TRY(launch(c, K_FIXED_SCATTER, [&] {
+        return launch_fixed_scatter(reinterpret_cast<const float4 *>(target_xyzw), n, g, c->fixed_C,
+                                    (unsigned *)c->fcount.p, (float4 *)c->fslots.p, (unsigned *)c->fover.p,
+                                    c->stream);
+    }));
+    c->fixed_built = true;
+    unsigned over = 0;
+    e = cudaMemcpyAsync(&over, c->fover.p, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "overflow read-back");
+    TRY(read_device_status(c));   // synchronises
+    if (overflow_out)
+        *overflow_out = over;
+    if (store_bytes_out)
+        *store_bytes_out = (uint64_t)slot_bytes + (uint64_t)g.V * 4;
+    return VICP_OK;
+}
+
+vicp_status vicp_fixed_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, const double *pose_dev,
+                                  int32_t *nn_out, float *d2_out, int32_t *n_fallback_out)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    TRY(check_cloud(c, src_xyzw, n_src, "source"));
+    if (!pose_dev || !nn_out || !d2_out)
+        return fail(c, VICP_ERR_INVALID, "pose, nn and d2 pointers must be non-NULL");
+    if (!c->fixed_built || c->dilated_L < 0)
+        return fail(c, VICP_ERR_STATE, "vicp_fixed_correspond needs vicp_fixed_build and vicp_dilate first");
+    TRY(ensure_query_buffers(c, n_src));
+    const float4 *src = reinterpret_cast<const float4 *>(src_xyzw);
+    DevCtl *d = ctl_of(c);
+    TRY(launch(c, K_FIXED_CORRESPOND, [&] {
+        return launch_correspond_fixed(src, n_src, pose_dev, c->geom, (const int *)c->root.p,
+                                       (const unsigned *)c->fcount.p, c->fixed_C, (const float4 *)c->fslots.p,
+                                       nn_out, d2_out, (int *)c->fb_list.p, (int *)c->hv_list.p,
+                                       (uint2 *)c->hv_range.p, d, c->stream);
+    }));
+    if (n_fallback_out) {
+        cudaError_t e = cudaMemcpyAsync(n_fallback_out, &d->fb_count, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                        c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "fallback count copy");
+    }
+    // global searches over the brick level of the CSR build; dense segments
+    // are scanned in the slots
+    TRY(launch(c, K_FALLBACK, [&] {
+        return launch_fallback(src, pose_dev, (const float4 *)c->bpts.p, (const float4 *)c->brick_box.p,
+                               (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
+                               (const int *)c->fb_list.p, (const int *)c->hv_list.p, (const uint2 *)c->hv_range.p,
+                               (const float4 *)c->fslots.p, d, nn_out, d2_out, n_src, 0, c->stream);
+    }));
+    cudaError_t e = cudaEventRecord(c->ev_nns, c->stream);
+    return e == cudaSuccess ? VICP_OK : cuda_fail(c, e, "event record");
+}
+
 int32_t vicp_kernel_count(void) { return K_COUNT; }
 
 const char *vicp_kernel_name(int32_t k) { return kernel_name(k); }
@@ -901,7 +986,7 @@ const char *kernel_name(int k)
 {
     static const char *names[K_COUNT] = {"bbox",       "histogram", "scan",     "scatter",      "brick_scan",
                                          "brick_boxes", "dilate",   "correspond", "fallback", "reduce_solve",
-                                         "maxcount"};
+                                         "maxcount",   "fixed_scatter", "fixed_correspond"};
     return (k >= 0 && k < K_COUNT) ? names[k] : "?";
 }
 }  // namespace vicp

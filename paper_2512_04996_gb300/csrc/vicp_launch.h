@@ -40,6 +40,8 @@ enum KernelId {
     K_FALLBACK,
     K_REDUCE_SOLVE,
     K_MAXCOUNT,
+    K_FIXED_SCATTER,
+    K_FIXED_CORRESPOND,
     K_COUNT
 };
 const char *kernel_name(int k);
@@ -95,10 +97,24 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
                               cudaStream_t st);
+// The localised search over a fixed-capacity store (C slots per voxel at
+// v * C, fill counts in count), listing like launch_correspond; the global
+// search then takes the slots as its dense-segment store.
+cudaError_t launch_correspond_fixed(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
+                                    const unsigned *count, unsigned C, const float4 *slots, int *nn, float *d2,
+                                    int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, cudaStream_t st);
+// Fixed-capacity build (vicp_fixed.cu): count must hold zeros; overflow
+// (one word) is added to.
+cudaError_t launch_fixed_scatter(const float4 *pts, int n, const GridGeom &g, unsigned C, unsigned *count,
+                                 float4 *slots, unsigned *overflow, cudaStream_t st);
 cudaError_t launch_fallback(const float4 *src, const double *pose, const float4 *bpts, const float4 *bbox,
                             const float4 *sb_box, const float4 *tgt, int n_tgt, const int *outside, const int *fb_list,
                             const int *hv_list, const uint2 *hv_range, const float4 *csr, DevCtl *ctl, int *nn,
                             float *d2, int m, int honor_stop, cudaStream_t st);
+// Standalone voxel histogram (vicp_hist.cu): method 0 warp-aggregated,
+// 1 per-block shared-memory hash; adds to counts.
+cudaError_t launch_voxel_histogram(const float4 *pts, int n, const GridGeom &g, int method, int *keys,
+                                   unsigned *counts, cudaStream_t st);
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
                                 float3 center, float2 *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);

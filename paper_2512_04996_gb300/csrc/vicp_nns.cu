@@ -18,11 +18,35 @@ namespace vicp {
 // ---------------------------------------------------------------------------
 constexpr int CORR_THREADS = 512;
 
+// Segment of a root voxel in the CSR store: [off[r], off[r + 1]) (clamped to
+// the store's length).
+struct CsrSeg {
+    const unsigned *off;
+    unsigned cap;
+    __device__ __forceinline__ void range(int r, unsigned &a, unsigned &b) const
+    {
+        a = __ldg(off + r);
+        b = max(a, min(__ldg(off + r + 1), cap));
+    }
+};
+
+// Segment of a root voxel in a fixed-capacity store: the first
+// min(count[r], C) of the C slots that start at r * C.
+struct FixedSeg {
+    const unsigned *count;
+    unsigned C;
+    __device__ __forceinline__ void range(int r, unsigned &a, unsigned &b) const
+    {
+        a = (unsigned)r * C;
+        b = a + min(__ldg(count + r), C);
+    }
+};
+
+template <class Seg>
 __global__ void __launch_bounds__(CORR_THREADS) k_correspond(const float4 *__restrict__ src, int m,
                                                              const double *__restrict__ pose, GridGeom g,
-                                                             const int *__restrict__ root,
-                                                             const unsigned *__restrict__ off,
-                                                             const float4 *__restrict__ csr, int n_cap,
+                                                             const int *__restrict__ root, Seg seg,
+                                                             const float4 *__restrict__ csr,
                                                              int *__restrict__ nn, float *__restrict__ d2,
                                                              int *__restrict__ fb_list, int *__restrict__ hv_list,
                                                              uint2 *__restrict__ hv_range, DevCtl *__restrict__ ctl,
@@ -49,8 +73,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_correspond(const float4 *__res
         const int v = voxel_key(g, s.x, s.y, s.z);
         const int r = (v >= 0) ? __ldg(root + v) : -1;
         if (r >= 0) {
-            a = __ldg(off + r);
-            b = max(a, min(__ldg(off + r + 1), (unsigned)n_cap));
+            seg.range(r, a, b);
             cand = b - a;
             heavy = cand > HEAVY;
             if (!heavy) {
@@ -110,8 +133,18 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
                               cudaStream_t st)
 {
-    return launch_kernel(k_correspond, dim3((m + CORR_THREADS - 1) / CORR_THREADS), dim3(CORR_THREADS), 0, st, src, m,
-                         pose, g, root, off, csr, n_cap, nn, d2, fb_list, hv_list, hv_range, ctl, honor_stop);
+    return launch_kernel(k_correspond<CsrSeg>, dim3((m + CORR_THREADS - 1) / CORR_THREADS), dim3(CORR_THREADS), 0, st,
+                         src, m, pose, g, root, CsrSeg{off, (unsigned)n_cap}, csr, nn, d2, fb_list, hv_list, hv_range,
+                         ctl, honor_stop);
+}
+
+cudaError_t launch_correspond_fixed(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
+                                    const unsigned *count, unsigned C, const float4 *slots, int *nn, float *d2,
+                                    int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, cudaStream_t st)
+{
+    return launch_kernel(k_correspond<FixedSeg>, dim3((m + CORR_THREADS - 1) / CORR_THREADS), dim3(CORR_THREADS), 0,
+                         st, src, m, pose, g, root, FixedSeg{count, C}, slots, nn, d2, fb_list, hv_list, hv_range,
+                         ctl, 0);
 }
 
 // ---------------------------------------------------------------------------

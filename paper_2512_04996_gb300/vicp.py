@@ -33,6 +33,8 @@ VICP_STATIC_MAX_VOXELS = 1 << 24
 VICP_STATIC_MAX_BRICK_SLOTS = 1 << 20
 VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
+VICP_HIST_WARP_AGGREGATED = 0
+VICP_HIST_SHARED_HASH = 1
 VICP_BATCH_MAX_PAIRS = 65536
 VICP_BATCH_SHAPES = 5
 VICP_BATCH_FLAG_NO_GRAPH = 1 << 0
@@ -113,6 +115,10 @@ SIGNATURES = {
     "vicp_last_error": (C.c_char_p, [_P]),
     "vicp_offsets_static": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32), _P, _P,
                                       _P]),
+    "vicp_fixed_build": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
+    "vicp_fixed_correspond": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
+    "vicp_voxel_histogram": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32),
+                                       C.c_int32, _P, _P, _P]),
     "vicp_batch_default_params": (None, [C.POINTER(vicp_batch_params)]),
     "vicp_batch_shape_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                         C.POINTER(C.c_int32)]),
@@ -278,6 +284,28 @@ class Context:
                     "vicp_step")
         return rmse
 
+    def fixed_build(self, target: torch.Tensor, capacity: int):
+        """Fixed-capacity store on the grid of the last build_grid (same
+        target).  Returns (points dropped, bytes of the store)."""
+        t = _cloud(target, "target")
+        over, nbytes = C.c_uint32(0), C.c_uint64(0)
+        self._check(self._lib.vicp_fixed_build(self.handle, t.data_ptr(), t.shape[0], int(capacity), C.byref(over),
+                                               C.byref(nbytes)), "vicp_fixed_build")
+        return int(over.value), int(nbytes.value)
+
+    def fixed_correspond(self, source: torch.Tensor, pose: torch.Tensor, nn=None, d2=None, n_fallback=None):
+        s = _cloud(source, "source")
+        m = s.shape[0]
+        if pose.dtype != torch.float64 or not pose.is_cuda or pose.numel() != 16 or not pose.is_contiguous():
+            raise ValueError("pose: contiguous CUDA float64 tensor with 16 entries")
+        nn = torch.empty(m, dtype=torch.int32, device=s.device) if nn is None else nn
+        d2 = torch.empty(m, dtype=torch.float32, device=s.device) if d2 is None else d2
+        if n_fallback is None:
+            n_fallback = torch.zeros(1, dtype=torch.int32, device=s.device)
+        self._check(self._lib.vicp_fixed_correspond(self.handle, s.data_ptr(), m, pose.data_ptr(), nn.data_ptr(),
+                                                    d2.data_ptr(), n_fallback.data_ptr()), "vicp_fixed_correspond")
+        return nn, d2, n_fallback
+
     def register(self, source: torch.Tensor, target: torch.Tensor, pose=None):
         s, t = _cloud(source, "source"), _cloud(target, "target")
         self._target = t
@@ -428,6 +456,34 @@ def vicp_offsets_static(target, origin, voxel_size: float, dims, keys=None, offs
         raise VicpError(r, f"vicp_offsets_static: {lib.vicp_status_string(r).decode()} (static scratch holds at "
                            f"most {VICP_STATIC_MAX_VOXELS} voxels and {VICP_STATIC_MAX_BRICK_SLOTS} brick slots)")
     return keys, offsets
+
+
+def vicp_voxel_histogram(target, origin, voxel_size: float, dims, method: int = VICP_HIST_WARP_AGGREGATED,
+                         keys=None, counts=None, stream=None):
+    """Voxel keys and per-voxel counts of `target` on an explicit grid by one
+    of the two histogram designs (see include/vicp.h).  `counts` (int32[V],
+    holding uint32) is added to; it is zeroed here only when not given.
+    Returns (keys, counts)."""
+    lib = load_library()
+    _cloud(target, "target")
+    n = target.shape[0]
+    V = int(dims[0]) * int(dims[1]) * int(dims[2])
+    if keys is None:
+        keys = torch.empty(n, dtype=torch.int32, device=target.device)
+    if counts is None:
+        counts = torch.zeros(V, dtype=torch.int32, device=target.device)
+    for t, size, what in ((keys, n, "keys"), (counts, V, "counts")):
+        if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous() or t.numel() < size:
+            raise ValueError(f"{what}: expected a contiguous CUDA int32 tensor of >= {size} entries")
+    st = stream if stream is not None else torch.cuda.current_stream(target.device)
+    o = (C.c_float * 3)(*[float(x) for x in origin])
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    r = lib.vicp_voxel_histogram(C.c_void_p(target.data_ptr()), n, o, float(voxel_size), d, int(method),
+                                 C.c_void_p(keys.data_ptr()), C.c_void_p(counts.data_ptr()),
+                                 C.c_void_p(st.cuda_stream))
+    if r != VICP_OK:
+        raise VicpError(r, f"vicp_voxel_histogram: {lib.vicp_status_string(r).decode()}")
+    return keys, counts
 
 
 # --- batched registration ---------------------------------------------------
