@@ -226,12 +226,12 @@ def _rot_deg(Ta, Tb) -> float:
     return math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(E) - 1.0) / 2.0))))
 
 
-def run_batched(dev, flush, reps: int = 5) -> dict:
+def run_batched(dev, flush, reps: int = 5, n_pairs: int = 256) -> dict:
     import torch
 
     from paper_2512_04996_gb300 import synth, vicp
 
-    ps = synth.batched_pairs()
+    ps = synth.batched_pairs(n_pairs=n_pairs)
     P = len(ps)
     stream = torch.cuda.current_stream(dev)
     tgt_np = np.ascontiguousarray(np.concatenate([p.target for p in ps]))
@@ -474,12 +474,12 @@ def run_hist_ablation(dev, tgt, view, occupied: int, flush, reps: int = 200) -> 
 # ----------------------------------------------------------------------------
 # differentiable loss: 64 pairs x 20k points, forward + backward
 # ----------------------------------------------------------------------------
-def run_loss(dev, flush, steps: int = 50) -> dict:
+def run_loss(dev, flush, steps: int = 50, n_pairs: int = 64) -> dict:
     import torch
 
     from paper_2512_04996_gb300 import synth, vicp
 
-    ps = synth.loss_pairs(workers=max(1, min(16, os.cpu_count() or 1)))
+    ps = synth.loss_pairs(n_pairs=n_pairs, workers=max(1, min(16, os.cpu_count() or 1)))
     P = len(ps)
     stream = torch.cuda.current_stream(dev)
     tgt = torch.from_numpy(np.ascontiguousarray(np.concatenate([p.target for p in ps]))).to(dev)
@@ -665,10 +665,15 @@ def run_ours(args, rank, ws, local):
     E = T @ np.linalg.inv(pair.T_gt)
     rot_err_deg = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(E[:3, :3]) - 1) / 2))))
 
-    hist_ablation = run_hist_ablation(dev, tgt, view, mem["occupied_voxels"], flush)
-    fixed_capacity = run_fixed(dev, pair, flush)
-    batched = run_batched(dev, flush)
-    differentiable = run_loss(dev, flush)
+    sections = set(args.sections.split(","))
+    run_all = "all" in sections
+    hist_ablation = run_hist_ablation(dev, tgt, view, mem["occupied_voxels"], flush) \
+        if run_all or "hist" in sections else None
+    fixed_capacity = run_fixed(dev, pair, flush) if run_all or "fixed" in sections else None
+    batched = run_batched(dev, flush, n_pairs=32 if args.small else 256) \
+        if run_all or "batched" in sections else None
+    differentiable = run_loss(dev, flush, n_pairs=16 if args.small else 64) \
+        if run_all or "loss" in sections else None
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -781,6 +786,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sections", default="all",
+                    help="extra measurements after the headline: all, or a comma list of hist, fixed, batched, "
+                         "loss, none (for profiler captures)")
+    ap.add_argument("--small", action="store_true",
+                    help="batched and loss sections on 32 and 16 pairs (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
