@@ -750,7 +750,19 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
                 a.d2[e.y] = __uint_as_float((unsigned)(best >> 32));
             }
         }
-        for (int qi = gw; qi < F; qi += n_warps) {
+        // global queries in chunks of FB_CHUNK, each chunk to whichever warp is
+        // free (a ticket per chunk): their costs vary widely, and a fixed share
+        // per warp leaves the whole grid waiting at the barrier for the warp
+        // that drew the slowest ones
+        constexpr int FB_CHUNK = 4;
+        for (;;) {
+            int q0 = 0;
+            if (lane == 0)
+                q0 = FB_CHUNK * (int)atomicAdd(&ctl->fb_next, 1u);
+            q0 = __shfl_sync(FULL_MASK, q0, 0);
+            if (q0 >= F)
+                break;
+            for (int qi = q0; qi < min(q0 + FB_CHUNK, F); ++qi) {
             const int2 e = a.fb_list[qi];
             if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap) {
                 if (lane == 0)   // a stale entry: skip it, report it
@@ -768,6 +780,7 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
                 a.nn[e.y] = (int)(unsigned)best;
                 a.d2[e.y] = __uint_as_float((unsigned)(best >> 32));
             }
+            }
         }
         if (lane == 0 && examined)
             atomicAdd(&ctl->stat_global_cand, examined);
@@ -777,6 +790,7 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
             ctl->stat_fallbacks += (unsigned long long)F;
             ctl->fb_count = 0;
             ctl->hv_count = 0;
+            ctl->fb_next = 0u;
         }
     }
     if (a.search_only)

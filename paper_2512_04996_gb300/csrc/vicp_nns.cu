@@ -207,7 +207,16 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
         }
     }
 
-    for (int qi = gw; qi < F; qi += n_warps) {
+    // global queries, one at a time to whichever warp is free (a ticket each):
+    // their costs vary widely, and a fixed share per warp leaves the kernel
+    // waiting for the warp that drew the slowest ones
+    for (;;) {
+        int qi = 0;
+        if (lane == 0)
+            qi = (int)atomicAdd(&ctl->fb_next, 1u);
+        qi = __shfl_sync(FULL_MASK, qi, 0);
+        if (qi >= F)
+            break;
         const int i = __ldg(fb_list + qi);
         if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
             if (lane == 0)
@@ -236,6 +245,7 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
             ctl->stat_fallbacks += (unsigned long long)F;
             ctl->fb_count = 0;
             ctl->hv_count = 0;
+            ctl->fb_next = 0u;
             ctl->fb_done = 0u;
         }
     }
