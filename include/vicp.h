@@ -334,7 +334,7 @@ VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, int32_t n, co
 typedef struct vicp_batch vicp_batch;
 
 #define VICP_BATCH_MAX_PAIRS 65536
-#define VICP_BATCH_SHAPES 5                     /* iteration kernel shapes (see vicp_batch_shape_info) */
+#define VICP_BATCH_SHAPES 7                     /* iteration kernel shapes (see vicp_batch_shape_info) */
 #define VICP_BATCH_FLAG_NO_GRAPH (1u << 0)      /* launch the iterations one by one instead of
                                                    replaying them as a captured CUDA graph */
 #define VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT (1u << 1) /* test hook: block 0 of the iteration kernel

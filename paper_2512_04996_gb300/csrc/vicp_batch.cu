@@ -933,6 +933,8 @@ const BatchShape BATCH_SHAPES[BATCH_N_SHAPES] = {
     {512, 2, 1},   // 1024-point items, wide blocks
     {128, 4, 4},   // 512-point items, narrow blocks
     {256, 8, 2},   // 2048-point items
+    {256, 2, 4},   // 512-point items, 64 registers: more warps per SM
+    {256, 2, 5},   // 512-point items, 48 registers (spills some of the reduction's sums)
 };
 
 using IterKernel = void (*)(const BatchIterArgs);
@@ -945,6 +947,8 @@ static IterKernel iter_kernel(int shape)
     case 2: return k_batch_iter<512, 2, 1>;
     case 3: return k_batch_iter<128, 4, 4>;
     case 4: return k_batch_iter<256, 8, 2>;
+    case 5: return k_batch_iter<256, 2, 4>;
+    case 6: return k_batch_iter<256, 2, 5>;
     }
     return nullptr;
 }

@@ -62,7 +62,7 @@ constexpr int BATCH_SMEM_PAIRS = 2048;   // unit-start tables up to this many pa
 struct BatchShape {
     int threads, ppt, min_blocks;
 };
-constexpr int BATCH_N_SHAPES = 5;
+constexpr int BATCH_N_SHAPES = 7;
 extern const BatchShape BATCH_SHAPES[BATCH_N_SHAPES];
 
 // Arguments of one iteration of all pairs.

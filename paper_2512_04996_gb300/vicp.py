@@ -36,7 +36,7 @@ VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
 VICP_HIST_WARP_AGGREGATED = 0
 VICP_HIST_SHARED_HASH = 1
 VICP_BATCH_MAX_PAIRS = 65536
-VICP_BATCH_SHAPES = 5
+VICP_BATCH_SHAPES = 7
 VICP_BATCH_FLAG_NO_GRAPH = 1 << 0
 VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT = 1 << 1
 

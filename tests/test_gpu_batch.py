@@ -112,7 +112,7 @@ def test_batch_correspond_equals_oracle(which):
     assert b.report(reset=True)["fallbacks"] == n_fb
 
 
-@pytest.mark.parametrize("shape", range(5))
+@pytest.mark.parametrize("shape", range(7))
 def test_every_shape_gives_the_same_neighbours(shape):
     ps = _small(n_pairs=6, n_min=900, n_max=9000, seed=11)
     T = torch.from_numpy(np.ascontiguousarray(np.stack([np.eye(4)] * len(ps)))).cuda()
