@@ -130,3 +130,47 @@ def test_batch_barrier_time_limit_and_recovery():
     st2, T2, it2, rm2, _ = fresh.register(src, n_src)
     assert st == 0 and st2 == 0
     assert np.array_equal(T, T2) and np.array_equal(it, it2) and np.array_equal(rm, rm2)
+
+
+def test_batch_allocator_serves_every_buffer_and_failure_is_reported():
+    """A batch context on a caller's allocator: registration works with every
+    buffer from the allocator, destroy returns them all, and an allocator
+    that runs dry gives VICP_ERR_OOM without leaking."""
+    from paper_2512_04996_gb300 import synth
+    v = vicp()
+    live = {}
+    budget = {"n": 10 ** 6}
+
+    @v.ALLOC_FN
+    def alloc(nbytes, stream, user):
+        if budget["n"] == 0:
+            return None
+        budget["n"] -= 1
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @v.FREE_FN
+    def free(ptr, nbytes, stream, user):
+        live.pop(ptr)
+
+    a = v.vicp_allocator(alloc, free, None)
+    ps = synth.batched_pairs(seed=67, n_pairs=3, n_min=800, n_max=2500)
+    tgt = torch.from_numpy(np.concatenate([p.target for p in ps])).cuda()
+    src = torch.from_numpy(np.concatenate([p.source for p in ps])).cuda()
+    n_tgt = np.array([p.target.shape[0] for p in ps], np.int32)
+    n_src = np.array([p.source.shape[0] for p in ps], np.int32)
+    dv = np.array([p.grid_divisions for p in ps], np.int32)
+    b = v.Batch(v.batch_default_params(max_iters=3), allocator=a)
+    b.build(tgt, n_tgt, None, dv)
+    st = b.register(src, n_src)[0]
+    assert st == 0 and len(live) > 10
+    b.close()
+    assert live == {}
+    budget["n"] = 8
+    b = v.Batch(v.batch_default_params(max_iters=3), allocator=a)
+    with pytest.raises(v.VicpError) as e:
+        b.build(tgt, n_tgt, None, dv)
+    assert e.value.status == v.VICP_ERR_OOM
+    b.close()
+    assert live == {}
