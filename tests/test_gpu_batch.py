@@ -276,3 +276,23 @@ def test_full_batched_workload_sampled():
         sst, S, sit, _ = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
         assert sst == 0
         _assert_pose_close(T[k], S, _extent(p.target))
+
+
+def test_more_pairs_than_the_shared_memory_tables_hold():
+    """2,100 small pairs (the dilation's per-pair unit tables then stay in
+    global memory): sampled pairs' grids and registrations against the
+    oracle."""
+    rng = np.random.default_rng(79)
+    ps = [synth.sphere_plane(seed=int(rng.integers(0, 2**31 - 1)), n=int(rng.integers(120, 400)), max_deg=10.0,
+                             max_trans=0.05) for _ in range(2100)]
+    iters = 4
+    b, t, s, n_src = _batch(ps, max_iters=iters)
+    st, T, it, rm, pst = b.register(s, n_src)
+    assert st == 0 and (it == iters).all()
+    for k in (0, 1, 1023, 2047, 2048, 2099):
+        p = ps[k]
+        g = _pair_grid_np(b, k)
+        og = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
+        assert_grid_equal(g, oracle.build_grid(og, p.target, L), p.target)
+        _, R, _, _ = oracle.register(og, L, p.target, p.source, np.eye(4), max_iters=iters, eps=0.0)
+        _assert_pose_close(T[k], R, _extent(p.target))
