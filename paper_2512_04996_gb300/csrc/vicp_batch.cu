@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
     __shared__ unsigned long long s_cand;
     __shared__ int s_fb, s_fb_base, s_hv, s_hv_base;
     __shared__ float s_whi[WARPS][N_SUMS], s_wlo[WARPS][N_SUMS];
-    __shared__ dfl s_tot[N_SUMS], s_M[16], s_dT[12];
+    __shared__ dfl s_tot[N_SUMS];
     extern __shared__ float s_dyn[];   // [2][WARPS][N_SUMS][33]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     DevCtl *const ctl = a.ctl;
@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
             if (warp == 0) {
                 double rmse;
                 BatchState *stp = a.state + it.pair;
-                const bool ok = solve_update(s_tot, bp->n_src, cf, a.pose + 16 * it.pair, s_M, s_dT, rmse);
+                const bool ok = solve_update(s_tot, bp->n_src, cf, a.pose + 16 * it.pair, rmse);
                 if (lane == 0) {
                     stp->items_done = 0u;
                     stp->last_rmse = rmse;

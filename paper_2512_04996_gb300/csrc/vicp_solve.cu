@@ -17,9 +17,10 @@ static_assert(N_SUMS == REDUCE_VALUES, "sum layout");
 //   [6..14] sum (s - c)(q - c)^T [15]    sum |s - q|^2
 // in double-float, each warp reduces them with shuffles in a fixed order, and
 // the warps' sums are added per block.  The last block to finish (atomic
-// ticket) adds all block partials in a fixed order, one lane solves Eq. 1,
-// and twelve lanes compose the update with the pose in FP64, so the result
-// is bit-identical from run to run whichever block finishes last.
+// ticket) adds all block partials in a fixed order and its first warp
+// solves Eq. 1 (a matrix entry per lane) and composes the update with the
+// pose in FP64, so the result is bit-identical from run to run whichever
+// block finishes last.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__restrict__ src, int m,
                                                               double *__restrict__ pose,
@@ -146,11 +147,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
     if (warp != 0)
         return;
 
-    // Warp 0 solves (its lanes share the scalar work and split the minors
-    // and cofactors) and composes the update with the pose.
-    __shared__ dfl s_M[16], s_dT[12];
+    // Warp 0 solves (a matrix entry per lane) and composes the update with
+    // the pose.
     double rmse;
-    const bool ok = solve_update(s_tot, m, cf, pose, s_M, s_dT, rmse);
+    const bool ok = solve_update(s_tot, m, cf, pose, rmse);
     if (lane == 0) {
         ctl->red_done = 0u;
         if (rmse_out)
