@@ -104,7 +104,7 @@ typedef struct vicp_grid_view {
     int32_t n_stored;          /* points inside the grid = offsets[V] */
     int32_t dilation_layers;   /* L of the last vicp_dilate, -1 before any */
     const int32_t *keys;       /* [n_target] voxel key x + nx*(y + ny*z), -1 outside */
-    const uint32_t *offsets;   /* [V+1] exclusive scan of the per-voxel counts */
+    const uint32_t *offsets;   /* [V+1] exclusive scan of the per-voxel counts (all entries) */
     const int32_t *ids;        /* [n_stored] point indices grouped by voxel; the order inside
                                   one voxel's segment is unspecified */
     const float *csr_points;   /* [n_stored x 4] x, y, z of ids[k]; w holds the bits of ids[k] */
@@ -230,7 +230,12 @@ VICP_API vicp_status vicp_register_host(vicp_ctx *ctx, const float *src_xyzw_hos
                                const float *tgt_xyzw_host, int32_t n_tgt, double pose_host[16],
                                int32_t *iters_out, double *rmse_out);
 
-/* Synchronous: waits for the stream and fills *out (n_stored is read back). */
+/* Synchronous: waits for the stream and fills *out (n_stored is read back).
+ * The build itself writes only the offsets its searches read (those of the
+ * occupied voxels and the ones just past them, every 32nd, and offsets[V]);
+ * the first vicp_get_grid or vicp_memory_report after a build completes the
+ * array (one kernel on the context's stream), so out->offsets holds all
+ * V + 1 entries. */
 VICP_API vicp_status vicp_get_grid(vicp_ctx *ctx, vicp_grid_view *out);
 
 /* Synchronous: waits for the stream, returns and clears the device status. */
@@ -425,7 +430,9 @@ VICP_API vicp_status vicp_batch_tune(vicp_batch *b, const float *src_xyzw, const
  * grid, with one difference: offsets hold positions in the POOLED store, so
  * offsets[0] is the pair's first position (not 0) and ids / csr_points point
  * at the start of the pooled store; ids and the csr w fields hold the pair's
- * own target indices.  Synchronous.  Errors: VICP_ERR_STATE, VICP_ERR_INVALID. */
+ * own target indices.  As with vicp_get_grid, the first call after a build
+ * completes the pooled offsets array (one kernel).  Synchronous.  Errors:
+ * VICP_ERR_STATE, VICP_ERR_INVALID. */
 VICP_API vicp_status vicp_batch_pair_grid(vicp_batch *b, int32_t pair, vicp_grid_view *out);
 
 /* Synchronous: device bytes held by the batch context now and at peak,

@@ -60,6 +60,7 @@ struct vicp_ctx {
     int lab_dims[3] = {0, 0, 0};   // grid dimensions that state belongs to
     Buf occ[2];       // occupancy bits: the current build's, and the next build's (kept zeroed)
     int occ_cur = 0;
+    bool off_dense = false;   // the build writes sparse offsets; vicp_get_grid completes them
     long long cap_V = -1;
     // brick level (V / 512)
     Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_box;
@@ -426,8 +427,9 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
         return cuda_fail(c, ev, "event record");
     TRY(launch(c, K_SCAN, [&] {
         return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, occ,
-                           (const unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, c->stream);
+                           (const unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, c->stream, false);
     }));
+    c->off_dense = false;
     TRY(launch(c, K_BRICK_SCAN, [&] {
         return launch_brick_scan((const unsigned *)c->bcounts.p, g, (unsigned *)c->boff.p, (int *)c->brick_list.p,
                                  (uint2 *)c->brick_range.p, (int *)c->bslot.p, (uint4 *)c->boxord.p, d, c->stream);
@@ -448,6 +450,20 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     c->dilated_L = -1;
     c->n_target = n;
     c->target = tgt;
+    return VICP_OK;
+}
+
+// Completes the build's sparse offsets (once per build) for the callers that
+// hand out or scan the whole array.
+vicp_status dense_offsets(vicp_ctx *c)
+{
+    if (c->off_dense)
+        return VICP_OK;
+    const GridGeom &g = c->geom;
+    TRY(launch(c, K_OFFSETS_FILL, [&] {
+        return launch_offsets_fill((unsigned *)c->off.p, (const unsigned *)c->occ[c->occ_cur].p, g.V, c->stream);
+    }));
+    c->off_dense = true;
     return VICP_OK;
 }
 
@@ -776,6 +792,7 @@ vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
     out->n_voxels = g.V;
     out->n_target = c->n_target;
     out->dilation_layers = c->dilated_L;
+    TRY(dense_offsets(c));
     uint32_t stored = 0;
     cudaError_t e = cudaMemcpyAsync(&stored, (const unsigned *)c->off.p + g.V, 4, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess)
@@ -813,6 +830,7 @@ vicp_status vicp_memory_report(vicp_ctx *c, vicp_memory *out)
     cudaError_t e = cudaMemsetAsync(&d->max_count, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "memory report");
+    TRY(dense_offsets(c));
     TRY(launch(c, K_MAXCOUNT, [&] { return launch_maxcount((const unsigned *)c->off.p, g, d, c->stream); }));
     unsigned mc[2] = {0, 0};
     uint32_t stored = 0;
@@ -986,7 +1004,7 @@ const char *kernel_name(int k)
 {
     static const char *names[K_COUNT] = {"bbox",       "histogram", "scan",     "scatter",      "brick_scan",
                                          "brick_boxes", "dilate",   "correspond", "fallback", "reduce_solve",
-                                         "maxcount",   "fixed_scatter", "fixed_correspond"};
+                                         "maxcount",   "fixed_scatter", "fixed_correspond", "offsets_fill"};
     return (k >= 0 && k < K_COUNT) ? names[k] : "?";
 }
 }  // namespace vicp

@@ -39,6 +39,7 @@ struct vicp_batch {
 
     // layout of the last build
     bool built = false;
+    bool off_dense = false;          // the build writes sparse offsets; vicp_batch_pair_grid completes them
     int P = 0;
     int N = 0;                       // pooled target points
     long long Vt = 0;                // pooled voxels (with alignment gaps)
@@ -360,8 +361,9 @@ vicp_status build(vicp_batch *b, int P, const float *tgt, const int32_t *n_tgt, 
     GridGeom gall{};
     gall.V = Vt;
     BCUDA(b, launch_scan((const unsigned *)b->counts.p, gall, (unsigned *)b->off.p, (const unsigned *)b->occ.p,
-                         (const unsigned *)b->tile_sum.p, (unsigned long long *)b->desc.p, d, st),
+                         (const unsigned *)b->tile_sum.p, (unsigned long long *)b->desc.p, d, st, false),
           "launch of the scan");
+    b->off_dense = false;
     BCUDA(b, launch_batch_brick_scan((const unsigned *)b->bcounts.p, pd, P, (const unsigned *)b->off.p,
                                      (unsigned *)b->boff.p, (int *)b->blist.p, (uint2 *)b->brange.p,
                                      (int *)b->bslot.p, (uint4 *)b->boxord.p, (BatchState *)b->state.p, st),
@@ -826,6 +828,12 @@ vicp_status vicp_batch_pair_grid(vicp_batch *b, int32_t pair, vicp_grid_view *ou
     if (pair < 0 || pair >= b->P)
         return bfail(b, VICP_ERR_INVALID, "pair %d out of range", pair);
     const BatchPair &bp = b->pairs[pair];
+    if (!b->off_dense) {   // complete the pooled offsets once per build
+        BCUDA(b, launch_offsets_fill((unsigned *)b->off.p, (const unsigned *)b->occ.p, b->Vt, b->stream),
+              "launch of the offsets fill");
+        b->launches += 1;
+        b->off_dense = true;
+    }
     unsigned ends[2] = {0u, 0u};
     const unsigned *off = (const unsigned *)b->off.p + bp.vbase;
     BCUDA(b, cudaMemcpyAsync(&ends[0], off, 4, cudaMemcpyDeviceToHost, b->stream), "offset read-back");

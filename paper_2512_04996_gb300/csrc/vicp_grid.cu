@@ -328,23 +328,30 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 // ---------------------------------------------------------------------------
 // MOC as a single-pass exclusive scan with lookback, without waiting.
 //
-// A tile is 16384 voxels: 512 threads, each owning the 32 voxels of one
-// occupancy word; CTA t scans tile t.  It reads its occupancy words, gathers
-// the counts of the occupied voxels only (all loads of a thread in flight
+// A tile is 16384 voxels; CTA t scans tile t, each thread owning WPT
+// consecutive occupancy words (32 WPT voxels).  It reads its occupancy
+// words, gathers the counts of the occupied voxels only (loads in flight
 // together) and scans them.  Its exclusive prefix is the sum of every
 // earlier tile's total, and the histogram has already written those totals,
 // so nothing ever has to be waited for: the CTA looks back over its
-// predecessors, 512 per round (one per thread), and adds their totals down
-// to the nearest predecessor that has already published its inclusive
-// prefix (any one that has not is simply summed through).  A published
-// prefix is one 64-bit word [epoch:30 | flag:2 | value:32], so flag and value
-// are read together; the epoch (bumped by the histogram each build) retires
-// the previous build's words without clearing them.  The tile totals stay
+// predecessors, one per thread and round, and adds their totals down to the
+// nearest predecessor that has already published its inclusive prefix (any
+// one that has not is simply summed through).  A published prefix is one
+// 64-bit word [epoch:30 | flag:2 | value:32], so flag and value are read
+// together; the epoch (bumped by the histogram each build) retires the
+// previous build's words without clearing them.  The tile totals stay
 // untouched while the scan runs (predecessors are read throughout); the
 // scatter, which runs next, zeroes them for the following build.
+//
+// Output.  Dense (512 threads x 1 word): every off[v], staged in shared
+// memory and written with coalesced 16-byte stores.  Sparse (256 threads x
+// 2 words, the build's form): only the entries the build and the searches
+// read -- off[v] and off[v + 1] of every occupied voxel v, off[32 k] for
+// every occupancy word k, and off[V] -- about 1/15 of the array's bytes at
+// the scene workloads' 0.5% occupancy.  Every other entry equals the nearest
+// written entry before it in its word (an empty voxel adds nothing), which
+// is how k_offsets_fill completes the array when a caller asks for it.
 // ---------------------------------------------------------------------------
-constexpr int SCAN_THREADS = SCAN_TILE / 32;   // 512
-constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 constexpr unsigned long long DESC_PREFIX = 2ull << 32;
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
@@ -367,8 +374,10 @@ __device__ __forceinline__ unsigned warp_sum_u32(unsigned v)
     return v;
 }
 
-// Exclusive block-wide scan of one value per thread; returns the thread's
-// exclusive prefix, *total gets the block total.  Uses s_w[SCAN_WARPS].
+// Exclusive block-wide scan of one value per thread (WARPS warps); returns
+// the thread's exclusive prefix, *total gets the block total.  Uses
+// s_w[WARPS + 1].
+template <int WARPS>
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_w, unsigned *total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -383,42 +392,68 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *s_w, u
         s_w[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const unsigned w = lane < SCAN_WARPS ? s_w[lane] : 0u;
+        const unsigned w = lane < WARPS ? s_w[lane] : 0u;
         unsigned wi = w;
 #pragma unroll
-        for (int d = 1; d < SCAN_WARPS; d <<= 1) {
+        for (int d = 1; d < WARPS; d <<= 1) {
             const unsigned y = __shfl_up_sync(FULL_MASK, wi, d);
             if (lane >= d)
                 wi += y;
         }
-        if (lane < SCAN_WARPS)
+        if (lane < WARPS)
             s_w[lane] = wi - w;
-        if (lane == SCAN_WARPS - 1)
-            s_w[SCAN_WARPS] = wi;
+        if (lane == WARPS - 1)
+            s_w[WARPS] = wi;
     }
     __syncthreads();
-    *total = s_w[SCAN_WARPS];
+    *total = s_w[WARPS];
     return s_w[warp] + (incl - v);
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__restrict__ counts, long long V,
-                                                       unsigned *__restrict__ off, const unsigned *__restrict__ occ,
-                                                       const unsigned *__restrict__ tile_sum,
-                                                       unsigned long long *__restrict__ desc,
-                                                       const DevCtl *__restrict__ ctl)
+// Sum of the counts of the set bits of `bits` (voxels base + i), four loads
+// in flight per round.
+__device__ __forceinline__ unsigned word_count_sum(const unsigned *__restrict__ counts, long long base, unsigned bits)
 {
+    unsigned sum = 0u;
+    while (bits) {
+        unsigned c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = 0u;
+            if (bits) {
+                c[u] = __ldg(counts + base + (__ffs(bits) - 1));
+                bits &= bits - 1u;
+            }
+        }
+        sum += (c[0] + c[1]) + (c[2] + c[3]);
+    }
+    return sum;
+}
+
+template <int THREADS, int WPT, bool DENSE>
+__global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
+    k_scan(const unsigned *__restrict__ counts, long long V, unsigned *__restrict__ off,
+           const unsigned *__restrict__ occ, const unsigned *__restrict__ tile_sum,
+           unsigned long long *__restrict__ desc, const DevCtl *__restrict__ ctl)
+{
+    static_assert(THREADS * WPT * 32 == SCAN_TILE, "tile");
+    static_assert(!DENSE || WPT == 1, "the dense output stages one word per thread");
+    constexpr int WARPS = THREADS / 32;
     pdl_begin();
-    __shared__ unsigned s_epoch, s_w[SCAN_WARPS + 1], s_first[SCAN_WARPS], s_sum[SCAN_WARPS];
+    __shared__ unsigned s_epoch, s_w[WARPS + 1], s_first[WARPS], s_sum[WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned tile = blockIdx.x;
     if (tid == 0)   // read by one thread per CTA (a hot line otherwise)
         s_epoch = *(volatile const unsigned *)&ctl->scan_epoch & 0x3fffffffu;
 
-    // this thread's 32 voxels: counts of the occupied ones only, loaded
-    // together (predicated, one round trip); the first lookback round's
-    // loads go out at the same time (they depend on the tile index only)
-    const long long base = (long long)tile * SCAN_TILE + 32ll * tid;
-    const unsigned bits = base < V ? __ldg(occ + (base >> 5)) : 0u;
+    // this thread's words and the counts of their occupied voxels; the first
+    // lookback round's loads go out at the same time (they depend on the
+    // tile index only)
+    const long long base = (long long)tile * SCAN_TILE + 32ll * WPT * tid;
+    unsigned bits[WPT];
+#pragma unroll
+    for (int w = 0; w < WPT; ++w)
+        bits[w] = base + 32 * w < V ? __ldg(occ + (base >> 5) + w) : 0u;
     unsigned long long d0 = 0ull;
     unsigned t0 = 0u;
     if ((long long)tile - 1 - tid >= 0) {
@@ -426,17 +461,23 @@ __global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__rest
         t0 = __ldg(tile_sum + (tile - 1 - tid));
     }
     unsigned sum = 0u;
+    if (DENSE) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
-        sum += ((bits >> i) & 1u) ? __ldg(counts + base + i) : 0u;
+        for (int i = 0; i < 32; ++i)
+            sum += ((bits[0] >> i) & 1u) ? __ldg(counts + base + i) : 0u;
+    } else {
+#pragma unroll
+        for (int w = 0; w < WPT; ++w)
+            sum += word_count_sum(counts, base + 32 * w, bits[w]);
+    }
     unsigned tile_total;
-    const unsigned thread_excl = block_excl_scan(sum, s_w, &tile_total);   // also orders s_epoch
+    const unsigned thread_excl = block_excl_scan<WARPS>(sum, s_w, &tile_total);   // also orders s_epoch
     const unsigned long long tag = (unsigned long long)s_epoch << 34;
 
-    // lookback: 512 predecessors per round, nearest first (thread i looks at
-    // tile - 1 - i); sum the totals before the nearest published prefix
+    // lookback: THREADS predecessors per round, nearest first (thread i looks
+    // at tile - 1 - i); sum the totals before the nearest published prefix
     unsigned excl = 0u;
-    for (long long look = (long long)tile - 1; look >= 0; look -= SCAN_THREADS) {
+    for (long long look = (long long)tile - 1; look >= 0; look -= THREADS) {
         const long long idx = look - tid;
         bool pre = false;
         unsigned v = 0u;
@@ -452,11 +493,11 @@ __global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__rest
         }
         const unsigned pm = __ballot_sync(FULL_MASK, pre);
         if (lane == 0)
-            s_first[warp] = pm ? (unsigned)(warp * 32 + __ffs(pm) - 1) : (unsigned)SCAN_THREADS;
+            s_first[warp] = pm ? (unsigned)(warp * 32 + __ffs(pm) - 1) : (unsigned)THREADS;
         __syncthreads();
-        unsigned first = SCAN_THREADS;
+        unsigned first = THREADS;
 #pragma unroll
-        for (int w = 0; w < SCAN_WARPS; ++w)
+        for (int w = 0; w < WARPS; ++w)
             first = min(first, s_first[w]);
         const unsigned ws = warp_sum_u32((unsigned)tid <= first ? v : 0u);
         if (lane == 0)
@@ -464,35 +505,55 @@ __global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__rest
         __syncthreads();
         unsigned round = 0u;
 #pragma unroll
-        for (int w = 0; w < SCAN_WARPS; ++w)
+        for (int w = 0; w < WARPS; ++w)
             round += s_sum[w];
         excl += round;
         __syncthreads();   // s_first / s_sum are reused
-        if (first < SCAN_THREADS)
+        if (first < THREADS)
             break;
     }
     if (tid == 0)
         st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + tile_total));
 
+    unsigned run = excl + thread_excl;
+    if (!DENSE) {
+        // the entries the build and the searches read, straight from registers
+#pragma unroll
+        for (int w = 0; w < WPT; ++w) {
+            const long long b = base + 32 * w;
+            if (b > V)
+                break;
+            off[b] = run;   // the word's first entry (off[V] itself when b == V)
+            for (unsigned m = bits[w]; m; m &= m - 1u) {
+                const int i = __ffs(m) - 1;
+                if (i)
+                    off[b + i] = run;
+                run += __ldg(counts + b + i);   // from L1
+                if (i < 31 && !((bits[w] >> (i + 1)) & 1u))
+                    off[b + i + 1] = run;
+            }
+            if (b < V && b + 32 >= V)   // the word holding voxel V-1 closes the array
+                off[V] = run;
+        }
+        return;
+    }
+
     // the 32 offsets of this thread, staged in shared memory (row stride 33
     // words: conflict-free both ways) and written out with coalesced 16-byte
     // stores
-    extern __shared__ unsigned s_off[];   // [SCAN_THREADS][33]
-    {
-        unsigned run = excl + thread_excl;
+    extern __shared__ unsigned s_off[];   // [THREADS][33]
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {   // the counts again, from L1
-            s_off[tid * 33 + i] = run;
-            run += ((bits >> i) & 1u) ? __ldg(counts + base + i) : 0u;
-        }
-        if (base < V && base + 32 >= V)   // the thread holding voxel V-1 closes the array
-            off[V] = run;
+    for (int i = 0; i < 32; ++i) {   // the counts again, from L1
+        s_off[tid * 33 + i] = run;
+        run += ((bits[0] >> i) & 1u) ? __ldg(counts + base + i) : 0u;
     }
+    if (base < V && base + 32 >= V)   // the thread holding voxel V-1 closes the array
+        off[V] = run;
     __syncthreads();
     const long long tbase = (long long)tile * SCAN_TILE;
 #pragma unroll
-    for (int j = 0; j < SCAN_TILE / (4 * SCAN_THREADS); ++j) {
-        const int v = 4 * tid + 4 * SCAN_THREADS * j;   // voxel within the tile
+    for (int j = 0; j < SCAN_TILE / (4 * THREADS); ++j) {
+        const int v = 4 * tid + 4 * THREADS * j;   // voxel within the tile
         const unsigned *r = s_off + (v >> 5) * 33 + (v & 31);
         const long long gv = tbase + v;
         if (gv + 4 <= V) {
@@ -504,19 +565,50 @@ __global__ void __launch_bounds__(SCAN_THREADS, 3) k_scan(const unsigned *__rest
                     off[gv + i] = r[i];
         }
     }
-    (void)tile_total;
 }
 
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
-                        const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st)
+                        const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st,
+                        bool dense)
 {
     const long long tiles = scan_tiles(g.V);
-    const size_t smem = (size_t)SCAN_THREADS * 33 * sizeof(unsigned);
-    cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!dense)
+        return launch_kernel(k_scan<256, 2, false>, dim3((unsigned)tiles), dim3(256), 0, st, counts, g.V, off, occ,
+                             tile_sum, desc, ctl);
+    constexpr int T = 512;
+    const size_t smem = (size_t)T * 33 * sizeof(unsigned);
+    cudaError_t e = cudaFuncSetAttribute(k_scan<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    return launch_kernel(k_scan, dim3((unsigned)tiles), dim3(SCAN_THREADS), smem, st, counts, g.V, off, occ, tile_sum,
-                         desc, ctl);
+    return launch_kernel(k_scan<T, 1, true>, dim3((unsigned)tiles), dim3(T), smem, st, counts, g.V, off, occ,
+                         tile_sum, desc, ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Completes a sparse offsets array (k_scan's sparse output): an entry the
+// scan did not write equals the nearest written one before it in its
+// occupancy word.  Thread per voxel; reads only written entries and writes
+// only the others, so threads never touch an entry another one writes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_offsets_fill(unsigned *__restrict__ off, const unsigned *__restrict__ occ,
+                                                      long long V)
+{
+    pdl_begin();
+    const long long v = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (v >= V)
+        return;
+    const unsigned bits = __ldg(occ + (v >> 5));
+    const unsigned written = 1u | bits | (bits << 1);
+    const int i = (int)(v & 31);
+    if ((written >> i) & 1u)
+        return;
+    const int j = 31 - __clz(written & ((1u << i) - 1u));   // i >= 1 here
+    off[v] = off[(v & ~31ll) + j];
+}
+
+cudaError_t launch_offsets_fill(unsigned *off, const unsigned *occ, long long V, cudaStream_t st)
+{
+    return launch_kernel(k_offsets_fill, dim3((unsigned)((V + 255) / 256)), dim3(256), 0, st, off, occ, V);
 }
 
 // ---------------------------------------------------------------------------

@@ -42,6 +42,7 @@ enum KernelId {
     K_MAXCOUNT,
     K_FIXED_SCATTER,
     K_FIXED_CORRESPOND,
+    K_OFFSETS_FILL,
     K_COUNT
 };
 const char *kernel_name(int k);
@@ -68,8 +69,13 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // occ must hold zeros (the previous build's scatter clears it).
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st);
+// dense: every off[v]; sparse: only off[v] and off[v + 1] of occupied voxels,
+// off[32 k] and off[V] (what the build and the searches read) -- the rest
+// is completed by launch_offsets_fill on the same occupancy bits.
 cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off, const unsigned *occ,
-                        const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st);
+                        const unsigned *tile_sum, unsigned long long *desc, const DevCtl *ctl, cudaStream_t st,
+                        bool dense);
+cudaError_t launch_offsets_fill(unsigned *off, const unsigned *occ, long long V, cudaStream_t st);
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
                               int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st);
 // The scatter also zeroes the tile totals and the occupancy buffer of the

@@ -131,7 +131,7 @@ extern "C" VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, in
         e = launch_histogram(reinterpret_cast<const float4 *>(target_xyzw), n, g, keys_out, counts, bcounts, occ,
                              tiles, ctl, st);
     if (e == cudaSuccess)
-        e = launch_scan(counts, g, offsets_out, occ, tiles, desc, ctl, st);
+        e = launch_scan(counts, g, offsets_out, occ, tiles, desc, ctl, st, true);
     unsigned err = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&err, &ctl->err, sizeof err, cudaMemcpyDeviceToHost, st);

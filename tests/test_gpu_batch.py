@@ -296,3 +296,38 @@ def test_more_pairs_than_the_shared_memory_tables_hold():
         assert_grid_equal(g, oracle.build_grid(og, p.target, L), p.target)
         _, R, _, _ = oracle.register(og, L, p.target, p.source, np.eye(4), max_iters=iters, eps=0.0)
         _assert_pose_close(T[k], R, _extent(p.target))
+
+
+def test_rebuild_reads_only_the_offsets_it_writes():
+    """As the single-grid test: a batch built and viewed (completed offsets)
+    on one set of targets, rebuilt on other targets with the same pair sizes
+    and searched without a view in between, finds the oracle's neighbours."""
+    from test_gpu_nns import _assert_nn_equal
+    ps = _small(n_pairs=6, n_min=500, n_max=5000, seed=19)
+    b, t, s, n_src = _batch(ps)
+    dims = [b.pair_grid(k)["dims"] for k in range(len(ps))]
+    ps2 = []
+    for p in ps:   # each target mirrored in x and y inside its own box: other voxels, same grid
+        tgt = p.target.copy()
+        lo, hi = tgt[:, :2].min(0), tgt[:, :2].max(0)
+        tgt[:, :2] = (lo + hi) - tgt[:, :2]
+        ps2.append(synth.Pair(p.name, tgt, p.source, p.T_gt, voxel_size=p.voxel_size,
+                              grid_divisions=p.grid_divisions))
+    b2, *_ = _batch(ps2)
+    assert [b2.pair_grid(k)["dims"] for k in range(len(ps))] == dims   # b's pooled arrays will be reused
+    tgt2, _, n_tgt, _, vs, dv = _pool(ps2)
+    b.build(torch.from_numpy(tgt2).cuda(), n_tgt, vs, dv)
+    T = np.stack([p.T_gt for p in ps2])
+    nn, d2 = b.correspond(s, n_src, torch.from_numpy(np.ascontiguousarray(T)).cuda())
+    nn, d2 = to_np(nn), to_np(d2)
+    at = 0
+    for k, p in enumerate(ps2):
+        m = p.source.shape[0]
+        og = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
+        ref = oracle.build_grid(og, p.target, L)
+        rnn, rd2, _ = oracle.correspond(og, ref, p.target, p.source, T[k])
+        _assert_nn_equal(nn[at:at + m], d2[at:at + m], rnn, rd2, p.target)
+        at += m
+    g = _pair_grid_np(b, 2)
+    og = oracle.fit_grid(ps2[2].target, ps2[2].voxel_size, ps2[2].grid_divisions)
+    assert np.array_equal(g["offsets"], oracle.build_grid(og, ps2[2].target, L)["off"])

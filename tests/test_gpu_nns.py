@@ -112,3 +112,33 @@ def test_nn_ties_go_to_smaller_index():
         grid, ref = oracle_grid_for(g, tgt, L)
         rnn, rd2, rfb = oracle.correspond(grid, ref, tgt, src, np.eye(4))
         assert np.array_equal(nn, rnn)
+
+
+def test_searches_read_only_the_offsets_the_build_writes(pairs):
+    """The build writes only part of the offsets array (occupied voxels, the
+    entries just past them, every 32nd one); a grid view completes it.  Fill
+    the array with one cloud's offsets, rebuild the same grid with another
+    cloud (other occupied voxels) and search without a view in between: any
+    read of an entry the second build did not write would see the first
+    cloud's offsets and miss the oracle's neighbours."""
+    p = pairs(2)
+    ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions)
+    rng = np.random.default_rng(12)
+    tgt_b = p.target[rng.random(p.target.shape[0]) < 0.6].copy()
+    tgt_b[:, 0] += np.float32(0.37 * g["voxel_size"])
+    tgt_b = np.ascontiguousarray(tgt_b)
+    ctx2, g2 = gpu_grid(tgt_b, L=10, origin=g["origin"], voxel_size=g["voxel_size"], dims=g["dims"])
+    assert not np.array_equal(g2["occupancy"], g["occupancy"])
+    # the first cloud's dense offsets in ctx2's array, then the second build
+    ctx2.build_grid(g["_target"])
+    ctx2.get_grid()
+    ctx2.build_grid(g2["_target"])
+    ctx2.dilate(10)
+    grid, ref = oracle_grid_for(g2, tgt_b, 10)
+    for T in (np.eye(4), p.T_gt):
+        nn, d2, nf = _gpu_correspond(ctx2, p.source, T)
+        rnn, rd2, rfb = oracle.correspond(grid, ref, tgt_b, p.source, T)
+        assert nf == int(rfb.sum())
+        _assert_nn_equal(nn, d2, rnn, rd2, tgt_b)
+    # and the completed array is the oracle's
+    assert np.array_equal(to_np(ctx2.get_grid()["offsets"]), ref["off"])
