@@ -166,8 +166,8 @@ def algorithmic_bytes(kernel: str, w: dict) -> float:
     V, N, M, occ = w["V"], w["N"], w["M"], w["occupied"]
     if kernel == "histogram":      # points in, keys out, one count RMW per occupied voxel
         return 16 * N + 4 * N + 8 * occ
-    if kernel == "scan":           # counts in, offsets + occupancy bits out
-        return 4 * V + 4 * (V + 1) + V / 8
+    if kernel == "scan":           # occupancy bits and occupied counts in; the offsets the searches read out
+        return V / 8 + 4 * occ + 4 * (2 * occ + V / 32 + 1)
     if kernel == "scatter":        # keys, points, offsets in; ids, voxel- and brick-ordered points out; RMW
         return 4 * N + 16 * N + 4 * N + 4 * N + 16 * N + 16 * N + 8 * occ
     if kernel == "brick_scan":     # brick counts in, brick offsets + list + ranges out
@@ -186,13 +186,15 @@ def algorithmic_bytes(kernel: str, w: dict) -> float:
 
 
 def _kernel_sha(kernel: str) -> str:
-    src = {"histogram": "vicp_grid.cu", "scan": "vicp_grid.cu", "scatter": "vicp_grid.cu",
-           "brick_scan": "vicp_grid.cu", "brick_boxes": "vicp_grid.cu", "dilate": "vicp_dilate.cu",
-           "correspond": "vicp_nns.cu", "fallback": "vicp_nns.cu", "reduce_solve": "vicp_solve.cu"}.get(kernel)
+    src = {"histogram": ("vicp_grid.cu",), "scan": ("vicp_grid.cu",), "scatter": ("vicp_grid.cu",),
+           "brick_scan": ("vicp_grid.cu",), "brick_boxes": ("vicp_grid.cu",),
+           "dilate": ("vicp_dilate.cu", "vicp_dilate.cuh"),
+           "correspond": ("vicp_nns.cu", "vicp_search.cuh"), "fallback": ("vicp_nns.cu", "vicp_search.cuh"),
+           "reduce_solve": ("vicp_solve.cu", "vicp_df.cuh")}.get(kernel)
     if not src:
         return ""
     h = hashlib.sha256()
-    for name in (src, "vicp_device.cuh"):
+    for name in src + ("vicp_device.cuh",):
         with open(os.path.join(ROOT, "paper_2512_04996_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

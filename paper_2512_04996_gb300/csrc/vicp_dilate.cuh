@@ -85,21 +85,28 @@ __device__ __forceinline__ unsigned row_word(unsigned left, unsigned right, int 
 // One axis of passes Y and Z on 32 output positions held in registers:
 // c[k] holds the words found at position k itself; `before` and `after` are
 // the best words from the halo beyond each end, already moved to positions 0
-// and 31.  Sweeping backward and then forward over the same array gives
-// min over i of stepn(c[i], |k - i|): a candidate reaching k through a
-// turning point j pays |i - j| + |k - j| >= |k - i|, so only the direct move
-// (j between them) can be the minimum.
+// and 31.  The result is min over i of stepn(c[i], |k - i|).  A forward and
+// a backward running minimum go through the array together, each in place
+// (two independent dependency chains of 31 steps instead of one of 62).
+// Where a chain meets a position the other has already passed, it also
+// carries that value on; every value either chain holds is the word of some
+// lattice path to its position, and a path that turns pays |i - j| +
+// |k - j| >= |k - i|, so the minimum at every position is still the direct
+// word from the nearest candidate -- the forward chain ends each position at
+// or below it for k >= 16, the backward chain for k < 16.
 template <unsigned INC_FWD, unsigned INC_BWD>
 __device__ __forceinline__ void sweep32(unsigned (&c)[32], unsigned before, unsigned after, unsigned lim)
 {
-    c[31] = min(c[31], after);
-#pragma unroll
-    for (int k = 30; k >= 0; --k)
-        c[k] = min(c[k], c[k + 1] >= lim ? NONE : c[k + 1] + INC_BWD);
     c[0] = min(c[0], before);
+    c[31] = min(c[31], after);
+    unsigned f = c[0], b = c[31];
 #pragma unroll
-    for (int k = 1; k < 32; ++k)
-        c[k] = min(c[k], c[k - 1] >= lim ? NONE : c[k - 1] + INC_FWD);
+    for (int i = 1; i < 32; ++i) {
+        c[i] = min(c[i], f >= lim ? NONE : f + INC_FWD);
+        f = c[i];
+        c[31 - i] = min(c[31 - i], b >= lim ? NONE : b + INC_BWD);
+        b = c[31 - i];
+    }
 }
 
 // ---------------------------------------------------------------------------

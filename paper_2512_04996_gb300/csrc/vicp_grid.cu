@@ -334,7 +334,7 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 // together) and scans them.  Its exclusive prefix is the sum of every
 // earlier tile's total, and the histogram has already written those totals,
 // so nothing ever has to be waited for: the CTA looks back over its
-// predecessors, one per thread and round, and adds their totals down to the
+// predecessors, 512 per round, and adds their totals down to the
 // nearest predecessor that has already published its inclusive prefix (any
 // one that has not is simply summed through).  A published prefix is one
 // 64-bit word [epoch:30 | flag:2 | value:32], so flag and value are read
@@ -353,6 +353,7 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 // is how k_offsets_fill completes the array when a caller asks for it.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long DESC_PREFIX = 2ull << 32;
+constexpr int LOOKBACK = 512;   // predecessors examined per lookback round
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
@@ -454,11 +455,14 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
 #pragma unroll
     for (int w = 0; w < WPT; ++w)
         bits[w] = base + 32 * w < V ? __ldg(occ + (base >> 5) + w) : 0u;
-    unsigned long long d0 = 0ull;
-    unsigned t0 = 0u;
-    if ((long long)tile - 1 - tid >= 0) {
-        d0 = ld_relaxed_u64(desc + (tile - 1 - tid));
-        t0 = __ldg(tile_sum + (tile - 1 - tid));
+    constexpr int CPT = LOOKBACK / THREADS;   // predecessors per thread and round
+    unsigned long long d0[CPT];
+    unsigned t0[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        const long long idx = (long long)tile - 1 - (c * THREADS + tid);
+        d0[c] = idx >= 0 ? ld_relaxed_u64(desc + idx) : 0ull;
+        t0[c] = idx >= 0 ? __ldg(tile_sum + idx) : 0u;
     }
     unsigned sum = 0u;
     if (DENSE) {
@@ -474,32 +478,45 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
     const unsigned thread_excl = block_excl_scan<WARPS>(sum, s_w, &tile_total);   // also orders s_epoch
     const unsigned long long tag = (unsigned long long)s_epoch << 34;
 
-    // lookback: THREADS predecessors per round, nearest first (thread i looks
-    // at tile - 1 - i); sum the totals before the nearest published prefix
+    // lookback: LOOKBACK predecessors per round, nearest first (thread i
+    // looks at tile - 1 - (c THREADS + i), c < CPT); sum the totals before the
+    // nearest published prefix
     unsigned excl = 0u;
-    for (long long look = (long long)tile - 1; look >= 0; look -= THREADS) {
-        const long long idx = look - tid;
-        bool pre = false;
-        unsigned v = 0u;
-        if (idx >= 0) {
-            unsigned long long d = d0;
-            unsigned t = t0;
-            if (look != (long long)tile - 1) {
-                d = ld_relaxed_u64(desc + idx);
-                t = __ldg(tile_sum + idx);
+    for (long long look = (long long)tile - 1; look >= 0; look -= LOOKBACK) {
+        bool pre[CPT];
+        unsigned v[CPT];
+        unsigned mine = LOOKBACK;   // this warp's nearest published prefix
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const long long idx = look - (c * THREADS + tid);
+            pre[c] = false;
+            v[c] = 0u;
+            if (idx >= 0) {
+                unsigned long long d = d0[c];
+                unsigned t = t0[c];
+                if (look != (long long)tile - 1) {
+                    d = ld_relaxed_u64(desc + idx);
+                    t = __ldg(tile_sum + idx);
+                }
+                pre[c] = (d >> 34) == (tag >> 34) && (d & DESC_PREFIX);
+                v[c] = pre[c] ? (unsigned)d : t;
             }
-            pre = (d >> 34) == (tag >> 34) && (d & DESC_PREFIX);
-            v = pre ? (unsigned)d : t;
+            const unsigned pm = __ballot_sync(FULL_MASK, pre[c]);
+            if (pm)
+                mine = min(mine, (unsigned)(c * THREADS + warp * 32 + __ffs(pm) - 1));
         }
-        const unsigned pm = __ballot_sync(FULL_MASK, pre);
         if (lane == 0)
-            s_first[warp] = pm ? (unsigned)(warp * 32 + __ffs(pm) - 1) : (unsigned)THREADS;
+            s_first[warp] = mine;
         __syncthreads();
-        unsigned first = THREADS;
+        unsigned first = LOOKBACK;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w)
             first = min(first, s_first[w]);
-        const unsigned ws = warp_sum_u32((unsigned)tid <= first ? v : 0u);
+        unsigned part = 0u;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            part += (unsigned)(c * THREADS + tid) <= first ? v[c] : 0u;
+        const unsigned ws = warp_sum_u32(part);
         if (lane == 0)
             s_sum[warp] = ws;
         __syncthreads();
@@ -509,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
             round += s_sum[w];
         excl += round;
         __syncthreads();   // s_first / s_sum are reused
-        if (first < THREADS)
+        if (first < LOOKBACK)
             break;
     }
     if (tid == 0)
