@@ -65,7 +65,8 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
                                                    unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
-                                                   unsigned *__restrict__ tile_sum, DevCtl *__restrict__ ctl)
+                                                   unsigned *__restrict__ tile_sum, unsigned *__restrict__ sb_left,
+                                                   DevCtl *__restrict__ ctl)
 {
     // A build follows the previous iteration's reduction and solve, whose
     // single-block tail leaves the GPU idle; the histogram touches none of
@@ -99,8 +100,12 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     if (key >= 0 && lane == __ffs(peers) - 1)
         atomicAdd(counts + key, (unsigned)__popc(peers));
     const unsigned bpeers = __match_any_sync(FULL_MASK, bk);
-    if (bk >= 0 && lane == __ffs(bpeers) - 1)
-        atomicAdd(bcounts + bk, (unsigned)__popc(bpeers));
+    if (bk >= 0 && lane == __ffs(bpeers) - 1) {
+        // the group that makes a brick non-empty counts it for its super-brick
+        // (the scatter finalises a super-brick's box when its last brick is done)
+        if (atomicAdd(bcounts + bk, (unsigned)__popc(bpeers)) == 0u && sb_left)
+            atomicAdd(sb_left + bk / SUPER_BRICKS, 1u);
+    }
     // occupancy bit of the voxel (one atomicOr per word and warp)
     const int word = key >= 0 ? (key >> 5) : -2;
     const unsigned wpeers = __match_any_sync(FULL_MASK, word);
@@ -115,11 +120,12 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
 }
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, DevCtl *ctl, cudaStream_t st)
+                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left, DevCtl *ctl,
+                             cudaStream_t st)
 {
     // occ must hold zeros: the caller clears it beforehand
     return launch_kernel(k_histogram, dim3((n + 255) / 256), dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ,
-                         tile_sum, ctl);
+                         tile_sum, sb_left, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -629,23 +635,82 @@ cudaError_t launch_offsets_fill(unsigned *off, const unsigned *occ, long long V,
 }
 
 // ---------------------------------------------------------------------------
+// Brick boxes as floats for the global search, finalised inside the scatter.
+// Each group of a warp's points in one brick merges its exact bounds into
+// the brick's order-preserving integer box (boxord) BEFORE it reserves its
+// slots with the atomicSub on the brick's count, with a fence between: so
+// the group whose atomicSub brings the count to zero knows every other
+// group's bounds are in, and writes the brick's float box (every stored
+// point lies inside it as float values, which is what the search's lower
+// bound needs), with the brick's point range [lo.w, hi.w) in the w fields
+// as integer bits.  It then merges the box into its super-brick's box in the
+// same way (sbord: min x, y, z, first slot, and the bitwise complements of
+// max x, y, z, last slot, so every word is an atomicMin from all ones) and
+// counts the super-brick's non-empty bricks down (sb_left, counted up by the
+// histogram); the last one writes the super-brick's float box with its
+// brick-slot range (bricks of a super-brick hold consecutive slots) and
+// resets sbord to all ones for the next build.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finish_brick(int slot, int bk, const unsigned *__restrict__ boxord,
+                                             const uint2 *__restrict__ range, float4 *__restrict__ box,
+                                             unsigned *__restrict__ sbord, unsigned *__restrict__ sb_left,
+                                             float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
+{
+    const uint4 lo = __ldcg(reinterpret_cast<const uint4 *>(boxord) + 2 * slot);
+    const uint4 hi = __ldcg(reinterpret_cast<const uint4 *>(boxord) + 2 * slot + 1);
+    const uint2 r = __ldg(range + slot);
+    box[2 * slot] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z),
+                                __uint_as_float(r.x));
+    box[2 * slot + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z),
+                                    __uint_as_float(r.y));
+    const int sb = bk / SUPER_BRICKS;
+    unsigned *o = sbord + 8 * sb;
+    atomicMin(o + 0, lo.x);
+    atomicMin(o + 1, lo.y);
+    atomicMin(o + 2, lo.z);
+    atomicMin(o + 3, (unsigned)slot);
+    atomicMin(o + 4, ~hi.x);
+    atomicMin(o + 5, ~hi.y);
+    atomicMin(o + 6, ~hi.z);
+    atomicMin(o + 7, ~(unsigned)slot);
+    __threadfence();
+    if (atomicSub(sb_left + sb, 1u) != 1u)
+        return;
+    __threadfence();
+    const uint4 sl = __ldcg(reinterpret_cast<const uint4 *>(o));
+    const uint4 sh = __ldcg(reinterpret_cast<const uint4 *>(o) + 1);
+    const int s = atomicAdd(&ctl->n_super, 1);
+    sb_box[2 * s] = make_float4(ordered_to_float(sl.x), ordered_to_float(sl.y), ordered_to_float(sl.z),
+                                __uint_as_float(sl.w));
+    sb_box[2 * s + 1] = make_float4(ordered_to_float(~sh.x), ordered_to_float(~sh.y), ordered_to_float(~sh.z),
+                                    __uint_as_float(~sh.w + 1u));
+    const uint4 ones = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    reinterpret_cast<uint4 *>(o)[0] = ones;
+    reinterpret_cast<uint4 *>(o)[1] = ones;
+}
+
+// ---------------------------------------------------------------------------
 // VDMA without locks: a warp's points of one voxel reserve their slots with
 // one atomicSub on the voxel's count (which the histogram left at the final
 // count), so the counts return to zero for the next build.  Slots fill from
 // the end of each segment; the order inside a segment is unspecified.  The
 // scatter also writes each point's coordinates and index next to its slot
-// (csr), does the same per brick (bpts, brick-ordered), and lists target
-// points outside an explicit grid.
+// (csr), does the same per brick (bpts, brick-ordered), finalises the brick
+// and super-brick boxes (above), and lists target points outside an
+// explicit grid.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts, const int *__restrict__ keys, int n,
                                                  GridGeom g, const unsigned *__restrict__ off,
                                                  unsigned *__restrict__ counts, const unsigned *__restrict__ boff,
                                                  unsigned *__restrict__ bcounts, const int *__restrict__ bslot,
-                                                 unsigned *__restrict__ boxord, int *__restrict__ ids,
-                                                 float4 *__restrict__ csr, float4 *__restrict__ bpts,
-                                                 int *__restrict__ outside, unsigned *__restrict__ tile_sum,
-                                                 int n_tiles, unsigned *__restrict__ occ_next,
-                                                 long long occ_next_words, DevCtl *__restrict__ ctl)
+                                                 unsigned *__restrict__ boxord, const uint2 *__restrict__ range,
+                                                 float4 *__restrict__ box, unsigned *__restrict__ sbord,
+                                                 unsigned *__restrict__ sb_left, float4 *__restrict__ sb_box,
+                                                 int *__restrict__ ids, float4 *__restrict__ csr,
+                                                 float4 *__restrict__ bpts, int *__restrict__ outside,
+                                                 unsigned *__restrict__ tile_sum, int n_tiles,
+                                                 unsigned *__restrict__ occ_next, long long occ_next_words,
+                                                 DevCtl *__restrict__ ctl)
 {
     pdl_begin();
     // the scan is done with the tile totals: zero them for the next build,
@@ -694,7 +759,7 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
     }
     // brick segment, and the brick's exact box: the group's min and max of
     // each coordinate (order-preserving unsigned images of the floats), merged
-    // by the group leader with one atomic per bound
+    // by the group leader with one atomic per bound before it reserves slots
     {
         const unsigned peers = __match_any_sync(FULL_MASK, bk);
         const int leader = __ffs(peers) - 1;
@@ -706,14 +771,21 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
                        mxz = __reduce_max_sync(peers, oz);
         unsigned old = 0u;
         if (lane == leader && bk >= 0) {
-            old = atomicSub(bcounts + bk, (unsigned)__popc(peers));
-            unsigned *b = boxord + 8 * __ldg(bslot + bk);
+            const int slot = __ldg(bslot + bk);
+            unsigned *b = boxord + 8 * slot;
             atomicMin(b + 0, mnx);
             atomicMin(b + 1, mny);
             atomicMin(b + 2, mnz);
             atomicMax(b + 4, mxx);
             atomicMax(b + 5, mxy);
             atomicMax(b + 6, mxz);
+            __threadfence();
+            const unsigned cnt = (unsigned)__popc(peers);
+            old = atomicSub(bcounts + bk, cnt);
+            if (old == cnt) {   // the brick's last points: its box is complete
+                __threadfence();
+                finish_brick(slot, bk, boxord, range, box, sbord, sb_left, sb_box, ctl);
+            }
         }
         old = __shfl_sync(FULL_MASK, old, leader);
         if (bk >= 0) {
@@ -728,87 +800,13 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
 
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
-                           unsigned *boxord, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
+                           unsigned *boxord, const uint2 *range, float4 *box, unsigned *sbord, unsigned *sb_left,
+                           float4 *sb_box, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
                            unsigned *occ_next, long long occ_next_words, DevCtl *ctl, cudaStream_t st)
 {
     return launch_kernel(k_scatter, dim3((n + 255) / 256), dim3(256), 0, st, pts, keys, n, g, off, counts, boff,
-                         bcounts, bslot, boxord, ids, csr, bpts, outside, tile_sum, (int)scan_tiles(g.V), occ_next,
-                         occ_next_words, ctl);
-}
-
-// ---------------------------------------------------------------------------
-// Brick boxes as floats: the scatter left each non-empty brick's exact bounds
-// as order-preserving unsigned integers; every stored point of the brick lies
-// inside the box as float values, which is what the global search's lower
-// bound needs.  The w fields carry the brick's point range [lo.w, hi.w) (as
-// integer bits), so one pair of loads gives the search both.  The thread of
-// the first brick of each super-brick (bricks of a super-brick hold
-// consecutive slots) also records the union of its bricks' boxes, with the
-// super-brick's brick-slot range in the w fields.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_brick_boxes(const uint4 *__restrict__ boxord, const int *__restrict__ list,
-                                                     const uint2 *__restrict__ range, float4 *__restrict__ box,
-                                                     float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
-{
-    pdl_begin();
-    const int nb = ctl->n_bricks;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
-        const uint4 lo = boxord[2 * k], hi = boxord[2 * k + 1];
-        const uint2 r = range[k];
-        box[2 * k] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z),
-                                 __uint_as_float(r.x));
-        box[2 * k + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z),
-                                     __uint_as_float(r.y));
-        const int sb = __ldg(list + k) / SUPER_BRICKS;
-        if (k == 0 || __ldg(list + k - 1) / SUPER_BRICKS != sb) {
-            // union over the super-brick's bricks (at most 64, consecutive
-            // slots), eight slots per round with their loads in flight together
-            uint4 l = lo, h = hi;
-            int e = k + 1;
-            bool more = true;
-            while (more) {
-                int key[8];
-                uint4 bl[8], bh[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    key[u] = e + u < nb ? __ldg(list + e + u) : -1;
-                    if (key[u] >= 0 && key[u] / SUPER_BRICKS == sb) {
-                        bl[u] = boxord[2 * (e + u)];
-                        bh[u] = boxord[2 * (e + u) + 1];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (more && key[u] >= 0 && key[u] / SUPER_BRICKS == sb) {
-                        l = make_uint4(min(l.x, bl[u].x), min(l.y, bl[u].y), min(l.z, bl[u].z), 0u);
-                        h = make_uint4(max(h.x, bh[u].x), max(h.y, bh[u].y), max(h.z, bh[u].z), 0u);
-                    } else {
-                        more = false;
-                    }
-                }
-                if (more)
-                    e += 8;
-            }
-            // e: the first slot past the super-brick
-            while (e < nb && __ldg(list + e) / SUPER_BRICKS == sb)
-                ++e;
-            const int slot = atomicAdd(&ctl->n_super, 1);
-            sb_box[2 * slot] = make_float4(ordered_to_float(l.x), ordered_to_float(l.y), ordered_to_float(l.z),
-                                           __uint_as_float((unsigned)k));
-            sb_box[2 * slot + 1] = make_float4(ordered_to_float(h.x), ordered_to_float(h.y), ordered_to_float(h.z),
-                                               __uint_as_float((unsigned)e));
-        }
-    }
-}
-
-cudaError_t launch_brick_boxes(const uint4 *boxord, const int *list, const uint2 *range, float4 *box, float4 *sb_box,
-                               DevCtl *ctl, const GridGeom &g, cudaStream_t st)
-{
-    const int nbt = brick_slots(g);
-    int blocks = (nbt + 255) / 256;
-    if (blocks > 152 * 2)
-        blocks = 152 * 2;
-    return launch_kernel(k_brick_boxes, dim3(blocks), dim3(256), 0, st, boxord, list, range, box, sb_box, ctl);
+                         bcounts, bslot, boxord, range, box, sbord, sb_left, sb_box, ids, csr, bpts, outside, tile_sum,
+                         (int)scan_tiles(g.V), occ_next, occ_next_words, ctl);
 }
 
 // ---------------------------------------------------------------------------

@@ -59,8 +59,8 @@ def test_host_only_helpers(lib):
     lib.vicp_kernel_name.restype = C.c_char_p
     lib.vicp_kernel_name.argtypes = [C.c_int32]
     names = [lib.vicp_kernel_name(i).decode() for i in range(lib.vicp_kernel_count())]
-    assert {"histogram", "scan", "brick_scan", "scatter", "brick_boxes", "dilate", "correspond", "fallback",
-            "reduce_solve"} <= set(names)
+    assert {"histogram", "scan", "brick_scan", "scatter", "dilate", "correspond", "fallback",
+            "reduce_solve", "offsets_fill"} <= set(names)
 
 
 def test_argument_errors_launch_nothing(lib):
