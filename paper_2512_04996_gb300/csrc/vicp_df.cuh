@@ -223,9 +223,10 @@ __device__ __forceinline__ void accumulate_corr(dfl (&acc)[N_SUMS], float3 s, fl
 //    (lane 4a + b: entry (a, b)).
 // Returns false, leaving the pose untouched, when the geometry is degenerate
 // (rank(H) < 2).  rmse = the RMSE of the m correspondences, on every lane.
-// Every lane of the warp must call it.
+// Every lane of the warp must call it.  Not inlined: one copy of its code
+// per kernel, which the single-pair kernel fetches ahead of the real solve.
 // ---------------------------------------------------------------------------
-static __device__ bool solve_update(const dfl *s_tot, int m, float3 cf, double *pose, double &rmse)
+static __device__ __noinline__ bool solve_update(const dfl *s_tot, int m, float3 cf, double *pose, double &rmse)
 {
     const int lane = threadIdx.x & 31;
     // the pose column this lane composes, loaded first

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
         return;
     __shared__ PoseF sp;
     __shared__ float s_hi[RED_THREADS / 32][REDUCE_VALUES], s_lo[RED_THREADS / 32][REDUCE_VALUES];
-    __shared__ int s_last;
+    __shared__ int s_last;   // this block's ticket
     load_pose_f_block(pose, sp);
     const PoseF P = sp;
     dfl acc[REDUCE_VALUES];
@@ -104,9 +104,30 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_solve(const float4 *__re
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        s_last = atomicAdd(&ctl->red_done, 1u) == gridDim.x - 1;
+        s_last = (int)atomicAdd(&ctl->red_done, 1u);
     __syncthreads();
-    if (!s_last)
+    if (s_last == 0 && gridDim.x > 2 && warp == 0) {
+        // The first block to finish runs the solve once on fixed sums of a
+        // well-posed problem, writing only its own shared memory: the solve
+        // runs once per iteration right after the step's L2 flush, so its
+        // instructions would otherwise come from DRAM one fetch after the
+        // other on the last block's critical path; this way they are in L2
+        // by the time the last block needs them.
+        __shared__ dfl s_warm[N_SUMS];
+        __shared__ double s_wpose[16];
+        if (lane < N_SUMS) {
+            // sums of 8 points: zero centroids, H = diag(4, 2, 1) + 1/2 in (0, 1), residual 1
+            const float h = lane == 6 ? 4.0f : (lane == 10 ? 2.0f : (lane == 14 ? 1.0f : (lane == 7 ? 0.5f : 0.0f)));
+            s_warm[lane] = dfl{lane == 15 ? 1.0f : h, 0.0f};
+        }
+        if (lane < 16)
+            s_wpose[lane] = (lane % 5) == 0 ? 1.0 : 0.0;
+        __syncwarp();
+        double r;
+        solve_update(s_warm, 8, cf, s_wpose, r);
+        return;
+    }
+    if (s_last != (int)gridDim.x - 1)
         return;
     __threadfence();
 
