@@ -225,7 +225,11 @@ VICP_API vicp_status vicp_register(vicp_ctx *ctx, const float *src_xyzw, int32_t
                           int32_t *iters_out, double *rmse_out);
 
 /* vicp_register with both clouds in host memory: copies them to
- * context-owned device buffers on the context's stream first. */
+ * context-owned device buffers -- the target on the context's stream before
+ * the grid build, the source on an internal copy stream while the grid is
+ * built (ordered after all work issued earlier on the context's stream; the
+ * first search waits for it).  Host buffers should be pinned for the copies
+ * to run asynchronously. */
 VICP_API vicp_status vicp_register_host(vicp_ctx *ctx, const float *src_xyzw_host, int32_t n_src,
                                const float *tgt_xyzw_host, int32_t n_tgt, double pose_host[16],
                                int32_t *iters_out, double *rmse_out);

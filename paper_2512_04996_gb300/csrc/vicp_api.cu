@@ -41,6 +41,8 @@ struct vicp_ctx {
     // the dilation), so everything issued later sees its results.
     cudaStream_t side = nullptr;
     cudaEvent_t ev_hist = nullptr, ev_nns = nullptr, ev_dil = nullptr;
+    cudaStream_t copy = nullptr;                          // host-input source copy, beside the build
+    cudaEvent_t ev_copy_go = nullptr, ev_src = nullptr;
     int device = 0;
     int sms = 152;
     std::string last_error;
@@ -511,11 +513,18 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     return VICP_OK;
 }
 
+// src_ready: an event the source's producer recorded (null: the source is
+// ready in stream order); the first search waits for it, the build does not.
 vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
-                         double pose_host[16], int32_t *iters_out, double *rmse_out)
+                         double pose_host[16], int32_t *iters_out, double *rmse_out, cudaEvent_t src_ready = nullptr)
 {
     TRY(build(c, tgt, n));
     TRY(dilate(c, -1));
+    if (src_ready) {
+        const cudaError_t w = cudaStreamWaitEvent(c->stream, src_ready, 0);
+        if (w != cudaSuccess)
+            return cuda_fail(c, w, "stream wait");
+    }
     double *pose = (double *)c->pose.p;
     cudaError_t e = cudaMemcpyAsync(pose, pose_host, 16 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess)
@@ -611,7 +620,10 @@ vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_al
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_hist, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_nns, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_dil, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_dil, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_copy_go, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_src, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         vicp_destroy(c);
         return VICP_ERR_CUDA;
@@ -661,11 +673,15 @@ void vicp_destroy(vicp_ctx *c)
     }
     for (cudaEvent_t e : c->event_pool)
         cudaEventDestroy(e);
-    for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil})
+    if (c->copy)
+        cudaStreamSynchronize(c->copy);
+    for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src})
         if (e)
             cudaEventDestroy(e);
     if (c->side)
         cudaStreamDestroy(c->side);
+    if (c->copy)
+        cudaStreamDestroy(c->copy);
     delete c;
 }
 
@@ -767,13 +783,23 @@ vicp_status vicp_register_host(vicp_ctx *c, const float *src_host, int32_t n_src
         TRY(buf_alloc(c, c->hsrc, sb, "source copy"));
     if (c->htgt.bytes < tb)
         TRY(buf_alloc(c, c->htgt, tb, "target copy"));
-    cudaError_t e = cudaMemcpyAsync(c->hsrc.p, src_host, sb, cudaMemcpyHostToDevice, c->stream);
+    // The target on the context's stream (the build needs it first); the
+    // source on the copy stream, after everything issued so far on the
+    // context's stream (earlier searches may still read the buffer), so it
+    // travels while the grid is built; the first search waits for it.
+    cudaError_t e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->stream);
+        e = cudaEventRecord(c->ev_copy_go, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->copy, c->ev_copy_go, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->hsrc.p, src_host, sb, cudaMemcpyHostToDevice, c->copy);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->ev_src, c->copy);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "host-to-device copy of the clouds");
     return registration(c, (const float4 *)c->hsrc.p, n_src, (const float *)c->htgt.p, n_tgt, pose_host,
-                        iters_out, rmse_out);
+                        iters_out, rmse_out, c->ev_src);
 }
 
 vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
