@@ -168,12 +168,10 @@ def algorithmic_bytes(kernel: str, w: dict) -> float:
         return 16 * N + 4 * N + 8 * occ
     if kernel == "scan":           # occupancy bits and occupied counts in; the offsets the searches read out
         return V / 8 + 4 * occ + 4 * (2 * occ + V / 32 + 1)
-    if kernel == "scatter":        # keys, points, offsets in; ids, voxel- and brick-ordered points out; RMW
-        return 4 * N + 16 * N + 4 * N + 4 * N + 16 * N + 16 * N + 8 * occ
+    if kernel == "scatter":        # keys, points, offsets in; ids, voxel- and brick-ordered points, brick boxes out; RMW
+        return 4 * N + 16 * N + 4 * N + 4 * N + 16 * N + 16 * N + 8 * occ + 32 * w["nonempty_bricks"]
     if kernel == "brick_scan":     # brick counts in, brick offsets + list + ranges out
         return 4 * w["bricks"] + 4 * (w["bricks"] + 1) + 12 * w["nonempty_bricks"]
-    if kernel == "brick_boxes":    # brick-ordered points in, boxes out
-        return 16 * N + 32 * w["nonempty_bricks"]
     if kernel == "dilate":         # occupancy bits in, root + ring out
         return V / 8 + 5 * V
     if kernel == "correspond":     # per query: point, root, offset pair, nn+d2; candidates 16 B each
@@ -187,7 +185,7 @@ def algorithmic_bytes(kernel: str, w: dict) -> float:
 
 def _kernel_sha(kernel: str) -> str:
     src = {"histogram": ("vicp_grid.cu",), "scan": ("vicp_grid.cu",), "scatter": ("vicp_grid.cu",),
-           "brick_scan": ("vicp_grid.cu",), "brick_boxes": ("vicp_grid.cu",),
+           "brick_scan": ("vicp_grid.cu",),
            "dilate": ("vicp_dilate.cu", "vicp_dilate.cuh"),
            "correspond": ("vicp_nns.cu", "vicp_search.cuh"), "fallback": ("vicp_nns.cu", "vicp_search.cuh"),
            "reduce_solve": ("vicp_solve.cu", "vicp_df.cuh")}.get(kernel)
