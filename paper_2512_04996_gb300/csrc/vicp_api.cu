@@ -65,7 +65,8 @@ struct vicp_ctx {
     bool off_dense = false;   // the build writes sparse offsets; vicp_get_grid completes them
     long long cap_V = -1;
     // brick level (V / 512)
-    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, boxord, sb_box, sbord, sb_left;
+    Buf bcounts, boff, brick_list, brick_range, brick_box, bslot, sb_box, sb_left;
+    Buf boxk[2];      // brick bounds by key: the current build's, and the next build's (kept all ones)
     long long cap_bricks = -1;
     // N-sized
     Buf keys, ids, csr, bpts, outside;
@@ -244,12 +245,13 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_alloc(c, c->brick_range, (size_t)n_bricks * 8, "brick ranges"));
         TRY(buf_alloc(c, c->brick_box, (size_t)n_bricks * 32, "brick boxes"));
         TRY(buf_alloc(c, c->bslot, (size_t)n_bricks * 4, "brick slots"));
-        TRY(buf_alloc(c, c->boxord, (size_t)n_bricks * 32, "brick box bounds"));
+        for (Buf &b : c->boxk) {
+            TRY(buf_alloc(c, b, (size_t)n_bricks * 32, "brick bounds"));
+            const cudaError_t e = cudaMemsetAsync(b.p, 0xff, b.bytes, c->stream);   // all ones between builds
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "brick bounds");
+        }
         TRY(buf_alloc(c, c->sb_box, (size_t)(n_bricks / SUPER_BRICKS + 1) * 32, "super-brick boxes"));
-        TRY(buf_alloc(c, c->sbord, (size_t)(n_bricks / SUPER_BRICKS) * 32, "super-brick box bounds"));
-        cudaError_t e = cudaMemsetAsync(c->sbord.p, 0xff, c->sbord.bytes, c->stream);   // all ones between builds
-        if (e != cudaSuccess)
-            return cuda_fail(c, e, "super-brick box bounds");
         TRY(buf_alloc(c, c->sb_left, (size_t)(n_bricks / SUPER_BRICKS) * 4, "super-brick counts"));
         TRY(buf_zero(c, c->sb_left, "zero super-brick counts"));   // kept at zero between builds
         c->cap_bricks = n_bricks;
@@ -428,7 +430,8 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     Buf &occ_next = c->occ[c->occ_cur ^ 1];
     TRY(launch(c, K_HISTOGRAM, [&] {
         return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, occ,
-                                (unsigned *)c->tile_sum.p, (unsigned *)c->sb_left.p, d, c->stream);
+                                (unsigned *)c->tile_sum.p, (unsigned *)c->sb_left.p,
+                                (unsigned *)c->boxk[c->occ_cur].p, d, c->stream);
     }));
     cudaError_t ev = cudaEventRecord(c->ev_hist, c->stream);   // the dilation may start from here
     if (ev != cudaSuccess)
@@ -440,13 +443,14 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     c->off_dense = false;
     TRY(launch(c, K_BRICK_SCAN, [&] {
         return launch_brick_scan((const unsigned *)c->bcounts.p, g, (unsigned *)c->boff.p, (int *)c->brick_list.p,
-                                 (uint2 *)c->brick_range.p, (int *)c->bslot.p, (uint4 *)c->boxord.p, d, c->stream);
+                                 (uint2 *)c->brick_range.p, (int *)c->bslot.p, d, c->stream);
     }));
     TRY(launch(c, K_SCATTER, [&] {
         return launch_scatter(tgt, (const int *)c->keys.p, n, g, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
                               (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (const int *)c->bslot.p,
-                              (unsigned *)c->boxord.p, (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p,
-                              (unsigned *)c->sbord.p, (unsigned *)c->sb_left.p, (float4 *)c->sb_box.p,
+                              (const unsigned *)c->boxk[c->occ_cur].p, (unsigned *)c->boxk[c->occ_cur ^ 1].p,
+                              (long long)(c->boxk[c->occ_cur ^ 1].bytes / 4), (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p, (unsigned *)c->sb_left.p,
+                              (float4 *)c->sb_box.p,
                               (int *)c->ids.p, (float4 *)c->csr.p, (float4 *)c->bpts.p,
                               (int *)c->outside.p, (unsigned *)c->tile_sum.p, (unsigned *)occ_next.p,
                               (long long)(occ_next.bytes / 4), d, c->stream);
@@ -661,7 +665,7 @@ void vicp_destroy(vicp_ctx *c)
     Buf *all[] = {&c->counts,  &c->off,      &c->root,       &c->ring,       &c->occ[0],    &c->occ[1], &c->desc, &c->tile_sum,
                   &c->inter,       &c->uflag,      &c->zdirty,
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
-                  &c->boxord,  &c->sb_box,  &c->sbord,      &c->sb_left,    &c->keys,
+                  &c->boxk[0], &c->boxk[1], &c->sb_box,     &c->sb_left,    &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
                   &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt,    &c->fslots,   &c->fcount,   &c->fover};

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
                                                    unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
                                                    unsigned *__restrict__ tile_sum, unsigned *__restrict__ sb_left,
-                                                   DevCtl *__restrict__ ctl)
+                                                   unsigned *__restrict__ boxk, DevCtl *__restrict__ ctl)
 {
     // A build follows the previous iteration's reduction and solve, whose
     // single-block tail leaves the GPU idle; the histogram touches none of
@@ -84,8 +84,9 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     int key = -2, bk = -2;   // lanes past the end match only each other and add nothing
+    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (j < n) {
-        const float4 q = __ldg(pts + j);
+        q = __ldg(pts + j);
         int ix, iy, iz;
         if (voxel_coords(g, q.x, q.y, q.z, ix, iy, iz)) {
             key = ix + g.nx * (iy + g.ny * iz);
@@ -100,11 +101,28 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     if (key >= 0 && lane == __ffs(peers) - 1)
         atomicAdd(counts + key, (unsigned)__popc(peers));
     const unsigned bpeers = __match_any_sync(FULL_MASK, bk);
+    // the brick's exact bounds: the group's min and max of each coordinate
+    // (order-preserving unsigned images of the floats; maxima as their
+    // complements, so every word is an atomicMin from all ones)
+    const unsigned ox = float_to_ordered(q.x), oy = float_to_ordered(q.y), oz = float_to_ordered(q.z);
+    const unsigned mnx = __reduce_min_sync(bpeers, ox), mny = __reduce_min_sync(bpeers, oy),
+                   mnz = __reduce_min_sync(bpeers, oz);
+    const unsigned cmx = __reduce_min_sync(bpeers, ~ox), cmy = __reduce_min_sync(bpeers, ~oy),
+                   cmz = __reduce_min_sync(bpeers, ~oz);
     if (bk >= 0 && lane == __ffs(bpeers) - 1) {
         // the group that makes a brick non-empty counts it for its super-brick
-        // (the scatter finalises a super-brick's box when its last brick is done)
+        // (the scatter writes a super-brick's box when its last brick is done)
         if (atomicAdd(bcounts + bk, (unsigned)__popc(bpeers)) == 0u && sb_left)
             atomicAdd(sb_left + bk / SUPER_BRICKS, 1u);
+        if (boxk) {
+            unsigned *b = boxk + 8 * bk;
+            atomicMin(b + 0, mnx);
+            atomicMin(b + 1, mny);
+            atomicMin(b + 2, mnz);
+            atomicMin(b + 4, cmx);
+            atomicMin(b + 5, cmy);
+            atomicMin(b + 6, cmz);
+        }
     }
     // occupancy bit of the voxel (one atomicOr per word and warp)
     const int word = key >= 0 ? (key >> 5) : -2;
@@ -120,18 +138,18 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
 }
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left, DevCtl *ctl,
-                             cudaStream_t st)
+                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
+                             unsigned *boxk, DevCtl *ctl, cudaStream_t st)
 {
     // occ must hold zeros: the caller clears it beforehand
     return launch_kernel(k_histogram, dim3((n + 255) / 256), dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ,
-                         tile_sum, sb_left, ctl);
+                         tile_sum, sb_left, boxk, ctl);
 }
 
 // ---------------------------------------------------------------------------
 // Brick offsets: one CTA scans the per-brick counts (few: V / 512) into
 // brick offsets, and lists the non-empty bricks in ascending order with their
-// point ranges and slot numbers; it also resets each listed brick's box.  The
+// point ranges and slot numbers.  The
 // count and the non-empty flag are scanned together as one 64-bit value
 // (flag count in the high half).  The counts are staged in shared memory with
 // coalesced loads; each thread sums a contiguous run of bricks, one
@@ -149,7 +167,7 @@ constexpr int BS_CHUNK = 24576;   // bricks staged in shared memory per pass (96
 __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__restrict__ bcounts, int nbt,
                                                            unsigned *__restrict__ boff, int *__restrict__ list,
                                                            uint2 *__restrict__ range, int *__restrict__ bslot,
-                                                           uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
+                                                           DevCtl *__restrict__ ctl)
 {
     pdl_begin();
     extern __shared__ unsigned s_c[];   // [BS_CHUNK]
@@ -210,8 +228,6 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_scan(const unsigned *__res
                 list[slot] = bi;
                 range[slot] = make_uint2(start, start + c);
                 bslot[bi] = slot;
-                boxord[2 * slot] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);   // min
-                boxord[2 * slot + 1] = make_uint4(0u, 0u, 0u, 0u);                          // max
             }
             run += brick_pair(c);
         }
@@ -251,7 +267,7 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 __global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned *__restrict__ bcounts, int nbt,
                                                                  unsigned *__restrict__ boff, int *__restrict__ list,
                                                                  uint2 *__restrict__ range, int *__restrict__ bslot,
-                                                                 uint4 *__restrict__ boxord, DevCtl *__restrict__ ctl)
+                                                                 DevCtl *__restrict__ ctl)
 {
     pdl_begin();
     __shared__ unsigned long long s_w[BM_THREADS / 32];
@@ -305,8 +321,6 @@ __global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned 
             list[slot] = i;
             range[slot] = make_uint2(start, start + c);
             bslot[i] = slot;
-            boxord[2 * slot] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);   // min
-            boxord[2 * slot + 1] = make_uint4(0u, 0u, 0u, 0u);                          // max
         }
         if (i == nbt - 1) {
             boff[nbt] = (unsigned)(run + pc);
@@ -316,19 +330,19 @@ __global__ void __launch_bounds__(BM_THREADS) k_brick_scan_multi(const unsigned 
 }
 
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
-                              int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st)
+                              int *bslot, DevCtl *ctl, cudaStream_t st)
 {
     const int nbt = brick_slots(g);
     if (nbt <= BM_MAX_BRICKS) {
         return launch_kernel(k_brick_scan_multi, dim3((nbt + BM_THREADS - 1) / BM_THREADS), dim3(BM_THREADS), 0, st,
-                             bcounts, nbt, boff, list, range, bslot, boxord, ctl);
+                             bcounts, nbt, boff, list, range, bslot, ctl);
     }
     const size_t smem = BS_CHUNK * sizeof(unsigned);
     cudaError_t e = cudaFuncSetAttribute(k_brick_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     return launch_kernel(k_brick_scan, dim3(1), dim3(BS_THREADS), smem, st, bcounts, nbt, boff, list, range, bslot,
-                         boxord, ctl);
+                         ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -635,58 +649,75 @@ cudaError_t launch_offsets_fill(unsigned *off, const unsigned *occ, long long V,
 }
 
 // ---------------------------------------------------------------------------
-// Brick boxes as floats for the global search, finalised inside the scatter.
-// Each group of a warp's points in one brick merges its exact bounds into
-// the brick's order-preserving integer box (boxord) BEFORE it reserves its
-// slots with the atomicSub on the brick's count, with a fence between: so
-// the group whose atomicSub brings the count to zero knows every other
-// group's bounds are in, and writes the brick's float box (every stored
-// point lies inside it as float values, which is what the search's lower
-// bound needs), with the brick's point range [lo.w, hi.w) in the w fields
-// as integer bits.  It then merges the box into its super-brick's box in the
-// same way (sbord: min x, y, z, first slot, and the bitwise complements of
-// max x, y, z, last slot, so every word is an atomicMin from all ones) and
-// counts the super-brick's non-empty bricks down (sb_left, counted up by the
-// histogram); the last one writes the super-brick's float box with its
-// brick-slot range (bricks of a super-brick hold consecutive slots) and
-// resets sbord to all ones for the next build.
+// Brick boxes as floats for the global search, written inside the scatter.
+// The histogram has merged every brick's exact bounds into boxk (by brick
+// key: min x, y, z and the complements of max x, y, z, each an atomicMin
+// from all ones), so they are complete when the scatter runs.  The group
+// whose slot reservation brings a brick's count to zero writes the brick's
+// float box (every stored point lies inside it as float values, which is
+// what the search's lower bound needs), with the brick's point range
+// [lo.w, hi.w) in the w fields as integer bits, then counts its super-brick
+// down (sb_left, counted up by the histogram); the last brick's warp writes
+// the super-brick's union box with its brick-slot range (bricks of a
+// super-brick hold consecutive slots).  Everything read here was written by
+// an earlier kernel, so no fence is needed.  The scatter also resets the
+// other boxk buffer, which the next build's histogram fills.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void finish_brick(int slot, int bk, const unsigned *__restrict__ boxord,
-                                             const uint2 *__restrict__ range, float4 *__restrict__ box,
-                                             unsigned *__restrict__ sbord, unsigned *__restrict__ sb_left,
-                                             float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
+__device__ __forceinline__ void finish_brick(int slot, int bk, const unsigned *__restrict__ boxk,
+                                             const uint2 *__restrict__ range, float4 *__restrict__ box)
 {
-    const uint4 lo = __ldcg(reinterpret_cast<const uint4 *>(boxord) + 2 * slot);
-    const uint4 hi = __ldcg(reinterpret_cast<const uint4 *>(boxord) + 2 * slot + 1);
+    const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(boxk) + 2 * bk);
+    const uint4 hi = __ldg(reinterpret_cast<const uint4 *>(boxk) + 2 * bk + 1);
     const uint2 r = __ldg(range + slot);
     box[2 * slot] = make_float4(ordered_to_float(lo.x), ordered_to_float(lo.y), ordered_to_float(lo.z),
                                 __uint_as_float(r.x));
-    box[2 * slot + 1] = make_float4(ordered_to_float(hi.x), ordered_to_float(hi.y), ordered_to_float(hi.z),
+    box[2 * slot + 1] = make_float4(ordered_to_float(~hi.x), ordered_to_float(~hi.y), ordered_to_float(~hi.z),
                                     __uint_as_float(r.y));
-    const int sb = bk / SUPER_BRICKS;
-    unsigned *o = sbord + 8 * sb;
-    atomicMin(o + 0, lo.x);
-    atomicMin(o + 1, lo.y);
-    atomicMin(o + 2, lo.z);
-    atomicMin(o + 3, (unsigned)slot);
-    atomicMin(o + 4, ~hi.x);
-    atomicMin(o + 5, ~hi.y);
-    atomicMin(o + 6, ~hi.z);
-    atomicMin(o + 7, ~(unsigned)slot);
-    __threadfence();
-    if (atomicSub(sb_left + sb, 1u) != 1u)
-        return;
-    __threadfence();
-    const uint4 sl = __ldcg(reinterpret_cast<const uint4 *>(o));
-    const uint4 sh = __ldcg(reinterpret_cast<const uint4 *>(o) + 1);
-    const int s = atomicAdd(&ctl->n_super, 1);
-    sb_box[2 * s] = make_float4(ordered_to_float(sl.x), ordered_to_float(sl.y), ordered_to_float(sl.z),
-                                __uint_as_float(sl.w));
-    sb_box[2 * s + 1] = make_float4(ordered_to_float(~sh.x), ordered_to_float(~sh.y), ordered_to_float(~sh.z),
-                                    __uint_as_float(~sh.w + 1u));
-    const uint4 ones = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-    reinterpret_cast<uint4 *>(o)[0] = ones;
-    reinterpret_cast<uint4 *>(o)[1] = ones;
+}
+
+// Super-brick sb's box by the whole warp: its bricks' bounds (two brick keys
+// per lane; a brick is non-empty when its offsets differ), their union, and
+// the slot range from the first non-empty brick's slot and their number.
+__device__ __forceinline__ void finish_super(int sb, const unsigned *__restrict__ boxk,
+                                             const unsigned *__restrict__ boff, const int *__restrict__ bslot,
+                                             float4 *__restrict__ sb_box, DevCtl *__restrict__ ctl)
+{
+    static_assert(SUPER_BRICKS == 64, "two bricks per lane");
+    const int lane = threadIdx.x & 31;
+    unsigned lx = 0xffffffffu, ly = 0xffffffffu, lz = 0xffffffffu;
+    unsigned hx = 0xffffffffu, hy = 0xffffffffu, hz = 0xffffffffu, first = 0xffffffffu;
+    int n = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int k = sb * SUPER_BRICKS + 32 * t + lane;
+        const bool ne = __ldg(boff + k + 1) > __ldg(boff + k);
+        if (ne) {
+            const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(boxk) + 2 * k);
+            const uint4 hi = __ldg(reinterpret_cast<const uint4 *>(boxk) + 2 * k + 1);
+            lx = min(lx, lo.x);
+            ly = min(ly, lo.y);
+            lz = min(lz, lo.z);
+            hx = min(hx, hi.x);
+            hy = min(hy, hi.y);
+            hz = min(hz, hi.z);
+            first = min(first, (unsigned)__ldg(bslot + k));
+        }
+        n += __popc(__ballot_sync(FULL_MASK, ne));
+    }
+    lx = __reduce_min_sync(FULL_MASK, lx);
+    ly = __reduce_min_sync(FULL_MASK, ly);
+    lz = __reduce_min_sync(FULL_MASK, lz);
+    hx = __reduce_min_sync(FULL_MASK, hx);
+    hy = __reduce_min_sync(FULL_MASK, hy);
+    hz = __reduce_min_sync(FULL_MASK, hz);
+    first = __reduce_min_sync(FULL_MASK, first);
+    if (lane == 0) {
+        const int s = atomicAdd(&ctl->n_super, 1);
+        sb_box[2 * s] = make_float4(ordered_to_float(lx), ordered_to_float(ly), ordered_to_float(lz),
+                                    __uint_as_float(first));
+        sb_box[2 * s + 1] = make_float4(ordered_to_float(~hx), ordered_to_float(~hy), ordered_to_float(~hz),
+                                        __uint_as_float(first + (unsigned)n));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -703,20 +734,22 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
                                                  GridGeom g, const unsigned *__restrict__ off,
                                                  unsigned *__restrict__ counts, const unsigned *__restrict__ boff,
                                                  unsigned *__restrict__ bcounts, const int *__restrict__ bslot,
-                                                 unsigned *__restrict__ boxord, const uint2 *__restrict__ range,
-                                                 float4 *__restrict__ box, unsigned *__restrict__ sbord,
-                                                 unsigned *__restrict__ sb_left, float4 *__restrict__ sb_box,
-                                                 int *__restrict__ ids, float4 *__restrict__ csr,
-                                                 float4 *__restrict__ bpts, int *__restrict__ outside,
-                                                 unsigned *__restrict__ tile_sum, int n_tiles,
-                                                 unsigned *__restrict__ occ_next, long long occ_next_words,
-                                                 DevCtl *__restrict__ ctl)
+                                                 const unsigned *__restrict__ boxk, unsigned *__restrict__ boxk_next,
+                                                 long long boxk_words, const uint2 *__restrict__ range,
+                                                 float4 *__restrict__ box, unsigned *__restrict__ sb_left,
+                                                 float4 *__restrict__ sb_box, int *__restrict__ ids,
+                                                 float4 *__restrict__ csr, float4 *__restrict__ bpts,
+                                                 int *__restrict__ outside, unsigned *__restrict__ tile_sum,
+                                                 int n_tiles, unsigned *__restrict__ occ_next,
+                                                 long long occ_next_words, DevCtl *__restrict__ ctl)
 {
     pdl_begin();
     // the scan is done with the tile totals: zero them for the next build,
-    // and clear the occupancy buffer the next build will fill
+    // and clear the occupancy and brick-bound buffers the next build will fill
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
         tile_sum[t] = 0u;
+    for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < boxk_words; w += gridDim.x * blockDim.x)
+        boxk_next[w] = 0xffffffffu;
     for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < occ_next_words; w += gridDim.x * blockDim.x)
         occ_next[w] = 0u;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -757,34 +790,23 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
             outside[old + rank] = j;
         }
     }
-    // brick segment, and the brick's exact box: the group's min and max of
-    // each coordinate (order-preserving unsigned images of the floats), merged
-    // by the group leader with one atomic per bound before it reserves slots
+    // brick segment; the group that brings the brick's count to zero writes
+    // its float box, and the one that finishes a super-brick has its warp
+    // write the super-brick's box (above)
     {
         const unsigned peers = __match_any_sync(FULL_MASK, bk);
         const int leader = __ffs(peers) - 1;
         const unsigned rank = __popc(peers & lanemask_lt());
-        const unsigned ox = float_to_ordered(q.x), oy = float_to_ordered(q.y), oz = float_to_ordered(q.z);
-        const unsigned mnx = __reduce_min_sync(peers, ox), mny = __reduce_min_sync(peers, oy),
-                       mnz = __reduce_min_sync(peers, oz);
-        const unsigned mxx = __reduce_max_sync(peers, ox), mxy = __reduce_max_sync(peers, oy),
-                       mxz = __reduce_max_sync(peers, oz);
         unsigned old = 0u;
+        int fin = -1;   // a super-brick this lane's group finished
         if (lane == leader && bk >= 0) {
-            const int slot = __ldg(bslot + bk);
-            unsigned *b = boxord + 8 * slot;
-            atomicMin(b + 0, mnx);
-            atomicMin(b + 1, mny);
-            atomicMin(b + 2, mnz);
-            atomicMax(b + 4, mxx);
-            atomicMax(b + 5, mxy);
-            atomicMax(b + 6, mxz);
-            __threadfence();
             const unsigned cnt = (unsigned)__popc(peers);
             old = atomicSub(bcounts + bk, cnt);
-            if (old == cnt) {   // the brick's last points: its box is complete
-                __threadfence();
-                finish_brick(slot, bk, boxord, range, box, sbord, sb_left, sb_box, ctl);
+            if (old == cnt) {   // the brick's last points
+                finish_brick(__ldg(bslot + bk), bk, boxk, range, box);
+                const int sb = bk / SUPER_BRICKS;
+                if (atomicSub(sb_left + sb, 1u) == 1u)
+                    fin = sb;
             }
         }
         old = __shfl_sync(FULL_MASK, old, leader);
@@ -795,18 +817,21 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
             else
                 atomicOr(&ctl->err, DEVERR_BOUNDS);
         }
+        for (unsigned fm = __ballot_sync(FULL_MASK, fin >= 0); fm; fm &= fm - 1u)
+            finish_super(__shfl_sync(FULL_MASK, fin, __ffs(fm) - 1), boxk, boff, bslot, sb_box, ctl);
     }
 }
 
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
-                           unsigned *boxord, const uint2 *range, float4 *box, unsigned *sbord, unsigned *sb_left,
-                           float4 *sb_box, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
-                           unsigned *occ_next, long long occ_next_words, DevCtl *ctl, cudaStream_t st)
+                           const unsigned *boxk, unsigned *boxk_next, long long boxk_next_words, const uint2 *range,
+                           float4 *box, unsigned *sb_left, float4 *sb_box, int *ids, float4 *csr, float4 *bpts,
+                           int *outside, unsigned *tile_sum, unsigned *occ_next, long long occ_next_words,
+                           DevCtl *ctl, cudaStream_t st)
 {
     return launch_kernel(k_scatter, dim3((n + 255) / 256), dim3(256), 0, st, pts, keys, n, g, off, counts, boff,
-                         bcounts, bslot, boxord, range, box, sbord, sb_left, sb_box, ids, csr, bpts, outside, tile_sum,
-                         (int)scan_tiles(g.V), occ_next, occ_next_words, ctl);
+                         bcounts, bslot, boxk, boxk_next, boxk_next_words, range, box, sb_left, sb_box, ids, csr,
+                         bpts, outside, tile_sum, (int)scan_tiles(g.V), occ_next, occ_next_words, ctl);
 }
 
 // ---------------------------------------------------------------------------

@@ -66,11 +66,12 @@ inline int reduce_blocks(int m, int sms)
 
 cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t st);
 // occ must hold zeros (the previous build's scatter clears it).
-// sb_left (may be null): per super-brick, its non-empty bricks are counted up
-// (the scatter counts them down again).
+// sb_left and boxk (may be null): per super-brick, its non-empty bricks are
+// counted up (the scatter counts them down again); per brick key, 8 words of
+// bounds are merged into boxk (all ones before the build).
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
-                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left, DevCtl *ctl,
-                             cudaStream_t st);
+                             unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
+                             unsigned *boxk, DevCtl *ctl, cudaStream_t st);
 // dense: every off[v]; sparse: only off[v] and off[v + 1] of occupied voxels,
 // off[32 k] and off[V] (what the build and the searches read) -- the rest
 // is completed by launch_offsets_fill on the same occupancy bits.
@@ -79,16 +80,18 @@ cudaError_t launch_scan(const unsigned *counts, const GridGeom &g, unsigned *off
                         bool dense);
 cudaError_t launch_offsets_fill(unsigned *off, const unsigned *occ, long long V, cudaStream_t st);
 cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsigned *boff, int *list, uint2 *range,
-                              int *bslot, uint4 *boxord, DevCtl *ctl, cudaStream_t st);
+                              int *bslot, DevCtl *ctl, cudaStream_t st);
 // The scatter also zeroes the tile totals and the occupancy buffer of the
-// next build (occ_next, occ_next_words words), and writes the brick and
-// super-brick float boxes (sbord: 8 words per super-brick, all ones between
-// builds; sb_left: zero between builds).
+// next build (occ_next, occ_next_words words), writes the brick and
+// super-brick float boxes from the histogram's bounds (boxk) and sets the
+// next build's whole bound buffer (boxk_next, boxk_next_words words) to all
+// ones.
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
-                           unsigned *boxord, const uint2 *range, float4 *box, unsigned *sbord, unsigned *sb_left,
-                           float4 *sb_box, int *ids, float4 *csr, float4 *bpts, int *outside, unsigned *tile_sum,
-                           unsigned *occ_next, long long occ_next_words, DevCtl *ctl, cudaStream_t st);
+                           const unsigned *boxk, unsigned *boxk_next, long long boxk_next_words, const uint2 *range,
+                           float4 *box, unsigned *sb_left, float4 *sb_box, int *ids, float4 *csr, float4 *bpts,
+                           int *outside, unsigned *tile_sum, unsigned *occ_next, long long occ_next_words,
+                           DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
 // Dilation: `inter` holds V words of pass Y (V x 4 bytes suffices for any
 // L), `rows` dilate_units(g) 32-bit row masks (neither needs clearing),
