@@ -62,6 +62,7 @@ struct vicp_ctx {
     int lab_dims[3] = {0, 0, 0};   // grid dimensions that state belongs to
     Buf occ[2];       // occupancy bits: the current build's, and the next build's (kept zeroed)
     int occ_cur = 0;
+    bool after_solve = false;   // the last kernel launched on `stream` is the reduction + solve
     bool off_dense = false;   // the build writes sparse offsets; vicp_get_grid completes them
     long long cap_V = -1;
     // brick level (V / 512)
@@ -190,6 +191,8 @@ vicp_status launch_on(vicp_ctx *c, int kernel, cudaStream_t st, F &&f)
         cudaEventRecord(e0, st);
     }
     cudaError_t e = f();
+    if (st == c->stream)
+        c->after_solve = kernel == K_REDUCE_SOLVE && e == cudaSuccess && !c->profiling;
     if (c->profiling) {
         e1 = take_event(c);
         cudaEventRecord(e1, st);
@@ -428,10 +431,11 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     c->occ_cur ^= 1;
     unsigned *occ = (unsigned *)c->occ[c->occ_cur].p;
     Buf &occ_next = c->occ[c->occ_cur ^ 1];
+    const bool after_solve = c->after_solve;
     TRY(launch(c, K_HISTOGRAM, [&] {
         return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, occ,
                                 (unsigned *)c->tile_sum.p, (unsigned *)c->sb_left.p,
-                                (unsigned *)c->boxk[c->occ_cur].p, d, c->stream);
+                                (unsigned *)c->boxk[c->occ_cur].p, d, c->stream, after_solve);
     }));
     cudaError_t ev = cudaEventRecord(c->ev_hist, c->stream);   // the dilation may start from here
     if (ev != cudaSuccess)
@@ -694,6 +698,7 @@ vicp_status vicp_set_stream(vicp_ctx *c, void *cuda_stream)
     if (!c)
         return VICP_ERR_INVALID;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->after_solve = false;
     return VICP_OK;
 }
 

@@ -62,21 +62,28 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // bumps the scan's descriptor epoch and clears the outside counter for this
 // build.
 // ---------------------------------------------------------------------------
+template <bool AFTER_SOLVE>
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
                                                    unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
                                                    unsigned *__restrict__ tile_sum, unsigned *__restrict__ sb_left,
                                                    unsigned *__restrict__ boxk, DevCtl *__restrict__ ctl)
 {
-    // A build follows the previous iteration's reduction and solve, whose
-    // single-block tail leaves the GPU idle; the histogram touches none of
-    // the arrays (nor control words) that the solve reads or writes, so it
-    // does not wait for it and the next build overlaps that tail.  Every
-    // reader of the solve's pose is still ordered after it: the event
-    // recorded after the histogram completes only after all earlier work of
-    // the stream, the dilation waits for that event, and the search waits
-    // for the dilation.
-    pdl_begin_nowait();
+    // In the ICP loop a build follows the previous iteration's reduction and
+    // solve (AFTER_SOLVE), whose single-block tail leaves the GPU idle; the
+    // histogram touches none of the arrays (nor control words) that the
+    // solve reads or writes, and every kernel before the solve has completed
+    // by the time the solve lets this launch start, so it does not wait and
+    // the next build overlaps that tail.  Every reader of the solve's pose is
+    // still ordered after it: the event recorded after the histogram
+    // completes only after all earlier work of the stream, the dilation waits
+    // for that event, and the search waits for the dilation.  After any
+    // other kernel (a previous build's scatter, for one, which resets the
+    // buffers this build fills) the histogram waits as every kernel does.
+    if (AFTER_SOLVE)
+        pdl_begin_nowait();
+    else
+        pdl_begin();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
@@ -139,11 +146,11 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
-                             unsigned *boxk, DevCtl *ctl, cudaStream_t st)
+                             unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve)
 {
     // occ must hold zeros: the caller clears it beforehand
-    return launch_kernel(k_histogram, dim3((n + 255) / 256), dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ,
-                         tile_sum, sb_left, boxk, ctl);
+    return launch_kernel(after_solve ? k_histogram<true> : k_histogram<false>, dim3((n + 255) / 256), dim3(256), 0,
+                         st, pts, n, g, keys, counts, bcounts, occ, tile_sum, sb_left, boxk, ctl);
 }
 
 // ---------------------------------------------------------------------------

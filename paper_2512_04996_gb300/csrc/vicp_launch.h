@@ -68,10 +68,12 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // occ must hold zeros (the previous build's scatter clears it).
 // sb_left and boxk (may be null): per super-brick, its non-empty bricks are
 // counted up (the scatter counts them down again); per brick key, 8 words of
-// bounds are merged into boxk (all ones before the build).
+// bounds are merged into boxk (all ones before the build).  after_solve:
+// the kernel launched just before it on `st` is the reduction + solve, and
+// the histogram does not wait for it (any other predecessor: it waits).
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
-                             unsigned *boxk, DevCtl *ctl, cudaStream_t st);
+                             unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve);
 // dense: every off[v]; sparse: only off[v] and off[v + 1] of occupied voxels,
 // off[32 k] and off[V] (what the build and the searches read) -- the rest
 // is completed by launch_offsets_fill on the same occupancy bits.

@@ -129,7 +129,7 @@ extern "C" VICP_API vicp_status vicp_offsets_static(const float *target_xyzw, in
         e = cudaMemsetAsync(occ, 0, (size_t)occ_words(g.V) * 4, st);
     if (e == cudaSuccess)
         e = launch_histogram(reinterpret_cast<const float4 *>(target_xyzw), n, g, keys_out, counts, bcounts, occ,
-                             tiles, nullptr, nullptr, ctl, st);
+                             tiles, nullptr, nullptr, ctl, st, false);
     if (e == cudaSuccess)
         e = launch_scan(counts, g, offsets_out, occ, tiles, desc, ctl, st, true);
     unsigned err = 0;
