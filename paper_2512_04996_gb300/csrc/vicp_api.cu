@@ -797,6 +797,7 @@ vicp_status vicp_register_host(vicp_ctx *c, const float *src_host, int32_t n_src
     // context's stream (earlier searches may still read the buffer), so it
     // travels while the grid is built; the first search waits for it.
     cudaError_t e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->stream);
+    c->after_solve = false;   // the build's histogram reads what this copy writes
     if (e == cudaSuccess)
         e = cudaEventRecord(c->ev_copy_go, c->stream);
     if (e == cudaSuccess)
