@@ -75,6 +75,10 @@ typedef struct vicp_allocator {
 /* Flags for vicp_params.flags. */
 #define VICP_FLAG_KEEP_GRID         (1u << 0) /* auto grid: fit once, reuse for later builds */
 #define VICP_FLAG_REBUILD_EACH_ITER (1u << 1) /* vicp_register: rebuild + dilate every iteration */
+#define VICP_FLAG_FP64_SOLVE        (1u << 2) /* vicp_step / vicp_register: centroid and cross-covariance
+                                                 sums in FP64 and the rigid solve in FP64 (Horn's
+                                                 quaternion by Jacobi sweeps); default: double-float
+                                                 (~48-bit) sums and solve on the FP32 pipes */
 
 
 /* Run parameters (Sec. 4.1 "Parameter": voxelisation scale, dilation
@@ -201,10 +205,12 @@ VICP_API vicp_status vicp_correspond(vicp_ctx *ctx, const float *src_xyzw, int32
                             const double *pose_dev, int32_t *nn_out, float *d2_out,
                             int32_t *n_fallback_out);
 
-/* One ICP iteration on the built grid (Sec. 2.1, Eq. 1): NNS as above, FP64
+/* One ICP iteration on the built grid (Sec. 2.1, Eq. 1): NNS as above, the
  * centroids and cross-covariance reduced deterministically, the optimal
- * rotation (Horn's quaternion method, FP64) and translation, and
- * pose <- dT * pose in place.
+ * rotation (Horn's quaternion method) and translation, and pose <- dT * pose
+ * in place (FP64).  The sums and the solve run in double-float arithmetic
+ * (about 48 significant bits on the FP32 pipes), or in FP64 when the
+ * context was created with VICP_FLAG_FP64_SOLVE.
  *   pose_dev: dev, 16 doubles, read and written.  rmse_dev: dev double, the
  *   RMSE of this iteration's correspondences (before the update); may be
  *   NULL.  Degenerate geometry (rank(H) < 2) leaves the pose unchanged and
@@ -288,14 +294,25 @@ VICP_API vicp_status vicp_fixed_build(vicp_ctx *ctx, const float *target_xyzw, i
 VICP_API vicp_status vicp_fixed_correspond(vicp_ctx *ctx, const float *src_xyzw, int32_t n_src,
                                            const double *pose_dev, int32_t *nn_out, float *d2_out,
                                            int32_t *n_fallback_out);
+/* Read-only view of the fixed-capacity store of the last vicp_fixed_build
+ * (Sec. 2.2's monolithic layout): *slots_out (dev, V * capacity x 4 floats:
+ * voxel v's slots at v * capacity, each x, y, z and the bits of the target
+ * index in w), *fill_out (dev uint32[V]: points that fell into voxel v; the
+ * first min(fill, capacity) slots are stored, which of a full voxel's points
+ * they are depends on the order the scatter's atomics ran in), and
+ * *capacity_out.  Any output may be NULL.  Valid until the next
+ * vicp_fixed_build or vicp_destroy.  Synchronous.  Errors: VICP_ERR_STATE
+ * before vicp_fixed_build. */
+VICP_API vicp_status vicp_fixed_view(vicp_ctx *ctx, const float **slots_out, const uint32_t **fill_out,
+                                     int32_t *capacity_out);
 
-/* Voxel keys and segment offsets of a target cloud -- the first two steps of
- * vicp_build_grid (Alg. 1: quantisation, histogram, exclusive scan of the
- * counts) -- computed WITHOUT allocating any device memory.  The paper has
- * no counterpart: it is for callers that may not allocate at the point of
- * the call, such as a loop that has committed a fixed device-memory plan
- * (cudaMalloc can block and synchronise the device) or a plug-in whose host
- * framework owns all device memory.  No context is needed.
+/* Voxel keys and segment offsets of a target cloud -- the keys and offsets
+ * steps of vicp_build_grid -- computed WITHOUT allocating any device memory.
+ * The paper has no counterpart: it is for callers that may not allocate at
+ * the point of the call, such as a loop that has committed a fixed
+ * device-memory plan (cudaMalloc can block and synchronise the device) or a
+ * plug-in whose host framework owns all device memory.  No context is
+ * needed.
  *
  * Working memory is one static device array inside the library (about
  * 70 MiB on every GPU the library is loaded on, held until the process
@@ -307,7 +324,12 @@ VICP_API vicp_status vicp_fixed_correspond(vicp_ctx *ctx, const float *src_xyzw,
  * must serialise them.  Each call clears the parts that must start at zero.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call outside any
- * stream capture.  The call synchronises `cuda_stream` before returning.
+ * stream capture.  The address is kept for the life of the process, so the
+ * library must not be used on a device after cudaDeviceReset (or any other
+ * teardown of the device's primary context) in the same process.  The call
+ * synchronises `cuda_stream` before returning, and runs on the device that
+ * is current when it is called: `cuda_stream`, the target and the outputs
+ * must belong to that device.
  *   target_xyzw: dev, n x 4 floats (w ignored), 16-byte aligned; n >= 1.
  *   origin[3], voxel_size, dims[3]: host; the explicit grid (as
  *     params.origin / voxel_size / dims of vicp_build_grid), dims >= 1.
@@ -350,6 +372,9 @@ typedef struct vicp_batch vicp_batch;
                                                    leaves before the first grid barrier, so the
                                                    other blocks' bounded wait (1 s) runs out and
                                                    the call returns VICP_ERR_TIMEOUT */
+#define VICP_BATCH_FLAG_FP64 (1u << 2)          /* per-pair centroid / cross-covariance sums and
+                                                   the rigid solve in FP64 (as VICP_FLAG_FP64_SOLVE);
+                                                   default: double-float */
 
 typedef struct vicp_batch_params {
     int32_t dilation_layers;  /* L of every pair, 0..31 */
@@ -365,8 +390,8 @@ typedef struct vicp_batch_params {
 VICP_API void vicp_batch_default_params(vicp_batch_params *p);
 
 /* Threads per block, source points per thread and resident blocks (on the
- * current device) of iteration kernel shape `shape`.  Errors:
- * VICP_ERR_INVALID. */
+ * current device; of the double-float variant) of iteration kernel shape
+ * `shape`.  Errors: VICP_ERR_INVALID. */
 VICP_API vicp_status vicp_batch_shape_info(int32_t shape, int32_t *threads, int32_t *points_per_thread,
                                            int32_t *resident_blocks);
 
@@ -451,6 +476,12 @@ VICP_API vicp_status vicp_batch_set_flags(vicp_batch *b, uint32_t flags);
 /* Kernels the batch context has launched since vicp_batch_create (a graph
  * replay counts its kernels). */
 VICP_API int64_t vicp_batch_launch_count(const vicp_batch *b);
+
+/* How the last registration's iterations ran: 1 replayed from the captured
+ * CUDA graph, 0 launched one by one (VICP_BATCH_FLAG_NO_GRAPH, or the
+ * capture of the cooperative launches failed once on this context), -1 no
+ * registration yet (or b NULL). */
+VICP_API int32_t vicp_batch_graph_replayed(const vicp_batch *b);
 
 /* Text of the last error on this batch context ("" if none). */
 VICP_API const char *vicp_batch_last_error(const vicp_batch *b);

@@ -2,9 +2,14 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 legs of ``bench.py`` may import this package.  It wraps ``vicp_oracle.c``, a
-plain single-threaded C restatement of the paper's steps (Alg. 1-4, Eq. 1),
-through ctypes.  It imports nothing from the CUDA package and the CUDA
-package imports nothing from it.
+plain C restatement of the paper's steps (Alg. 1-4, Eq. 1), through ctypes.
+It imports nothing from the CUDA package and the CUDA package imports nothing
+from it.
+
+The C file is built twice: single-threaded (the default), and with OpenMP
+over the loops whose iterations are independent (keys, one dilation round,
+the searches); ``use_threads(n)`` selects the second for n > 1.  Both give
+bit-identical results (pinned in ``tests/test_oracle_threads.py``).
 
 Functions take and return numpy arrays.  Point clouds are (N, 4) float32,
 C-contiguous (x, y, z, w; w ignored).  Poses are 4x4 float64 row-major.
@@ -23,26 +28,38 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vicp_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "libvicp_oracle.so")
+_LIB_OMP = os.path.join(_LIB_DIR, "libvicp_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}          # "plain" / "omp" -> CDLL
+_threads = 1        # threads of the calls that follow (1: the plain build)
 
 OK = 0
 ERR_INVALID = 1
 ERR_DEGENERATE = 7
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc.  -ffp-contract=off keeps every float
-    operation separately rounded (gcc contracts a*b+c into FMA by default on
-    aarch64), which the bit-exact comparisons rely on."""
-    os.makedirs(_LIB_DIR, exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+def _compile(lib: str, extra, force: bool) -> bool:
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(_SRC):
+        return True
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", *extra,
            "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        return False
+    os.replace(tmp, lib)
+    return True
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc, single-threaded and (where gcc has
+    OpenMP) multi-threaded.  -ffp-contract=off keeps every float operation
+    separately rounded (gcc contracts a*b+c into FMA by default on aarch64),
+    which the bit-exact comparisons rely on."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if not _compile(_LIB, [], force):
+        raise RuntimeError("gcc failed to build the oracle")
+    _compile(_LIB_OMP, ["-fopenmp"], force)   # optional: use_threads() reports 1 without it
     return _LIB
 
 
@@ -74,12 +91,17 @@ class Grid:
         return g
 
 
-def _load():
-    global _lib
+def _open(which: str):
+    """The CDLL of one build, loaded once ("plain" or "omp"; None if the
+    OpenMP build is not available)."""
     with _lock:
-        if _lib is None:
+        if which not in _libs:
             build()
-            lib = C.CDLL(_LIB)
+            path = _LIB if which == "plain" else _LIB_OMP
+            if not os.path.exists(path):
+                _libs[which] = None
+                return None
+            lib = C.CDLL(path)
             P = C.c_void_p
             i32, i64, f32, f64 = C.c_int32, C.c_int64, C.c_float, C.c_double
             G = C.POINTER(_Grid)
@@ -103,13 +125,44 @@ def _load():
                 "og_build": (None, [G, P, i32, i32, P, P, P, P, P, P]),
                 "og_iterate": (C.c_int, [G, P, P, P, P, i32, P, i32, P, P, P, P, P, P]),
                 "og_register": (C.c_int, [G, i32, P, i32, P, i32, P, i32, f64, P, P]),
+                "og_set_threads": (i32, [i32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = lib
-    return _lib
+            _libs[which] = lib
+    return _libs[which]
+
+
+def _load():
+    if _threads > 1:
+        lib = _open("omp")
+        if lib is not None:
+            return lib
+    return _open("plain")
+
+
+def use_threads(n: int) -> int:
+    """Run the following calls on n threads (n <= 1: the single-threaded
+    build).  Returns the thread count the calls will use (1 where gcc has no
+    OpenMP)."""
+    global _threads
+    n = int(n)
+    if n <= 1:
+        _threads = 1
+        return 1
+    lib = _open("omp")
+    if lib is None:
+        _threads = 1
+        return 1
+    _threads = int(lib.og_set_threads(n))
+    return _threads
+
+
+def threads() -> int:
+    """Threads the oracle's calls use now."""
+    return _threads
 
 
 def _ptr(a: np.ndarray):

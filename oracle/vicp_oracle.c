@@ -11,6 +11,14 @@
  * C `float`/`double` compiled with -ffp-contract=off, so each operation is
  * rounded exactly once, in source order.
  *
+ * The file is compiled twice: plain (one thread), and with OpenMP, where the
+ * loops whose iterations are independent of one another -- the keys of the
+ * points, the voxels of one dilation round, the searches of the source
+ * points -- are shared out over threads.  Every iteration computes exactly
+ * what it computes in the plain build and writes only its own outputs, and
+ * every loop that accumulates (histogram, CSR fill, reductions) stays
+ * sequential, so both builds give bit-identical results.
+ *
  * Readings of the paper where it is silent or ambiguous (each is applied
  * identically by the CUDA path, and each is pinned by a test):
  *   - Grid: origin = component-wise minimum of the target, voxel edge h
@@ -48,6 +56,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OG_OK 0
 #define OG_ERR_INVALID 1
@@ -60,6 +71,19 @@ typedef struct {
     float inv_h;   /* (float)(1.0 / (double)h)             */
     int32_t dims[3];
 } og_grid;
+
+/* Threads of the OpenMP build (1 in the plain build). */
+int32_t og_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+    return (int32_t)omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Grid fitting (Sec. 4.1 "Parameter"; reading: bounding-box origin)        */
@@ -133,6 +157,7 @@ int32_t og_voxel_key(const og_grid *g, float x, float y, float z)
 
 void og_keys(const og_grid *g, const float *pts, int32_t n, int32_t *keys)
 {
+#pragma omp parallel for schedule(static)
     for (int32_t j = 0; j < n; ++j) {
         const float *q = pts + 4 * (int64_t)j;
         keys[j] = og_voxel_key(g, q[0], q[1], q[2]);
@@ -214,6 +239,7 @@ void og_dilate(const og_grid *g, const uint32_t *off, int32_t L, int32_t *root, 
     int32_t *prev = (int32_t *)malloc((size_t)V * sizeof(int32_t));
     for (int32_t r = 1; r <= L; ++r) {
         memcpy(prev, root, (size_t)V * sizeof(int32_t));
+#pragma omp parallel for schedule(static)
         for (int64_t z = 0; z < nz; ++z)
             for (int64_t y = 0; y < ny; ++y)
                 for (int64_t x = 0; x < nx; ++x) {
@@ -290,6 +316,7 @@ void og_correspond(const og_grid *g, const uint32_t *off, const int32_t *ids, co
                    const float *tgt, int32_t n, const float *src, int32_t m, const double pose[16],
                    int32_t *nn, float *d2, uint8_t *fallback)
 {
+#pragma omp parallel for schedule(dynamic, 64)
     for (int32_t i = 0; i < m; ++i) {
         float s[3];
         og_transform(pose, src + 4 * (int64_t)i, s);

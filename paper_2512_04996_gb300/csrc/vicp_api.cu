@@ -192,7 +192,8 @@ vicp_status launch_on(vicp_ctx *c, int kernel, cudaStream_t st, F &&f)
     }
     cudaError_t e = f();
     if (st == c->stream)
-        c->after_solve = kernel == K_REDUCE_SOLVE && e == cudaSuccess && !c->profiling;
+        c->after_solve = (kernel == K_REDUCE_SOLVE || kernel == K_REDUCE_SOLVE_F64) && e == cudaSuccess &&
+                         !c->profiling;
     if (c->profiling) {
         e1 = take_event(c);
         cudaEventRecord(e1, st);
@@ -405,6 +406,13 @@ vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double
     TRY(run_nns(c, src, m, pose, nn, (float *)c->d2.p, honor_stop));
     const float3 ctr = grid_center(c->geom);
     const int nparts = reduce_blocks(m, c->sms);
+    if (c->params.flags & VICP_FLAG_FP64_SOLVE) {
+        TRY(launch(c, K_REDUCE_SOLVE_F64, [&] {
+            return launch_reduce_solve_f64(src, m, pose, c->target, c->n_target, nn, ctr, (double *)c->partials.p,
+                                           nparts, rmse, ctl_of(c), honor_stop, c->params.rmse_eps, c->stream);
+        }));
+        return VICP_OK;
+    }
     TRY(launch(c, K_REDUCE_SOLVE, [&] {
         return launch_reduce_solve(src, m, pose, c->target, c->n_target, nn, ctr, (float2 *)c->partials.p, nparts,
                                    rmse, ctl_of(c), honor_stop, c->params.rmse_eps, c->stream);
@@ -945,6 +953,22 @@ vicp_status vicp_fixed_build(vicp_ctx *c, const float *target_xyzw, int32_t n, i
     return VICP_OK;
 }
 
+vicp_status vicp_fixed_view(vicp_ctx *c, const float **slots_out, const uint32_t **fill_out, int32_t *capacity_out)
+{
+    if (!c)
+        return VICP_ERR_INVALID;
+    if (!c->fixed_built)
+        return fail(c, VICP_ERR_STATE, "vicp_fixed_view needs vicp_fixed_build first");
+    TRY(read_device_status(c));   // synchronises
+    if (slots_out)
+        *slots_out = static_cast<const float *>(c->fslots.p);
+    if (fill_out)
+        *fill_out = static_cast<const uint32_t *>(c->fcount.p);
+    if (capacity_out)
+        *capacity_out = (int32_t)c->fixed_C;
+    return VICP_OK;
+}
+
 vicp_status vicp_fixed_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, const double *pose_dev,
                                   int32_t *nn_out, float *d2_out, int32_t *n_fallback_out)
 {
@@ -1043,7 +1067,8 @@ const char *kernel_name(int k)
 {
     static const char *names[K_COUNT] = {"bbox",       "histogram", "scan",     "scatter",      "brick_scan",
                                          "dilate",   "correspond", "fallback", "reduce_solve",
-                                         "maxcount",   "fixed_scatter", "fixed_correspond", "offsets_fill"};
+                                         "maxcount",   "fixed_scatter", "fixed_correspond", "offsets_fill",
+                                         "reduce_solve_f64"};
     return (k >= 0 && k < K_COUNT) ? names[k] : "?";
 }
 }  // namespace vicp

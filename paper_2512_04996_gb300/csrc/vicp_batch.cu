@@ -22,6 +22,7 @@
 // sets DEVERR_TIMEOUT and leaves the kernel.
 #include "vicp_batch.h"
 #include "vicp_df.cuh"
+#include "vicp_f64.cuh"
 #include "vicp_dilate.cuh"
 #include "vicp_launch.h"
 #include "vicp_search.cuh"
@@ -600,10 +601,148 @@ __device__ __forceinline__ PoseF pose_f_warp(const double *__restrict__ pose)
 }
 
 // ---------------------------------------------------------------------------
-// The iteration kernel (see the top of this file).  Dynamic shared memory:
-// the transposed per-lane sums of phase 3, 2 x WARPS x 16 x 33 floats.
+// Phase 3 of the iteration kernel with FP64 sums and an FP64 solve: the same
+// items and the same fixed summation order (thread, warp, block per item,
+// then the pair's items in item order by the block of its last item) as the
+// double-float phase 3 of k_batch_iter, in doubles.  s_dyn_f holds
+// WARPS x 16 x 33 doubles; the partials one double per (item, sum).
 // ---------------------------------------------------------------------------
-template <int TH, int PPT, int MINB>
+template <int TH, int PPT>
+__device__ __forceinline__ void batch_phase3_f64(const BatchIterArgs &a, float *s_dyn_f, BatchItem &s_item,
+                                                 int &s_skip, int &s_last, PoseF &s_pose)
+{
+    constexpr int WARPS = TH / 32;
+    __shared__ double s_w[WARPS][F64_SUMS];
+    __shared__ double s_tot[F64_SUMS];
+    double(*s_t)[F64_SUMS][33] = reinterpret_cast<double(*)[F64_SUMS][33]>(s_dyn_f);
+    double *partials = reinterpret_cast<double *>(a.partials);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    DevCtl *const ctl = a.ctl;
+    for (int itx = blockIdx.x; itx < a.n_items; itx += gridDim.x) {
+        if (tid == 0) {
+            s_item = a.items[itx];
+            s_skip = *(volatile const int *)&a.state[s_item.pair].stop;
+        }
+        __syncthreads();
+        const BatchItem it = s_item;
+        if (s_skip) {
+            __syncthreads();
+            continue;
+        }
+        load_pose_f_block(a.pose + 16 * it.pair, s_pose);
+        const PoseF P = s_pose;
+        const BatchPair *bp = a.pairs + it.pair;
+        const double3 c = make_double3((double)bp->cx, (double)bp->cy, (double)bp->cz);
+        const int tbase = bp->tbase, n_tgt = bp->n_tgt;
+        double acc[F64_SUMS];
+#pragma unroll
+        for (int k = 0; k < F64_SUMS; ++k)
+            acc[k] = 0.0;
+        int j[PPT];
+        float4 p[PPT], q[PPT];
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            const int i = it.i0 + tid + TH * u;
+            j[u] = -1;
+            if (i < it.i1) {
+                j[u] = __ldcg(a.nn + i);
+                p[u] = __ldg(a.src + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            if ((unsigned)j[u] < (unsigned)n_tgt)
+                q[u] = __ldg(a.tgt + tbase + j[u]);
+            else if (it.i0 + tid + TH * u < it.i1)   // no valid match: report, leave it out
+                atomicOr(&ctl->err, DEVERR_BOUNDS);
+        }
+#pragma unroll
+        for (int u = 0; u < PPT; ++u)
+            if ((unsigned)j[u] < (unsigned)n_tgt)
+                accumulate_corr_f64(acc, transform_pt(P, p[u]), q[u], c);
+        // warp sums through shared memory: lane l adds value l % 16 over
+        // lanes 16 (l / 16) .. 16 (l / 16) + 15 in order, then the halves
+#pragma unroll
+        for (int k = 0; k < F64_SUMS; ++k)
+            s_t[warp][k][lane] = acc[k];
+        __syncwarp();
+        {
+            const int k = lane & 15, h = (lane >> 4) * 16;
+            double v = s_t[warp][k][h];
+#pragma unroll
+            for (int t = 1; t < 16; ++t)
+                v += s_t[warp][k][h + t];
+            v += __shfl_xor_sync(FULL_MASK, v, 16);
+            if (lane < 16)
+                s_w[warp][k] = v;
+        }
+        __syncthreads();
+        if (tid < F64_SUMS) {   // the block's warps, in order
+            double v = s_w[0][tid];
+#pragma unroll
+            for (int w = 1; w < WARPS; ++w)
+                v += s_w[w][tid];
+            partials[(size_t)itx * F64_SUMS + tid] = v;
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0)
+            s_last = atomicAdd(&a.state[it.pair].items_done, 1u) == (unsigned)(bp->n_items - 1);
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            // the pair's item sums in item order, as in the double-float phase 3
+            const int item0 = bp->item0, n_items = bp->n_items;
+            {
+                const int k = tid & 15, grp = tid >> 4;
+                double v = 0.0;
+                for (int b = grp; b < n_items; b += TH / 16)
+                    v += __ldcg(partials + (size_t)(item0 + b) * F64_SUMS + k);
+                v += __shfl_xor_sync(FULL_MASK, v, 16);
+                if (lane < 16)
+                    s_w[warp][lane] = v;
+            }
+            __syncthreads();
+            if (tid < F64_SUMS) {
+                double t = s_w[0][tid];
+#pragma unroll
+                for (int w = 1; w < WARPS; ++w)
+                    t += s_w[w][tid];
+                s_tot[tid] = t;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double rmse;
+                BatchState *stp = a.state + it.pair;
+                const bool ok = solve_update_f64(s_tot, bp->n_src, c, a.pose + 16 * it.pair, rmse);
+                if (lane == 0) {
+                    stp->items_done = 0u;
+                    stp->last_rmse = rmse;
+                    if (!ok) {
+                        stp->err |= DEVERR_DEGENERATE;
+                        stp->stop = 1;
+                        atomicOr(&ctl->err, DEVERR_DEGENERATE);
+                    } else {
+                        const int k = stp->iters;
+                        stp->iters = k + 1;
+                        if (a.eps > 0.0 && k >= 1 && fabs(rmse - stp->prev_rmse) < a.eps)
+                            stp->stop = 1;
+                        stp->prev_rmse = rmse;
+                    }
+                }
+            }
+        }
+        __syncthreads();   // s_item, s_pose and the sums are rewritten for the next item
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The iteration kernel (see the top of this file).  Dynamic shared memory:
+// the transposed per-lane sums of phase 3, WARPS x 16 x 33 words of 8 bytes
+// (a float pair per word for double-float sums, a double for FP64 sums).
+// With F64 the sums of phase 3 and the solve are FP64 (vicp_f64.cuh).
+// ---------------------------------------------------------------------------
+template <int TH, int PPT, int MINB, bool F64>
 __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
 {
     constexpr int WARPS = TH / 32;
@@ -797,6 +936,10 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
         return;
 
     // ---- phase 3: per-item sums; the last item of a pair solves it --------
+    if constexpr (F64) {
+        batch_phase3_f64<TH, PPT>(a, s_dyn, s_item, s_skip, s_last, s_pose);
+        return;
+    }
     float(*s_thi)[N_SUMS][33] = reinterpret_cast<float(*)[N_SUMS][33]>(s_dyn);
     float(*s_tlo)[N_SUMS][33] = reinterpret_cast<float(*)[N_SUMS][33]>(s_dyn + WARPS * N_SUMS * 33);
     for (int itx = blockIdx.x; itx < a.n_items; itx += gridDim.x) {
@@ -939,27 +1082,28 @@ const BatchShape BATCH_SHAPES[BATCH_N_SHAPES] = {
 
 using IterKernel = void (*)(const BatchIterArgs);
 
-static IterKernel iter_kernel(int shape)
+static IterKernel iter_kernel(int shape, bool f64)
 {
     switch (shape) {
-    case 0: return k_batch_iter<256, 4, 2>;
-    case 1: return k_batch_iter<256, 2, 3>;
-    case 2: return k_batch_iter<512, 2, 1>;
-    case 3: return k_batch_iter<128, 4, 4>;
-    case 4: return k_batch_iter<256, 8, 2>;
-    case 5: return k_batch_iter<256, 2, 4>;
-    case 6: return k_batch_iter<256, 2, 5>;
+    case 0: return f64 ? k_batch_iter<256, 4, 2, true> : k_batch_iter<256, 4, 2, false>;
+    case 1: return f64 ? k_batch_iter<256, 2, 3, true> : k_batch_iter<256, 2, 3, false>;
+    case 2: return f64 ? k_batch_iter<512, 2, 1, true> : k_batch_iter<512, 2, 1, false>;
+    case 3: return f64 ? k_batch_iter<128, 4, 4, true> : k_batch_iter<128, 4, 4, false>;
+    case 4: return f64 ? k_batch_iter<256, 8, 2, true> : k_batch_iter<256, 8, 2, false>;
+    case 5: return f64 ? k_batch_iter<256, 2, 4, true> : k_batch_iter<256, 2, 4, false>;
+    case 6: return f64 ? k_batch_iter<256, 2, 5, true> : k_batch_iter<256, 2, 5, false>;
     }
     return nullptr;
 }
 
+// 2 x WARPS x 16 x 33 floats = WARPS x 16 x 33 doubles
 static size_t iter_smem(int shape) { return (size_t)2 * (BATCH_SHAPES[shape].threads / 32) * N_SUMS * 33 * 4; }
 
-int batch_iter_blocks(int shape)
+int batch_iter_blocks(int shape, bool f64)
 {
     if (shape < 0 || shape >= BATCH_N_SHAPES)
         return 0;
-    IterKernel k = iter_kernel(shape);
+    IterKernel k = iter_kernel(shape, f64);
     const size_t smem = iter_smem(shape);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -975,9 +1119,9 @@ int batch_iter_blocks(int shape)
     return sms * per_sm;
 }
 
-cudaError_t launch_batch_iter(int shape, int blocks, const BatchIterArgs &a, cudaStream_t st)
+cudaError_t launch_batch_iter(int shape, bool f64, int blocks, const BatchIterArgs &a, cudaStream_t st)
 {
-    IterKernel k = iter_kernel(shape);
+    IterKernel k = iter_kernel(shape, f64);
     if (!k || blocks < 1)
         return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};

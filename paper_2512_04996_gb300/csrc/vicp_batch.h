@@ -115,11 +115,12 @@ cudaError_t launch_batch_brick_boxes(const uint4 *boxord, const int *list, const
 cudaError_t launch_batch_dilate(const unsigned *occ, const BatchPair *pairs, int P, const int *ustart_xy,
                                 const int *ustart_z, int L, void *inter, unsigned *rows, unsigned char *dirty,
                                 int *root, unsigned char *ring, cudaStream_t st);
-// Resident blocks of the iteration kernel of a shape (0 if it cannot run).
-int batch_iter_blocks(int shape);
+// Resident blocks of the iteration kernel of a shape (0 if it cannot run);
+// f64: the variant with FP64 sums and solve.
+int batch_iter_blocks(int shape, bool f64);
 // One iteration of every pair (or the search alone): a cooperative
-// persistent launch of `blocks` blocks (<= batch_iter_blocks(shape)).
-cudaError_t launch_batch_iter(int shape, int blocks, const BatchIterArgs &a, cudaStream_t st);
+// persistent launch of `blocks` blocks (<= batch_iter_blocks(shape, f64)).
+cudaError_t launch_batch_iter(int shape, bool f64, int blocks, const BatchIterArgs &a, cudaStream_t st);
 
 // Differentiable loss (vicp_diff.cu): SE(3) exponential T = Exp(xi) T0 and
 // J(xi)^T g (J the left Jacobian), one thread per pose; the loss of Eq. 1

@@ -64,6 +64,8 @@ struct vicp_batch {
     const void *g_src = nullptr;
     int g_shape = -1, g_iters = -1, g_M = -1, g_items = -1;
     double g_eps = 0.0;
+    bool g_f64 = false;
+    int last_graph = -1;             // the last registration's iterations: 1 graph replay, 0 direct
 
     // device buffers
     BBuf counts, off, root, ring, inter, occ, desc, tile_sum, rows, dirty;
@@ -505,14 +507,18 @@ BatchIterArgs iter_args(vicp_batch *b, const float4 *src, double *pose, int *nn,
     return a;
 }
 
-// `blocks`: batch_iter_blocks(shape), queried by the caller outside any
+// FP64 sums and solve (VICP_BATCH_FLAG_FP64) for this context's iterations.
+bool fp64_of(const vicp_batch *b) { return (b->params.flags & VICP_BATCH_FLAG_FP64) != 0; }
+
+// `blocks`: batch_iter_blocks(shape, f64), queried by the caller outside any
 // stream capture.
-vicp_status launch_iters(vicp_batch *b, int shape, int blocks, const BatchIterArgs &a, int iters, cudaStream_t st)
+vicp_status launch_iters(vicp_batch *b, int shape, bool f64, int blocks, const BatchIterArgs &a, int iters,
+                         cudaStream_t st)
 {
     if (blocks < 1)
         return bfail(b, VICP_ERR_CUDA, "iteration kernel shape %d cannot be resident", shape);
     for (int k = 0; k < iters; ++k)
-        BCUDA(b, launch_batch_iter(shape, blocks, a, st), "launch of the batched iteration");
+        BCUDA(b, launch_batch_iter(shape, f64, blocks, a, st), "launch of the batched iteration");
     b->launches += iters;
     return VICP_OK;
 }
@@ -525,11 +531,13 @@ vicp_status run_iterations(vicp_batch *b, int shape, const float4 *src)
     if (iters == 0)
         return VICP_OK;
     const BatchIterArgs a = iter_args(b, src, (double *)b->pose.p, (int *)b->nn.p, (float *)b->d2.p, 0);
-    const int blocks = batch_iter_blocks(shape);
+    const bool f64 = fp64_of(b);
+    const int blocks = batch_iter_blocks(shape, f64);
+    b->last_graph = 0;
     if ((b->params.flags & VICP_BATCH_FLAG_NO_GRAPH) || b->graph_broken)
-        return launch_iters(b, shape, blocks, a, iters, b->stream);
+        return launch_iters(b, shape, f64, blocks, a, iters, b->stream);
     if (!b->graph || b->g_src != src || b->g_shape != shape || b->g_iters != iters || b->g_M != b->M ||
-        b->g_items != b->n_items || b->g_eps != b->params.rmse_eps) {
+        b->g_items != b->n_items || b->g_eps != b->params.rmse_eps || b->g_f64 != f64) {
         drop_graph(b);
         if (!b->capture)
             BCUDA(b, cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
@@ -537,7 +545,7 @@ vicp_status run_iterations(vicp_batch *b, int shape, const float4 *src)
         cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             const int64_t before = b->launches;
-            const vicp_status s = launch_iters(b, shape, blocks, a, iters, b->capture);
+            const vicp_status s = launch_iters(b, shape, f64, blocks, a, iters, b->capture);
             b->launches = before;   // counted when replayed
             e = cudaStreamEndCapture(b->capture, &g);
             if (s != VICP_OK && e == cudaSuccess)
@@ -552,7 +560,7 @@ vicp_status run_iterations(vicp_batch *b, int shape, const float4 *src)
             cudaGetLastError();
             b->graph = nullptr;
             b->graph_broken = true;
-            return launch_iters(b, shape, blocks, a, iters, b->stream);
+            return launch_iters(b, shape, f64, blocks, a, iters, b->stream);
         }
         b->g_src = src;
         b->g_shape = shape;
@@ -560,9 +568,11 @@ vicp_status run_iterations(vicp_batch *b, int shape, const float4 *src)
         b->g_M = b->M;
         b->g_items = b->n_items;
         b->g_eps = b->params.rmse_eps;
+        b->g_f64 = f64;
     }
     BCUDA(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
     b->launches += iters;
+    b->last_graph = 1;
     return VICP_OK;
 }
 
@@ -637,7 +647,7 @@ vicp_status vicp_batch_shape_info(int32_t shape, int32_t *threads, int32_t *poin
     if (points_per_thread)
         *points_per_thread = BATCH_SHAPES[shape].ppt;
     if (resident_blocks)
-        *resident_blocks = batch_iter_blocks(shape);
+        *resident_blocks = batch_iter_blocks(shape, false);
     return VICP_OK;
 }
 
@@ -741,7 +751,7 @@ vicp_status vicp_batch_correspond(vicp_batch *b, const float *src_xyzw, const in
     BTRY(reset_loop(b));
     const BatchIterArgs a = iter_args(b, reinterpret_cast<const float4 *>(src_xyzw), const_cast<double *>(poses_dev),
                                       nn_out, d2_out, 1);
-    BTRY(launch_iters(b, shape, batch_iter_blocks(shape), a, 1, b->stream));
+    BTRY(launch_iters(b, shape, false, batch_iter_blocks(shape, false), a, 1, b->stream));   // search only
     const vicp_status s = read_status(b);
     return s == VICP_ERR_DEGENERATE ? VICP_OK : s;
 }
@@ -766,7 +776,7 @@ vicp_status vicp_batch_tune(vicp_batch *b, const float *src_xyzw, const int32_t 
     vicp_status s = VICP_OK;
     for (int shape = 0; shape < BATCH_N_SHAPES && s == VICP_OK; ++shape) {
         float ms = -1.0f;
-        if (batch_iter_blocks(shape) > 0) {
+        if (batch_iter_blocks(shape, fp64_of(b)) > 0) {
             s = prepare_items(b, n_src, shape);
             for (int t = 0; t < trials && s == VICP_OK; ++t) {
                 if (cudaMemcpyAsync(b->pose.p, poses, (size_t)P * 16 * sizeof(double), cudaMemcpyHostToDevice, st) !=
@@ -780,9 +790,9 @@ vicp_status vicp_batch_tune(vicp_batch *b, const float *src_xyzw, const int32_t 
                 const BatchIterArgs a =
                     iter_args(b, reinterpret_cast<const float4 *>(src_xyzw), (double *)b->pose.p, (int *)b->nn.p,
                               (float *)b->d2.p, 0);
-                const int blocks = batch_iter_blocks(shape);
+                const int blocks = batch_iter_blocks(shape, fp64_of(b));
                 cudaEventRecord(e0, st);
-                s = launch_iters(b, shape, blocks, a, iters, st);
+                s = launch_iters(b, shape, fp64_of(b), blocks, a, iters, st);
                 cudaEventRecord(e1, st);
                 if (s != VICP_OK)
                     break;
@@ -941,6 +951,8 @@ vicp_status vicp_batch_set_flags(vicp_batch *b, uint32_t flags)
 }
 
 int64_t vicp_batch_launch_count(const vicp_batch *b) { return b ? b->launches : 0; }
+
+int32_t vicp_batch_graph_replayed(const vicp_batch *b) { return b ? b->last_graph : -1; }
 
 const char *vicp_batch_last_error(const vicp_batch *b) { return b ? b->last_error.c_str() : ""; }
 

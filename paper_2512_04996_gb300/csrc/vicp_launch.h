@@ -42,6 +42,7 @@ enum KernelId {
     K_FIXED_SCATTER,
     K_FIXED_CORRESPOND,
     K_OFFSETS_FILL,
+    K_REDUCE_SOLVE_F64,
     K_COUNT
 };
 const char *kernel_name(int k);
@@ -132,5 +133,10 @@ cudaError_t launch_voxel_histogram(const float4 *pts, int n, const GridGeom &g, 
 cudaError_t launch_reduce_solve(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt, const int *nn,
                                 float3 center, float2 *partials, int nparts, double *rmse_out, DevCtl *ctl,
                                 int honor_stop, double eps, cudaStream_t st);
+// The same update with FP64 sums and an FP64 solve (vicp_solve64.cu);
+// partials holds nparts x 16 doubles.
+cudaError_t launch_reduce_solve_f64(const float4 *src, int m, double *pose, const float4 *tgt, int n_tgt,
+                                    const int *nn, float3 center, double *partials, int nparts, double *rmse_out,
+                                    DevCtl *ctl, int honor_stop, double eps, cudaStream_t st);
 
 }  // namespace vicp

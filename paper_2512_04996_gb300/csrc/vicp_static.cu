@@ -45,7 +45,9 @@ std::mutex g_setup_lock;
 unsigned char *g_addr[MAX_DEVICES] = {};
 
 // Device address of the scratch on the current device (looked up once per
-// device, with that device current).
+// device, with that device current, and kept until the process exits: a
+// cudaDeviceReset would leave a stale address behind, which the header
+// rules out).
 vicp_status scratch_address(unsigned char **out)
 {
     int dev = 0;

@@ -33,12 +33,14 @@ VICP_STATIC_MAX_VOXELS = 1 << 24
 VICP_STATIC_MAX_BRICK_SLOTS = 1 << 20
 VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
+VICP_FLAG_FP64_SOLVE = 1 << 2
 VICP_HIST_WARP_AGGREGATED = 0
 VICP_HIST_SHARED_HASH = 1
 VICP_BATCH_MAX_PAIRS = 65536
 VICP_BATCH_SHAPES = 7
 VICP_BATCH_FLAG_NO_GRAPH = 1 << 0
 VICP_BATCH_FLAG_TEST_BARRIER_TIMEOUT = 1 << 1
+VICP_BATCH_FLAG_FP64 = 1 << 2
 
 
 class VicpError(RuntimeError):
@@ -117,6 +119,7 @@ SIGNATURES = {
                                       _P]),
     "vicp_fixed_build": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
     "vicp_fixed_correspond": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
+    "vicp_fixed_view": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_int32)]),
     "vicp_voxel_histogram": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32),
                                        C.c_int32, _P, _P, _P]),
     "vicp_batch_default_params": (None, [C.POINTER(vicp_batch_params)]),
@@ -133,6 +136,7 @@ SIGNATURES = {
     "vicp_batch_report": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(vicp_stats),
                                     C.c_int32]),
     "vicp_batch_launch_count": (C.c_int64, [_P]),
+    "vicp_batch_graph_replayed": (C.c_int32, [_P]),
     "vicp_batch_set_flags": (C.c_int, [_P, C.c_uint32]),
     "vicp_se3_exp": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
     "vicp_se3_left_jacobian_t": (C.c_int, [C.c_int32, _P, _P, _P, _P]),
@@ -306,6 +310,18 @@ class Context:
                                                     d2.data_ptr(), n_fallback.data_ptr()), "vicp_fixed_correspond")
         return nn, d2, n_fallback
 
+    def fixed_view(self) -> dict:
+        """Copies of the fixed-capacity store: slots (V * C, 4) float32 and
+        fill counts (V,) int32 holding uint32, with the capacity C."""
+        slots, fill, cap = C.c_void_p(), C.c_void_p(), C.c_int32(0)
+        self._check(self._lib.vicp_fixed_view(self.handle, C.byref(slots), C.byref(fill), C.byref(cap)),
+                    "vicp_fixed_view")
+        V = int(self.grid_view().n_voxels)
+        Cap = int(cap.value)
+        return {"capacity": Cap,
+                "slots": _view(slots.value, (V * Cap, 4), "<f4", torch.float32, self.device).clone(),
+                "fill": _view(fill.value, (V,), "<u4", torch.uint32, self.device).clone()}
+
     def register(self, source: torch.Tensor, target: torch.Tensor, pose=None):
         s, t = _cloud(source, "source"), _cloud(target, "target")
         self._target = t
@@ -446,12 +462,15 @@ def vicp_offsets_static(target, origin, voxel_size: float, dims, keys=None, offs
     for t, size, what in ((keys, n, "keys"), (offsets, V + 1, "offsets")):
         if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous() or t.numel() < size:
             raise ValueError(f"{what}: expected a contiguous CUDA int32 tensor of >= {size} entries")
+        if t.device != target.device:
+            raise ValueError(f"{what}: must be on the target's device {target.device}")
     st = stream if stream is not None else torch.cuda.current_stream(target.device)
     o = (C.c_float * 3)(*[float(x) for x in origin])
     d = (C.c_int32 * 3)(*[int(x) for x in dims])
-    r = lib.vicp_offsets_static(C.c_void_p(target.data_ptr()), n, o, float(voxel_size), d,
-                                C.c_void_p(keys.data_ptr()), C.c_void_p(offsets.data_ptr()),
-                                C.c_void_p(st.cuda_stream))
+    with torch.cuda.device(target.device):   # the library works on the current device
+        r = lib.vicp_offsets_static(C.c_void_p(target.data_ptr()), n, o, float(voxel_size), d,
+                                    C.c_void_p(keys.data_ptr()), C.c_void_p(offsets.data_ptr()),
+                                    C.c_void_p(st.cuda_stream))
     if r != VICP_OK:
         raise VicpError(r, f"vicp_offsets_static: {lib.vicp_status_string(r).decode()} (static scratch holds at "
                            f"most {VICP_STATIC_MAX_VOXELS} voxels and {VICP_STATIC_MAX_BRICK_SLOTS} brick slots)")
@@ -658,6 +677,11 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(self._lib.vicp_batch_launch_count(self.handle))
+
+    def graph_replayed(self) -> int:
+        """1: the last registration replayed the captured CUDA graph; 0: it
+        launched the iterations one by one; -1: no registration yet."""
+        return int(self._lib.vicp_batch_graph_replayed(self.handle))
 
     def set_flags(self, flags: int):
         self._check(self._lib.vicp_batch_set_flags(self.handle, int(flags)), "vicp_batch_set_flags")

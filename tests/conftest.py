@@ -24,3 +24,13 @@ def pairs():
         return cache[k]
 
     return get
+
+
+@pytest.fixture()
+def oracle_threads():
+    """The oracle on all host cores for the duration of one test (its
+    OpenMP build gives the same results as the single-threaded one)."""
+    import oracle
+    n = oracle.use_threads(os.cpu_count() or 1)
+    yield n
+    oracle.use_threads(1)

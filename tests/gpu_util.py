@@ -81,5 +81,24 @@ def transform_f32(T, pts):
 
 
 def rot_err(Ta, Tb):
-    E = Ta[:3, :3] @ Tb[:3, :3].T
-    return float(np.arccos(np.clip((np.trace(E) - 1.0) / 2.0, -1.0, 1.0)))
+    """Angle (rad) of the rotation between two poses, from the Frobenius norm
+    of the difference of their rotations (|Ra - Rb|_F = 2 sqrt(2) sin(a/2)),
+    which keeps full relative precision for small angles where the arccos of
+    the trace cannot resolve less than about 1e-8 rad."""
+    d = np.linalg.norm(np.asarray(Ta)[:3, :3] - np.asarray(Tb)[:3, :3])
+    return float(2.0 * np.arcsin(min(1.0, d / (2.0 * np.sqrt(2.0)))))
+
+
+def assert_nn_equal(nn, d2, rnn, rd2):
+    """Each neighbour equals the oracle's; another index is allowed only when
+    its float squared distance is within 1e-6 relative of the oracle's.
+    Where the indices agree, the squared distances agree bit for bit."""
+    nn, d2, rnn, rd2 = (np.asarray(x) for x in (nn, d2, rnn, rd2))
+    assert nn.shape == rnn.shape
+    same = nn == rnn
+    if not same.all():
+        bad = ~same
+        rel = np.abs(d2[bad].astype(np.float64) - rd2[bad]) / np.maximum(rd2[bad], 1e-30)
+        assert (rel <= 1e-6).all(), (np.flatnonzero(bad)[:5], nn[bad][:5], rnn[bad][:5])
+    both_nan = np.isnan(d2) & np.isnan(rd2)
+    assert np.array_equal(d2[same & ~both_nan], rd2[same & ~both_nan])

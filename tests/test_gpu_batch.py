@@ -123,10 +123,15 @@ def test_every_shape_gives_the_same_neighbours(shape):
     assert torch.equal(nn, nn0) and torch.equal(d2, d20)
 
 
-def test_batch_register_matches_oracle():
+def _prec_flags(prec):
+    return vicp().VICP_BATCH_FLAG_FP64 if prec == "fp64" else 0
+
+
+@pytest.mark.parametrize("prec", ["double_float", "fp64"])
+def test_batch_register_matches_oracle(prec):
     ps = _small(n_pairs=6, n_min=500, n_max=4000, seed=19)
     iters = 12
-    b, t, s, n_src = _batch(ps, max_iters=iters, rmse_eps=0.0)
+    b, t, s, n_src = _batch(ps, max_iters=iters, rmse_eps=0.0, flags=_prec_flags(prec))
     st, T, it, rm, ps_status = b.register(s, n_src)
     assert st == 0 and (ps_status == 0).all() and (it == iters).all()
     for k, p in enumerate(ps):
@@ -166,13 +171,14 @@ def test_batch_equals_single_pair_path():
         _assert_pose_close(T[k], S, _extent(p.target))
 
 
-def test_batch_deterministic_graph_and_direct():
+@pytest.mark.parametrize("prec", ["double_float", "fp64"])
+def test_batch_deterministic_graph_and_direct(prec):
     v = vicp()
     ps = _small(n_pairs=5, n_min=1000, n_max=6000, seed=31)
-    b, t, s, n_src = _batch(ps, max_iters=8)
+    b, t, s, n_src = _batch(ps, max_iters=8, flags=_prec_flags(prec))
     r1 = b.register(s, n_src)
     r2 = b.register(s, n_src)   # replayed graph
-    bd, td, sd, _ = _batch(ps, max_iters=8, flags=v.VICP_BATCH_FLAG_NO_GRAPH)
+    bd, td, sd, _ = _batch(ps, max_iters=8, flags=v.VICP_BATCH_FLAG_NO_GRAPH | _prec_flags(prec))
     r3 = bd.register(sd, n_src)
     for r in (r2, r3):
         assert r[0] == 0 and np.array_equal(r[1], r1[1]) and np.array_equal(r[2], r1[2])
@@ -253,26 +259,34 @@ def test_argument_checks():
     assert st == 0
 
 
-def test_full_batched_workload_sampled():
+_FULL_ORACLE = {}
+
+
+@pytest.mark.parametrize("prec", ["double_float", "fp64"])
+def test_full_batched_workload_sampled(oracle_threads, prec):
     """The 256-pair workload (sizes log-uniform in 2k..64k, 4.6M points in
     all, 40 iterations) in the launch configuration of the benchmark; the
-    oracle registers the four smallest pairs and one mid-sized pair, and the
-    single-pair GPU path every fourth pair."""
+    oracle registers every sixteenth pair by size (from the smallest to the
+    largest), and the single-pair GPU path every fourth pair."""
     ps = synth.batched_pairs()
     assert len(ps) == 256
-    b, t, s, n_src = _batch(ps, max_iters=40)
+    b, t, s, n_src = _batch(ps, max_iters=40, flags=_prec_flags(prec))
     st, T, it, rm, pst = b.register(s, n_src)
     assert st == 0 and (pst == 0).all() and (it == 40).all()
     sizes = np.array([p.source.shape[0] for p in ps])
     order = np.argsort(sizes)
-    for k in list(order[:4]) + [int(order[len(order) // 3])]:
+    for k in [int(x) for x in order[::16]] + [int(order[-1])]:
         p = ps[k]
-        og = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
-        rst, R, rit, hist = oracle.register(og, L, p.target, p.source, np.eye(4), max_iters=40, eps=0.0)
+        if k not in _FULL_ORACLE:
+            og = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
+            _FULL_ORACLE[k] = oracle.register(og, L, p.target, p.source, np.eye(4), max_iters=40, eps=0.0)
+        rst, R, rit, hist = _FULL_ORACLE[k]
         _assert_pose_close(T[k], R, _extent(p.target))
+    single_flags = vicp().VICP_FLAG_FP64_SOLVE if prec == "fp64" else 0
     for k in range(0, 256, 4):
         p = ps[k]
-        ctx = context(L=L, voxel_size=p.voxel_size, divisions=p.grid_divisions, max_iters=40, eps=0.0)
+        ctx = context(L=L, voxel_size=p.voxel_size, divisions=p.grid_divisions, max_iters=40, eps=0.0,
+                      flags=single_flags)
         sst, S, sit, _ = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
         assert sst == 0
         _assert_pose_close(T[k], S, _extent(p.target))

@@ -1,16 +1,24 @@
 """The fixed-capacity voxel store (vicp_fixed_build / vicp_fixed_correspond)
-against the CSR store: with a capacity of the largest voxel count nothing is
-dropped and every neighbour, distance and global-search count equals
-vicp_correspond's bit for bit (all three workloads, the scene included); with
-a smaller capacity the dropped points equal sum(max(0, count - C)) over the
-oracle's histogram, queries whose root voxel kept all its points are
-unchanged, and the others get a stored point no closer than the CSR answer."""
+against the oracle and against the CSR store.
+
+With a capacity of the largest voxel count nothing is dropped: every
+neighbour equals the oracle's (equal index, or squared distance within 1e-6
+relative) and the CSR path's bit for bit, on all three workloads.
+
+With a smaller capacity the store keeps min(count, C) points of each voxel;
+which ones depends on the order of the scatter's atomics, so the test reads
+back the kept points, checks that they are a valid truncation (each lies in
+its voxel, none twice, exactly min(count, C) per voxel, the dropped total
+equals sum(max(0, count - C)) over the oracle's histogram), builds the
+oracle's CSR of exactly those points and holds every neighbour to the
+oracle's search over it (the root labels and the global search are the full
+build's, as the store replaces only the voxel segments)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from gpu_util import gpu_grid, to_np, vicp
+from gpu_util import assert_nn_equal, gpu_grid, oracle_grid_for, to_np, vicp
 from paper_2512_04996_gb300.synth import random_rigid
 
 pytestmark = pytest.mark.gpu
@@ -25,41 +33,66 @@ def _searches(ctx, src, T):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_capacity_of_the_largest_voxel_equals_csr(pairs, k):
+def test_capacity_of_the_largest_voxel_matches_oracle(pairs, oracle_threads, k):
     p = pairs(k)
     ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions)
+    grid, ref = oracle_grid_for(g, p.target, 10)
     rep = ctx.memory_report()
     C = rep["max_voxel_count"]
+    assert C == int(ref["counts"].max())
     over, nbytes = ctx.fixed_build(g["_target"], C)
     assert over == 0
     assert nbytes == g["n_voxels"] * C * 16 + 4 * g["n_voxels"]
     for T in (np.eye(4), p.T_gt, random_rigid(np.random.default_rng(k), 20.0, 0.2)):
         (nn, d2, nf), (fnn, fd2, fnf) = _searches(ctx, p.source, T)
+        rnn, rd2, rfb = oracle.correspond(grid, ref, p.target, p.source, T)
+        assert_nn_equal(fnn, fd2, rnn, rd2)
+        assert int(fnf[0]) == int(rfb.sum())
+        # and the CSR path's answers bit for bit
         assert np.array_equal(nn, fnn) and np.array_equal(d2.view(np.uint32), fd2.view(np.uint32))
         assert int(nf[0]) == int(fnf[0])
 
 
-def test_small_capacity_drops_and_approximates(pairs):
-    p = pairs(2)
+def _kept_csr(ctx, keys, counts, C):
+    """The oracle-layout CSR (offsets, ids ascending per voxel) of the points
+    the fixed store kept, after checking that they are a valid truncation."""
+    fv = ctx.fixed_view()
+    assert fv["capacity"] == C
+    fill = to_np(fv["fill"]).astype(np.int64)
+    assert np.array_equal(fill, counts.astype(np.int64))        # every point was counted in its voxel
+    kept = np.minimum(fill, C)
+    V = counts.shape[0]
+    slot_ids = to_np(fv["slots"])[:, 3].view(np.int32).reshape(V, C)
+    used = np.arange(C)[None, :] < kept[:, None]
+    vox = np.repeat(np.arange(V), C).reshape(V, C)[used]
+    ids = slot_ids[used]
+    assert np.all((ids >= 0) & (ids < keys.shape[0]))
+    assert np.array_equal(keys[ids], vox)                       # each kept point lies in its voxel
+    assert np.unique(ids).shape[0] == ids.shape[0]              # none twice
+    order = np.lexsort((ids, vox))                              # voxel order, ascending index inside
+    off = np.zeros(V + 1, np.uint32)
+    off[1:] = np.cumsum(kept).astype(np.uint32)
+    return off, np.ascontiguousarray(ids[order].astype(np.int32))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_small_capacity_matches_oracle_on_kept_points(pairs, k):
+    p = pairs(k)
     ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions)
-    counts = np.diff(g["offsets"].astype(np.int64))
+    grid, ref = oracle_grid_for(g, p.target, 10)
+    counts = ref["counts"]
     C = max(1, int(counts.max()) // 4)
     over, _ = ctx.fixed_build(g["_target"], C)
-    assert over == int(np.maximum(counts - C, 0).sum()) and over > 0
-    (nn, d2, nf), (fnn, fd2, fnf) = _searches(ctx, p.source, p.T_gt)
-    # the root voxel of each query, from the CSR grid
-    from gpu_util import transform_f32
-    grid = oracle.Grid(g["origin"], g["voxel_size"], g["inv_voxel_size"], g["dims"])
-    keys = oracle.keys(grid, transform_f32(p.T_gt, p.source))
-    root = np.where(keys >= 0, g["root"][np.maximum(keys, 0)], -1)
-    full = (root >= 0) & (counts[np.maximum(root, 0)] <= C)
-    assert full.sum() > 0 and (~full & (root >= 0)).sum() > 0
-    assert np.array_equal(nn[full], fnn[full]) and np.array_equal(d2[full], fd2[full])
-    part = (root >= 0) & ~full
-    assert np.all((fnn[part] >= 0) & (fnn[part] < p.target.shape[0]))
-    assert np.all(fd2[part] >= d2[part])
-    # the global searches are the same queries
-    assert np.array_equal(nn[root < 0], fnn[root < 0])
+    assert over == int(np.maximum(counts.astype(np.int64) - C, 0).sum()) and over > 0
+    off_t, ids_t = _kept_csr(ctx, ref["keys"], counts, C)
+    trunc = dict(off=off_t, ids=ids_t, root=ref["root"])
+    for T in (p.T_gt, random_rigid(np.random.default_rng(10 + k), 15.0, 0.1)):
+        (nn, d2, nf), (fnn, fd2, fnf) = _searches(ctx, p.source, T)
+        rnn, rd2, rfb = oracle.correspond(grid, trunc, p.target, p.source, T)
+        assert_nn_equal(fnn, fd2, rnn, rd2)
+        assert int(fnf[0]) == int(rfb.sum())
+        # a truncated segment never gives a closer point than the full one
+        assert np.all(fd2[~rfb] >= d2[~rfb])
 
 
 def test_fixed_store_argument_checks(pairs):
@@ -69,6 +102,9 @@ def test_fixed_store_argument_checks(pairs):
     t = torch.from_numpy(p.target).cuda()
     with pytest.raises(v.VicpError) as e:
         ctx.fixed_build(t, 8)
+    assert e.value.status == v.VICP_ERR_STATE
+    with pytest.raises(v.VicpError) as e:
+        ctx.fixed_view()
     assert e.value.status == v.VICP_ERR_STATE
     ctx.build_grid(t)
     with pytest.raises(v.VicpError) as e:

@@ -12,6 +12,12 @@ from paper_2512_04996_gb300.synth import random_rigid
 pytestmark = pytest.mark.gpu
 
 ROT_TOL = 1e-5
+PRECISIONS = ["double_float", "fp64"]
+
+
+def _prec_flags(prec):
+    from paper_2512_04996_gb300 import vicp
+    return vicp.VICP_FLAG_FP64_SOLVE if prec == "fp64" else 0
 
 
 def _extent(target):
@@ -24,10 +30,16 @@ def _assert_pose_close(T, R, extent):
     assert np.linalg.norm(T[:3, 3] - R[:3, 3]) <= 1e-5 * extent
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_single_step(pairs, k):
+def test_single_step(pairs, k, prec):
+    """One step at a pose: the same correspondences as the oracle, so the
+    update differs only by the rounding of the sums and the solve -- within
+    the pose tolerance for double-float, and within 1e-9 rad / 1e-9 x extent
+    and 1e-12 relative RMSE for FP64."""
     p = pairs(k)
-    ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions)
+    ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions,
+                      flags=_prec_flags(prec))
     grid, ref = oracle_grid_for(g, p.target, 10)
     T0 = np.eye(4) if k != 1 else random_rigid(np.random.default_rng(9), 3.0, 0.02)
     pose = torch.from_numpy(T0.copy()).cuda()
@@ -36,14 +48,21 @@ def test_single_step(pairs, k):
     assert ctx.sync() == 0
     st, R, r_rmse, *_ = oracle.iterate(grid, ref, p.target, p.source, T0)
     assert st == 0
-    _assert_pose_close(to_np(pose), R, _extent(p.target))
-    assert abs(float(to_np(rmse)[0]) - r_rmse) <= 1e-9 * r_rmse
+    T = to_np(pose)
+    _assert_pose_close(T, R, _extent(p.target))
+    if prec == "fp64":
+        assert rot_err(T, R) <= 1e-9 and np.linalg.norm(T[:3, 3] - R[:3, 3]) <= 1e-9 * _extent(p.target)
+        assert abs(float(to_np(rmse)[0]) - r_rmse) <= 1e-12 * r_rmse
+    else:
+        assert abs(float(to_np(rmse)[0]) - r_rmse) <= 1e-9 * r_rmse
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("k", [1, 2])
-def test_register_fixed_iterations(pairs, k):
+def test_register_fixed_iterations(pairs, k, prec):
     p = pairs(k)
-    ctx = context(L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions, max_iters=p.iters, eps=0.0)
+    ctx = context(L=10, voxel_size=p.voxel_size, divisions=p.grid_divisions, max_iters=p.iters, eps=0.0,
+                  flags=_prec_flags(prec))
     st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
     assert st == 0 and it == p.iters
     grid = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
@@ -53,16 +72,45 @@ def test_register_fixed_iterations(pairs, k):
     assert abs(rm - hist[-1]) <= 1e-7 * hist[-1]
 
 
-def test_register_scene_three_iterations_rebuilding_each(pairs):
+_SCENE_ORACLE = {}
+
+
+def _scene_oracle(p, max_iters, eps):
+    key = (max_iters, eps)
+    if key not in _SCENE_ORACLE:
+        grid = oracle.fit_grid(p.target, p.voxel_size, 0)
+        _SCENE_ORACLE[key] = oracle.register(grid, 10, p.target, p.source, np.eye(4), max_iters=max_iters, eps=eps)
+    return _SCENE_ORACLE[key]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_register_scene_thirty_iterations_rebuilding_each(pairs, oracle_threads, prec):
+    """The benchmark's configuration end to end: the 226k-point scene, grid
+    rebuilt and dilated every iteration, 30 iterations from the identity,
+    against the oracle's 30 iterations (pose, iteration count, RMSE)."""
     from paper_2512_04996_gb300 import vicp
     p = pairs(3)
-    ctx = context(L=10, voxel_size=p.voxel_size, max_iters=3, eps=0.0,
-                  flags=vicp.VICP_FLAG_KEEP_GRID | vicp.VICP_FLAG_REBUILD_EACH_ITER)
+    ctx = context(L=10, voxel_size=p.voxel_size, max_iters=30, eps=0.0,
+                  flags=vicp.VICP_FLAG_KEEP_GRID | vicp.VICP_FLAG_REBUILD_EACH_ITER | _prec_flags(prec))
     st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
-    assert st == 0 and it == 3
-    grid = oracle.fit_grid(p.target, p.voxel_size, 0)
-    rst, R, rit, hist = oracle.register(grid, 10, p.target, p.source, np.eye(4), max_iters=3, eps=0.0)
+    assert st == 0 and it == 30
+    rst, R, rit, hist = _scene_oracle(p, 30, 0.0)
+    assert rst == 0 and rit == it
     _assert_pose_close(T, R, _extent(p.target))
+    assert abs(rm - hist[-1]) <= 1e-7 * hist[-1]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_register_scene_paper_stopping_rule(pairs, oracle_threads, prec):
+    """The scene under the paper's stopping rule (RMSE difference 1e-5, at
+    most 50 iterations): the same iteration count and pose as the oracle."""
+    p = pairs(3)
+    ctx = context(L=10, voxel_size=p.voxel_size, max_iters=50, eps=1e-5, flags=_prec_flags(prec))
+    st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+    rst, R, rit, hist = _scene_oracle(p, 50, 1e-5)
+    assert st == 0 and rst == 0 and it == rit and 2 <= it <= 50
+    _assert_pose_close(T, R, _extent(p.target))
+    assert abs(rm - hist[-1]) <= 1e-7 * hist[-1]
 
 
 def test_paper_stopping_rule(pairs):
@@ -118,11 +166,12 @@ def test_steps_equal_register(pairs):
     assert np.array_equal(to_np(pose), T)
 
 
-def test_degenerate_geometry_reports_and_keeps_pose():
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_degenerate_geometry_reports_and_keeps_pose(prec):
     from paper_2512_04996_gb300 import vicp
     tgt = np.zeros((500, 4), np.float32)
     tgt[:, 0] = np.linspace(0, 1, 500)
-    ctx = context(L=4, divisions=16, max_iters=5, eps=0.0)
+    ctx = context(L=4, divisions=16, max_iters=5, eps=0.0, flags=_prec_flags(prec))
     st, T, it, rm = ctx.register(torch.from_numpy(tgt).cuda(), torch.from_numpy(tgt).cuda())
     assert st == vicp.VICP_ERR_DEGENERATE and it == 0
     assert np.array_equal(T, np.eye(4))
@@ -149,3 +198,19 @@ def test_profile_counts_launches(pairs):
     assert ctx.launch_count() - before == 9
     for name in ("correspond", "fallback", "reduce_solve"):
         assert prof[name][0] == 3 and prof[name][1] > 0.0
+
+
+def test_fp64_and_double_float_agree_and_are_deterministic(pairs):
+    """The two precisions register the object workload to the same pose
+    (both within the oracle's tolerance of each other), and the FP64 path
+    gives bit-identical results from run to run."""
+    p = pairs(2)
+    out = {}
+    for prec in ("double_float", "fp64", "fp64"):
+        ctx = context(L=10, divisions=128, max_iters=10, eps=0.0, flags=_prec_flags(prec))
+        st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
+        assert st == 0 and it == 10
+        if prec in out:
+            assert np.array_equal(out[prec][0], T) and out[prec][1] == rm
+        out[prec] = (T, rm)
+    _assert_pose_close(out["fp64"][0], out["double_float"][0], _extent(p.target))

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import to_np, vicp
+from gpu_util import assert_nn_equal, to_np, vicp
 from oracle import diff
 from paper_2512_04996_gb300 import synth
 
@@ -56,8 +56,8 @@ def _setup(ps, poses):
     b.build(t, n_tgt, None, np.array([p.grid_divisions for p in ps], np.int32))
     s = torch.from_numpy(src).cuda()
     T = torch.from_numpy(np.ascontiguousarray(poses)).cuda()
-    nn, _ = b.correspond(s, n_src, T)
-    return v, b, t, s, n_src, T, to_np(nn)
+    nn, d2 = b.correspond(s, n_src, T)
+    return v, b, t, s, n_src, T, to_np(nn), to_np(d2)
 
 
 def _split(a, n_src):
@@ -75,15 +75,15 @@ def test_loss_and_analytic_gradients_match_oracle(loss_pairs, where):
     rng = np.random.default_rng(2)
     poses = np.stack([diff.se3_exp(_xi(rng, 0.01, 0.005)) @ p.T_gt if where == "truth" else np.eye(4)
                       for p in ps])
-    v, b, t, s, n_src, T, nn = _setup(ps, poses)
+    v, b, t, s, n_src, T, nn, d2 = _setup(ps, poses)
     loss, gp, gs = b.loss(s, n_src, T, torch.from_numpy(nn).cuda(), grad_pose=True, grad_src=True)
     loss, gp, gs = to_np(loss), to_np(gp), to_np(gs)
-    nn_k, gs_k = _split(nn, n_src), _split(gs, n_src)
+    nn_k, gs_k, d2_k = _split(nn, n_src), _split(gs, n_src), _split(d2, n_src)
     for k, p in enumerate(ps):
-        if k < 2:   # the search itself against the oracle
-            og = oracle.fit_grid(p.target, 0.0, p.grid_divisions)
-            rnn, _, _ = oracle.correspond(og, oracle.build_grid(og, p.target, L), p.target, p.source, poses[k])
-            assert (nn_k[k] == rnn).mean() > 0.999
+        # the search itself against the oracle, every pair
+        og = oracle.fit_grid(p.target, 0.0, p.grid_divisions)
+        rnn, rd2, _ = oracle.correspond(og, oracle.build_grid(og, p.target, L), p.target, p.source, poses[k])
+        assert_nn_equal(nn_k[k], d2_k[k], rnn, rd2)
         ref = diff.loss(p.target, p.source, poses[k], nn_k[k])
         assert abs(loss[k] - ref) <= 1e-12 * ref
         assert _rel(gp[k], diff.grad_left(p.target, p.source, poses[k], nn_k[k])) <= 1e-9
@@ -102,7 +102,7 @@ def test_autograd_gradients_pass_the_finite_difference_check(loss_pairs, angle):
     T0 = np.stack([diff.se3_exp(_xi(rng, 0.02, 0.01)) @ p.T_gt for p in ps])
     xi = np.stack([_xi(rng, angle, 0.02) if angle else np.zeros(6) for _ in ps])
     T = np.stack([diff.se3_exp(xi[k]) @ T0[k] for k in range(len(ps))])
-    v, b, t, s, n_src, Td, nn = _setup(ps, T)
+    v, b, t, s, n_src, Td, nn, _ = _setup(ps, T)
     xi_t = torch.from_numpy(xi).cuda().requires_grad_(True)
     src_t = s.clone().requires_grad_(True)
     loss = v.point_to_point_loss(xi_t, src_t, b, n_src, torch.from_numpy(np.ascontiguousarray(T0)).cuda())
@@ -123,7 +123,7 @@ def test_recomputed_correspondences_give_identical_gradients(loss_pairs):
     ps = loss_pairs[:3]
     rng = np.random.default_rng(4)
     T0 = np.ascontiguousarray(np.stack([diff.se3_exp(_xi(rng, 0.02, 0.01)) @ p.T_gt for p in ps]))
-    v, b, t, s, n_src, Td, nn = _setup(ps, T0)
+    v, b, t, s, n_src, Td, nn, _ = _setup(ps, T0)
     grads = []
     for recompute in (False, True):
         xi_t = torch.zeros((len(ps), 6), dtype=torch.float64, device="cuda", requires_grad=True)
@@ -140,7 +140,7 @@ def test_float32_parameters(loss_pairs):
     gradient equal to the float64 one rounded."""
     ps = loss_pairs[:2]
     T0 = np.ascontiguousarray(np.stack([p.T_gt for p in ps]))
-    v, b, t, s, n_src, Td, nn = _setup(ps, T0)
+    v, b, t, s, n_src, Td, nn, _ = _setup(ps, T0)
     out = []
     for dt in (torch.float64, torch.float32):
         xi_t = torch.zeros((len(ps), 6), dtype=dt, device="cuda", requires_grad=True)
@@ -157,7 +157,7 @@ def test_full_loss_workload_sampled():
     assert len(ps) == 64
     rng = np.random.default_rng(6)
     T0 = np.ascontiguousarray(np.stack([diff.se3_exp(_xi(rng, 0.02, 0.01)) @ p.T_gt for p in ps]))
-    v, b, t, s, n_src, Td, nn = _setup(ps, T0)
+    v, b, t, s, n_src, Td, nn, _ = _setup(ps, T0)
     xi_t = torch.zeros((64, 6), dtype=torch.float32, device="cuda", requires_grad=True)
     loss = v.point_to_point_loss(xi_t, s, b, n_src, torch.from_numpy(T0).cuda())
     loss.sum().backward()

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import gpu_grid, oracle_grid_for, to_np, transform_f32
+from gpu_util import assert_nn_equal, gpu_grid, oracle_grid_for, to_np, transform_f32
 from paper_2512_04996_gb300.synth import random_rigid
 
 pytestmark = pytest.mark.gpu
@@ -21,15 +21,8 @@ def _gpu_correspond(ctx, src, T):
     return to_np(nn), to_np(d2), int(to_np(nf)[0])
 
 
-def _assert_nn_equal(nn, d2, rnn, rd2, target, src_T=None):
-    same = nn == rnn
-    if not same.all():
-        # allowed only for a different index at a squared distance within 1e-6
-        bad = ~same
-        rel = np.abs(d2[bad].astype(np.float64) - rd2[bad]) / np.maximum(rd2[bad], 1e-30)
-        assert (rel <= 1e-6).all(), (np.flatnonzero(bad)[:5], nn[bad][:5], rnn[bad][:5])
-    both_nan = np.isnan(d2) & np.isnan(rd2)
-    assert np.array_equal(d2[same & ~both_nan], rd2[same & ~both_nan])
+def _assert_nn_equal(nn, d2, rnn, rd2, target=None):
+    assert_nn_equal(nn, d2, rnn, rd2)
 
 
 @pytest.mark.parametrize("k", [1, 2])
@@ -46,21 +39,21 @@ def test_correspond_matches_oracle(pairs, k, which):
     _assert_nn_equal(nn, d2, rnn, rd2, p.target)
 
 
-def test_correspond_scene_sampled(pairs):
-    """Full 226k-point scene on the GPU; the oracle checks a 12k-point sample
-    (each point's search is independent of the others)."""
+@pytest.mark.parametrize("which", ["identity", "ground_truth"])
+def test_correspond_scene_full(pairs, oracle_threads, which):
+    """The full 226k-point scene: every source point's neighbour against the
+    oracle's, and the global-search count."""
     p = pairs(3)
     ctx, g = gpu_grid(p.target, L=10, voxel_size=p.voxel_size)
     grid, ref = oracle_grid_for(g, p.target, 10)
-    T = p.T_gt
+    T = p.T_gt if which == "ground_truth" else np.eye(4)
     nn, d2, nf = _gpu_correspond(ctx, p.source, T)
-    idx = np.random.default_rng(3).choice(p.source.shape[0], 12000, replace=False)
-    rnn, rd2, rfb = oracle.correspond(grid, ref, p.target, p.source[idx], T)
-    _assert_nn_equal(nn[idx], d2[idx], rnn, rd2, p.target)
-    # fallback count of the full cloud: points outside the grid or in an unlabelled voxel
+    rnn, rd2, rfb = oracle.correspond(grid, ref, p.target, p.source, T)
+    _assert_nn_equal(nn, d2, rnn, rd2, p.target)
+    assert nf == int(rfb.sum()) and 0 < nf < p.source.shape[0]
+    # the fallback set is the points outside the grid or in an unlabelled voxel
     keys = oracle.keys(grid, transform_f32(T, p.source))
-    want = int(((keys < 0) | (ref["root"][np.maximum(keys, 0)] < 0)).sum())
-    assert nf == want and 0 < nf < p.source.shape[0]
+    assert np.array_equal(rfb, (keys < 0) | (ref["root"][np.maximum(keys, 0)] < 0))
 
 
 def test_global_search_with_outside_targets_and_odd_sources():

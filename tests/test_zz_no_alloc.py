@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from gpu_util import context, to_np, vicp
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +54,11 @@ def test_static_offsets_equal_build_grid_on_consecutive_calls(pairs):
     # first call (looks up the scratch address on this device)
     keys, off = _run_static(v, scene, e_scene, k_scene, o_scene)
     assert np.array_equal(keys, e_scene["keys"]) and np.array_equal(off, e_scene["offsets"])
+    # and directly against the oracle's keys and offsets on the same grid
+    g = oracle.explicit_grid(e_scene["origin"], e_scene["voxel_size"], e_scene["dims"])
+    rkeys = oracle.keys(g, pairs(3).target)
+    assert np.array_equal(keys, rkeys)
+    assert np.array_equal(off, oracle.offsets(oracle.histogram(rkeys, g.n_voxels)))
 
     free0 = torch.cuda.mem_get_info()[0]
     keys, off = _run_static(v, small, e_small, k_small, o_small)   # smaller grid after a larger one
