@@ -79,6 +79,8 @@ typedef struct vicp_allocator {
                                                  sums in FP64 and the rigid solve in FP64 (Horn's
                                                  quaternion by Jacobi sweeps); default: double-float
                                                  (~48-bit) sums and solve on the FP32 pipes */
+#define VICP_FLAG_SPARSE_GRID       (1u << 3) /* the sparse (hashed) grid, see vicp_get_sparse_grid: no
+                                                 per-voxel count, offset, root or ring arrays */
 
 
 /* Run parameters (Sec. 4.1 "Parameter": voxelisation scale, dilation
@@ -130,7 +132,8 @@ typedef struct vicp_memory {
     uint32_t max_voxel_count;        /* C_max */
     uint32_t occupied_voxels;
     uint32_t nonempty_bricks;        /* 8x8x8-voxel bricks holding a point (global-search index) */
-    uint32_t reserved;
+    uint32_t labelled_voxels;        /* sparse grid: voxels within L of a point (the labelled-voxel
+                                        table's entries); 0 for the dense grid */
 } vicp_memory;
 
 /* Work counters of the searches since the last reset. */
@@ -247,6 +250,55 @@ VICP_API vicp_status vicp_register_host(vicp_ctx *ctx, const float *src_xyzw_hos
  * array (one kernel on the context's stream), so out->offsets holds all
  * V + 1 entries. */
 VICP_API vicp_status vicp_get_grid(vicp_ctx *ctx, vicp_grid_view *out);
+
+/* The sparse (hashed) grid, a context created with VICP_FLAG_SPARSE_GRID.
+ * The paper's dynamic assignment (Sec. 3) makes the point store compact but
+ * keeps per-voxel count / address words for every voxel (Table 1 note 1),
+ * and VANICP's dilation labels every voxel; at fine voxel sizes those dense
+ * arrays dominate the memory (Sec. 2.2's argument, one level up).  The
+ * sparse grid keeps, instead, only
+ *   - the occupied voxels, in an open-addressing table (voxel key -> slot;
+ *     at least 2 n_target slots, so at most half full) whose slots carry the
+ *     counts and the segment offsets (an exclusive scan in slot order, so
+ *     segments lie in the store in slot order), and
+ *   - the labelled voxels (within L of a point), in a second table (voxel
+ *     key -> root voxel key; the ring is the Manhattan distance between the
+ *     two voxels), sized after each dilation to keep it at most half full
+ *     (one synchronisation per vicp_dilate: pass Z counts the labels, and a
+ *     table that was too small is grown and the dilation run again).
+ * Keys, CSR ids and points, the occupancy bits, the dilation's pass-Y words
+ * and the global search's brick level are as in the dense grid, and every
+ * search result equals the dense grid's.  Not available with the
+ * fixed-capacity store (VICP_ERR_STATE) or vicp_get_grid.
+ * All pointers are device pointers owned by the context, valid until the
+ * next build or vicp_destroy. */
+typedef struct vicp_sparse_view {
+    float origin[3];
+    float voxel_size;
+    float inv_voxel_size;
+    int32_t dims[3];
+    int64_t n_voxels;
+    int32_t n_target;
+    int32_t n_stored;
+    int32_t dilation_layers;           /* -1 before any dilation */
+    int64_t occupied_slots;            /* slots of the occupied-voxel table (a power of two) */
+    const uint32_t *occupied_keys;     /* [occupied_slots] voxel key, 0xffffffff for an empty slot */
+    const uint32_t *occupied_offsets;  /* [occupied_slots + 1]: the points of the voxel in slot s are
+                                          ids[occupied_offsets[s] .. occupied_offsets[s + 1]); valid for
+                                          occupied slots s (and s + 1), and [occupied_slots] = n_stored */
+    int64_t labelled_slots;            /* slots of the labelled-voxel table (0 before a dilation) */
+    const uint32_t *labelled_keys;     /* [labelled_slots] voxel key, 0xffffffff for an empty slot */
+    const int32_t *labelled_root;      /* [labelled_slots] root voxel key of the voxel in that slot */
+    int64_t labelled_voxels;           /* entries in the labelled-voxel table */
+    const int32_t *keys;               /* [n_target] voxel key of each target point, -1 outside */
+    const int32_t *ids;                /* [n_stored] point indices grouped by voxel */
+    const float *csr_points;           /* [n_stored x 4] x, y, z of ids[k]; w holds the bits of ids[k] */
+    const uint32_t *occupancy;         /* [ceil(V/32)] bit v set iff voxel v holds a point */
+} vicp_sparse_view;
+
+/* Synchronous: the sparse grid of the last build / dilation.  Errors:
+ * VICP_ERR_STATE (not a sparse-grid context, or no build). */
+VICP_API vicp_status vicp_get_sparse_grid(vicp_ctx *ctx, vicp_sparse_view *out);
 
 /* Synchronous: waits for the stream, returns and clears the device status. */
 VICP_API vicp_status vicp_sync(vicp_ctx *ctx);

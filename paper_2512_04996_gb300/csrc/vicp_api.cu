@@ -83,6 +83,17 @@ struct vicp_ctx {
     Buf fslots, fcount, fover;
     unsigned fixed_C = 0;
     bool fixed_built = false;
+    // sparse grid (VICP_FLAG_SPARSE_GRID): hashed occupied voxels (keys of the
+    // current and of the next build, counts, offsets by slot; the scan's slot
+    // occupancy bits and tile state) and hashed labelled voxels (keys, root
+    // keys, per-block counts of pass Z + its overflow flag), instead of the
+    // V-sized counts, offsets, root and ring arrays
+    Buf okeys[2], ocount, ooff, socc[2], stile, sdesc, pslot;
+    Buf lkeys, lroot, lparts;
+    long long cap_o = 0, cap_l = 0;   // slots (powers of two)
+    int o_cur = 0;
+    long long cap_occV = -1;
+    long long lab_count = 0;          // labelled voxels of the last dilation
 
     // accounting / timing
     int64_t launches = 0;
@@ -213,21 +224,50 @@ vicp_status launch(vicp_ctx *c, int kernel, F &&f)
 
 DevCtl *ctl_of(vicp_ctx *c) { return static_cast<DevCtl *>(c->ctl.p); }
 
+bool sparse_of(const vicp_ctx *c) { return (c->params.flags & VICP_FLAG_SPARSE_GRID) != 0; }
+
+long long pow2_at_least(long long x)
+{
+    long long p = 1;
+    while (p < x)
+        p <<= 1;
+    return p;
+}
+
+HashTable table_of(const Buf &keys, long long slots)
+{
+    int lg = 0;
+    while ((1ll << lg) < slots)
+        ++lg;
+    return HashTable{static_cast<unsigned *>(keys.p), (unsigned)(slots - 1), 32 - lg};
+}
+
+// The scan over the occupied-voxel table runs on its slots as if they were
+// voxels.
+GridGeom slot_geom(long long slots)
+{
+    GridGeom g{};
+    g.V = slots;
+    return g;
+}
+
 // --- workspace sizing ------------------------------------------------------
 vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
 {
-    if (V > c->cap_V) {
+    if (V > c->cap_occV) {   // voxel occupancy bits: both grids (the dilation reads them)
+        for (Buf &o : c->occ) {
+            TRY(buf_alloc(c, o, (size_t)occ_words(V) * 4, "occupancy"));
+            TRY(buf_zero(c, o, "zero occupancy"));
+        }
+        c->cap_occV = V;
+    }
+    if (!sparse_of(c) && V > c->cap_V) {   // the dense grid's per-voxel arrays
         TRY(buf_alloc(c, c->counts, (size_t)V * 4, "counts"));
         TRY(buf_zero(c, c->counts, "zero counts"));   // counts are kept at zero between builds
         TRY(buf_alloc(c, c->off, (size_t)(V + 1) * 4, "offsets"));
         TRY(buf_alloc(c, c->root, (size_t)V * 4, "root"));
         TRY(buf_alloc(c, c->ring, (size_t)V, "ring"));
         c->labels_clean = false;
-        TRY(buf_alloc(c, c->inter, (size_t)V * 4, "dilation pass-Y words"));
-        for (Buf &o : c->occ) {
-            TRY(buf_alloc(c, o, (size_t)occ_words(V) * 4, "occupancy"));
-            TRY(buf_zero(c, o, "zero occupancy"));
-        }
         TRY(buf_alloc(c, c->desc, (size_t)scan_tiles(V) * 8, "scan descriptors"));
         TRY(buf_zero(c, c->desc, "zero scan descriptors"));
         TRY(buf_alloc(c, c->tile_sum, (size_t)scan_tiles(V) * 4, "scan tile sums"));
@@ -237,7 +277,7 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
     if (dilate_units(c->geom) * 4 > (long long)c->uflag.bytes) {
         TRY(buf_alloc(c, c->uflag, (size_t)dilate_units(c->geom) * 4, "dilation row masks"));
     }
-    if (dilate_column_units(c->geom) > (long long)c->zdirty.bytes) {
+    if (!sparse_of(c) && dilate_column_units(c->geom) > (long long)c->zdirty.bytes) {
         TRY(buf_alloc(c, c->zdirty, (size_t)dilate_column_units(c->geom), "dilation label flags"));
         c->labels_clean = false;
     }
@@ -260,6 +300,52 @@ vicp_status ensure_voxel_buffers(vicp_ctx *c, long long V, long long n_bricks)
         TRY(buf_zero(c, c->sb_left, "zero super-brick counts"));   // kept at zero between builds
         c->cap_bricks = n_bricks;
     }
+    return VICP_OK;
+}
+
+// The sparse grid's occupied-voxel table: at least twice as many slots as
+// target points (a voxel holds at least one), so it is at most half full.
+vicp_status ensure_sparse_buffers(vicp_ctx *c, long long n)
+{
+    const long long slots = pow2_at_least(n * 2 > 1024 ? n * 2 : 1024);
+    if (slots > c->cap_o) {
+        for (Buf &k : c->okeys) {
+            TRY(buf_alloc(c, k, (size_t)slots * 4, "occupied-voxel table"));
+            const cudaError_t e = cudaMemsetAsync(k.p, 0xff, k.bytes, c->stream);   // empty
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "occupied-voxel table");
+        }
+        TRY(buf_alloc(c, c->ocount, (size_t)slots * 4, "occupied-voxel counts"));
+        TRY(buf_zero(c, c->ocount, "zero occupied-voxel counts"));   // kept at zero between builds
+        TRY(buf_alloc(c, c->ooff, (size_t)(slots + 1) * 4, "occupied-voxel offsets"));
+        for (Buf &o : c->socc) {
+            TRY(buf_alloc(c, o, (size_t)occ_words(slots) * 4, "slot occupancy"));
+            TRY(buf_zero(c, o, "zero slot occupancy"));
+        }
+        TRY(buf_alloc(c, c->stile, (size_t)scan_tiles(slots) * 4, "slot scan tile sums"));
+        TRY(buf_zero(c, c->stile, "zero slot scan tile sums"));
+        TRY(buf_alloc(c, c->sdesc, (size_t)scan_tiles(slots) * 8, "slot scan descriptors"));
+        TRY(buf_zero(c, c->sdesc, "zero slot scan descriptors"));
+        c->cap_o = slots;
+        c->o_cur = 0;
+    }
+    if (n * 4 > (long long)c->pslot.bytes)
+        TRY(buf_alloc(c, c->pslot, (size_t)n * 4, "point slots"));
+    return VICP_OK;
+}
+
+// The labelled-voxel table with `slots` slots (keys are cleared by the
+// dilation itself), and pass Z's per-block counts + overflow flag.
+vicp_status ensure_label_table(vicp_ctx *c, long long slots, int L)
+{
+    if (slots > c->cap_l) {
+        TRY(buf_alloc(c, c->lkeys, (size_t)slots * 4, "labelled-voxel table"));
+        TRY(buf_alloc(c, c->lroot, (size_t)slots * 4, "labelled-voxel roots"));
+        c->cap_l = slots;
+    }
+    const size_t parts = (size_t)(dilate_hashed_blocks(c->geom, L) + 1) * 4;
+    if (parts > c->lparts.bytes)
+        TRY(buf_alloc(c, c->lparts, parts, "labelled-voxel counts"));
     return VICP_OK;
 }
 
@@ -379,16 +465,32 @@ vicp_status read_device_status(vicp_ctx *c)
     return VICP_OK;
 }
 
-// Correspond + global search into nn/d2 (shared by vicp_correspond and the step).
-vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, int *nn, float *d2, int honor_stop)
+// The localised search (Alg. 4's root-voxel scan) on the dense or the
+// sparse grid.
+vicp_status run_localised(vicp_ctx *c, const float4 *src, int m, const double *pose, int *nn, float *d2,
+                          int honor_stop)
 {
     const GridGeom &g = c->geom;
     DevCtl *d = ctl_of(c);
-    TRY(launch(c, K_CORRESPOND, [&] {
+    if (sparse_of(c))
+        return launch(c, K_CORRESPOND, [&] {
+            return launch_correspond_hashed(src, m, pose, g, table_of(c->lkeys, c->cap_l), (const int *)c->lroot.p,
+                                            table_of(c->okeys[c->o_cur], c->cap_o), (const unsigned *)c->ooff.p,
+                                            (const float4 *)c->csr.p, c->n_target, nn, d2, (int *)c->fb_list.p,
+                                            (int *)c->hv_list.p, (uint2 *)c->hv_range.p, d, honor_stop, c->stream);
+        });
+    return launch(c, K_CORRESPOND, [&] {
         return launch_correspond(src, m, pose, g, (const int *)c->root.p, (const unsigned *)c->off.p,
                                  (const float4 *)c->csr.p, c->n_target, nn, d2, (int *)c->fb_list.p,
                                  (int *)c->hv_list.p, (uint2 *)c->hv_range.p, d, honor_stop, c->stream);
-    }));
+    });
+}
+
+// Correspond + global search into nn/d2 (shared by vicp_correspond and the step).
+vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, int *nn, float *d2, int honor_stop)
+{
+    DevCtl *d = ctl_of(c);
+    TRY(run_localised(c, src, m, pose, nn, d2, honor_stop));
     TRY(launch(c, K_FALLBACK, [&] {
         return launch_fallback(src, pose, (const float4 *)c->bpts.p, (const float4 *)c->brick_box.p,
                                (const float4 *)c->sb_box.p, c->target, c->n_target, (const int *)c->outside.p,
@@ -432,25 +534,40 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
         TRY(set_geometry(c, c->params.origin, c->params.voxel_size, c->params.dims));
     }
     const GridGeom &g = c->geom;
+    const bool sparse = sparse_of(c);
     TRY(ensure_voxel_buffers(c, g.V, brick_slots(g)));
     TRY(ensure_point_buffers(c, n));
+    if (sparse)
+        TRY(ensure_sparse_buffers(c, n));
     DevCtl *d = ctl_of(c);
     // this build fills the zeroed occupancy buffer; its scatter clears the other
     c->occ_cur ^= 1;
     unsigned *occ = (unsigned *)c->occ[c->occ_cur].p;
     Buf &occ_next = c->occ[c->occ_cur ^ 1];
     const bool after_solve = c->after_solve;
+    // the sparse grid likewise fills the empty occupied-voxel table and the
+    // zeroed slot occupancy bits that the previous scatter left, and its
+    // scatter resets the others for the next build
+    if (sparse)
+        c->o_cur ^= 1;
+    const HashTable ho = sparse ? table_of(c->okeys[c->o_cur], c->cap_o) : HashTable{};
+    unsigned *counts = (unsigned *)(sparse ? c->ocount.p : c->counts.p);
+    unsigned *off = (unsigned *)(sparse ? c->ooff.p : c->off.p);
+    unsigned *tiles = (unsigned *)(sparse ? c->stile.p : c->tile_sum.p);
+    unsigned *socc = sparse ? (unsigned *)c->socc[c->o_cur].p : nullptr;
     TRY(launch(c, K_HISTOGRAM, [&] {
-        return launch_histogram(tgt, n, g, (int *)c->keys.p, (unsigned *)c->counts.p, (unsigned *)c->bcounts.p, occ,
-                                (unsigned *)c->tile_sum.p, (unsigned *)c->sb_left.p,
-                                (unsigned *)c->boxk[c->occ_cur].p, d, c->stream, after_solve);
+        return launch_histogram(tgt, n, g, (int *)c->keys.p, counts, (unsigned *)c->bcounts.p, occ, tiles,
+                                (unsigned *)c->sb_left.p, (unsigned *)c->boxk[c->occ_cur].p, d, c->stream, after_solve,
+                                sparse ? &ho : nullptr, socc, (int *)c->pslot.p);
     }));
     cudaError_t ev = cudaEventRecord(c->ev_hist, c->stream);   // the dilation may start from here
     if (ev != cudaSuccess)
         return cuda_fail(c, ev, "event record");
     TRY(launch(c, K_SCAN, [&] {
-        return launch_scan((const unsigned *)c->counts.p, g, (unsigned *)c->off.p, occ,
-                           (const unsigned *)c->tile_sum.p, (unsigned long long *)c->desc.p, d, c->stream, false);
+        if (sparse)
+            return launch_scan(counts, slot_geom(c->cap_o), off, socc, tiles, (unsigned long long *)c->sdesc.p, d,
+                               c->stream, false);
+        return launch_scan(counts, g, off, occ, tiles, (unsigned long long *)c->desc.p, d, c->stream, false);
     }));
     c->off_dense = false;
     TRY(launch(c, K_BRICK_SCAN, [&] {
@@ -458,19 +575,69 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
                                  (uint2 *)c->brick_range.p, (int *)c->bslot.p, d, c->stream);
     }));
     TRY(launch(c, K_SCATTER, [&] {
-        return launch_scatter(tgt, (const int *)c->keys.p, n, g, (const unsigned *)c->off.p, (unsigned *)c->counts.p,
-                              (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p, (const int *)c->bslot.p,
-                              (const unsigned *)c->boxk[c->occ_cur].p, (unsigned *)c->boxk[c->occ_cur ^ 1].p,
-                              (long long)(c->boxk[c->occ_cur ^ 1].bytes / 4), (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p, (unsigned *)c->sb_left.p,
-                              (float4 *)c->sb_box.p,
-                              (int *)c->ids.p, (float4 *)c->csr.p, (float4 *)c->bpts.p,
-                              (int *)c->outside.p, (unsigned *)c->tile_sum.p, (unsigned *)occ_next.p,
-                              (long long)(occ_next.bytes / 4), d, c->stream);
+        const int *idx = (const int *)(sparse ? c->pslot.p : c->keys.p);   // what indexes the counts
+        return launch_scatter(tgt, idx, n, g, off, counts, (const unsigned *)c->boff.p, (unsigned *)c->bcounts.p,
+                              (const int *)c->bslot.p, (const unsigned *)c->boxk[c->occ_cur].p,
+                              (unsigned *)c->boxk[c->occ_cur ^ 1].p, (long long)(c->boxk[c->occ_cur ^ 1].bytes / 4),
+                              (const uint2 *)c->brick_range.p, (float4 *)c->brick_box.p, (unsigned *)c->sb_left.p,
+                              (float4 *)c->sb_box.p, (int *)c->ids.p, (float4 *)c->csr.p, (float4 *)c->bpts.p,
+                              (int *)c->outside.p, tiles, (unsigned *)occ_next.p, (long long)(occ_next.bytes / 4), d,
+                              c->stream, sparse ? scan_tiles(c->cap_o) : -1,
+                              sparse ? (unsigned *)c->okeys[c->o_cur ^ 1].p : nullptr, sparse ? c->cap_o : 0,
+                              sparse ? (unsigned *)c->socc[c->o_cur ^ 1].p : nullptr,
+                              sparse ? occ_words(c->cap_o) : 0);
     }));
     c->built = true;
     c->dilated_L = -1;
     c->n_target = n;
     c->target = tgt;
+    return VICP_OK;
+}
+
+// The sparse grid's dilation (on the side stream, after the waits of
+// dilate()): pass Z inserts the labelled voxels into the labelled-voxel
+// table, then the host checks that the table had room at most half full --
+// one synchronisation per dilation -- and, if not, grows it to twice the
+// labelled count and runs the dilation again.
+vicp_status dilate_sparse(vicp_ctx *c, int L)
+{
+    const GridGeom &g = c->geom;
+    long long slots = c->cap_l > 0 ? c->cap_l : pow2_at_least(c->n_target * 2 > 4096 ? (long long)c->n_target * 2 : 4096);
+    const int blocks = dilate_hashed_blocks(g, L);
+    for (int attempt = 0;; ++attempt) {
+        TRY(ensure_label_table(c, slots, L));
+        cudaError_t e = cudaMemsetAsync(c->lparts.p, 0, (size_t)(blocks + 1) * 4, c->side);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "labelled-voxel counts");
+        TRY(launch_on(c, K_DILATE, c->side, [&] {
+            return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
+                                        (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (int *)c->lroot.p,
+                                        (unsigned *)c->lparts.p, c->side);
+        }));
+        std::vector<unsigned> parts((size_t)blocks + 1);
+        e = cudaMemcpyAsync(parts.data(), c->lparts.p, parts.size() * 4, cudaMemcpyDeviceToHost, c->side);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->side);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "labelled-voxel count read-back");
+        long long count = 0;
+        for (int b = 0; b < blocks; ++b)
+            count += parts[b];
+        const bool overflow = parts[blocks] != 0;
+        if (!overflow && 2 * count <= c->cap_l) {
+            c->lab_count = count;
+            break;
+        }
+        if (attempt >= 3)
+            return fail(c, VICP_ERR_CUDA, "labelled-voxel table: %lld voxels do not fit %lld slots", count, c->cap_l);
+        slots = pow2_at_least(2 * count > 2 * c->cap_l ? 2 * count : 2 * c->cap_l);
+    }
+    cudaError_t e = cudaEventRecord(c->ev_dil, c->side);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->stream, c->ev_dil, 0);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream wait");
+    c->dilated_L = L;
     return VICP_OK;
 }
 
@@ -496,12 +663,18 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     if (L > DILATE_MAX_L)
         return fail(c, VICP_ERR_INVALID, "dilation layers must be in [0, %d]", DILATE_MAX_L);
     const GridGeom &g = c->geom;
+    // pass-Y words: 16 bits a voxel while L <= 15, else 32
+    const size_t inter_bytes = (size_t)g.V * (L <= 15 ? 2 : 4);
+    if (c->inter.bytes < inter_bytes)
+        TRY(buf_alloc(c, c->inter, inter_bytes, "dilation pass-Y words"));
     // on the side stream, after the histogram and after the last search
     cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_hist, 0);
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(c->side, c->ev_nns, 0);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "stream wait");
+    if (sparse_of(c))
+        return dilate_sparse(c, L);
     if (!c->labels_clean || c->lab_dims[0] != g.nx || c->lab_dims[1] != g.ny || c->lab_dims[2] != g.nz) {
         // new arrays or new dimensions: every voxel "unlabelled" (all bytes 0xff), no labels recorded
         e = cudaMemsetAsync(c->root.p, 0xff, (size_t)g.V * 4, c->side);
@@ -572,6 +745,40 @@ vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float 
         *iters_out = loop.iters;
     if (rmse_out)
         *rmse_out = loop.last;
+    return st;
+}
+
+// The sparse grid's memory accounting: the same figures as the dense
+// grid's, from the occupied-voxel table (its slot offsets are valid at
+// occupied slots and just past them).  Synchronous.
+vicp_status memory_report_sparse(vicp_ctx *c, vicp_memory *out)
+{
+    const GridGeom &g = c->geom;
+    DevCtl *d = ctl_of(c);
+    TRY(launch(c, K_MAXCOUNT, [&] {
+        return launch_maxcount((const unsigned *)c->ooff.p, slot_geom(c->cap_o), d, c->stream,
+                               (const unsigned *)c->okeys[c->o_cur].p);
+    }));
+    unsigned mc[2] = {0, 0};
+    uint32_t stored = 0;
+    int32_t nbricks = 0;
+    cudaError_t e = cudaMemcpyAsync(mc, &d->max_count, sizeof mc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nbricks, &d->n_bricks, sizeof nbricks, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&stored, (const unsigned *)c->ooff.p + c->cap_o, 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "memory report read-back");
+    vicp_status st = read_device_status(c);
+    const uint64_t V = (uint64_t)g.V, So = (uint64_t)c->cap_o, Sl = (uint64_t)c->cap_l;
+    out->static_bytes = So * 4 * 3 + 4;   // occupied-voxel table: keys, counts, offsets
+    out->csr_store_bytes = So * 4 * 2 + 4 + (uint64_t)stored * 4 + Sl * 8;   // + ids + labelled-voxel table
+    out->max_voxel_count = mc[0];
+    out->occupied_voxels = mc[1];
+    out->nonempty_bricks = (uint32_t)nbricks;
+    out->fixed_capacity_bytes = V * (uint64_t)mc[0] * 4;
+    out->paper_static_layout_bytes = V * 65536ull;
+    out->labelled_voxels = (uint32_t)c->lab_count;
     return st;
 }
 
@@ -680,7 +887,9 @@ void vicp_destroy(vicp_ctx *c)
                   &c->boxk[0], &c->boxk[1], &c->sb_box,     &c->sb_left,    &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
                   &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
-                  &c->hsrc,    &c->htgt,    &c->fslots,   &c->fcount,   &c->fover};
+                  &c->hsrc,    &c->htgt,    &c->fslots,   &c->fcount,   &c->fover,
+                  &c->okeys[0], &c->okeys[1], &c->ocount, &c->ooff, &c->socc[0], &c->socc[1], &c->stile, &c->sdesc,
+                  &c->pslot,   &c->lkeys,   &c->lroot,    &c->lparts};
     for (Buf *b : all)
         buf_free(c, *b);
     for (auto &t : c->pending) {
@@ -740,12 +949,7 @@ vicp_status vicp_correspond(vicp_ctx *c, const float *src_xyzw, int32_t n_src, c
     if (n_fallback_out) {
         // fb_count is zero between searches; the correspond kernel counts this
         // search's global queries and the fallback kernel clears it again.
-        TRY(launch(c, K_CORRESPOND, [&] {
-            return launch_correspond(src, n_src, pose_dev, c->geom, (const int *)c->root.p,
-                                     (const unsigned *)c->off.p, (const float4 *)c->csr.p, c->n_target, nn_out,
-                                     d2_out, (int *)c->fb_list.p, (int *)c->hv_list.p, (uint2 *)c->hv_range.p, d,
-                                     0, c->stream);
-        }));
+        TRY(run_localised(c, src, n_src, pose_dev, nn_out, d2_out, 0));
         cudaError_t e = cudaMemcpyAsync(n_fallback_out, &d->fb_count, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                         c->stream);
         if (e != cudaSuccess)
@@ -826,6 +1030,8 @@ vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
         return VICP_ERR_INVALID;
     if (!c->built)
         return fail(c, VICP_ERR_STATE, "no grid built");
+    if (sparse_of(c))
+        return fail(c, VICP_ERR_STATE, "the sparse grid has no dense arrays: use vicp_get_sparse_grid");
     const GridGeom &g = c->geom;
     std::memset(out, 0, sizeof *out);
     out->origin[0] = g.ox;
@@ -856,6 +1062,47 @@ vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
     return st;
 }
 
+vicp_status vicp_get_sparse_grid(vicp_ctx *c, vicp_sparse_view *out)
+{
+    if (!c || !out)
+        return VICP_ERR_INVALID;
+    if (!sparse_of(c))
+        return fail(c, VICP_ERR_STATE, "not a sparse-grid context (VICP_FLAG_SPARSE_GRID)");
+    if (!c->built)
+        return fail(c, VICP_ERR_STATE, "no grid built");
+    const GridGeom &g = c->geom;
+    std::memset(out, 0, sizeof *out);
+    for (int a = 0; a < 3; ++a)
+        out->origin[a] = a == 0 ? g.ox : (a == 1 ? g.oy : g.oz);
+    out->voxel_size = g.h;
+    out->inv_voxel_size = g.inv_h;
+    out->dims[0] = g.nx;
+    out->dims[1] = g.ny;
+    out->dims[2] = g.nz;
+    out->n_voxels = g.V;
+    out->n_target = c->n_target;
+    out->dilation_layers = c->dilated_L;
+    uint32_t stored = 0;
+    cudaError_t e = cudaMemcpyAsync(&stored, (const unsigned *)c->ooff.p + c->cap_o, 4, cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "read n_stored");
+    vicp_status st = read_device_status(c);
+    out->n_stored = (int32_t)stored;
+    out->occupied_slots = c->cap_o;
+    out->occupied_keys = (const uint32_t *)c->okeys[c->o_cur].p;
+    out->occupied_offsets = (const uint32_t *)c->ooff.p;
+    out->labelled_slots = c->dilated_L >= 0 ? c->cap_l : 0;
+    out->labelled_keys = c->dilated_L >= 0 ? (const uint32_t *)c->lkeys.p : nullptr;
+    out->labelled_root = c->dilated_L >= 0 ? (const int32_t *)c->lroot.p : nullptr;
+    out->labelled_voxels = c->dilated_L >= 0 ? c->lab_count : 0;
+    out->keys = (const int32_t *)c->keys.p;
+    out->ids = (const int32_t *)c->ids.p;
+    out->csr_points = (const float *)c->csr.p;
+    out->occupancy = (const uint32_t *)c->occ[c->occ_cur].p;
+    return st;
+}
+
 vicp_status vicp_sync(vicp_ctx *c)
 {
     if (!c)
@@ -877,6 +1124,8 @@ vicp_status vicp_memory_report(vicp_ctx *c, vicp_memory *out)
     cudaError_t e = cudaMemsetAsync(&d->max_count, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "memory report");
+    if (sparse_of(c))
+        return memory_report_sparse(c, out);
     TRY(dense_offsets(c));
     TRY(launch(c, K_MAXCOUNT, [&] { return launch_maxcount((const unsigned *)c->off.p, g, d, c->stream); }));
     unsigned mc[2] = {0, 0};
@@ -914,6 +1163,8 @@ vicp_status vicp_fixed_build(vicp_ctx *c, const float *target_xyzw, int32_t n, i
 {
     if (!c)
         return VICP_ERR_INVALID;
+    if (sparse_of(c))
+        return fail(c, VICP_ERR_STATE, "the fixed-capacity store needs the dense grid's labels");
     TRY(check_cloud(c, target_xyzw, n, "target"));
     if (capacity < 1)
         return fail(c, VICP_ERR_INVALID, "capacity must be >= 1");

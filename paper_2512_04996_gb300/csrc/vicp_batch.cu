@@ -473,8 +473,8 @@ __global__ void __launch_bounds__(dil::THREADS) k_batch_dilate_z(const typename 
         const long long vb = pairs[p].vbase;
         const int nxb = (g.nx + dil::UX - 1) / dil::UX, nyb = (g.ny + dil::UY - 1) / dil::UY;
         const int u0 = starts[p];
-        dil::dilate_z_unit<W>(u - u0, inter + vb, rows + __ldg(ustart_xy + p), dirty + u0, g, L, nxb, nyb, root + vb,
-                              ring + vb);
+        dil::dilate_z_unit<W>(u - u0, inter + vb, rows + __ldg(ustart_xy + p),
+                              dil::DenseLabels{dirty + u0, root + vb, ring + vb}, g, L, nxb, nyb);
     }
 }
 

@@ -53,6 +53,7 @@ constexpr int SUPER_BRICKS = SUPER * SUPER * SUPER;
 constexpr unsigned DEVERR_TIMEOUT = 1u;      // a bounded wait gave up
 constexpr unsigned DEVERR_DEGENERATE = 2u;   // rank(H) < 2 in a solve
 constexpr unsigned DEVERR_BOUNDS = 4u;       // an index failed its bounds check (write skipped)
+constexpr unsigned DEVERR_CAPACITY = 8u;     // a hashed voxel table could not take a key (insert skipped)
 
 // Per-context control block in device memory.  Kernels of one stream use it
 // in launch order; the comments say which kernel writes each field.
@@ -166,6 +167,58 @@ __device__ __forceinline__ int brick_key(const GridGeom &g, int ix, int iy, int 
 
 // Length of the brick index space (padded to whole super-bricks).
 __host__ __device__ __forceinline__ int brick_slots(const GridGeom &g) { return g.sx * g.sy * g.sz * SUPER_BRICKS; }
+
+// ---------------------------------------------------------------------------
+// Hashed voxel tables (the sparse grid): open addressing with linear
+// probing over a power-of-two number of slots, keyed by voxel key (>= 0);
+// an empty slot holds HASH_EMPTY.  The home slot is the top bits of the key
+// times 2^32 / golden ratio (Fibonacci hashing), so that neighbouring voxel
+// keys land far apart.
+// ---------------------------------------------------------------------------
+constexpr unsigned HASH_EMPTY = 0xffffffffu;
+// Longest probe sequence: an insert that meets this many other keys gives up
+// (the table is too full; the library keeps tables at most half full, where
+// linear probing's runs stay far shorter), and a lookup never looks further.
+constexpr unsigned HASH_MAX_PROBE = 256u;
+
+struct HashTable {
+    unsigned *keys;   // [mask + 1]
+    unsigned mask;    // slots - 1
+    int shift;        // 32 - log2(slots)
+};
+
+__host__ __device__ __forceinline__ unsigned hash_home(unsigned key, unsigned mask, int shift)
+{
+    return shift >= 32 ? 0u : ((key * 2654435769u) >> shift) & mask;
+}
+
+// Slot of `key`, inserted if absent; -1 after HASH_MAX_PROBE slots taken by
+// other keys (the caller records DEVERR_CAPACITY).
+__device__ __forceinline__ int hash_insert(const HashTable &h, unsigned key)
+{
+    unsigned s = hash_home(key, h.mask, h.shift);
+    for (unsigned probe = 0; probe <= h.mask && probe < HASH_MAX_PROBE; ++probe, s = (s + 1u) & h.mask) {
+        const unsigned k = atomicCAS(h.keys + s, HASH_EMPTY, key);
+        if (k == HASH_EMPTY || k == key)
+            return (int)s;
+    }
+    return -1;
+}
+
+// Slot of `key`, or -1 if it is absent (the probe stops at the first empty
+// slot, or where an insert would have given up).
+__device__ __forceinline__ int hash_find(const unsigned *__restrict__ keys, unsigned mask, int shift, unsigned key)
+{
+    unsigned s = hash_home(key, mask, shift);
+    for (unsigned probe = 0; probe <= mask && probe < HASH_MAX_PROBE; ++probe, s = (s + 1u) & mask) {
+        const unsigned k = __ldg(keys + s);
+        if (k == key)
+            return (int)s;
+        if (k == HASH_EMPTY)
+            return -1;
+    }
+    return -1;
+}
 
 // Floats mapped to unsigned integers whose order matches the float order, so
 // atomicMin/atomicMax reduce them (and back).

@@ -49,13 +49,18 @@ namespace vicp {
 
 using namespace dil;
 
+// `clear` (sparse grid: the labelled-voxel table's keys, which pass Z fills)
+// is set to HASH_EMPTY on the way: pass Z starts only after this kernel.
 template <class W>
 __global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restrict__ occ, long long n_words, GridGeom g,
                                                        int L, int nxb, int nyb, int units,
                                                        typename W::Stored *__restrict__ inter,
-                                                       unsigned *__restrict__ rows)
+                                                       unsigned *__restrict__ rows, unsigned *__restrict__ clear,
+                                                       long long clear_words)
 {
     pdl_begin();
+    for (long long w = (long long)blockIdx.x * THREADS + threadIdx.x; w < clear_words; w += (long long)gridDim.x * THREADS)
+        clear[w] = HASH_EMPTY;
     for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
         dilate_xy_unit<W>(u, occ, n_words, g, L, nxb, nyb, inter, rows);
 }
@@ -68,8 +73,35 @@ __global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *
                                                       unsigned char *__restrict__ ring)
 {
     pdl_begin();
+    const DenseLabels out{dirty, root, ring};
     for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
-        dilate_z_unit<W>(u, inter, rows, dirty, g, L, nxb, nyb, root, ring);
+        dilate_z_unit<W>(u, inter, rows, out, g, L, nxb, nyb);
+}
+
+// Pass Z into the labelled-voxel table; each block writes the number of
+// voxels it labelled to counts[blockIdx.x], and counts[gridDim.x] (zero
+// beforehand) is set to 1 if an insert gave up.
+template <class W>
+__global__ void __launch_bounds__(THREADS) k_dilate_z_hashed(const typename W::Stored *__restrict__ inter,
+                                                             const unsigned *__restrict__ rows, GridGeom g, int L,
+                                                             int nxb, int nyb, int units, HashTable table,
+                                                             int *__restrict__ root, unsigned *__restrict__ counts)
+{
+    pdl_begin();
+    __shared__ unsigned s_count;
+    if (threadIdx.x == 0)
+        s_count = 0u;
+    __syncthreads();
+    const HashLabels out{table, root, counts + gridDim.x};
+    unsigned n = 0u;
+    for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
+        n += dilate_z_unit<W>(u, inter, rows, out, g, L, nxb, nyb);
+    n = __reduce_add_sync(FULL_MASK, n);
+    if ((threadIdx.x & 31) == 0 && n)
+        atomicAdd(&s_count, n);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        counts[blockIdx.x] = s_count;
 }
 
 // Blocks that can be resident at once (the kernels loop over their units).
@@ -86,19 +118,34 @@ static int resident_blocks(K kernel)
 
 template <class W>
 static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
-                              unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st)
+                              unsigned char *dirty, int *root, unsigned char *ring, const HashTable *labels,
+                              unsigned *counts, cudaStream_t st)
 {
     using S = typename W::Stored;
-    static const int xy_blocks = resident_blocks(k_dilate_xy<W>), z_blocks = resident_blocks(k_dilate_z<W>);
+    static const int xy_blocks = resident_blocks(k_dilate_xy<W>), z_blocks = resident_blocks(k_dilate_z<W>),
+                     zh_blocks = resident_blocks(k_dilate_z_hashed<W>);
     const int nxb = (g.nx + UX - 1) / UX, nyb = (g.ny + UY - 1) / UY, nzb = (g.nz + UZ - 1) / UZ;
     const int u_xy = nxb * nyb * g.nz;   // < V < 2^31
     cudaError_t e = launch_kernel(k_dilate_xy<W>, dim3(min(xy_blocks, (u_xy + WARPS - 1) / WARPS)), dim3(THREADS), 0,
-                                  st, occ, occ_words(g.V), g, L, nxb, nyb, u_xy, static_cast<S *>(inter), rows);
+                                  st, occ, occ_words(g.V), g, L, nxb, nyb, u_xy, static_cast<S *>(inter), rows,
+                                  labels ? labels->keys : nullptr, labels ? (long long)labels->mask + 1 : 0ll);
     if (e != cudaSuccess)
         return e;
     const int u_z = nxb * g.ny * nzb;   // < V < 2^31
+    if (labels)
+        return launch_kernel(k_dilate_z_hashed<W>, dim3(min(zh_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0,
+                             st, static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, *labels, root, counts);
     return launch_kernel(k_dilate_z<W>, dim3(min(z_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0, st,
                          static_cast<const S *>(inter), rows, dirty, g, L, nxb, nyb, u_z, root, ring);
+}
+
+int dilate_hashed_blocks(const GridGeom &g, int L)
+{
+    const int nxb = (g.nx + UX - 1) / UX, nzb = (g.nz + UZ - 1) / UZ;
+    const int u_z = nxb * g.ny * nzb;
+    const int res = L <= L_COMPACT_MAX ? resident_blocks(k_dilate_z_hashed<Words16>)
+                                       : resident_blocks(k_dilate_z_hashed<Words32>);
+    return min(res, (u_z + WARPS - 1) / WARPS);
 }
 
 long long dilate_units(const GridGeom &g)
@@ -115,8 +162,16 @@ cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *i
                           unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st)
 {
     if (L <= L_COMPACT_MAX)
-        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, st);
-    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, st);
+        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, st);
+}
+
+cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
+                                 const HashTable &labels, int *root, unsigned *counts, cudaStream_t st)
+{
+    if (L <= L_COMPACT_MAX)
+        return run_dilate<Words16>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, st);
 }
 
 }  // namespace vicp

@@ -212,6 +212,22 @@ __device__ __forceinline__ void dilate_xy_unit(int u, const unsigned *__restrict
     }
 }
 
+// Where pass Z puts its labels: the dense root / ring arrays (with the
+// per-unit flags that let unlabelled units skip their writes), or the
+// labelled-voxel table of the sparse grid (voxel key -> root key; the ring
+// is the Manhattan distance between the two keys' voxels), which holds the
+// labelled voxels only and starts empty at every dilation.
+struct DenseLabels {
+    unsigned char *dirty;
+    int *root;
+    unsigned char *ring;
+};
+struct HashLabels {
+    HashTable table;     // keys: the labelled voxels
+    int *root;           // [slots] root key of each labelled voxel
+    unsigned *overflow;  // set to 1 when an insert gave up (the table is too small)
+};
+
 // ---------------------------------------------------------------------------
 // Pass Z and the output.  Warp u = xb + nxb*(y + ny*zb) covers x in
 // [32xb, 32xb+32) of row y, z in [32zb, 32zb+32).  Lane l reads whether row y
@@ -219,12 +235,12 @@ __device__ __forceinline__ void dilate_xy_unit(int u, const unsigned *__restrict
 // planes z0 - L + l and z0 + 32 + l; only those planes are read from the
 // intermediate array, all before the sweeps (halo planes four at a time).
 // ---------------------------------------------------------------------------
-template <class W>
-__device__ __forceinline__ void dilate_z_unit(int u, const typename W::Stored *__restrict__ inter,
-                                              const unsigned *__restrict__ rows, unsigned char *__restrict__ dirty,
-                                              const GridGeom &g, int L, int nxb, int nyb, int *__restrict__ root,
-                                              unsigned char *__restrict__ ring)
+template <class W, class Out = DenseLabels>
+__device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Stored *__restrict__ inter,
+                                                  const unsigned *__restrict__ rows, const Out &out, const GridGeom &g,
+                                                  int L, int nxb, int nyb)
 {
+    constexpr bool HASHED = !__is_same(Out, DenseLabels);
     constexpr unsigned STEP_ZF = (1u << W::ZD) - (1u << W::ZZ);   // moved from z-1 to z: dz -= 1
     constexpr unsigned STEP_ZB = (1u << W::ZD) + (1u << W::ZZ);   // moved from z+1 to z: dz += 1
     const int lane = threadIdx.x & 31;
@@ -247,22 +263,27 @@ __device__ __forceinline__ void dilate_z_unit(int u, const typename W::Stored *_
             set = (__ldg(rows + (z * nyb + yb) * nxb + xb) >> ybit) & 1u;
         pm[j] = __ballot_sync(FULL_MASK, set);
     }
-    // A unit with nothing within L keeps "unlabelled" unless the previous
-    // dilation labelled some of its voxels; those are reset here.
     const bool labels = (pm[0] | pm[1] | pm[2]) != 0u;
-    const bool was = __ldg(dirty + u) != 0;
-    if (lane == 0 && labels != was)
-        dirty[u] = labels ? 1 : 0;
-    if (x >= g.nx || !(labels || was))
-        return;
-    if (!labels) {
-        int v = col + plane * z0;
+    if constexpr (HASHED) {
+        if (x >= g.nx || !labels)
+            return 0u;
+    } else {
+        // A unit with nothing within L keeps "unlabelled" unless the previous
+        // dilation labelled some of its voxels; those are reset here.
+        const bool was = __ldg(out.dirty + u) != 0;
+        if (lane == 0 && labels != was)
+            out.dirty[u] = labels ? 1 : 0;
+        if (x >= g.nx || !(labels || was))
+            return 0u;
+        if (!labels) {
+            int v = col + plane * z0;
 #pragma unroll 8
-        for (int k = 0; k < kmax; ++k, v += plane) {
-            root[v] = -1;
-            ring[v] = 255;
+            for (int k = 0; k < kmax; ++k, v += plane) {
+                out.root[v] = -1;
+                out.ring[v] = 255;
+            }
+            return 0u;
         }
-        return;
     }
 
     unsigned c[UZ];
@@ -301,15 +322,29 @@ __device__ __forceinline__ void dilate_z_unit(int u, const typename W::Stored *_
     const unsigned valid = (unsigned)(L + 1) << W::ZD;   // words below this are labels
     int v = col + plane * z0;
     const unsigned vb = (unsigned)v - W::bias((unsigned)g.nx, (unsigned)plane);
+    unsigned labelled = 0u;
 #pragma unroll
     for (int k = 0; k < UZ; ++k, v += plane) {
         if (k < kmax) {
             const unsigned w = c[k];
             const bool hit = w < valid;
-            root[v] = hit ? (int)(vb + (unsigned)plane * k + W::offset(w, (unsigned)g.nx, (unsigned)plane)) : -1;
-            ring[v] = hit ? (unsigned char)(w >> W::ZD) : (unsigned char)255;
+            const int r = (int)(vb + (unsigned)plane * k + W::offset(w, (unsigned)g.nx, (unsigned)plane));
+            if constexpr (HASHED) {
+                if (hit) {
+                    const int slot = hash_insert(out.table, (unsigned)v);
+                    if (slot >= 0)
+                        out.root[slot] = r;
+                    else
+                        atomicOr(out.overflow, 1u);
+                    ++labelled;
+                }
+            } else {
+                out.root[v] = hit ? r : -1;
+                out.ring[v] = hit ? (unsigned char)(w >> W::ZD) : (unsigned char)255;
+            }
         }
     }
+    return labelled;
 }
 
 }  // namespace dil

@@ -61,13 +61,22 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // per word) and the per-tile totals the scan starts from.  Block 0 also
 // bumps the scan's descriptor epoch and clears the outside counter for this
 // build.
+//
+// SPARSE (the hashed grid): the voxel's group leader inserts the key into the
+// occupied-voxel table `ho` (its slot is broadcast to the group and stored
+// per point in `pslot`), and the counts, the occupancy bits the scan reads
+// (`socc`) and the tile totals are indexed by that slot instead of by the
+// voxel key; the voxel occupancy bits (`occ`, read by the dilation) are set
+// as in the dense grid.
 // ---------------------------------------------------------------------------
-template <bool AFTER_SOLVE>
+template <bool AFTER_SOLVE, bool SPARSE>
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
                                                    unsigned *__restrict__ bcounts, unsigned *__restrict__ occ,
                                                    unsigned *__restrict__ tile_sum, unsigned *__restrict__ sb_left,
-                                                   unsigned *__restrict__ boxk, DevCtl *__restrict__ ctl)
+                                                   unsigned *__restrict__ boxk, DevCtl *__restrict__ ctl,
+                                                   HashTable ho, unsigned *__restrict__ socc,
+                                                   int *__restrict__ pslot)
 {
     // In the ICP loop a build follows the previous iteration's reduction and
     // solve (AFTER_SOLVE), whose single-block tail leaves the GPU idle; the
@@ -105,8 +114,21 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     }
     const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(FULL_MASK, key);
-    if (key >= 0 && lane == __ffs(peers) - 1)
-        atomicAdd(counts + key, (unsigned)__popc(peers));
+    int idx = key;   // index of the voxel's count: its key, or its slot in the table
+    if (SPARSE) {
+        int slot = -1;
+        if (key >= 0 && lane == __ffs(peers) - 1) {
+            slot = hash_insert(ho, (unsigned)key);
+            if (slot < 0)
+                atomicOr(&ctl->err, DEVERR_CAPACITY);
+        }
+        slot = __shfl_sync(FULL_MASK, slot, __ffs(peers) - 1);
+        idx = key >= 0 ? slot : key;
+        if (j < n)
+            pslot[j] = idx;   // -1 outside the grid (or, with a full table, uncounted)
+    }
+    if (idx >= 0 && lane == __ffs(peers) - 1)
+        atomicAdd(counts + idx, (unsigned)__popc(peers));
     const unsigned bpeers = __match_any_sync(FULL_MASK, bk);
     // the brick's exact bounds: the group's min and max of each coordinate
     // (order-preserving unsigned images of the floats; maxima as their
@@ -137,8 +159,15 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     const unsigned wbits = __reduce_or_sync(wpeers, key >= 0 ? 1u << (key & 31) : 0u);
     if (word >= 0 && lane == __ffs(wpeers) - 1)
         atomicOr(occ + word, wbits);
+    if (SPARSE) {   // the scan's occupancy bit of the slot
+        const int sw = idx >= 0 ? (idx >> 5) : -2;
+        const unsigned spe = __match_any_sync(FULL_MASK, sw);
+        const unsigned sbits = __reduce_or_sync(spe, idx >= 0 ? 1u << (idx & 31) : 0u);
+        if (sw >= 0 && lane == __ffs(spe) - 1)
+            atomicOr(socc + sw, sbits);
+    }
     // per-tile totals for the scan (one atomicAdd per tile and warp)
-    const int tile = key >= 0 ? (key / SCAN_TILE) : -2;
+    const int tile = idx >= 0 ? (idx / SCAN_TILE) : -2;
     const unsigned tpeers = __match_any_sync(FULL_MASK, tile);
     if (tile >= 0 && lane == __ffs(tpeers) - 1)
         atomicAdd(tile_sum + tile, (unsigned)__popc(tpeers));
@@ -146,11 +175,18 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
-                             unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve)
+                             unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve, const HashTable *ho,
+                             unsigned *socc, int *pslot)
 {
     // occ must hold zeros: the caller clears it beforehand
-    return launch_kernel(after_solve ? k_histogram<true> : k_histogram<false>, dim3((n + 255) / 256), dim3(256), 0,
-                         st, pts, n, g, keys, counts, bcounts, occ, tile_sum, sb_left, boxk, ctl);
+    const HashTable h = ho ? *ho : HashTable{nullptr, 0u, 32};
+    if (ho)
+        return launch_kernel(after_solve ? k_histogram<true, true> : k_histogram<false, true>, dim3((n + 255) / 256),
+                             dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ, tile_sum, sb_left, boxk, ctl, h,
+                             socc, pslot);
+    return launch_kernel(after_solve ? k_histogram<true, false> : k_histogram<false, false>, dim3((n + 255) / 256),
+                         dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ, tile_sum, sb_left, boxk, ctl, h,
+                         socc, pslot);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,13 +784,19 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ pts,
                                                  float4 *__restrict__ csr, float4 *__restrict__ bpts,
                                                  int *__restrict__ outside, unsigned *__restrict__ tile_sum,
                                                  int n_tiles, unsigned *__restrict__ occ_next,
-                                                 long long occ_next_words, DevCtl *__restrict__ ctl)
+                                                 long long occ_next_words, DevCtl *__restrict__ ctl,
+                                                 unsigned *__restrict__ empty_next, long long empty_next_words,
+                                                 unsigned *__restrict__ zero_next, long long zero_next_words)
 {
     pdl_begin();
     // the scan is done with the tile totals: zero them for the next build,
     // and clear the occupancy and brick-bound buffers the next build will fill
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
         tile_sum[t] = 0u;
+    for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < empty_next_words; w += gridDim.x * blockDim.x)
+        empty_next[w] = HASH_EMPTY;
+    for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < zero_next_words; w += gridDim.x * blockDim.x)
+        zero_next[w] = 0u;
     for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < boxk_words; w += gridDim.x * blockDim.x)
         boxk_next[w] = 0xffffffffu;
     for (long long w = blockIdx.x * blockDim.x + threadIdx.x; w < occ_next_words; w += gridDim.x * blockDim.x)
@@ -834,23 +876,29 @@ cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const Grid
                            const unsigned *boxk, unsigned *boxk_next, long long boxk_next_words, const uint2 *range,
                            float4 *box, unsigned *sb_left, float4 *sb_box, int *ids, float4 *csr, float4 *bpts,
                            int *outside, unsigned *tile_sum, unsigned *occ_next, long long occ_next_words,
-                           DevCtl *ctl, cudaStream_t st)
+                           DevCtl *ctl, cudaStream_t st, long long n_tiles, unsigned *empty_next,
+                           long long empty_next_words, unsigned *zero_next, long long zero_next_words)
 {
     return launch_kernel(k_scatter, dim3((n + 255) / 256), dim3(256), 0, st, pts, keys, n, g, off, counts, boff,
                          bcounts, bslot, boxk, boxk_next, boxk_next_words, range, box, sb_left, sb_box, ids, csr,
-                         bpts, outside, tile_sum, (int)scan_tiles(g.V), occ_next, occ_next_words, ctl);
+                         bpts, outside, tile_sum, (int)(n_tiles >= 0 ? n_tiles : scan_tiles(g.V)), occ_next,
+                         occ_next_words, ctl, empty_next, empty_next_words, zero_next, zero_next_words);
 }
 
 // ---------------------------------------------------------------------------
 // Memory report helper: largest voxel count and number of occupied voxels.
 // ---------------------------------------------------------------------------
+// keys (sparse grid: the occupied-voxel table, whose offsets are valid at
+// occupied slots and just past them only): empty slots are skipped.
 __global__ void __launch_bounds__(256) k_maxcount(const unsigned *__restrict__ off, long long V,
-                                                  DevCtl *__restrict__ ctl)
+                                                  DevCtl *__restrict__ ctl, const unsigned *__restrict__ keys)
 {
     pdl_begin();
     unsigned mx = 0u, occupied = 0u;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V;
          v += (long long)gridDim.x * blockDim.x) {
+        if (keys && keys[v] == HASH_EMPTY)
+            continue;
         const unsigned c = off[v + 1] - off[v];
         mx = max(mx, c);
         occupied += c != 0u;
@@ -866,12 +914,13 @@ __global__ void __launch_bounds__(256) k_maxcount(const unsigned *__restrict__ o
     }
 }
 
-cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st)
+cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st,
+                            const unsigned *keys)
 {
     long long blocks = (g.V + 255) / 256;
     if (blocks > 2432)
         blocks = 2432;
-    return launch_kernel(k_maxcount, dim3((unsigned)blocks), dim3(256), 0, st, off, g.V, ctl);
+    return launch_kernel(k_maxcount, dim3((unsigned)blocks), dim3(256), 0, st, off, g.V, ctl, keys);
 }
 
 }  // namespace vicp

@@ -72,9 +72,13 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // bounds are merged into boxk (all ones before the build).  after_solve:
 // the kernel launched just before it on `st` is the reduction + solve, and
 // the histogram does not wait for it (any other predecessor: it waits).
+// ho (the sparse grid; null: dense): counts, tile_sum and socc are indexed
+// by the voxel's slot in the occupied-voxel table ho, and pslot[j] receives
+// point j's slot (-1 outside the grid); occ is still indexed by voxel key.
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
-                             unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve);
+                             unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve,
+                             const HashTable *ho = nullptr, unsigned *socc = nullptr, int *pslot = nullptr);
 // dense: every off[v]; sparse: only off[v] and off[v + 1] of occupied voxels,
 // off[32 k] and off[V] (what the build and the searches read) -- the rest
 // is completed by launch_offsets_fill on the same occupancy bits.
@@ -88,14 +92,21 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 // next build (occ_next, occ_next_words words), writes the brick and
 // super-brick float boxes from the histogram's bounds (boxk) and sets the
 // next build's whole bound buffer (boxk_next, boxk_next_words words) to all
-// ones.
+// ones.  keys index off / counts: voxel keys (dense grid) or the points'
+// slots in the occupied-voxel table (sparse grid; n_tiles then counts the
+// slots' scan tiles, and the next build's table keys (empty_next, set to
+// HASH_EMPTY) and slot occupancy bits (zero_next, zeroed) are reset too).
 cudaError_t launch_scatter(const float4 *pts, const int *keys, int n, const GridGeom &g, const unsigned *off,
                            unsigned *counts, const unsigned *boff, unsigned *bcounts, const int *bslot,
                            const unsigned *boxk, unsigned *boxk_next, long long boxk_next_words, const uint2 *range,
                            float4 *box, unsigned *sb_left, float4 *sb_box, int *ids, float4 *csr, float4 *bpts,
                            int *outside, unsigned *tile_sum, unsigned *occ_next, long long occ_next_words,
-                           DevCtl *ctl, cudaStream_t st);
-cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st);
+                           DevCtl *ctl, cudaStream_t st, long long n_tiles = -1, unsigned *empty_next = nullptr,
+                           long long empty_next_words = 0, unsigned *zero_next = nullptr,
+                           long long zero_next_words = 0);
+// keys (may be null): the sparse grid's occupied-voxel table over g.V slots.
+cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl, cudaStream_t st,
+                            const unsigned *keys = nullptr);
 // Dilation: `inter` holds V words of pass Y (V x 4 bytes suffices for any
 // L), `rows` dilate_units(g) 32-bit row masks (neither needs clearing),
 // `dirty` dilate_column_units(g) bytes marking the column units whose voxels
@@ -103,6 +114,15 @@ cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl,
 // `dirty` is 0: clear all three when they are new or the dimensions change.
 cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
                           unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st);
+// The sparse grid's dilation: passes X and Y as above (the kernel also sets
+// the keys of `labels` to HASH_EMPTY first), then pass Z inserts every
+// labelled voxel into `labels` with its root key in root[slot]; block b of
+// pass Z writes its labelled-voxel count to counts[b], b <
+// dilate_hashed_blocks(g, L), and sets counts[dilate_hashed_blocks(g, L)]
+// (zero beforehand) to 1 if the table was too small for an insert.
+cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
+                                 const HashTable &labels, int *root, unsigned *counts, cudaStream_t st);
+int dilate_hashed_blocks(const GridGeom &g, int L);
 long long dilate_units(const GridGeom &g);
 long long dilate_column_units(const GridGeom &g);
 // The localised search lists queries whose root segment is long (with the
@@ -112,6 +132,14 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
                               int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
                               cudaStream_t st);
+// The localised search on the sparse grid: root labels from the
+// labelled-voxel table (keys in `labelled`, root keys in lroot), segments
+// [off[slot], off[slot + 1]) by the root's slot in the occupied-voxel table.
+cudaError_t launch_correspond_hashed(const float4 *src, int m, const double *pose, const GridGeom &g,
+                                     const HashTable &labelled, const int *lroot, const HashTable &occupied,
+                                     const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
+                                     int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
+                                     cudaStream_t st);
 // The localised search over a fixed-capacity store (C slots per voxel at
 // v * C, fill counts in count), listing like launch_correspond; the global
 // search then takes the slots as its dense-segment store.

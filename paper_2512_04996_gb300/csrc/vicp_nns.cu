@@ -42,10 +42,36 @@ struct FixedSeg {
     }
 };
 
-template <class Seg>
+// Root label of voxel v, as the index of its segment in the store: the
+// dense root array (the root's voxel key), or the sparse grid's two tables
+// (the labelled-voxel table gives the root's voxel key, the occupied-voxel
+// table that voxel's slot, which indexes the offsets).  -1: unlabelled.
+struct DenseRoot {
+    const int *root;
+    __device__ __forceinline__ int operator()(int v) const { return __ldg(root + v); }
+};
+
+struct HashedRoot {
+    const unsigned *lkeys;   // labelled voxels
+    unsigned lmask;
+    int lshift;
+    const int *lroot;        // their root keys
+    const unsigned *okeys;   // occupied voxels
+    unsigned omask;
+    int oshift;
+    __device__ __forceinline__ int operator()(int v) const
+    {
+        const int ls = hash_find(lkeys, lmask, lshift, (unsigned)v);
+        if (ls < 0)
+            return -1;
+        return hash_find(okeys, omask, oshift, (unsigned)__ldg(lroot + ls));
+    }
+};
+
+template <class Seg, class Root>
 __global__ void __launch_bounds__(CORR_THREADS) k_correspond(const float4 *__restrict__ src, int m,
                                                              const double *__restrict__ pose, GridGeom g,
-                                                             const int *__restrict__ root, Seg seg,
+                                                             Root root, Seg seg,
                                                              const float4 *__restrict__ csr,
                                                              int *__restrict__ nn, float *__restrict__ d2,
                                                              int *__restrict__ fb_list, int *__restrict__ hv_list,
@@ -71,7 +97,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_correspond(const float4 *__res
     if (i < m) {
         const float3 s = transform_pt(P, __ldg(src + i));
         const int v = voxel_key(g, s.x, s.y, s.z);
-        const int r = (v >= 0) ? __ldg(root + v) : -1;
+        const int r = (v >= 0) ? root(v) : -1;
         if (r >= 0) {
             seg.range(r, a, b);
             cand = b - a;
@@ -133,18 +159,31 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
                               cudaStream_t st)
 {
-    return launch_kernel(k_correspond<CsrSeg>, dim3((m + CORR_THREADS - 1) / CORR_THREADS), dim3(CORR_THREADS), 0, st,
-                         src, m, pose, g, root, CsrSeg{off, (unsigned)n_cap}, csr, nn, d2, fb_list, hv_list, hv_range,
-                         ctl, honor_stop);
+    return launch_kernel(k_correspond<CsrSeg, DenseRoot>, dim3((m + CORR_THREADS - 1) / CORR_THREADS),
+                         dim3(CORR_THREADS), 0, st, src, m, pose, g, DenseRoot{root}, CsrSeg{off, (unsigned)n_cap},
+                         csr, nn, d2, fb_list, hv_list, hv_range, ctl, honor_stop);
+}
+
+cudaError_t launch_correspond_hashed(const float4 *src, int m, const double *pose, const GridGeom &g,
+                                     const HashTable &labelled, const int *lroot, const HashTable &occupied,
+                                     const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
+                                     int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
+                                     cudaStream_t st)
+{
+    const HashedRoot root{labelled.keys, labelled.mask, labelled.shift, lroot,
+                          occupied.keys, occupied.mask, occupied.shift};
+    return launch_kernel(k_correspond<CsrSeg, HashedRoot>, dim3((m + CORR_THREADS - 1) / CORR_THREADS),
+                         dim3(CORR_THREADS), 0, st, src, m, pose, g, root, CsrSeg{off, (unsigned)n_cap}, csr, nn, d2,
+                         fb_list, hv_list, hv_range, ctl, honor_stop);
 }
 
 cudaError_t launch_correspond_fixed(const float4 *src, int m, const double *pose, const GridGeom &g, const int *root,
                                     const unsigned *count, unsigned C, const float4 *slots, int *nn, float *d2,
                                     int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, cudaStream_t st)
 {
-    return launch_kernel(k_correspond<FixedSeg>, dim3((m + CORR_THREADS - 1) / CORR_THREADS), dim3(CORR_THREADS), 0,
-                         st, src, m, pose, g, root, FixedSeg{count, C}, slots, nn, d2, fb_list, hv_list, hv_range,
-                         ctl, 0);
+    return launch_kernel(k_correspond<FixedSeg, DenseRoot>, dim3((m + CORR_THREADS - 1) / CORR_THREADS),
+                         dim3(CORR_THREADS), 0, st, src, m, pose, g, DenseRoot{root}, FixedSeg{count, C}, slots, nn,
+                         d2, fb_list, hv_list, hv_range, ctl, 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -34,6 +34,7 @@ VICP_STATIC_MAX_BRICK_SLOTS = 1 << 20
 VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
 VICP_FLAG_FP64_SOLVE = 1 << 2
+VICP_FLAG_SPARSE_GRID = 1 << 3
 VICP_HIST_WARP_AGGREGATED = 0
 VICP_HIST_SHARED_HASH = 1
 VICP_BATCH_MAX_PAIRS = 65536
@@ -67,7 +68,16 @@ class vicp_memory(C.Structure):
     _fields_ = [("current_bytes", C.c_uint64), ("peak_bytes", C.c_uint64), ("static_bytes", C.c_uint64),
                 ("csr_store_bytes", C.c_uint64), ("fixed_capacity_bytes", C.c_uint64),
                 ("paper_static_layout_bytes", C.c_uint64), ("max_voxel_count", C.c_uint32),
-                ("occupied_voxels", C.c_uint32), ("nonempty_bricks", C.c_uint32), ("reserved", C.c_uint32)]
+                ("occupied_voxels", C.c_uint32), ("nonempty_bricks", C.c_uint32), ("labelled_voxels", C.c_uint32)]
+
+
+class vicp_sparse_view(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("voxel_size", C.c_float), ("inv_voxel_size", C.c_float),
+                ("dims", C.c_int32 * 3), ("n_voxels", C.c_int64), ("n_target", C.c_int32),
+                ("n_stored", C.c_int32), ("dilation_layers", C.c_int32), ("occupied_slots", C.c_int64),
+                ("occupied_keys", C.c_void_p), ("occupied_offsets", C.c_void_p), ("labelled_slots", C.c_int64),
+                ("labelled_keys", C.c_void_p), ("labelled_root", C.c_void_p), ("labelled_voxels", C.c_int64),
+                ("keys", C.c_void_p), ("ids", C.c_void_p), ("csr_points", C.c_void_p), ("occupancy", C.c_void_p)]
 
 
 class vicp_batch_params(C.Structure):
@@ -106,6 +116,7 @@ SIGNATURES = {
     "vicp_register_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double)]),
     "vicp_get_grid": (C.c_int, [_P, C.POINTER(vicp_grid_view)]),
+    "vicp_get_sparse_grid": (C.c_int, [_P, C.POINTER(vicp_sparse_view)]),
     "vicp_sync": (C.c_int, [_P]),
     "vicp_memory_report": (C.c_int, [_P, C.POINTER(vicp_memory)]),
     "vicp_profile_enable": (C.c_int, [_P, C.c_int32]),
@@ -371,6 +382,29 @@ class Context:
             out["root"] = _view(v.root, (V,), "<i4", torch.int32, d).clone()
             out["ring"] = _view(v.ring, (V,), "|u1", torch.uint8, d).clone()
         return out
+
+    def get_sparse_grid(self) -> dict:
+        """Copies of the sparse grid's arrays (a context created with
+        VICP_FLAG_SPARSE_GRID) as torch tensors on the device."""
+        v = vicp_sparse_view()
+        self._check(self._lib.vicp_get_sparse_grid(self.handle, C.byref(v)), "vicp_get_sparse_grid")
+        V, n, ns = int(v.n_voxels), int(v.n_target), int(v.n_stored)
+        So, Sl = int(v.occupied_slots), int(v.labelled_slots)
+        d = self.device
+        return {
+            "origin": tuple(float(v.origin[a]) for a in range(3)), "voxel_size": float(v.voxel_size),
+            "inv_voxel_size": float(v.inv_voxel_size), "dims": tuple(int(v.dims[a]) for a in range(3)),
+            "n_voxels": V, "n_target": n, "n_stored": ns, "dilation_layers": int(v.dilation_layers),
+            "labelled_voxels": int(v.labelled_voxels),
+            "occupied_keys": _view(v.occupied_keys, (So,), "<u4", torch.uint32, d).clone(),
+            "occupied_offsets": _view(v.occupied_offsets, (So + 1,), "<u4", torch.uint32, d).clone(),
+            "labelled_keys": _view(v.labelled_keys, (Sl,), "<u4", torch.uint32, d).clone(),
+            "labelled_root": _view(v.labelled_root, (Sl,), "<i4", torch.int32, d).clone(),
+            "keys": _view(v.keys, (n,), "<i4", torch.int32, d).clone(),
+            "ids": _view(v.ids, (ns,), "<i4", torch.int32, d).clone(),
+            "csr_points": _view(v.csr_points, (ns, 4), "<f4", torch.float32, d).clone(),
+            "occupancy": _view(v.occupancy, ((V + 31) // 32,), "<u4", torch.uint32, d).clone(),
+        }
 
     def memory_report(self) -> dict:
         m = vicp_memory()
