@@ -33,6 +33,8 @@ The line also carries, besides the headline:
     oracle on sampled pairs;
   * `differentiable`: forward + backward of the point-to-point loss over 64
     pairs of 20k points, and its values against the oracle's;
+  * `sparse_grid`: the same step on the sparse (hashed) grid, and the peak
+    device bytes of the dense, sparse and fixed-capacity layouts;
   * the fixed-capacity store and the histogram ablation;
   * `cpu_baseline`: the CPU oracle on all host cores (and on one).
 
@@ -556,6 +558,68 @@ def run_batched(dev, flush, rank: int, ws: int, reps: int = 5, n_pairs: int = 25
 
 
 # ----------------------------------------------------------------------------
+# the sparse (hashed) grid against the dense grid on the scene
+# ----------------------------------------------------------------------------
+def run_sparse(dev, pair, flush, steps: int, dense_pose, dense_mem) -> dict:
+    import torch
+
+    from paper_2512_04996_gb300 import vicp
+
+    stream = torch.cuda.current_stream(dev)
+    src = torch.from_numpy(pair.source).to(dev)
+    tgt = torch.from_numpy(pair.target).to(dev)
+    flags = vicp.VICP_FLAG_KEEP_GRID | vicp.VICP_FLAG_SPARSE_GRID
+    ctx = vicp.Context(voxel_size=pair.voxel_size, dilation_layers=L_LAYERS, max_iters=1, rmse_eps=0.0, flags=flags)
+    pose = torch.eye(4, dtype=torch.float64, device=dev).contiguous()
+    eye = pose.clone()
+
+    def one_step(k):
+        if k % ITERS_PER_REGISTRATION == 0:
+            pose.copy_(eye)
+        ctx.build_grid(tgt)
+        ctx.dilate(L_LAYERS)
+        ctx.step(src, pose)
+
+    for k in range(5):
+        one_step(k)
+    ms = _timed_steps(one_step, steps, flush, stream)
+    ctx.profile_enable(True)
+    for k in range(min(steps, 200)):
+        flush.fill_(k & 0xff)
+        one_step(k)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.build_grid(tgt)
+    ctx.dilate(L_LAYERS)
+
+    def step_only(k):
+        if k % ITERS_PER_REGISTRATION == 0:
+            pose.copy_(eye)
+        ctx.step(src, pose)
+    amort = _timed_steps(step_only, steps, flush, stream)
+    mem = ctx.memory_report()
+    ctx_r = vicp.Context(voxel_size=pair.voxel_size, dilation_layers=L_LAYERS, max_iters=ITERS_PER_REGISTRATION,
+                         rmse_eps=0.0, flags=flags | vicp.VICP_FLAG_REBUILD_EACH_ITER)
+    st, T, it, rm = ctx_r.register(src, tgt)
+    ext = _extent(pair.target)
+    return {
+        "what": "the headline step on the sparse (hashed) grid: occupied and labelled voxels in hash tables "
+                "instead of per-voxel counts, offsets, root and ring (one host synchronisation per dilation "
+                "to size the labelled-voxel table)",
+        "iters_per_s": round(len(ms) / (sum(ms) / 1e3), 1),
+        "amortised_grid_built_once_iters_per_s": round(len(amort) / (sum(amort) / 1e3), 1),
+        "kernels_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items() if v[0]},
+        "registration_30_vs_dense": {**_pose_err(T, dense_pose, ext), "status": st, "iters": it},
+        "memory": {"peak_device_bytes": {"dense_csr": dense_mem["peak_bytes"], "sparse": mem["peak_bytes"]},
+                   "per_voxel_arrays_bytes": {"dense_csr": dense_mem["csr_store_bytes"] - 4 * pair.target.shape[0],
+                                              "sparse_tables": mem["csr_store_bytes"] - 4 * pair.target.shape[0]},
+                   "fixed_capacity_bytes": mem["fixed_capacity_bytes"],
+                   "paper_64KB_per_voxel_bytes": mem["paper_static_layout_bytes"],
+                   "labelled_voxels": mem["labelled_voxels"], "occupied_voxels": mem["occupied_voxels"]},
+    }
+
+
+# ----------------------------------------------------------------------------
 # fixed-capacity store (direct addressing) against the CSR store
 # ----------------------------------------------------------------------------
 def run_fixed(dev, pair, flush, reps: int = 100) -> dict:
@@ -894,7 +958,7 @@ def run_ours(args, rank, ws, local):
         ctx_r = vicp.Context(voxel_size=pair.voxel_size, dilation_layers=L_LAYERS, max_iters=ITERS_PER_REGISTRATION,
                              rmse_eps=0.0, flags=vicp.VICP_FLAG_KEEP_GRID | vicp.VICP_FLAG_REBUILD_EACH_ITER | fl)
         st, T, it, rm = ctx_r.register(src, tgt)
-        reg[name] = {"status": st, "iters": it, "rmse": rm,
+        reg[name] = {"status": st, "iters": it, "rmse": rm, "pose": T.tolist(),
                      "pose_err_vs_oracle": {**_pose_err(T, R, ext), "oracle_iters": rit,
                                             "rmse_rel_diff": abs(rm - hist[-1]) / hist[-1]},
                      "rot_err_vs_truth_deg": round(math.degrees(_rot_err_rad(T, pair.T_gt)), 5),
@@ -916,6 +980,10 @@ def run_ours(args, rank, ws, local):
 
     sections = set(args.sections.split(","))
     run_all = "all" in sections
+    sparse = None
+    if run_all or "sparse" in sections:
+        dense_T = np.array(reg["double_float"]["pose"])
+        sparse = run_sparse(dev, pair, flush, min(max(args.steps, 200), 600), dense_T, mem)
     workloads = None
     if run_all or "workloads" in sections:
         workloads = {p.name: run_workload(dev, p, flush, steps=min(max(args.steps, 200), 1000))
@@ -963,6 +1031,7 @@ def run_ours(args, rank, ws, local):
                    "fixed_capacity_bytes": mem["fixed_capacity_bytes"],
                    "paper_64KB_per_voxel_bytes": mem["paper_static_layout_bytes"],
                    "max_voxel_count": mem["max_voxel_count"], "occupied_voxels": mem["occupied_voxels"]},
+        "sparse_grid": sparse,
         "workloads": workloads,
         "histogram_ablation": hist_ablation,
         "fixed_capacity_layout": fixed_capacity,
@@ -1082,8 +1151,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sections", default="all",
-                    help="extra measurements after the headline: all, or a comma list of workloads, hist, fixed, "
-                         "batched, loss, none (for profiler captures)")
+                    help="extra measurements after the headline: all, or a comma list of sparse, workloads, hist, "
+                         "fixed, batched, loss, none (for profiler captures)")
     ap.add_argument("--small", action="store_true",
                     help="batched and loss sections on 32 and 16 pairs (for profiler captures)")
     args = ap.parse_args()

@@ -263,9 +263,14 @@ VICP_API vicp_status vicp_get_grid(vicp_ctx *ctx, vicp_grid_view *out);
  *     segments lie in the store in slot order), and
  *   - the labelled voxels (within L of a point), in a second table (voxel
  *     key -> root voxel key; the ring is the Manhattan distance between the
- *     two voxels), sized after each dilation to keep it at most half full
- *     (one synchronisation per vicp_dilate: pass Z counts the labels, and a
- *     table that was too small is grown and the dilation run again).
+ *     two voxels), sized after a dilation to keep it at most half full
+ *     (vicp_dilate synchronises once: pass Z counts the labels, and a table
+ *     that was too small is grown and the dilation run again).  Under
+ *     VICP_FLAG_KEEP_GRID the size found by the first dilation of the kept
+ *     grid is kept and later dilations run without that synchronisation; a
+ *     cloud that then needs more room is reported by the next synchronising
+ *     call as VICP_ERR_STATE (its labels are incomplete), and the next
+ *     vicp_dilate checks and grows the table again.
  * Keys, CSR ids and points, the occupancy bits, the dilation's pass-Y words
  * and the global search's brick level are as in the dense grid, and every
  * search result equals the dense grid's.  Not available with the

@@ -94,6 +94,8 @@ struct vicp_ctx {
     int o_cur = 0;
     long long cap_occV = -1;
     long long lab_count = 0;          // labelled voxels of the last dilation
+    bool lab_kept = false;            // with VICP_FLAG_KEEP_GRID: the table size was checked for ...
+    int lab_L = -1, lab_kept_dims[3] = {0, 0, 0};   // ... this L and these grid dimensions
 
     // accounting / timing
     int64_t launches = 0;
@@ -459,6 +461,12 @@ vicp_status read_device_status(vicp_ctx *c)
             return fail(c, VICP_ERR_TIMEOUT, "a device-side wait gave up (device status 0x%x)", err);
         if (err & DEVERR_BOUNDS)
             return fail(c, VICP_ERR_CUDA, "a device-side bounds check failed (device status 0x%x)", err);
+        if (err & DEVERR_CAPACITY) {
+            c->lab_kept = false;   // the next dilation checks its table size again
+            return fail(c, VICP_ERR_STATE,
+                        "a hashed voxel table of the sparse grid was too small for this cloud (the table size "
+                        "found at the first build is kept under VICP_FLAG_KEEP_GRID): build and dilate again");
+        }
         if (err & DEVERR_DEGENERATE)
             return fail(c, VICP_ERR_DEGENERATE, "rank(H) < 2: degenerate correspondence geometry");
     }
@@ -604,6 +612,23 @@ vicp_status dilate_sparse(vicp_ctx *c, int L)
     const GridGeom &g = c->geom;
     long long slots = c->cap_l > 0 ? c->cap_l : pow2_at_least(c->n_target * 2 > 4096 ? (long long)c->n_target * 2 : 4096);
     const int blocks = dilate_hashed_blocks(g, L);
+    unsigned *err = &ctl_of(c)->err;
+    // VICP_FLAG_KEEP_GRID keeps the grid of the first build, and with it the
+    // table size checked then: later dilations of the same grid run without
+    // the check (a cloud that needs more room is reported by the next
+    // synchronising call as VICP_ERR_STATE, and the next dilation checks).
+    if ((c->params.flags & VICP_FLAG_KEEP_GRID) && c->lab_kept && c->lab_L == L && c->lab_kept_dims[0] == g.nx &&
+        c->lab_kept_dims[1] == g.ny && c->lab_kept_dims[2] == g.nz) {
+        cudaError_t e = cudaMemsetAsync((unsigned *)c->lparts.p + blocks, 0, 4, c->side);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "labelled-voxel overflow flag");
+        TRY(launch_on(c, K_DILATE, c->side, [&] {
+            return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
+                                        (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (int *)c->lroot.p,
+                                        (unsigned *)c->lparts.p, err, c->side);
+        }));
+    } else {
+    c->lab_kept = false;
     for (int attempt = 0;; ++attempt) {
         TRY(ensure_label_table(c, slots, L));
         cudaError_t e = cudaMemsetAsync(c->lparts.p, 0, (size_t)(blocks + 1) * 4, c->side);
@@ -612,7 +637,7 @@ vicp_status dilate_sparse(vicp_ctx *c, int L)
         TRY(launch_on(c, K_DILATE, c->side, [&] {
             return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
                                         (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (int *)c->lroot.p,
-                                        (unsigned *)c->lparts.p, c->side);
+                                        (unsigned *)c->lparts.p, err, c->side);
         }));
         std::vector<unsigned> parts((size_t)blocks + 1);
         e = cudaMemcpyAsync(parts.data(), c->lparts.p, parts.size() * 4, cudaMemcpyDeviceToHost, c->side);
@@ -626,11 +651,22 @@ vicp_status dilate_sparse(vicp_ctx *c, int L)
         const bool overflow = parts[blocks] != 0;
         if (!overflow && 2 * count <= c->cap_l) {
             c->lab_count = count;
+            c->lab_kept = true;
+            c->lab_L = L;
+            c->lab_kept_dims[0] = g.nx;
+            c->lab_kept_dims[1] = g.ny;
+            c->lab_kept_dims[2] = g.nz;
             break;
+        }
+        if (overflow) {   // this dilation is run again: its capacity report is withdrawn
+            e = launch_clear_bits(err, DEVERR_CAPACITY, c->side);
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "status update");
         }
         if (attempt >= 3)
             return fail(c, VICP_ERR_CUDA, "labelled-voxel table: %lld voxels do not fit %lld slots", count, c->cap_l);
         slots = pow2_at_least(2 * count > 2 * c->cap_l ? 2 * count : 2 * c->cap_l);
+    }
     }
     cudaError_t e = cudaEventRecord(c->ev_dil, c->side);
     if (e == cudaSuccess)

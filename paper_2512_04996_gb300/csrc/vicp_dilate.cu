@@ -85,14 +85,15 @@ template <class W>
 __global__ void __launch_bounds__(THREADS) k_dilate_z_hashed(const typename W::Stored *__restrict__ inter,
                                                              const unsigned *__restrict__ rows, GridGeom g, int L,
                                                              int nxb, int nyb, int units, HashTable table,
-                                                             int *__restrict__ root, unsigned *__restrict__ counts)
+                                                             int *__restrict__ root, unsigned *__restrict__ counts,
+                                                             unsigned *__restrict__ err)
 {
     pdl_begin();
     __shared__ unsigned s_count;
     if (threadIdx.x == 0)
         s_count = 0u;
     __syncthreads();
-    const HashLabels out{table, root, counts + gridDim.x};
+    const HashLabels out{table, root, counts + gridDim.x, err};
     unsigned n = 0u;
     for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
         n += dilate_z_unit<W>(u, inter, rows, out, g, L, nxb, nyb);
@@ -119,7 +120,7 @@ static int resident_blocks(K kernel)
 template <class W>
 static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
                               unsigned char *dirty, int *root, unsigned char *ring, const HashTable *labels,
-                              unsigned *counts, cudaStream_t st)
+                              unsigned *counts, unsigned *err, cudaStream_t st)
 {
     using S = typename W::Stored;
     static const int xy_blocks = resident_blocks(k_dilate_xy<W>), z_blocks = resident_blocks(k_dilate_z<W>),
@@ -134,7 +135,8 @@ static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, voi
     const int u_z = nxb * g.ny * nzb;   // < V < 2^31
     if (labels)
         return launch_kernel(k_dilate_z_hashed<W>, dim3(min(zh_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0,
-                             st, static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, *labels, root, counts);
+                             st, static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, *labels, root, counts,
+                             err);
     return launch_kernel(k_dilate_z<W>, dim3(min(z_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0, st,
                          static_cast<const S *>(inter), rows, dirty, g, L, nxb, nyb, u_z, root, ring);
 }
@@ -162,16 +164,26 @@ cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *i
                           unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st)
 {
     if (L <= L_COMPACT_MAX)
-        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, st);
-    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, st);
+        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, nullptr, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, nullptr, st);
 }
 
 cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
-                                 const HashTable &labels, int *root, unsigned *counts, cudaStream_t st)
+                                 const HashTable &labels, int *root, unsigned *counts, unsigned *err, cudaStream_t st)
 {
     if (L <= L_COMPACT_MAX)
-        return run_dilate<Words16>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, st);
-    return run_dilate<Words32>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, st);
+        return run_dilate<Words16>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, err, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, err, st);
+}
+
+// Clears bits of a device word (atomically, so that concurrent kernels'
+// bits are kept).
+__global__ void k_clear_bits(unsigned *word, unsigned bits) { atomicAnd(word, ~bits); }
+
+cudaError_t launch_clear_bits(unsigned *word, unsigned bits, cudaStream_t st)
+{
+    k_clear_bits<<<1, 1, 0, st>>>(word, bits);
+    return cudaGetLastError();
 }
 
 }  // namespace vicp

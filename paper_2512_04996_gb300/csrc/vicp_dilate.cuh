@@ -225,7 +225,8 @@ struct DenseLabels {
 struct HashLabels {
     HashTable table;     // keys: the labelled voxels
     int *root;           // [slots] root key of each labelled voxel
-    unsigned *overflow;  // set to 1 when an insert gave up (the table is too small)
+    unsigned *overflow;  // set to 1 when an insert gave up (the table is too small) ...
+    unsigned *err;       // ... and DEVERR_CAPACITY set in the device status word
 };
 
 // ---------------------------------------------------------------------------
@@ -320,8 +321,9 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
     sweep32<STEP_ZF, STEP_ZB>(c, before, after, (unsigned)L << W::ZD);
 
     const unsigned valid = (unsigned)(L + 1) << W::ZD;   // words below this are labels
-    int v = col + plane * z0;
-    const unsigned vb = (unsigned)v - W::bias((unsigned)g.nx, (unsigned)plane);
+    const int v0 = col + plane * z0;
+    const unsigned vb = (unsigned)v0 - W::bias((unsigned)g.nx, (unsigned)plane);
+    int v = v0;
     unsigned labelled = 0u;
 #pragma unroll
     for (int k = 0; k < UZ; ++k, v += plane) {
@@ -332,10 +334,12 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
             if constexpr (HASHED) {
                 if (hit) {
                     const int slot = hash_insert(out.table, (unsigned)v);
-                    if (slot >= 0)
+                    if (slot >= 0) {
                         out.root[slot] = r;
-                    else
+                    } else {
                         atomicOr(out.overflow, 1u);
+                        atomicOr(out.err, DEVERR_CAPACITY);
+                    }
                     ++labelled;
                 }
             } else {

@@ -118,10 +118,13 @@ cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *i
 // the keys of `labels` to HASH_EMPTY first), then pass Z inserts every
 // labelled voxel into `labels` with its root key in root[slot]; block b of
 // pass Z writes its labelled-voxel count to counts[b], b <
-// dilate_hashed_blocks(g, L), and sets counts[dilate_hashed_blocks(g, L)]
-// (zero beforehand) to 1 if the table was too small for an insert.
+// dilate_hashed_blocks(g, L), and, if the table was too small for an
+// insert, sets counts[dilate_hashed_blocks(g, L)] (zero beforehand) to 1 and
+// DEVERR_CAPACITY in *err.
 cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
-                                 const HashTable &labels, int *root, unsigned *counts, cudaStream_t st);
+                                 const HashTable &labels, int *root, unsigned *counts, unsigned *err, cudaStream_t st);
+// *word &= ~bits, atomically.
+cudaError_t launch_clear_bits(unsigned *word, unsigned bits, cudaStream_t st);
 int dilate_hashed_blocks(const GridGeom &g, int L);
 long long dilate_units(const GridGeom &g);
 long long dilate_column_units(const GridGeom &g);

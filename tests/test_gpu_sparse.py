@@ -227,3 +227,32 @@ def test_sparse_rejects_the_dense_views(pairs):
     with pytest.raises(vicp.VicpError) as e:
         dense.get_sparse_grid()
     assert e.value.status == vicp.VICP_ERR_STATE
+
+
+def test_sparse_kept_grid_reports_a_cloud_that_outgrows_the_table(pairs):
+    """Under VICP_FLAG_KEEP_GRID the labelled-voxel table keeps the size the
+    first dilation found: a much larger cloud in the same grid is reported by
+    the next synchronising call (VICP_ERR_STATE), and the dilation after that
+    checks and grows the table again, giving the oracle's labels."""
+    from paper_2512_04996_gb300 import vicp
+    p = pairs(2)
+    _, g0 = _sparse_grid(p.target, L=10, divisions=128)
+    kw = dict(origin=g0["origin"], voxel_size=g0["voxel_size"], dims=g0["dims"])
+    ctx = context(L=10, flags=_sparse_flags(vicp.VICP_FLAG_KEEP_GRID), **kw)
+    small = np.ascontiguousarray(p.target[:50])
+    ctx.build_grid(torch.from_numpy(small).cuda())
+    ctx.dilate(10)
+    assert ctx.sync() == 0
+    big = torch.from_numpy(p.target).cuda()
+    ctx.build_grid(big)
+    ctx.dilate(10)                           # kept size: no check, too small
+    assert ctx.sync() == vicp.VICP_ERR_STATE
+    ctx.build_grid(big)
+    ctx.dilate(10)                           # checked again: grown
+    assert ctx.sync() == 0
+    g = {key: to_np(v) for key, v in ctx.get_sparse_grid().items()}
+    grid, ref = _oracle_for(g, p.target, 10)
+    assert_sparse_equal(g, ref, p.target)
+    ctx.build_grid(big)                      # and kept from here on
+    ctx.dilate(10)
+    assert ctx.sync() == 0
