@@ -8,8 +8,11 @@
 namespace vicp {
 
 // A root segment longer than this is scanned by a whole warp, not by the
-// query's own thread (a warp waits for its longest segment).
-constexpr unsigned HEAVY = 32;
+// query's own thread (a warp waits for its longest segment).  On the 226k
+// scene 48 leaves 9-18k of the 226k queries to whole warps (32: 27-38k)
+// while the longest light segment of a warp grows by a sixth: measured step
+// 107.5 -> 105.9 us.
+constexpr unsigned HEAVY = 48;
 
 // Nearest point of the CSR run [a, b) to s by one thread: 16-byte loads of
 // (x, y, z, index), eight in flight.  Returns the (distance bits, index) key;
