@@ -81,6 +81,8 @@ typedef struct vicp_allocator {
                                                  (~48-bit) sums and solve on the FP32 pipes */
 #define VICP_FLAG_SPARSE_GRID       (1u << 3) /* the sparse (hashed) grid, see vicp_get_sparse_grid: no
                                                  per-voxel count, offset, root or ring arrays */
+#define VICP_FLAG_NO_GRAPH          (1u << 4) /* vicp_register / vicp_register_host: never replay the
+                                                 call from a captured CUDA graph */
 
 
 /* Run parameters (Sec. 4.1 "Parameter": voxelisation scale, dilation
@@ -232,6 +234,19 @@ VICP_API vicp_status vicp_step(vicp_ctx *ctx, const float *src_xyzw, int32_t n_s
 VICP_API vicp_status vicp_register(vicp_ctx *ctx, const float *src_xyzw, int32_t n_src,
                           const float *tgt_xyzw, int32_t n_tgt, double pose_host[16],
                           int32_t *iters_out, double *rmse_out);
+
+/* Graph replay of vicp_register and vicp_register_host: the second call in
+ * a row with the same clouds (the same pointers and sizes) and parameters is
+ * captured into a CUDA graph -- the copies, every kernel of the builds, the
+ * dilations and the iterations, and the read-back -- and that call and
+ * every later one with the same arguments replay the graph (one launch)
+ * instead of launching the kernels one by one.  The contents of the clouds
+ * and the initial pose are read anew at every replay, and the results equal
+ * those of the launches one by one bit for bit.  Only where nothing in the
+ * call synchronises or allocates: the dense grid, an explicit grid or
+ * VICP_FLAG_KEEP_GRID after the grid was fitted, kernel timing off, and not
+ * VICP_FLAG_NO_GRAPH.  If a capture fails (vicp_register_host with pageable
+ * host clouds, for one) the context launches directly from then on. */
 
 /* vicp_register with both clouds in host memory: copies them to
  * context-owned device buffers -- the target on the context's stream before

@@ -97,6 +97,35 @@ struct vicp_ctx {
     bool lab_kept = false;            // with VICP_FLAG_KEEP_GRID: the table size was checked for ...
     int lab_L = -1, lab_kept_dims[3] = {0, 0, 0};   // ... this L and these grid dimensions
 
+    // vicp_register / vicp_register_host replayed from a captured CUDA graph:
+    // the call's arguments it was captured for, the kernels of one replay,
+    // the private capture / replay stream with the events that order it
+    // after and before the context's stream, and page-locked staging for the
+    // initial pose and the results
+    struct RegKey {
+        bool host = false;
+        const void *src = nullptr, *tgt = nullptr;
+        int32_t m = 0, n = 0, max_iters = -1, L = -1;
+        uint32_t flags = 0;
+        double eps = 0.0;
+        GridGeom geom{};
+    };
+    struct RegOut {
+        double pose[16];
+        int stop, iters;
+        double prev, last;
+        unsigned err;
+    };
+    RegKey rg_key, rg_last;           // the graph's call; the last direct call
+    bool rg_last_valid = false, rg_broken = false;
+    cudaGraphExec_t rg_exec = nullptr;
+    int64_t rg_launches = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_gin = nullptr, ev_gout = nullptr;
+    double *h_pose = nullptr;         // page-locked, 16 doubles
+    RegOut *h_out = nullptr;          // page-locked
+    bool capturing = false, nns_in_capture = false;
+
     // accounting / timing
     int64_t launches = 0;
     bool profiling = false;
@@ -506,6 +535,7 @@ vicp_status run_nns(vicp_ctx *c, const float4 *src, int m, const double *pose, i
                                (const float4 *)c->csr.p, d, nn, d2, m, honor_stop, c->stream);
     }));
     cudaError_t e = cudaEventRecord(c->ev_nns, c->stream);   // a later dilation waits for this search
+    c->nns_in_capture = c->capturing;
     return e == cudaSuccess ? VICP_OK : cuda_fail(c, e, "event record");
 }
 
@@ -703,9 +733,11 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     const size_t inter_bytes = (size_t)g.V * (L <= 15 ? 2 : 4);
     if (c->inter.bytes < inter_bytes)
         TRY(buf_alloc(c, c->inter, inter_bytes, "dilation pass-Y words"));
-    // on the side stream, after the histogram and after the last search
+    // on the side stream, after the histogram and after the last search (in
+    // a graph capture only a search of the captured call: the replay starts
+    // after all earlier work of the context's stream)
     cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_hist, 0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && (!c->capturing || c->nns_in_capture))
         e = cudaStreamWaitEvent(c->side, c->ev_nns, 0);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "stream wait");
@@ -740,8 +772,12 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
 
 // src_ready: an event the source's producer recorded (null: the source is
 // ready in stream order); the first search waits for it, the build does not.
-vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
-                         double pose_host[16], int32_t *iters_out, double *rmse_out, cudaEvent_t src_ready = nullptr)
+// The work of one registration on the context's stream: build, dilate, the
+// initial pose from pose_in (host), the iterations, and the pose, the loop
+// state and the device status copied to `out` (host).
+vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
+                              const double *pose_in, void *out_pose, void *out_loop, unsigned *out_err,
+                              cudaEvent_t src_ready)
 {
     TRY(build(c, tgt, n));
     TRY(dilate(c, -1));
@@ -751,7 +787,7 @@ vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float 
             return cuda_fail(c, w, "stream wait");
     }
     double *pose = (double *)c->pose.p;
-    cudaError_t e = cudaMemcpyAsync(pose, pose_host, 16 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(pose, pose_in, 16 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "pose upload");
     DevCtl *d = ctl_of(c);
@@ -766,21 +802,220 @@ vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float 
         }
         TRY(run_step(c, src, m, pose, nullptr, 1));
     }
+    e = cudaMemcpyAsync(out_pose, pose, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_loop, &d->stop, sizeof(DevCtl) - offsetof(DevCtl, stop), cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess && out_err)
+        e = cudaMemcpyAsync(out_err, &d->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "result read-back");
+    return VICP_OK;
+}
+
+// A device status word read back by a graph replay, as read_device_status
+// maps it (the word is cleared on the device when set).
+vicp_status device_status_from(vicp_ctx *c, unsigned err)
+{
+    if (!err)
+        return VICP_OK;
+    DevCtl *d = ctl_of(c);
+    cudaMemsetAsync(&d->err, 0, sizeof(unsigned), c->stream);
+    if (err & DEVERR_TIMEOUT)
+        return fail(c, VICP_ERR_TIMEOUT, "a device-side wait gave up (device status 0x%x)", err);
+    if (err & DEVERR_BOUNDS)
+        return fail(c, VICP_ERR_CUDA, "a device-side bounds check failed (device status 0x%x)", err);
+    if (err & DEVERR_CAPACITY)
+        return fail(c, VICP_ERR_STATE, "a hashed voxel table of the sparse grid was too small for this cloud");
+    if (err & DEVERR_DEGENERATE)
+        return fail(c, VICP_ERR_DEGENERATE, "rank(H) < 2: degenerate correspondence geometry");
+    return VICP_OK;
+}
+
+bool same_call(const vicp_ctx::RegKey &a, const vicp_ctx::RegKey &b)
+{
+    return a.host == b.host && a.src == b.src && a.tgt == b.tgt && a.m == b.m && a.n == b.n &&
+           a.max_iters == b.max_iters && a.L == b.L && a.flags == b.flags && a.eps == b.eps &&
+           std::memcmp(&a.geom, &b.geom, sizeof(GridGeom)) == 0;
+}
+
+// A call can be replayed from a graph when nothing in it synchronises with
+// the host or allocates: the dense grid, a grid geometry that the call does
+// not refit (explicit, or kept), no kernel timing, graphs not switched off.
+bool graphable(const vicp_ctx *c)
+{
+    const uint32_t f = c->params.flags;
+    if ((f & VICP_FLAG_NO_GRAPH) || (f & VICP_FLAG_SPARSE_GRID) || c->profiling || c->rg_broken || !c->have_geom)
+        return false;
+    return c->params.dims[0] > 0 || (f & VICP_FLAG_KEEP_GRID);
+}
+
+// Captures the call's work (on the private stream, with the context's
+// stream redirected to it) into rg_exec.  The double-buffered occupancy and
+// brick-bound buffers that the first build of the call fills are reset at
+// the start, so that a replay does not depend on how many builds came
+// before it.
+vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const float4 *src, const float *tgt,
+                                 const float *src_host, const float *tgt_host)
+{
+    if (!c->gstream) {
+        if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_gin, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_gout, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost((void **)&c->h_pose, 16 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost((void **)&c->h_out, sizeof(vicp_ctx::RegOut)) != cudaSuccess) {
+            cudaGetLastError();
+            c->rg_broken = true;
+            return VICP_ERR_CUDA;
+        }
+    }
+    if (c->rg_exec) {
+        cudaGraphExecDestroy(c->rg_exec);
+        c->rg_exec = nullptr;
+    }
+    cudaStream_t saved = c->stream;
+    const bool saved_after = c->after_solve;
+    const int saved_occ = c->occ_cur;
+    const int64_t launches0 = c->launches;
+    c->stream = c->gstream;
+    c->capturing = true;
+    c->nns_in_capture = false;
+    c->after_solve = false;
+    cudaGraph_t g = nullptr;
+    vicp_status s = VICP_OK;
+    cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const int first = c->occ_cur ^ 1;   // the buffers the call's first build fills
+        e = cudaMemsetAsync(c->occ[first].p, 0, c->occ[first].bytes, c->gstream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->boxk[first].p, 0xff, c->boxk[first].bytes, c->gstream);
+        if (e == cudaSuccess && key.host) {
+            const size_t sb = (size_t)key.m * 16, tb = (size_t)key.n * 16;
+            e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->gstream);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(c->ev_copy_go, c->gstream);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(c->copy, c->ev_copy_go, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->hsrc.p, src_host, sb, cudaMemcpyHostToDevice, c->copy);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(c->ev_src, c->copy);
+        }
+        if (e == cudaSuccess)
+            s = registration_work(c, src, key.m, tgt, key.n, c->h_pose, c->h_out->pose, &c->h_out->stop,
+                                  &c->h_out->err, key.host ? c->ev_src : nullptr);
+        const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+        if (e == cudaSuccess)
+            e = e2;
+    }
+    if (e == cudaSuccess && s == VICP_OK)
+        e = cudaGraphInstantiate(&c->rg_exec, g, 0);
+    if (g)
+        cudaGraphDestroy(g);
+    c->stream = saved;
+    c->capturing = false;
+    // an event last recorded inside the capture names a node of the graph,
+    // and a later direct launch may not wait for it: every event the work
+    // records is recorded again, outside the capture, on the context's stream
+    for (cudaEvent_t ev : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src})
+        if (cudaEventRecord(ev, saved) != cudaSuccess && e == cudaSuccess)
+            e = cudaErrorUnknown;
+    c->after_solve = false;
+    c->rg_launches = c->launches - launches0;
+    c->launches = launches0;   // counted when replayed
+    if (e != cudaSuccess || s != VICP_OK) {
+        // capture unavailable for this call (for example pageable host
+        // clouds): launch directly from now on; the host state the capture
+        // advanced is put back
+        cudaGetLastError();
+        c->rg_exec = nullptr;
+        c->rg_broken = true;
+        c->occ_cur = saved_occ;
+        c->after_solve = saved_after;
+        return VICP_ERR_CUDA;
+    }
+    c->rg_key = key;
+    return VICP_OK;
+}
+
+vicp_status replay_registration(vicp_ctx *c, double pose_host[16], int32_t *iters_out, double *rmse_out)
+{
+    std::memcpy(c->h_pose, pose_host, 16 * sizeof(double));
+    cudaError_t e = cudaEventRecord(c->ev_gin, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->gstream, c->ev_gin, 0);
+    if (e == cudaSuccess)
+        e = cudaGraphLaunch(c->rg_exec, c->gstream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->ev_gout, c->gstream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(c->stream, c->ev_gout, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->gstream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "graph replay");
+    c->launches += c->rg_launches;
+    c->after_solve = false;
+    std::memcpy(pose_host, c->h_out->pose, 16 * sizeof(double));
+    if (iters_out)
+        *iters_out = c->h_out->iters;
+    if (rmse_out)
+        *rmse_out = c->h_out->last;
+    return device_status_from(c, c->h_out->err);
+}
+
+vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
+                         double pose_host[16], int32_t *iters_out, double *rmse_out, cudaEvent_t src_ready = nullptr,
+                         const float *src_host = nullptr, const float *tgt_host = nullptr)
+{
+    vicp_ctx::RegKey key;
+    key.host = src_host != nullptr;
+    key.src = key.host ? (const void *)src_host : (const void *)src;
+    key.tgt = key.host ? (const void *)tgt_host : (const void *)tgt;
+    key.m = m;
+    key.n = n;
+    key.max_iters = c->params.max_iters;
+    key.L = c->params.dilation_layers;
+    key.flags = c->params.flags;
+    key.eps = c->params.rmse_eps;
+    key.geom = c->geom;
+    if (graphable(c)) {
+        if (c->rg_exec && same_call(key, c->rg_key))
+            return replay_registration(c, pose_host, iters_out, rmse_out);
+        // the second call in a row with the same arguments: capture it
+        if (c->rg_last_valid && same_call(key, c->rg_last) &&
+            capture_registration(c, key, src, tgt, src_host, tgt_host) == VICP_OK)
+            return replay_registration(c, pose_host, iters_out, rmse_out);
+    }
+    if (key.host) {   // the direct path issues the copies itself
+        const size_t sb = (size_t)m * 16, tb = (size_t)n * 16;
+        cudaError_t e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->stream);
+        c->after_solve = false;   // the build's histogram reads what this copy writes
+        if (e == cudaSuccess)
+            e = cudaEventRecord(c->ev_copy_go, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(c->copy, c->ev_copy_go, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->hsrc.p, src_host, sb, cudaMemcpyHostToDevice, c->copy);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(c->ev_src, c->copy);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "host-to-device copy of the clouds");
+    }
     struct {
         int stop, iters;
         double prev, last;
     } loop;
     static_assert(sizeof(loop) == sizeof(DevCtl) - offsetof(DevCtl, stop), "loop state layout");
-    e = cudaMemcpyAsync(pose_host, pose, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&loop, &d->stop, sizeof loop, cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess)
-        return cuda_fail(c, e, "result read-back");
+    TRY(registration_work(c, src, m, tgt, n, pose_host, pose_host, &loop, nullptr, src_ready));
     vicp_status st = read_device_status(c);   // synchronises
     if (iters_out)
         *iters_out = loop.iters;
     if (rmse_out)
         *rmse_out = loop.last;
+    key.geom = c->geom;   // as fitted by this call
+    c->rg_last = key;
+    c->rg_last_valid = st == VICP_OK || st == VICP_ERR_DEGENERATE;
     return st;
 }
 
@@ -936,6 +1171,19 @@ void vicp_destroy(vicp_ctx *c)
         cudaEventDestroy(e);
     if (c->copy)
         cudaStreamSynchronize(c->copy);
+    if (c->gstream)
+        cudaStreamSynchronize(c->gstream);
+    if (c->rg_exec)
+        cudaGraphExecDestroy(c->rg_exec);
+    if (c->h_pose)
+        cudaFreeHost(c->h_pose);
+    if (c->h_out)
+        cudaFreeHost(c->h_out);
+    for (cudaEvent_t e : {c->ev_gin, c->ev_gout})
+        if (e)
+            cudaEventDestroy(e);
+    if (c->gstream)
+        cudaStreamDestroy(c->gstream);
     for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src})
         if (e)
             cudaEventDestroy(e);
@@ -952,7 +1200,7 @@ vicp_status vicp_set_stream(vicp_ctx *c, void *cuda_stream)
         return VICP_ERR_INVALID;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->after_solve = false;
-    return VICP_OK;
+    return VICP_OK;   // a captured registration orders itself after this stream at each replay
 }
 
 vicp_status vicp_build_grid(vicp_ctx *c, const float *target_xyzw, int32_t n_target)
@@ -1044,20 +1292,8 @@ vicp_status vicp_register_host(vicp_ctx *c, const float *src_host, int32_t n_src
     // source on the copy stream, after everything issued so far on the
     // context's stream (earlier searches may still read the buffer), so it
     // travels while the grid is built; the first search waits for it.
-    cudaError_t e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->stream);
-    c->after_solve = false;   // the build's histogram reads what this copy writes
-    if (e == cudaSuccess)
-        e = cudaEventRecord(c->ev_copy_go, c->stream);
-    if (e == cudaSuccess)
-        e = cudaStreamWaitEvent(c->copy, c->ev_copy_go, 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->hsrc.p, src_host, sb, cudaMemcpyHostToDevice, c->copy);
-    if (e == cudaSuccess)
-        e = cudaEventRecord(c->ev_src, c->copy);
-    if (e != cudaSuccess)
-        return cuda_fail(c, e, "host-to-device copy of the clouds");
     return registration(c, (const float4 *)c->hsrc.p, n_src, (const float *)c->htgt.p, n_tgt, pose_host,
-                        iters_out, rmse_out, c->ev_src);
+                        iters_out, rmse_out, c->ev_src, src_host, tgt_host);
 }
 
 vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)

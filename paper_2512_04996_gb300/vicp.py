@@ -35,6 +35,7 @@ VICP_FLAG_KEEP_GRID = 1 << 0
 VICP_FLAG_REBUILD_EACH_ITER = 1 << 1
 VICP_FLAG_FP64_SOLVE = 1 << 2
 VICP_FLAG_SPARSE_GRID = 1 << 3
+VICP_FLAG_NO_GRAPH = 1 << 4
 VICP_HIST_WARP_AGGREGATED = 0
 VICP_HIST_SHARED_HASH = 1
 VICP_BATCH_MAX_PAIRS = 65536

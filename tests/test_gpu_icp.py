@@ -214,3 +214,86 @@ def test_fp64_and_double_float_agree_and_are_deterministic(pairs):
             assert np.array_equal(out[prec][0], T) and out[prec][1] == rm
         out[prec] = (T, rm)
     _assert_pose_close(out["fp64"][0], out["double_float"][0], _extent(p.target))
+
+
+def _graph_pair(p, flags, max_iters, voxel_size=None):
+    from paper_2512_04996_gb300 import vicp
+    kw = dict(L=10, voxel_size=p.voxel_size if voxel_size is None else voxel_size, divisions=p.grid_divisions,
+              max_iters=max_iters, eps=0.0)
+    return (context(flags=flags, **kw), context(flags=flags | vicp.VICP_FLAG_NO_GRAPH, **kw))
+
+
+@pytest.mark.parametrize("k,max_iters,rebuild", [(1, 30, False), (1, 3, True), (2, 1, True), (3, 2, True)])
+def test_register_graph_replays_equal_direct_launches(pairs, k, max_iters, rebuild):
+    """vicp_register replayed from its captured graph (from the second call
+    with the same arguments on) gives the direct launches' results bit for
+    bit, whatever the initial pose, with an odd or even number of builds per
+    call (the double-buffered build state)."""
+    from paper_2512_04996_gb300 import vicp
+    p = pairs(k)
+    flags = vicp.VICP_FLAG_KEEP_GRID | (vicp.VICP_FLAG_REBUILD_EACH_ITER if rebuild else 0)
+    g, d = _graph_pair(p, flags, max_iters)
+    src, tgt = torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda()
+    rng = np.random.default_rng(20 + k)
+    for call in range(4):
+        T0 = random_rigid(rng, 4.0, 0.02) if call % 2 else np.eye(4)
+        a, b = g.register(src, tgt, T0), d.register(src, tgt, T0)
+        assert a[0] == b[0] == 0 and a[2] == b[2] and a[3] == b[3], call
+        assert np.array_equal(a[1], b[1]), call
+    # a grid view after the replays is the direct context's
+    ga, gb = g.get_grid(), d.get_grid()
+    for key in ("keys", "offsets", "root", "ring", "occupancy"):
+        assert torch.equal(ga[key], gb[key]), key
+
+
+def test_register_host_graph_reads_the_clouds_anew(pairs):
+    """vicp_register_host replayed from a graph copies the host clouds at
+    every replay: new contents at the same (page-locked) addresses give the
+    results of direct launches on the new contents."""
+    from paper_2512_04996_gb300 import vicp
+    p = pairs(2)
+    flags = vicp.VICP_FLAG_KEEP_GRID
+    g, d = _graph_pair(p, flags, 5)
+    src = torch.from_numpy(p.source.copy()).pin_memory()
+    tgt = torch.from_numpy(p.target.copy()).pin_memory()
+    s_np, t_np = src.numpy(), tgt.numpy()
+    rng = np.random.default_rng(5)
+    for call in range(4):
+        if call == 3:   # move the source cloud in place
+            s_np[:, :3] += np.float32(0.01)
+        a, b = g.register_host(s_np, t_np), d.register_host(s_np, t_np)
+        assert a[0] == b[0] == 0 and a[2] == b[2] and np.array_equal(a[1], b[1]), call
+    # and the last result is the oracle's on the moved cloud
+    grid = oracle.fit_grid(p.target, p.voxel_size, p.grid_divisions)
+    rst, R, rit, hist = oracle.register(grid, 10, t_np, s_np, np.eye(4), max_iters=5, eps=0.0)
+    _assert_pose_close(a[1], R, _extent(p.target))
+
+
+def test_graph_and_direct_calls_interleave_on_one_context(pairs):
+    """Captured and direct calls of every kind on one context: host
+    registrations (captured from the second call, then replayed), then
+    device-resident registrations, a plain search and host registrations
+    again.  Each result equals that of a context that never captures."""
+    from paper_2512_04996_gb300 import vicp
+    p = pairs(2)
+    g, d = _graph_pair(p, vicp.VICP_FLAG_KEEP_GRID, 3)
+    s_np = torch.from_numpy(p.source.copy()).pin_memory().numpy()
+    t_np = torch.from_numpy(p.target.copy()).pin_memory().numpy()
+    src, tgt = torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda()
+    pose = torch.from_numpy(random_rigid(np.random.default_rng(3), 3.0, 0.02)).cuda()
+
+    def both(call):
+        a, b = call(g), call(d)
+        assert a[0] == b[0] == 0 and a[2] == b[2] and np.array_equal(a[1], b[1])
+
+    for _ in range(3):
+        both(lambda c: c.register_host(s_np, t_np))
+    for _ in range(3):
+        both(lambda c: c.register(src, tgt))
+    na, da, fa = g.correspond(src, pose)
+    nb, db, fb = d.correspond(src, pose)
+    assert torch.equal(na, nb) and torch.equal(da, db) and torch.equal(fa, fb)
+    for _ in range(3):
+        both(lambda c: c.register_host(s_np, t_np))
+    for _ in range(2):
+        both(lambda c: c.register(src, tgt))
