@@ -190,9 +190,24 @@ cudaError_t launch_correspond_fixed(const float4 *src, int m, const double *pose
 // Global search ("Globalsearch" of Alg. 4) of the queries the localised
 // search listed (global_search: a warp per query over the brick levels), and
 // the dense root segments it left (all lanes of a warp scan one).
+//
+// Scheduling without global atomics: block b takes the list entries b,
+// b + B, b + 2B, ... of both lists (B blocks; strided, so that a block's
+// share mixes the regions of the source cloud and the shares cost about the
+// same), global queries first and dense segments after them, and its warps
+// take these items one at a time from a shared-memory counter.  Per-query
+// costs vary several-fold, so the warps of a block balance each other; the
+// shares balance the blocks.  (A single global ticket counter would put one
+// same-address atomic per item, plus one per warp at the end, into the L2
+// line that also holds the list lengths every block reads: on the 226k
+// scene those ~17k serialised operations, not the searches, set the
+// kernel's duration.)
 // ---------------------------------------------------------------------------
 constexpr int FB_THREADS = 256;
 constexpr int FB_WARPS = FB_THREADS / 32;
+
+// Entries b, b + B, ... below n: how many.
+__device__ __forceinline__ int strided_share(int n, int b, int B) { return n > b ? (n - 1 - b) / B + 1 : 0; }
 
 __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__restrict__ src,
                                                          const double *__restrict__ pose,
@@ -213,65 +228,65 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
         return;   // the correspond kernel appended nothing either
     __shared__ PoseF sp;
     __shared__ unsigned long long s_examined;   // block total: one global atomic
-    if (threadIdx.x == 0)
+    __shared__ int s_F, s_Hv, s_ns, s_no;
+    __shared__ unsigned s_next;                 // next item of this block's share
+    if (threadIdx.x == 0) {
         s_examined = 0ull;
+        s_F = min(*(volatile int *)&ctl->fb_count, m);
+        s_Hv = min(*(volatile int *)&ctl->hv_count, m);
+        s_ns = *(volatile int *)&ctl->n_super;
+        s_no = *(volatile int *)&ctl->n_outside;
+        s_next = 0u;
+    }
     load_pose_f_block(pose, sp);   // also orders the initialisation above
     const PoseF P = sp;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int F = min(*(volatile int *)&ctl->fb_count, m);
-    const int Hv = min(*(volatile int *)&ctl->hv_count, m);
-    const int ns = *(volatile int *)&ctl->n_super;
-    const int no = *(volatile int *)&ctl->n_outside;
+    const int lane = threadIdx.x & 31;
+    const int F = s_F, Hv = s_Hv, ns = s_ns, no = s_no;
+    const int B = (int)gridDim.x, b = (int)blockIdx.x;
+    const int nG = strided_share(F, b, B), nH = strided_share(Hv, b, B);
     unsigned long long examined = 0ull;   // every lane counts the same; lane 0 reports
 
-    // the dense root segments the localised search left: all lanes scan one.
-    // They go to the warps in reverse order: the global queries below go in
-    // forward order, so the warps left one global query short take the extra
-    // segments.
-    const int n_warps = gridDim.x * FB_WARPS, gw = blockIdx.x * FB_WARPS + warp;
-    for (int qi = n_warps - 1 - gw; qi < Hv; qi += n_warps) {
-        const int i = __ldg(hv_list + qi);
-        const uint2 r = __ldg(hv_range + qi);
-        if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
-            if (lane == 0)
-                atomicOr(&ctl->err, DEVERR_BOUNDS);
-            continue;
-        }
-        const float3 s = transform_pt(P, __ldg(src + i));
-        unsigned long long unused = 0ull;
-        const unsigned long long best = scan_run(csr, r.x, r.y, s, lane, ~0ull, unused);
-        if (lane == 0) {
-            nn[i] = (int)(unsigned)best;
-            d2[i] = __uint_as_float((unsigned)(best >> 32));
-        }
-    }
-
-    // global queries, one at a time to whichever warp is free (a ticket each):
-    // their costs vary widely, and a fixed share per warp leaves the kernel
-    // waiting for the warp that drew the slowest ones
     for (;;) {
-        int qi = 0;
+        int k = 0;
         if (lane == 0)
-            qi = (int)atomicAdd(&ctl->fb_next, 1u);
-        qi = __shfl_sync(FULL_MASK, qi, 0);
-        if (qi >= F)
+            k = (int)atomicAdd(&s_next, 1u);
+        k = __shfl_sync(FULL_MASK, k, 0);
+        if (k >= nG + nH)
             break;
-        const int i = __ldg(fb_list + qi);
-        if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
-            if (lane == 0)
-                atomicOr(&ctl->err, DEVERR_BOUNDS);
-            continue;
-        }
-        const float3 s = transform_pt(P, __ldg(src + i));
-        const unsigned long long best = global_search(s, bpts, bbox, sb_box, ns, tgt, n_tgt, outside, no, lane,
-                                                      examined);
-        if (lane == 0) {
-            nn[i] = (int)(unsigned)best;
-            d2[i] = __uint_as_float((unsigned)(best >> 32));
+        if (k < nG) {   // a global query
+            const int i = __ldg(fb_list + b + k * B);
+            if ((unsigned)i >= (unsigned)m) {   // a stale entry: skip it, report it
+                if (lane == 0)
+                    atomicOr(&ctl->err, DEVERR_BOUNDS);
+                continue;
+            }
+            const float3 s = transform_pt(P, __ldg(src + i));
+            const unsigned long long best =
+                global_search(s, bpts, bbox, sb_box, ns, tgt, n_tgt, outside, no, lane, examined);
+            if (lane == 0) {
+                nn[i] = (int)(unsigned)best;
+                d2[i] = __uint_as_float((unsigned)(best >> 32));
+            }
+        } else {        // a dense root segment: all lanes scan it
+            const int qi = b + (k - nG) * B;
+            const int i = __ldg(hv_list + qi);
+            const uint2 r = __ldg(hv_range + qi);
+            if ((unsigned)i >= (unsigned)m) {
+                if (lane == 0)
+                    atomicOr(&ctl->err, DEVERR_BOUNDS);
+                continue;
+            }
+            const float3 s = transform_pt(P, __ldg(src + i));
+            unsigned long long unused = 0ull;
+            const unsigned long long best = scan_run(csr, r.x, r.y, s, lane, ~0ull, unused);
+            if (lane == 0) {
+                nn[i] = (int)(unsigned)best;
+                d2[i] = __uint_as_float((unsigned)(best >> 32));
+            }
         }
     }
     // work counter: one global atomic per block; the last block to finish
-    // clears the fallback counter for the next search
+    // clears the list lengths for the next search
     if (lane == 0 && examined)
         atomicAdd(&s_examined, examined);
     __syncthreads();
@@ -284,7 +299,6 @@ __global__ void __launch_bounds__(FB_THREADS, 4) k_fallback(const float4 *__rest
             ctl->stat_fallbacks += (unsigned long long)F;
             ctl->fb_count = 0;
             ctl->hv_count = 0;
-            ctl->fb_next = 0u;
             ctl->fb_done = 0u;
         }
     }
