@@ -399,7 +399,12 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 // so nothing ever has to be waited for: the CTA looks back over its
 // predecessors, 512 per round, and adds their totals down to the
 // nearest predecessor that has already published its inclusive prefix (any
-// one that has not is simply summed through).  A published prefix is one
+// one that has not is simply summed through).  Up to SCAN_DIRECT_TILES
+// tiles, the CTA instead adds all earlier totals itself (a few L1-cached
+// 16-byte loads per thread): every CTA reading its 512 nearest descriptors
+// from L2 put hundreds of thousands of loads on a few lines, and the
+// occupancy and count loads queued behind them (on the 226k scene the last
+// tiles ended 12 us after the median one).  A published prefix is one
 // 64-bit word [epoch:30 | flag:2 | value:32], so flag and value are read
 // together; the epoch (bumped by the histogram each build) retires the
 // previous build's words without clearing them.  The tile totals stay
@@ -417,6 +422,7 @@ cudaError_t launch_brick_scan(const unsigned *bcounts, const GridGeom &g, unsign
 // ---------------------------------------------------------------------------
 constexpr unsigned long long DESC_PREFIX = 2ull << 32;
 constexpr int LOOKBACK = 512;   // predecessors examined per lookback round
+constexpr int SCAN_DIRECT_TILES = 4096;   // up to this many tiles: no lookback, earlier totals summed directly
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
@@ -494,8 +500,65 @@ __device__ __forceinline__ unsigned word_count_sum(const unsigned *__restrict__ 
     return sum;
 }
 
+// A word with more than this many occupied voxels takes its 32 counts with
+// eight 16-byte loads (one round trip; the counts of empty voxels are zero
+// at scan time) instead of one load per occupied voxel.  A plane of the
+// cloud facing the grid's z axis fills whole scan tiles, and their threads
+// would otherwise take 16 rounds of loads per word to sum the counts and
+// then 32 dependent load-add steps to write the offsets: on the 226k depth
+// scene those few tiles ended 13 us after all others.
+constexpr int SCAN_DENSE_BITS = 4;
+
+// Sum of the 32 counts of the word at voxel b (b a multiple of 32).
+__device__ __forceinline__ unsigned word_count_sum_vec(const unsigned *__restrict__ counts, long long b)
+{
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(counts + b);
+    unsigned sum = 0u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            c[q] = __ldg(c4 + 4 * h + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            sum += (c[q].x + c[q].y) + (c[q].z + c[q].w);
+    }
+    return sum;
+}
+
+// All 32 offsets of the word at voxel b from its first one, `run`, written
+// with 16-byte stores; returns the offset after the word.
+__device__ __forceinline__ unsigned word_offsets_vec(const unsigned *__restrict__ counts, unsigned *__restrict__ off,
+                                                     long long b, unsigned run)
+{
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(counts + b);
+    uint4 *o4 = reinterpret_cast<uint4 *>(off + b);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            c[q] = __ldg(c4 + 4 * h + q);   // from L1
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 o;
+            o.x = run;
+            run += c[q].x;
+            o.y = run;
+            run += c[q].y;
+            o.z = run;
+            run += c[q].z;
+            o.w = run;
+            run += c[q].w;
+            o4[4 * h + q] = o;
+        }
+    }
+    return run;
+}
+
 template <int THREADS, int WPT, bool DENSE>
-__global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
+__global__ void __launch_bounds__(THREADS, DENSE ? 3 : 1024 / THREADS)
     k_scan(const unsigned *__restrict__ counts, long long V, unsigned *__restrict__ off,
            const unsigned *__restrict__ occ, const unsigned *__restrict__ tile_sum,
            unsigned long long *__restrict__ desc, const DevCtl *__restrict__ ctl)
@@ -519,13 +582,37 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
     for (int w = 0; w < WPT; ++w)
         bits[w] = base + 32 * w < V ? __ldg(occ + (base >> 5) + w) : 0u;
     constexpr int CPT = LOOKBACK / THREADS;   // predecessors per thread and round
+    const bool direct = gridDim.x <= SCAN_DIRECT_TILES;
     unsigned long long d0[CPT];
     unsigned t0[CPT];
+    unsigned before = 0u;   // direct: this thread's part of the earlier tiles' totals
+    if (direct) {
+        if ((reinterpret_cast<uintptr_t>(tile_sum) & 15u) == 0u) {
+            for (int j = 4 * tid; j < (int)tile; j += 4 * THREADS) {
+                if (j + 4 <= (int)tile) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(tile_sum + j));
+                    before += (q.x + q.y) + (q.z + q.w);
+                } else {
+                    for (int k = j; k < (int)tile; ++k)
+                        before += __ldg(tile_sum + k);
+                }
+            }
+        } else {
+            for (int j = tid; j < (int)tile; j += THREADS)
+                before += __ldg(tile_sum + j);
+        }
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        const long long idx = (long long)tile - 1 - (c * THREADS + tid);
-        d0[c] = idx >= 0 ? ld_relaxed_u64(desc + idx) : 0ull;
-        t0[c] = idx >= 0 ? __ldg(tile_sum + idx) : 0u;
+        for (int c = 0; c < CPT; ++c) {
+            d0[c] = 0ull;
+            t0[c] = 0u;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const long long idx = (long long)tile - 1 - (c * THREADS + tid);
+            d0[c] = idx >= 0 ? ld_relaxed_u64(desc + idx) : 0ull;
+            t0[c] = idx >= 0 ? __ldg(tile_sum + idx) : 0u;
+        }
     }
     unsigned sum = 0u;
     if (DENSE) {
@@ -534,8 +621,18 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
             sum += ((bits[0] >> i) & 1u) ? __ldg(counts + base + i) : 0u;
     } else {
 #pragma unroll
-        for (int w = 0; w < WPT; ++w)
-            sum += word_count_sum(counts, base + 32 * w, bits[w]);
+        for (int w = 0; w < WPT; ++w) {
+            const long long b = base + 32 * w;
+            if (__popc(bits[w]) > SCAN_DENSE_BITS && b + 32 <= V)
+                sum += word_count_sum_vec(counts, b);
+            else
+                sum += word_count_sum(counts, b, bits[w]);
+        }
+    }
+    if (direct) {
+        before = warp_sum_u32(before);
+        if (lane == 0)
+            s_sum[warp] = before;   // read after the block scan's barriers
     }
     unsigned tile_total;
     const unsigned thread_excl = block_excl_scan<WARPS>(sum, s_w, &tile_total);   // also orders s_epoch
@@ -545,7 +642,12 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
     // looks at tile - 1 - (c THREADS + i), c < CPT); sum the totals before the
     // nearest published prefix
     unsigned excl = 0u;
-    for (long long look = (long long)tile - 1; look >= 0; look -= LOOKBACK) {
+    if (direct) {
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w)
+            excl += s_sum[w];
+    }
+    for (long long look = direct ? -1ll : (long long)tile - 1; look >= 0; look -= LOOKBACK) {
         bool pre[CPT];
         unsigned v[CPT];
         unsigned mine = LOOKBACK;   // this warp's nearest published prefix
@@ -592,7 +694,7 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
         if (first < LOOKBACK)
             break;
     }
-    if (tid == 0)
+    if (tid == 0 && !direct)
         st_relaxed_u64(desc + tile, tag | DESC_PREFIX | (unsigned)(excl + tile_total));
 
     unsigned run = excl + thread_excl;
@@ -603,6 +705,12 @@ __global__ void __launch_bounds__(THREADS, DENSE ? 3 : 2048 / THREADS)
             const long long b = base + 32 * w;
             if (b > V)
                 break;
+            if (__popc(bits[w]) > SCAN_DENSE_BITS && b + 32 <= V) {   // every entry of the word
+                run = word_offsets_vec(counts, off, b, run);
+                if (b + 32 == V)
+                    off[V] = run;
+                continue;
+            }
             off[b] = run;   // the word's first entry (off[V] itself when b == V)
             for (unsigned m = bits[w]; m; m &= m - 1u) {
                 const int i = __ffs(m) - 1;
