@@ -202,11 +202,11 @@ def test_profile_counts_launches(pairs):
 
 def test_fp64_and_double_float_agree_and_are_deterministic(pairs):
     """The two precisions register the object workload to the same pose
-    (both within the oracle's tolerance of each other), and the FP64 path
-    gives bit-identical results from run to run."""
+    (both within the oracle's tolerance of each other), and each gives
+    bit-identical results from run to run."""
     p = pairs(2)
     out = {}
-    for prec in ("double_float", "fp64", "fp64"):
+    for prec in ("double_float", "double_float", "fp64", "fp64"):
         ctx = context(L=10, divisions=128, max_iters=10, eps=0.0, flags=_prec_flags(prec))
         st, T, it, rm = ctx.register(torch.from_numpy(p.source).cuda(), torch.from_numpy(p.target).cuda())
         assert st == 0 and it == 10

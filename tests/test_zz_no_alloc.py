@@ -4,6 +4,8 @@ same grid: bit-exact keys and offsets on consecutive calls with different
 clouds and grid sizes, device memory unchanged by calls after the first, and
 the size and argument checks.  Collected last so that it also runs after every
 other GPU test in one process."""
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -60,12 +62,21 @@ def test_static_offsets_equal_build_grid_on_consecutive_calls(pairs):
     assert np.array_equal(keys, rkeys)
     assert np.array_equal(off, oracle.offsets(oracle.histogram(rkeys, g.n_voxels)))
 
-    free0 = torch.cuda.mem_get_info()[0]
-    keys, off = _run_static(v, small, e_small, k_small, o_small)   # smaller grid after a larger one
-    assert np.array_equal(keys, e_small["keys"]) and np.array_equal(off, e_small["offsets"])
-    keys, off = _run_static(v, scene, e_scene, k_scene, o_scene)   # and back: scratch cleared each call
-    assert np.array_equal(keys, e_scene["keys"]) and np.array_equal(off, e_scene["offsets"])
-    assert torch.cuda.mem_get_info()[0] == free0
+    # device memory must not move across the next calls: objects of earlier
+    # tests that hold device buffers are collected first, and the collector
+    # is held off meanwhile (a context freed mid-test raised the free count)
+    gc.collect()
+    torch.cuda.synchronize()
+    gc.disable()
+    try:
+        free0 = torch.cuda.mem_get_info()[0]
+        keys, off = _run_static(v, small, e_small, k_small, o_small)   # smaller grid after a larger one
+        assert np.array_equal(keys, e_small["keys"]) and np.array_equal(off, e_small["offsets"])
+        keys, off = _run_static(v, scene, e_scene, k_scene, o_scene)   # and back: scratch cleared each call
+        assert np.array_equal(keys, e_scene["keys"]) and np.array_equal(off, e_scene["offsets"])
+        assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        gc.enable()
 
 
 def test_static_offsets_repeat_same_input(pairs):
