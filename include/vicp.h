@@ -341,6 +341,11 @@ VICP_API vicp_status vicp_read_stats(vicp_ctx *ctx, vicp_stats *out, int32_t res
 /* Kernels this context has launched since vicp_create. */
 VICP_API int64_t vicp_launch_count(const vicp_ctx *ctx);
 
+/* 1 if the last vicp_register / vicp_register_host call on this context
+ * replayed its captured CUDA graph, 0 if it launched its kernels one by one
+ * (or no registration has run yet); -1 for a NULL context. */
+VICP_API int32_t vicp_graph_replayed(const vicp_ctx *ctx);
+
 /* Text of the last error on this context ("" if none). */
 VICP_API const char *vicp_last_error(const vicp_ctx *ctx);
 

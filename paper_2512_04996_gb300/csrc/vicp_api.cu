@@ -118,6 +118,7 @@ struct vicp_ctx {
     };
     RegKey rg_key, rg_last;           // the graph's call; the last direct call
     bool rg_last_valid = false, rg_broken = false;
+    bool rg_replayed = false;         // the last registration call replayed the graph
     cudaGraphExec_t rg_exec = nullptr;
     int64_t rg_launches = 0;
     cudaStream_t gstream = nullptr;
@@ -979,13 +980,18 @@ vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float 
     key.flags = c->params.flags;
     key.eps = c->params.rmse_eps;
     key.geom = c->geom;
+    c->rg_replayed = false;
     if (graphable(c)) {
-        if (c->rg_exec && same_call(key, c->rg_key))
+        if (c->rg_exec && same_call(key, c->rg_key)) {
+            c->rg_replayed = true;
             return replay_registration(c, pose_host, iters_out, rmse_out);
+        }
         // the second call in a row with the same arguments: capture it
         if (c->rg_last_valid && same_call(key, c->rg_last) &&
-            capture_registration(c, key, src, tgt, src_host, tgt_host) == VICP_OK)
+            capture_registration(c, key, src, tgt, src_host, tgt_host) == VICP_OK) {
+            c->rg_replayed = true;
             return replay_registration(c, pose_host, iters_out, rmse_out);
+        }
     }
     if (key.host) {   // the direct path issues the copies itself
         const size_t sb = (size_t)m * 16, tb = (size_t)n * 16;
@@ -1582,6 +1588,13 @@ vicp_status vicp_read_stats(vicp_ctx *c, vicp_stats *out, int32_t reset)
 int64_t vicp_launch_count(const vicp_ctx *c) { return c ? c->launches : 0; }
 
 const char *vicp_last_error(const vicp_ctx *c) { return c ? c->last_error.c_str() : ""; }
+
+int32_t vicp_graph_replayed(const vicp_ctx *c)
+{
+    if (!c)
+        return -1;
+    return c->rg_replayed ? 1 : 0;
+}
 
 }  // extern "C"
 

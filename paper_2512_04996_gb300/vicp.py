@@ -126,6 +126,7 @@ SIGNATURES = {
     "vicp_profile_read": (C.c_int, [_P, _P, _P]),
     "vicp_read_stats": (C.c_int, [_P, C.POINTER(vicp_stats), C.c_int32]),
     "vicp_launch_count": (C.c_int64, [_P]),
+    "vicp_graph_replayed": (C.c_int32, [_P]),
     "vicp_last_error": (C.c_char_p, [_P]),
     "vicp_offsets_static": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_float, C.POINTER(C.c_int32), _P, _P,
                                       _P]),
@@ -430,6 +431,11 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.vicp_launch_count(self.handle))
+
+    def graph_replayed(self) -> bool:
+        """Whether the last register / register_host call replayed its
+        captured CUDA graph."""
+        return bool(self._lib.vicp_graph_replayed(self.handle))
 
 
 # --- the C names, as plain functions over a Context ------------------------

@@ -240,6 +240,7 @@ def test_register_graph_replays_equal_direct_launches(pairs, k, max_iters, rebui
         a, b = g.register(src, tgt, T0), d.register(src, tgt, T0)
         assert a[0] == b[0] == 0 and a[2] == b[2] and a[3] == b[3], call
         assert np.array_equal(a[1], b[1]), call
+        assert g.graph_replayed() == (call >= 1) and not d.graph_replayed(), call
     # a grid view after the replays is the direct context's
     ga, gb = g.get_grid(), d.get_grid()
     for key in ("keys", "offsets", "root", "ring", "occupancy"):
