@@ -749,7 +749,6 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
     __shared__ PoseF s_pose;
     __shared__ BatchItem s_item;
     __shared__ int s_skip, s_flag, s_last;
-    __shared__ unsigned s_next;   // phase 2: next item of this block's share
     __shared__ unsigned long long s_cand;
     __shared__ int s_fb, s_fb_base, s_hv, s_hv_base;
     __shared__ float s_whi[WARPS][N_SUMS], s_wlo[WARPS][N_SUMS];
@@ -867,61 +866,59 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
     if (!grid_barrier(ctl, &s_flag))
         return;
 
-    // ---- phase 2: global searches, then dense segments, a warp each -------
-    // Block b takes the entries b, b + B, ... of both lists (global queries
-    // first) and its warps take them in turn from a shared counter: the
-    // global searches are shared out over all warps whatever pair they
-    // belong to, with no global atomic per item.
+    // ---- phase 2: dense segments, then global searches, a warp each -------
     {
         const int F = min(*(volatile int *)&ctl->fb_count, a.list_cap);
         const int Hv = min(*(volatile int *)&ctl->hv_count, a.list_cap);
-        const int B = (int)gridDim.x, bk = (int)blockIdx.x;
-        const int nG = F > bk ? (F - 1 - bk) / B + 1 : 0, nH = Hv > bk ? (Hv - 1 - bk) / B + 1 : 0;
-        if (tid == 0)
-            s_next = 0u;
-        __syncthreads();
+        const int n_warps = gridDim.x * WARPS, gw = blockIdx.x * WARPS + warp;
         unsigned long long examined = 0ull;
+        for (int qi = n_warps - 1 - gw; qi < Hv; qi += n_warps) {
+            const int4 e = a.hv_list[qi];
+            if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap || e.z > e.w ||
+                (unsigned)e.w > (unsigned)a.n_stored) {   // a stale entry: skip it, report it
+                if (lane == 0)
+                    atomicOr(&ctl->err, DEVERR_BOUNDS);
+                continue;
+            }
+            const PoseF P = pose_f_warp(a.pose + 16 * e.x);
+            const float3 s = transform_pt(P, __ldg(a.src + e.y));
+            unsigned long long unused = 0ull;
+            const unsigned long long best = scan_run(a.csr, (unsigned)e.z, (unsigned)e.w, s, lane, ~0ull, unused);
+            if (lane == 0) {
+                a.nn[e.y] = (int)(unsigned)best;
+                a.d2[e.y] = __uint_as_float((unsigned)(best >> 32));
+            }
+        }
+        // global queries in chunks of FB_CHUNK, each chunk to whichever warp is
+        // free (a ticket per chunk): their costs vary widely, and a fixed share
+        // per warp leaves the whole grid waiting at the barrier for the warp
+        // that drew the slowest ones
+        constexpr int FB_CHUNK = 4;
         for (;;) {
-            int k = 0;
+            int q0 = 0;
             if (lane == 0)
-                k = (int)atomicAdd(&s_next, 1u);
-            k = __shfl_sync(FULL_MASK, k, 0);
-            if (k >= nG + nH)
+                q0 = FB_CHUNK * (int)atomicAdd(&ctl->fb_next, 1u);
+            q0 = __shfl_sync(FULL_MASK, q0, 0);
+            if (q0 >= F)
                 break;
-            if (k < nG) {
-                const int2 e = a.fb_list[bk + k * B];
-                if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap) {
-                    if (lane == 0)   // a stale entry: skip it, report it
-                        atomicOr(&ctl->err, DEVERR_BOUNDS);
-                    continue;
-                }
-                const BatchPair *bp = a.pairs + e.x;
-                const PoseF P = pose_f_warp(a.pose + 16 * e.x);
-                const float3 s = transform_pt(P, __ldg(a.src + e.y));
-                const int tbase = bp->tbase;
-                const unsigned long long best =
-                    global_search(s, a.bpts, a.bbox + 2 * bp->bbase, a.sb_box + 2 * bp->sbbase, a.state[e.x].n_super,
-                                  a.tgt + tbase, bp->n_tgt, a.outside + tbase, a.state[e.x].n_outside, lane, examined);
-                if (lane == 0) {
-                    a.nn[e.y] = (int)(unsigned)best;
-                    a.d2[e.y] = __uint_as_float((unsigned)(best >> 32));
-                }
-            } else {
-                const int4 e = a.hv_list[bk + (k - nG) * B];
-                if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap || e.z > e.w ||
-                    (unsigned)e.w > (unsigned)a.n_stored) {   // a stale entry: skip it, report it
-                    if (lane == 0)
-                        atomicOr(&ctl->err, DEVERR_BOUNDS);
-                    continue;
-                }
-                const PoseF P = pose_f_warp(a.pose + 16 * e.x);
-                const float3 s = transform_pt(P, __ldg(a.src + e.y));
-                unsigned long long unused = 0ull;
-                const unsigned long long best = scan_run(a.csr, (unsigned)e.z, (unsigned)e.w, s, lane, ~0ull, unused);
-                if (lane == 0) {
-                    a.nn[e.y] = (int)(unsigned)best;
-                    a.d2[e.y] = __uint_as_float((unsigned)(best >> 32));
-                }
+            for (int qi = q0; qi < min(q0 + FB_CHUNK, F); ++qi) {
+            const int2 e = a.fb_list[qi];
+            if ((unsigned)e.x >= (unsigned)a.n_pairs || (unsigned)e.y >= (unsigned)a.list_cap) {
+                if (lane == 0)   // a stale entry: skip it, report it
+                    atomicOr(&ctl->err, DEVERR_BOUNDS);
+                continue;
+            }
+            const BatchPair *bp = a.pairs + e.x;
+            const PoseF P = pose_f_warp(a.pose + 16 * e.x);
+            const float3 s = transform_pt(P, __ldg(a.src + e.y));
+            const int tbase = bp->tbase;
+            const unsigned long long best =
+                global_search(s, a.bpts, a.bbox + 2 * bp->bbase, a.sb_box + 2 * bp->sbbase, a.state[e.x].n_super,
+                              a.tgt + tbase, bp->n_tgt, a.outside + tbase, a.state[e.x].n_outside, lane, examined);
+            if (lane == 0) {
+                a.nn[e.y] = (int)(unsigned)best;
+                a.d2[e.y] = __uint_as_float((unsigned)(best >> 32));
+            }
             }
         }
         if (lane == 0 && examined)
@@ -932,6 +929,7 @@ __global__ void __launch_bounds__(TH, MINB) k_batch_iter(const BatchIterArgs a)
             ctl->stat_fallbacks += (unsigned long long)F;
             ctl->fb_count = 0;
             ctl->hv_count = 0;
+            ctl->fb_next = 0u;
         }
     }
     if (a.search_only)

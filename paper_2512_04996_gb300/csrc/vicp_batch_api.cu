@@ -471,6 +471,7 @@ vicp_status reset_loop(vicp_batch *b)
     BCUDA(b, cudaMemsetAsync(&d->fb_count, 0, sizeof(int), st), "list reset");
     BCUDA(b, cudaMemsetAsync(&d->hv_count, 0, sizeof(int), st), "list reset");
     BCUDA(b, cudaMemsetAsync(&d->bar_count, 0, sizeof(unsigned), st), "barrier reset");
+    BCUDA(b, cudaMemsetAsync(&d->fb_next, 0, sizeof(unsigned), st), "ticket reset");
     return VICP_OK;
 }
 

@@ -71,7 +71,7 @@ struct DevCtl {
     int hv_count;           // correspond: dense segments listed; reset by the fallback kernel
     unsigned bar_gen;       // batched iteration: grid barrier generation
     int n_super;            // non-empty super-bricks; reset by the histogram
-    unsigned spare;         // unused (keeps the layout)
+    unsigned fb_next;       // batched iteration: next chunk of listed global queries; reset with fb_count
     // Work counters (added by the search kernels, read and cleared by the host).
     unsigned long long stat_queries;       // source points searched
     unsigned long long stat_fallbacks;     // of which took the global search
