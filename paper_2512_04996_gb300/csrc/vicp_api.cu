@@ -122,7 +122,6 @@ struct vicp_ctx {
     cudaGraphExec_t rg_exec = nullptr;
     int64_t rg_launches = 0;
     cudaStream_t gstream = nullptr;
-    cudaEvent_t ev_gin = nullptr, ev_gout = nullptr;
     double *h_pose = nullptr;         // page-locked, 16 doubles
     RegOut *h_out = nullptr;          // page-locked
     bool capturing = false, nns_in_capture = false;
@@ -861,8 +860,6 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
 {
     if (!c->gstream) {
         if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_gin, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_gout, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost((void **)&c->h_pose, 16 * sizeof(double)) != cudaSuccess ||
             cudaMallocHost((void **)&c->h_out, sizeof(vicp_ctx::RegOut)) != cudaSuccess) {
             cudaGetLastError();
@@ -942,17 +939,11 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
 vicp_status replay_registration(vicp_ctx *c, double pose_host[16], int32_t *iters_out, double *rmse_out)
 {
     std::memcpy(c->h_pose, pose_host, 16 * sizeof(double));
-    cudaError_t e = cudaEventRecord(c->ev_gin, c->stream);
+    // launched into the context's stream itself: ordered after everything
+    // issued there before, with no event between them
+    cudaError_t e = cudaGraphLaunch(c->rg_exec, c->stream);
     if (e == cudaSuccess)
-        e = cudaStreamWaitEvent(c->gstream, c->ev_gin, 0);
-    if (e == cudaSuccess)
-        e = cudaGraphLaunch(c->rg_exec, c->gstream);
-    if (e == cudaSuccess)
-        e = cudaEventRecord(c->ev_gout, c->gstream);
-    if (e == cudaSuccess)
-        e = cudaStreamWaitEvent(c->stream, c->ev_gout, 0);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(c->gstream);
+        e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "graph replay");
     c->launches += c->rg_launches;
@@ -1185,9 +1176,6 @@ void vicp_destroy(vicp_ctx *c)
         cudaFreeHost(c->h_pose);
     if (c->h_out)
         cudaFreeHost(c->h_out);
-    for (cudaEvent_t e : {c->ev_gin, c->ev_gout})
-        if (e)
-            cudaEventDestroy(e);
     if (c->gstream)
         cudaStreamDestroy(c->gstream);
     for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src})
