@@ -112,9 +112,7 @@ struct vicp_ctx {
     };
     struct RegOut {
         double pose[16];
-        int stop, iters;
-        double prev, last;
-        unsigned err;
+        DevCtl ctl;   // the control block after the call (loop state, status word)
     };
     RegKey rg_key, rg_last;           // the graph's call; the last direct call
     bool rg_last_valid = false, rg_broken = false;
@@ -770,31 +768,38 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
     return VICP_OK;
 }
 
-// src_ready: an event the source's producer recorded (null: the source is
-// ready in stream order); the first search waits for it, the build does not.
-// The work of one registration on the context's stream: build, dilate, the
-// initial pose from pose_in (host), the iterations, and the pose, the loop
-// state and the device status copied to `out` (host).
+// The work of one registration: the initial pose from pose_in (host) and
+// the loop state reset on the internal copy stream, where they run beside
+// the build (host_copies: the caller has already queued the source cloud's
+// copy there, after the context's earlier work; otherwise the copy stream is
+// ordered after that work here), then on the context's stream build,
+// dilate, a wait for the copy stream, the iterations, and the pose and the
+// control block (loop state, status word) copied to out_pose / out_ctl
+// (host).
 vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
-                              const double *pose_in, void *out_pose, void *out_loop, unsigned *out_err,
-                              cudaEvent_t src_ready)
+                              const double *pose_in, void *out_pose, DevCtl *out_ctl, bool host_copies)
 {
+    double *pose = (double *)c->pose.p;
+    DevCtl *d = ctl_of(c);
+    cudaError_t e = cudaSuccess;
+    if (!host_copies) {
+        e = cudaEventRecord(c->ev_copy_go, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(c->copy, c->ev_copy_go, 0);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pose, pose_in, 16 * sizeof(double), cudaMemcpyHostToDevice, c->copy);
+    if (e == cudaSuccess)   // stop, iters, prev_rmse, last_rmse (the build's kernels use other fields)
+        e = cudaMemsetAsync(&d->stop, 0, sizeof(DevCtl) - offsetof(DevCtl, stop), c->copy);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->ev_src, c->copy);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "pose upload and loop state reset");
     TRY(build(c, tgt, n));
     TRY(dilate(c, -1));
-    if (src_ready) {
-        const cudaError_t w = cudaStreamWaitEvent(c->stream, src_ready, 0);
-        if (w != cudaSuccess)
-            return cuda_fail(c, w, "stream wait");
-    }
-    double *pose = (double *)c->pose.p;
-    cudaError_t e = cudaMemcpyAsync(pose, pose_in, 16 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    e = cudaStreamWaitEvent(c->stream, c->ev_src, 0);
     if (e != cudaSuccess)
-        return cuda_fail(c, e, "pose upload");
-    DevCtl *d = ctl_of(c);
-    // reset the loop state: stop, iters, prev_rmse, last_rmse
-    e = cudaMemsetAsync(&d->stop, 0, sizeof(DevCtl) - offsetof(DevCtl, stop), c->stream);
-    if (e != cudaSuccess)
-        return cuda_fail(c, e, "loop state reset");
+        return cuda_fail(c, e, "stream wait");
     for (int k = 0; k < c->params.max_iters; ++k) {
         if (k > 0 && (c->params.flags & VICP_FLAG_REBUILD_EACH_ITER)) {
             TRY(build(c, tgt, n));
@@ -804,10 +809,7 @@ vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const f
     }
     e = cudaMemcpyAsync(out_pose, pose, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_loop, &d->stop, sizeof(DevCtl) - offsetof(DevCtl, stop), cudaMemcpyDeviceToHost,
-                            c->stream);
-    if (e == cudaSuccess && out_err)
-        e = cudaMemcpyAsync(out_err, &d->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+        e = cudaMemcpyAsync(out_ctl, d, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "result read-back");
     return VICP_OK;
@@ -900,8 +902,7 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
                 e = cudaEventRecord(c->ev_src, c->copy);
         }
         if (e == cudaSuccess)
-            s = registration_work(c, src, key.m, tgt, key.n, c->h_pose, c->h_out->pose, &c->h_out->stop,
-                                  &c->h_out->err, key.host ? c->ev_src : nullptr);
+            s = registration_work(c, src, key.m, tgt, key.n, c->h_pose, c->h_out->pose, &c->h_out->ctl, key.host);
         const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
         if (e == cudaSuccess)
             e = e2;
@@ -950,14 +951,14 @@ vicp_status replay_registration(vicp_ctx *c, double pose_host[16], int32_t *iter
     c->after_solve = false;
     std::memcpy(pose_host, c->h_out->pose, 16 * sizeof(double));
     if (iters_out)
-        *iters_out = c->h_out->iters;
+        *iters_out = c->h_out->ctl.iters;
     if (rmse_out)
-        *rmse_out = c->h_out->last;
-    return device_status_from(c, c->h_out->err);
+        *rmse_out = c->h_out->ctl.last_rmse;
+    return device_status_from(c, c->h_out->ctl.err);
 }
 
 vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
-                         double pose_host[16], int32_t *iters_out, double *rmse_out, cudaEvent_t src_ready = nullptr,
+                         double pose_host[16], int32_t *iters_out, double *rmse_out,
                          const float *src_host = nullptr, const float *tgt_host = nullptr)
 {
     vicp_ctx::RegKey key;
@@ -999,17 +1000,16 @@ vicp_status registration(vicp_ctx *c, const float4 *src, int32_t m, const float 
         if (e != cudaSuccess)
             return cuda_fail(c, e, "host-to-device copy of the clouds");
     }
-    struct {
-        int stop, iters;
-        double prev, last;
-    } loop;
-    static_assert(sizeof(loop) == sizeof(DevCtl) - offsetof(DevCtl, stop), "loop state layout");
-    TRY(registration_work(c, src, m, tgt, n, pose_host, pose_host, &loop, nullptr, src_ready));
-    vicp_status st = read_device_status(c);   // synchronises
+    DevCtl ctl_h;
+    TRY(registration_work(c, src, m, tgt, n, pose_host, pose_host, &ctl_h, key.host));
+    const cudaError_t se = cudaStreamSynchronize(c->stream);
+    if (se != cudaSuccess)
+        return cuda_fail(c, se, "synchronise");
+    vicp_status st = device_status_from(c, ctl_h.err);
     if (iters_out)
-        *iters_out = loop.iters;
+        *iters_out = ctl_h.iters;
     if (rmse_out)
-        *rmse_out = loop.last;
+        *rmse_out = ctl_h.last_rmse;
     key.geom = c->geom;   // as fitted by this call
     c->rg_last = key;
     c->rg_last_valid = st == VICP_OK || st == VICP_ERR_DEGENERATE;
@@ -1287,7 +1287,7 @@ vicp_status vicp_register_host(vicp_ctx *c, const float *src_host, int32_t n_src
     // context's stream (earlier searches may still read the buffer), so it
     // travels while the grid is built; the first search waits for it.
     return registration(c, (const float4 *)c->hsrc.p, n_src, (const float *)c->htgt.p, n_tgt, pose_host,
-                        iters_out, rmse_out, c->ev_src, src_host, tgt_host);
+                        iters_out, rmse_out, src_host, tgt_host);
 }
 
 vicp_status vicp_get_grid(vicp_ctx *c, vicp_grid_view *out)
