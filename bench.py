@@ -608,9 +608,9 @@ def run_sparse(dev, pair, flush, steps: int, dense_pose, dense_mem) -> dict:
     st, T, it, rm = ctx_r.register(src, tgt)
     ext = _extent(pair.target)
     return {
-        "what": "the headline step on the sparse (hashed) grid: occupied and labelled voxels in hash tables "
-                "instead of per-voxel counts, offsets, root and ring (one host synchronisation per dilation "
-                "to size the labelled-voxel table)",
+        "what": "the headline step on the sparse (hashed) grid: occupied voxels and labelled row segments "
+                "in hash tables instead of per-voxel counts, offsets, root and ring (one host synchronisation "
+                "per dilation to size the labelled-segment table)",
         "iters_per_s": round(len(ms) / (sum(ms) / 1e3), 1),
         "amortised_grid_built_once_iters_per_s": round(len(amort) / (sum(amort) / 1e3), 1),
         "kernels_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in prof.items() if v[0]},

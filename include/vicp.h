@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define VICP_ABI_VERSION 1
+#define VICP_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define VICP_API __attribute__((visibility("default")))
@@ -276,16 +276,22 @@ VICP_API vicp_status vicp_get_grid(vicp_ctx *ctx, vicp_grid_view *out);
  *     at least 2 n_target slots, so at most half full) whose slots carry the
  *     counts and the segment offsets (an exclusive scan in slot order, so
  *     segments lie in the store in slot order), and
- *   - the labelled voxels (within L of a point), in a second table (voxel
- *     key -> root voxel key; the ring is the Manhattan distance between the
- *     two voxels), sized after a dilation to keep it at most half full
- *     (vicp_dilate synchronises once: pass Z counts the labels, and a table
- *     that was too small is grown and the dilation run again).  Under
- *     VICP_FLAG_KEEP_GRID the size found by the first dilation of the kept
- *     grid is kept and later dilations run without that synchronisation; a
+ *   - the labelled voxels (within L of a point), by row segment: a segment
+ *     is 32 voxels along x of one row of one plane (voxel x, y, z lies in
+ *     segment x/32 + nxb (y + ny z), nxb = ceil(nx / 32)); a second table
+ *     holds every segment with a labelled voxel (segment -> the mask of its
+ *     labelled voxels, bit x mod 32, and the index of its first root), and
+ *     the labelled voxels' root voxel keys lie segment after segment in a
+ *     root array, a segment's in the order of their x (the ring is the
+ *     Manhattan distance between a voxel and its root).  The table is sized
+ *     after a dilation to keep it at most half full, the root array to hold
+ *     every label (vicp_dilate synchronises once: pass Z counts them, and
+ *     what was too small is grown and the dilation run again).  Under
+ *     VICP_FLAG_KEEP_GRID the sizes found by the first dilation of the kept
+ *     grid are kept and later dilations run without that synchronisation; a
  *     cloud that then needs more room is reported by the next synchronising
  *     call as VICP_ERR_STATE (its labels are incomplete), and the next
- *     vicp_dilate checks and grows the table again.
+ *     vicp_dilate checks and grows them again.
  * Keys, CSR ids and points, the occupancy bits, the dilation's pass-Y words
  * and the global search's brick level are as in the dense grid, and every
  * search result equals the dense grid's.  Not available with the
@@ -306,10 +312,14 @@ typedef struct vicp_sparse_view {
     const uint32_t *occupied_offsets;  /* [occupied_slots + 1]: the points of the voxel in slot s are
                                           ids[occupied_offsets[s] .. occupied_offsets[s + 1]); valid for
                                           occupied slots s (and s + 1), and [occupied_slots] = n_stored */
-    int64_t labelled_slots;            /* slots of the labelled-voxel table (0 before a dilation) */
-    const uint32_t *labelled_keys;     /* [labelled_slots] voxel key, 0xffffffff for an empty slot */
-    const int32_t *labelled_root;      /* [labelled_slots] root voxel key of the voxel in that slot */
-    int64_t labelled_voxels;           /* entries in the labelled-voxel table */
+    int64_t labelled_slots;            /* slots of the labelled-segment table (0 before a dilation) */
+    const uint32_t *labelled_keys;     /* [labelled_slots] segment, 0xffffffff for an empty slot */
+    const uint32_t *labelled_segments; /* [labelled_slots x 2]: the segment's label mask (bit i: voxel
+                                          32 (segment mod nxb) + i of its row) and the index in
+                                          labelled_root of its first labelled voxel's root */
+    const int32_t *labelled_root;      /* [labelled_voxels] root voxel keys, segment by segment */
+    int64_t labelled_voxels;           /* labelled voxels */
+    int64_t labelled_segment_count;    /* entries in the labelled-segment table */
     const int32_t *keys;               /* [n_target] voxel key of each target point, -1 outside */
     const int32_t *ids;                /* [n_stored] point indices grouped by voxel */
     const float *csr_points;           /* [n_stored x 4] x, y, z of ids[k]; w holds the bits of ids[k] */

@@ -89,11 +89,13 @@ struct vicp_ctx {
     // keys, per-block counts of pass Z + its overflow flag), instead of the
     // V-sized counts, offsets, root and ring arrays
     Buf okeys[2], ocount, ooff, socc[2], stile, sdesc, pslot;
-    Buf lkeys, lroot, lparts;
+    Buf lkeys, lseg, lroot, lparts;   // labelled-segment table (keys, masks + first roots), roots, counts
     long long cap_o = 0, cap_l = 0;   // slots (powers of two)
+    long long cap_r = 0;              // root array of the labelled voxels
     int o_cur = 0;
     long long cap_occV = -1;
     long long lab_count = 0;          // labelled voxels of the last dilation
+    long long lab_segs = 0;           // ... and their row segments
     bool lab_kept = false;            // with VICP_FLAG_KEEP_GRID: the table size was checked for ...
     int lab_L = -1, lab_kept_dims[3] = {0, 0, 0};   // ... this L and these grid dimensions
 
@@ -363,18 +365,23 @@ vicp_status ensure_sparse_buffers(vicp_ctx *c, long long n)
     return VICP_OK;
 }
 
-// The labelled-voxel table with `slots` slots (keys are cleared by the
-// dilation itself), and pass Z's per-block counts + overflow flag.
-vicp_status ensure_label_table(vicp_ctx *c, long long slots, int L)
+// The labelled-segment table with `slots` slots (keys are cleared by the
+// dilation itself), the root array with `roots` entries, and pass Z's
+// per-block counts + overflow flag + root counter.
+vicp_status ensure_label_table(vicp_ctx *c, long long slots, long long roots, int L)
 {
     if (slots > c->cap_l) {
-        TRY(buf_alloc(c, c->lkeys, (size_t)slots * 4, "labelled-voxel table"));
-        TRY(buf_alloc(c, c->lroot, (size_t)slots * 4, "labelled-voxel roots"));
+        TRY(buf_alloc(c, c->lkeys, (size_t)slots * 4, "labelled-segment table"));
+        TRY(buf_alloc(c, c->lseg, (size_t)slots * 8, "labelled-segment masks"));
         c->cap_l = slots;
     }
-    const size_t parts = (size_t)(dilate_hashed_blocks(c->geom, L) + 1) * 4;
+    if (roots > c->cap_r) {
+        TRY(buf_alloc(c, c->lroot, (size_t)roots * 4, "labelled roots"));
+        c->cap_r = roots;
+    }
+    const size_t parts = (size_t)(dilate_hashed_blocks(c->geom, L) + 2) * 4;
     if (parts > c->lparts.bytes)
-        TRY(buf_alloc(c, c->lparts, parts, "labelled-voxel counts"));
+        TRY(buf_alloc(c, c->lparts, parts, "labelled-segment counts"));
     return VICP_OK;
 }
 
@@ -509,7 +516,8 @@ vicp_status run_localised(vicp_ctx *c, const float4 *src, int m, const double *p
     DevCtl *d = ctl_of(c);
     if (sparse_of(c))
         return launch(c, K_CORRESPOND, [&] {
-            return launch_correspond_hashed(src, m, pose, g, table_of(c->lkeys, c->cap_l), (const int *)c->lroot.p,
+            return launch_correspond_hashed(src, m, pose, g, table_of(c->lkeys, c->cap_l), (const uint2 *)c->lseg.p,
+                                            (const int *)c->lroot.p,
                                             table_of(c->okeys[c->o_cur], c->cap_o), (const unsigned *)c->ooff.p,
                                             (const float4 *)c->csr.p, c->n_target, nn, d2, (int *)c->fb_list.p,
                                             (int *)c->hv_list.p, (uint2 *)c->hv_range.p, d, honor_stop, c->stream);
@@ -631,54 +639,57 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
 }
 
 // The sparse grid's dilation (on the side stream, after the waits of
-// dilate()): pass Z inserts the labelled voxels into the labelled-voxel
-// table, then the host checks that the table had room at most half full --
-// one synchronisation per dilation -- and, if not, grows it to twice the
-// labelled count and runs the dilation again.
+// dilate()): pass Z enters the labelled row segments into the segment table
+// and their roots into the root array, then the host checks that the table
+// was at most half full and the roots fitted -- one synchronisation per
+// dilation -- and, if not, grows them (the table to twice the segments, the
+// roots to their count + 1/8) and runs the dilation again.
 vicp_status dilate_sparse(vicp_ctx *c, int L)
 {
     const GridGeom &g = c->geom;
-    long long slots = c->cap_l > 0 ? c->cap_l : pow2_at_least(c->n_target * 2 > 4096 ? (long long)c->n_target * 2 : 4096);
+    const long long n4 = (long long)c->n_target * 4 > 4096 ? (long long)c->n_target * 4 : 4096;
+    long long slots = c->cap_l > 0 ? c->cap_l : pow2_at_least(n4 / 4);
+    long long roots = c->cap_r > 0 ? c->cap_r : 2 * n4;
     const int blocks = dilate_hashed_blocks(g, L);
     unsigned *err = &ctl_of(c)->err;
+    unsigned *parts_d = (unsigned *)c->lparts.p;
+    auto run = [&]() -> vicp_status {   // counts, the overflow flag and the root counter start at zero
+        parts_d = (unsigned *)c->lparts.p;
+        cudaError_t e = cudaMemsetAsync(parts_d, 0, (size_t)(blocks + 2) * 4, c->side);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "labelled-segment counts");
+        return launch_on(c, K_DILATE, c->side, [&] {
+            return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
+                                        (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (uint2 *)c->lseg.p,
+                                        (int *)c->lroot.p, (unsigned)c->cap_r, parts_d, err, c->side);
+        });
+    };
     // VICP_FLAG_KEEP_GRID keeps the grid of the first build, and with it the
-    // table size checked then: later dilations of the same grid run without
+    // table sizes checked then: later dilations of the same grid run without
     // the check (a cloud that needs more room is reported by the next
     // synchronising call as VICP_ERR_STATE, and the next dilation checks).
     if ((c->params.flags & VICP_FLAG_KEEP_GRID) && c->lab_kept && c->lab_L == L && c->lab_kept_dims[0] == g.nx &&
         c->lab_kept_dims[1] == g.ny && c->lab_kept_dims[2] == g.nz) {
-        cudaError_t e = cudaMemsetAsync((unsigned *)c->lparts.p + blocks, 0, 4, c->side);
-        if (e != cudaSuccess)
-            return cuda_fail(c, e, "labelled-voxel overflow flag");
-        TRY(launch_on(c, K_DILATE, c->side, [&] {
-            return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
-                                        (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (int *)c->lroot.p,
-                                        (unsigned *)c->lparts.p, err, c->side);
-        }));
+        TRY(run());
     } else {
     c->lab_kept = false;
     for (int attempt = 0;; ++attempt) {
-        TRY(ensure_label_table(c, slots, L));
-        cudaError_t e = cudaMemsetAsync(c->lparts.p, 0, (size_t)(blocks + 1) * 4, c->side);
-        if (e != cudaSuccess)
-            return cuda_fail(c, e, "labelled-voxel counts");
-        TRY(launch_on(c, K_DILATE, c->side, [&] {
-            return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
-                                        (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (int *)c->lroot.p,
-                                        (unsigned *)c->lparts.p, err, c->side);
-        }));
-        std::vector<unsigned> parts((size_t)blocks + 1);
-        e = cudaMemcpyAsync(parts.data(), c->lparts.p, parts.size() * 4, cudaMemcpyDeviceToHost, c->side);
+        TRY(ensure_label_table(c, slots, roots, L));
+        TRY(run());
+        std::vector<unsigned> parts((size_t)blocks + 2);
+        cudaError_t e = cudaMemcpyAsync(parts.data(), parts_d, parts.size() * 4, cudaMemcpyDeviceToHost, c->side);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(c->side);
         if (e != cudaSuccess)
-            return cuda_fail(c, e, "labelled-voxel count read-back");
-        long long count = 0;
+            return cuda_fail(c, e, "labelled-segment count read-back");
+        long long segs = 0;
         for (int b = 0; b < blocks; ++b)
-            count += parts[b];
+            segs += parts[b];
         const bool overflow = parts[blocks] != 0;
-        if (!overflow && 2 * count <= c->cap_l) {
+        const long long count = parts[blocks + 1];   // roots handed out (all labelled voxels when they fitted)
+        if (!overflow && 2 * segs <= c->cap_l && count <= c->cap_r) {
             c->lab_count = count;
+            c->lab_segs = segs;
             c->lab_kept = true;
             c->lab_L = L;
             c->lab_kept_dims[0] = g.nx;
@@ -692,8 +703,11 @@ vicp_status dilate_sparse(vicp_ctx *c, int L)
                 return cuda_fail(c, e, "status update");
         }
         if (attempt >= 3)
-            return fail(c, VICP_ERR_CUDA, "labelled-voxel table: %lld voxels do not fit %lld slots", count, c->cap_l);
-        slots = pow2_at_least(2 * count > 2 * c->cap_l ? 2 * count : 2 * c->cap_l);
+            return fail(c, VICP_ERR_CUDA, "labelled-segment table: %lld segments / %lld voxels do not fit %lld / %lld",
+                        segs, count, c->cap_l, c->cap_r);
+        // a root count past the array is a lower bound: grow at least twofold
+        slots = pow2_at_least(2 * segs > 2 * c->cap_l ? 2 * segs : 2 * c->cap_l);
+        roots = count + count / 8 > 2 * c->cap_r ? count + count / 8 : 2 * c->cap_r;
     }
     }
     cudaError_t e = cudaEventRecord(c->ev_dil, c->side);
@@ -1038,9 +1052,10 @@ vicp_status memory_report_sparse(vicp_ctx *c, vicp_memory *out)
     if (e != cudaSuccess)
         return cuda_fail(c, e, "memory report read-back");
     vicp_status st = read_device_status(c);
-    const uint64_t V = (uint64_t)g.V, So = (uint64_t)c->cap_o, Sl = (uint64_t)c->cap_l;
+    const uint64_t V = (uint64_t)g.V, So = (uint64_t)c->cap_o, Sl = (uint64_t)c->cap_l, Sr = (uint64_t)c->cap_r;
     out->static_bytes = So * 4 * 3 + 4;   // occupied-voxel table: keys, counts, offsets
-    out->csr_store_bytes = So * 4 * 2 + 4 + (uint64_t)stored * 4 + Sl * 8;   // + ids + labelled-voxel table
+    // + ids + the labelled-segment table (keys, masks and first roots) and the roots
+    out->csr_store_bytes = So * 4 * 2 + 4 + (uint64_t)stored * 4 + Sl * 12 + Sr * 4;
     out->max_voxel_count = mc[0];
     out->occupied_voxels = mc[1];
     out->nonempty_bricks = (uint32_t)nbricks;
@@ -1157,7 +1172,7 @@ void vicp_destroy(vicp_ctx *c)
                   &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt,    &c->fslots,   &c->fcount,   &c->fover,
                   &c->okeys[0], &c->okeys[1], &c->ocount, &c->ooff, &c->socc[0], &c->socc[1], &c->stile, &c->sdesc,
-                  &c->pslot,   &c->lkeys,   &c->lroot,    &c->lparts};
+                  &c->pslot,   &c->lkeys,   &c->lseg,     &c->lroot,    &c->lparts};
     for (Buf *b : all)
         buf_free(c, *b);
     for (auto &t : c->pending) {
@@ -1360,8 +1375,10 @@ vicp_status vicp_get_sparse_grid(vicp_ctx *c, vicp_sparse_view *out)
     out->occupied_offsets = (const uint32_t *)c->ooff.p;
     out->labelled_slots = c->dilated_L >= 0 ? c->cap_l : 0;
     out->labelled_keys = c->dilated_L >= 0 ? (const uint32_t *)c->lkeys.p : nullptr;
+    out->labelled_segments = c->dilated_L >= 0 ? (const uint32_t *)c->lseg.p : nullptr;
     out->labelled_root = c->dilated_L >= 0 ? (const int32_t *)c->lroot.p : nullptr;
     out->labelled_voxels = c->dilated_L >= 0 ? c->lab_count : 0;
+    out->labelled_segment_count = c->dilated_L >= 0 ? c->lab_segs : 0;
     out->keys = (const int32_t *)c->keys.p;
     out->ids = (const int32_t *)c->ids.p;
     out->csr_points = (const float *)c->csr.p;

@@ -49,7 +49,7 @@ namespace vicp {
 
 using namespace dil;
 
-// `clear` (sparse grid: the labelled-voxel table's keys, which pass Z fills)
+// `clear` (sparse grid: the labelled-segment table's keys, which pass Z fills)
 // is set to HASH_EMPTY on the way: pass Z starts only after this kernel.
 template <class W>
 __global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restrict__ occ, long long n_words, GridGeom g,
@@ -78,14 +78,16 @@ __global__ void __launch_bounds__(THREADS) k_dilate_z(const typename W::Stored *
         dilate_z_unit<W>(u, inter, rows, out, g, L, nxb, nyb);
 }
 
-// Pass Z into the labelled-voxel table; each block writes the number of
-// voxels it labelled to counts[blockIdx.x], and counts[gridDim.x] (zero
-// beforehand) is set to 1 if an insert gave up.
+// Pass Z into the labelled-segment table; each block writes the number of
+// segments it entered to counts[blockIdx.x], counts[gridDim.x] (zero
+// beforehand) is set to 1 if an insert gave up or the roots ran out, and
+// counts[gridDim.x + 1] (zero beforehand) counts the roots handed out.
 template <class W>
 __global__ void __launch_bounds__(THREADS) k_dilate_z_hashed(const typename W::Stored *__restrict__ inter,
                                                              const unsigned *__restrict__ rows, GridGeom g, int L,
                                                              int nxb, int nyb, int units, HashTable table,
-                                                             int *__restrict__ root, unsigned *__restrict__ counts,
+                                                             uint2 *__restrict__ seg, int *__restrict__ root,
+                                                             unsigned cap_root, unsigned *__restrict__ counts,
                                                              unsigned *__restrict__ err)
 {
     pdl_begin();
@@ -93,11 +95,10 @@ __global__ void __launch_bounds__(THREADS) k_dilate_z_hashed(const typename W::S
     if (threadIdx.x == 0)
         s_count = 0u;
     __syncthreads();
-    const HashLabels out{table, root, counts + gridDim.x, err};
+    const HashLabels out{table, seg, root, cap_root, counts + gridDim.x + 1, counts + gridDim.x, err};
     unsigned n = 0u;
     for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
-        n += dilate_z_unit<W>(u, inter, rows, out, g, L, nxb, nyb);
-    n = __reduce_add_sync(FULL_MASK, n);
+        n += dilate_z_unit<W>(u, inter, rows, out, g, L, nxb, nyb);   // the same on every lane
     if ((threadIdx.x & 31) == 0 && n)
         atomicAdd(&s_count, n);
     __syncthreads();
@@ -120,7 +121,7 @@ static int resident_blocks(K kernel)
 template <class W>
 static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
                               unsigned char *dirty, int *root, unsigned char *ring, const HashTable *labels,
-                              unsigned *counts, unsigned *err, cudaStream_t st)
+                              uint2 *seg, unsigned cap_root, unsigned *counts, unsigned *err, cudaStream_t st)
 {
     using S = typename W::Stored;
     static const int xy_blocks = resident_blocks(k_dilate_xy<W>), z_blocks = resident_blocks(k_dilate_z<W>),
@@ -135,8 +136,8 @@ static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, voi
     const int u_z = nxb * g.ny * nzb;   // < V < 2^31
     if (labels)
         return launch_kernel(k_dilate_z_hashed<W>, dim3(min(zh_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0,
-                             st, static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, *labels, root, counts,
-                             err);
+                             st, static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, *labels, seg, root,
+                             cap_root, counts, err);
     return launch_kernel(k_dilate_z<W>, dim3(min(z_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0, st,
                          static_cast<const S *>(inter), rows, dirty, g, L, nxb, nyb, u_z, root, ring);
 }
@@ -164,16 +165,20 @@ cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *i
                           unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st)
 {
     if (L <= L_COMPACT_MAX)
-        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, nullptr, st);
-    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, nullptr, st);
+        return run_dilate<Words16>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, 0u, nullptr, nullptr,
+                                   st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, dirty, root, ring, nullptr, nullptr, 0u, nullptr, nullptr, st);
 }
 
 cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
-                                 const HashTable &labels, int *root, unsigned *counts, unsigned *err, cudaStream_t st)
+                                 const HashTable &labels, uint2 *seg, int *root, unsigned cap_root, unsigned *counts,
+                                 unsigned *err, cudaStream_t st)
 {
     if (L <= L_COMPACT_MAX)
-        return run_dilate<Words16>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, err, st);
-    return run_dilate<Words32>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, counts, err, st);
+        return run_dilate<Words16>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, seg, cap_root, counts,
+                                   err, st);
+    return run_dilate<Words32>(occ, g, L, inter, rows, nullptr, root, nullptr, &labels, seg, cap_root, counts, err,
+                               st);
 }
 
 // Clears bits of a device word (atomically, so that concurrent kernels'

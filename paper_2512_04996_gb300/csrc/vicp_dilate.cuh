@@ -214,20 +214,29 @@ __device__ __forceinline__ void dilate_xy_unit(int u, const unsigned *__restrict
 
 // Where pass Z puts its labels: the dense root / ring arrays (with the
 // per-unit flags that let unlabelled units skip their writes), or the
-// labelled-voxel table of the sparse grid (voxel key -> root key; the ring
-// is the Manhattan distance between the two keys' voxels), which holds the
-// labelled voxels only and starts empty at every dilation.
+// labelled-segment table of the sparse grid (row segment -> label mask and
+// first root index; the roots in a packed array; the ring is the Manhattan
+// distance between a voxel and its root), which holds the labelled segments
+// only and starts empty at every dilation.
 struct DenseLabels {
     unsigned char *dirty;
     int *root;
     unsigned char *ring;
 };
 struct HashLabels {
-    HashTable table;     // keys: the labelled voxels
-    int *root;           // [slots] root key of each labelled voxel
-    unsigned *overflow;  // set to 1 when an insert gave up (the table is too small) ...
-    unsigned *err;       // ... and DEVERR_CAPACITY set in the device status word
+    HashTable table;       // keys: the labelled row segments (32 voxels along x of one row of one plane)
+    uint2 *seg;            // [slots] the segment's label mask and the index of its first root in `root`
+    int *root;             // [cap_root] root keys of the labelled voxels, segment by segment
+    unsigned cap_root;
+    unsigned *root_count;  // roots handed out so far (zero before the dilation)
+    unsigned *overflow;    // set to 1 when an insert gave up or the roots ran out (too small) ...
+    unsigned *err;         // ... and DEVERR_CAPACITY set in the device status word
 };
+
+template <class W>
+__device__ __forceinline__ unsigned dilate_z_segments(unsigned (&c)[32], unsigned before, unsigned after,
+                                                      const HashLabels &out, const GridGeom &g, int L, int col,
+                                                      int z0, int kmax, bool in_x, int xb, int y, int nxb);
 
 // ---------------------------------------------------------------------------
 // Pass Z and the output.  Warp u = xb + nxb*(y + ny*zb) covers x in
@@ -266,7 +275,7 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
     }
     const bool labels = (pm[0] | pm[1] | pm[2]) != 0u;
     if constexpr (HASHED) {
-        if (x >= g.nx || !labels)
+        if (!labels)   // the whole warp: the segments' ballots need every lane
             return 0u;
     } else {
         // A unit with nothing within L keeps "unlabelled" unless the previous
@@ -287,10 +296,11 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
         }
     }
 
+    const bool in_x = x < g.nx;   // (hashed: lanes past the grid take part, with no words)
     unsigned c[UZ];
 #pragma unroll
     for (int k = 0; k < UZ; ++k)
-        c[k] = ((pm[0] >> k) & 1u) ? W::load_z(inter, col + plane * (z0 + k)) : NONE;
+        c[k] = (in_x && ((pm[0] >> k) & 1u)) ? W::load_z(inter, col + plane * (z0 + k)) : NONE;
     unsigned before = NONE, after = NONE;
 #pragma unroll 1
     for (int side = 1; side <= 2; ++side) {
@@ -305,7 +315,7 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int zz = side == 1 ? z0 - L + s[i] : z0 + UZ + s[i];
-                wv[i] = s[i] >= 0 ? W::load_z(inter, col + plane * zz) : NONE;
+                wv[i] = (in_x && s[i] >= 0) ? W::load_z(inter, col + plane * zz) : NONE;
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -318,6 +328,8 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
             }
         }
     }
+    if constexpr (HASHED)
+        return dilate_z_segments<W>(c, before, after, out, g, L, col, z0, kmax, in_x, xb, y, nxb);
     sweep32<STEP_ZF, STEP_ZB>(c, before, after, (unsigned)L << W::ZD);
 
     const unsigned valid = (unsigned)(L + 1) << W::ZD;   // words below this are labels
@@ -331,24 +343,87 @@ __device__ __forceinline__ unsigned dilate_z_unit(int u, const typename W::Store
             const unsigned w = c[k];
             const bool hit = w < valid;
             const int r = (int)(vb + (unsigned)plane * k + W::offset(w, (unsigned)g.nx, (unsigned)plane));
-            if constexpr (HASHED) {
-                if (hit) {
-                    const int slot = hash_insert(out.table, (unsigned)v);
-                    if (slot >= 0) {
-                        out.root[slot] = r;
-                    } else {
-                        atomicOr(out.overflow, 1u);
-                        atomicOr(out.err, DEVERR_CAPACITY);
-                    }
-                    ++labelled;
-                }
-            } else {
+            if constexpr (!HASHED) {
                 out.root[v] = hit ? r : -1;
                 out.ring[v] = hit ? (unsigned char)(w >> W::ZD) : (unsigned char)255;
+                labelled += hit ? 1u : 0u;
             }
         }
     }
     return labelled;
+}
+
+// Pass Z's output into the sparse grid's labelled-segment table.  Plane k
+// of the unit is one row segment (x in [32 xb, 32 xb + 32) of row y); its
+// labelled voxels, a ballot over the lanes, are one entry: the label mask
+// and the index of the segment's first root in the root array, whose slice
+// for the whole unit one lane reserves with a single atomic.  Lane k then
+// inserts segment k (at most 32 inserts per unit, all at once), and every
+// lane stores the roots of its labelled voxels at their rank in the
+// segment.  Returns the segments entered (for the table's size).
+template <class W>
+__device__ __forceinline__ unsigned dilate_z_segments(unsigned (&c)[32], unsigned before, unsigned after,
+                                                      const HashLabels &out, const GridGeom &g, int L, int col,
+                                                      int z0, int kmax, bool in_x, int xb, int y, int nxb)
+{
+    constexpr unsigned STEP_ZF = (1u << W::ZD) - (1u << W::ZZ);
+    constexpr unsigned STEP_ZB = (1u << W::ZD) + (1u << W::ZZ);
+    const int lane = threadIdx.x & 31;
+    const int plane = g.nx * g.ny;
+    sweep32<STEP_ZF, STEP_ZB>(c, before, after, (unsigned)L << W::ZD);
+    const unsigned valid = (unsigned)(L + 1) << W::ZD;   // words below this are labels
+
+    // lane k: the label mask of plane k
+    unsigned my_mask = 0u;
+#pragma unroll
+    for (int k = 0; k < UZ; ++k) {
+        const unsigned m = __ballot_sync(FULL_MASK, in_x && k < kmax && c[k] < valid);
+        if (lane == k)
+            my_mask = m;
+    }
+    const unsigned cnt = __popc(my_mask);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d)
+            incl += t;
+    }
+    const unsigned total = __shfl_sync(FULL_MASK, incl, 31);
+    if (total == 0u)
+        return 0u;
+    unsigned base = 0u;
+    if (lane == 0)
+        base = atomicAdd(out.root_count, total);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if ((unsigned long long)base + total > out.cap_root) {   // the root array is too small
+        if (lane == 0) {
+            atomicOr(out.overflow, 1u);
+            atomicOr(out.err, DEVERR_CAPACITY);
+        }
+        return 0u;
+    }
+    const unsigned my_base = base + incl - cnt;
+    if (my_mask) {
+        const unsigned sid = (unsigned)xb + (unsigned)nxb * ((unsigned)y + (unsigned)g.ny * (unsigned)(z0 + lane));
+        const int slot = hash_insert(out.table, sid);
+        if (slot >= 0) {
+            out.seg[slot] = make_uint2(my_mask, my_base);
+        } else {
+            atomicOr(out.overflow, 1u);
+            atomicOr(out.err, DEVERR_CAPACITY);
+        }
+    }
+    const unsigned vb = (unsigned)(col + plane * z0) - W::bias((unsigned)g.nx, (unsigned)plane);
+#pragma unroll
+    for (int k = 0; k < UZ; ++k) {
+        const unsigned mk = __shfl_sync(FULL_MASK, my_mask, k), bk = __shfl_sync(FULL_MASK, my_base, k);
+        if ((mk >> lane) & 1u) {
+            const int r = (int)(vb + (unsigned)plane * k + W::offset(c[k], (unsigned)g.nx, (unsigned)plane));
+            out.root[bk + __popc(mk & ((1u << lane) - 1u))] = r;
+        }
+    }
+    return __popc(__ballot_sync(FULL_MASK, my_mask != 0u));
 }
 
 }  // namespace dil

@@ -115,14 +115,18 @@ cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl,
 cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
                           unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st);
 // The sparse grid's dilation: passes X and Y as above (the kernel also sets
-// the keys of `labels` to HASH_EMPTY first), then pass Z inserts every
-// labelled voxel into `labels` with its root key in root[slot]; block b of
-// pass Z writes its labelled-voxel count to counts[b], b <
-// dilate_hashed_blocks(g, L), and, if the table was too small for an
-// insert, sets counts[dilate_hashed_blocks(g, L)] (zero beforehand) to 1 and
-// DEVERR_CAPACITY in *err.
+// the keys of `labels` to HASH_EMPTY first), then pass Z enters every row
+// segment (32 voxels along x of one row of one plane) holding labelled
+// voxels into `labels` with seg[slot] = (label mask, index of the segment's
+// first root), and the labelled voxels' root keys into root[0 .. cap_root),
+// segment by segment.  Block b of pass Z writes its segment count to
+// counts[b], b < B = dilate_hashed_blocks(g, L); if an insert gave up or the
+// roots did not fit, it sets counts[B] (zero beforehand) to 1 and
+// DEVERR_CAPACITY in *err; counts[B + 1] (zero beforehand) ends as the
+// number of labelled voxels.
 cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
-                                 const HashTable &labels, int *root, unsigned *counts, unsigned *err, cudaStream_t st);
+                                 const HashTable &labels, uint2 *seg, int *root, unsigned cap_root, unsigned *counts,
+                                 unsigned *err, cudaStream_t st);
 // *word &= ~bits, atomically.
 cudaError_t launch_clear_bits(unsigned *word, unsigned bits, cudaStream_t st);
 int dilate_hashed_blocks(const GridGeom &g, int L);
@@ -136,13 +140,14 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
                               int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
                               cudaStream_t st);
 // The localised search on the sparse grid: root labels from the
-// labelled-voxel table (keys in `labelled`, root keys in lroot), segments
-// [off[slot], off[slot + 1]) by the root's slot in the occupied-voxel table.
+// labelled-segment table (segment ids in `labelled`, (mask, first root
+// index) in lseg, root keys in lroot), segments [off[slot], off[slot + 1])
+// by the root's slot in the occupied-voxel table.
 cudaError_t launch_correspond_hashed(const float4 *src, int m, const double *pose, const GridGeom &g,
-                                     const HashTable &labelled, const int *lroot, const HashTable &occupied,
-                                     const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
-                                     int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
-                                     cudaStream_t st);
+                                     const HashTable &labelled, const uint2 *lseg, const int *lroot,
+                                     const HashTable &occupied, const unsigned *off, const float4 *csr, int n_cap,
+                                     int *nn, float *d2, int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl,
+                                     int honor_stop, cudaStream_t st);
 // The localised search over a fixed-capacity store (C slots per voxel at
 // v * C, fill counts in count), listing like launch_correspond; the global
 // search then takes the slots as its dense-segment store.

@@ -44,27 +44,37 @@ struct FixedSeg {
 
 // Root label of voxel v, as the index of its segment in the store: the
 // dense root array (the root's voxel key), or the sparse grid's two tables
-// (the labelled-voxel table gives the root's voxel key, the occupied-voxel
-// table that voxel's slot, which indexes the offsets).  -1: unlabelled.
+// (the labelled-segment table gives v's row segment -- its label mask and
+// the index of its first root -- and so the root's voxel key, at v's rank
+// among the segment's labelled voxels; the occupied-voxel table gives that
+// voxel's slot, which indexes the offsets).  -1: unlabelled.
 struct DenseRoot {
     const int *root;
     __device__ __forceinline__ int operator()(int v) const { return __ldg(root + v); }
 };
 
 struct HashedRoot {
-    const unsigned *lkeys;   // labelled voxels
+    const unsigned *lkeys;   // labelled row segments
     unsigned lmask;
     int lshift;
-    const int *lroot;        // their root keys
+    const uint2 *lseg;       // their label masks and first-root indices
+    const int *lroot;        // the labelled voxels' root keys, segment by segment
     const unsigned *okeys;   // occupied voxels
     unsigned omask;
     int oshift;
+    int nx, nxb;             // grid row length, 32-voxel segments per row
     __device__ __forceinline__ int operator()(int v) const
     {
-        const int ls = hash_find(lkeys, lmask, lshift, (unsigned)v);
+        const int x = v % nx, row = v / nx;   // row = y + ny z
+        const int ls = hash_find(lkeys, lmask, lshift, (unsigned)((x >> 5) + nxb * row));
         if (ls < 0)
             return -1;
-        return hash_find(okeys, omask, oshift, (unsigned)__ldg(lroot + ls));
+        const uint2 e = __ldg(lseg + ls);
+        const unsigned bit = (unsigned)x & 31u;
+        if (!((e.x >> bit) & 1u))
+            return -1;
+        const int r = __ldg(lroot + e.y + __popc(e.x & ((1u << bit) - 1u)));
+        return hash_find(okeys, omask, oshift, (unsigned)r);
     }
 };
 
@@ -165,13 +175,13 @@ cudaError_t launch_correspond(const float4 *src, int m, const double *pose, cons
 }
 
 cudaError_t launch_correspond_hashed(const float4 *src, int m, const double *pose, const GridGeom &g,
-                                     const HashTable &labelled, const int *lroot, const HashTable &occupied,
-                                     const unsigned *off, const float4 *csr, int n_cap, int *nn, float *d2,
-                                     int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl, int honor_stop,
-                                     cudaStream_t st)
+                                     const HashTable &labelled, const uint2 *lseg, const int *lroot,
+                                     const HashTable &occupied, const unsigned *off, const float4 *csr, int n_cap,
+                                     int *nn, float *d2, int *fb_list, int *hv_list, uint2 *hv_range, DevCtl *ctl,
+                                     int honor_stop, cudaStream_t st)
 {
-    const HashedRoot root{labelled.keys, labelled.mask, labelled.shift, lroot,
-                          occupied.keys, occupied.mask, occupied.shift};
+    const HashedRoot root{labelled.keys, labelled.mask, labelled.shift, lseg, lroot,
+                          occupied.keys, occupied.mask, occupied.shift, g.nx, (g.nx + 31) / 32};
     return launch_kernel(k_correspond<CsrSeg, HashedRoot>, dim3((m + CORR_THREADS - 1) / CORR_THREADS),
                          dim3(CORR_THREADS), 0, st, src, m, pose, g, root, CsrSeg{off, (unsigned)n_cap}, csr, nn, d2,
                          fb_list, hv_list, hv_range, ctl, honor_stop);

@@ -77,7 +77,8 @@ class vicp_sparse_view(C.Structure):
                 ("dims", C.c_int32 * 3), ("n_voxels", C.c_int64), ("n_target", C.c_int32),
                 ("n_stored", C.c_int32), ("dilation_layers", C.c_int32), ("occupied_slots", C.c_int64),
                 ("occupied_keys", C.c_void_p), ("occupied_offsets", C.c_void_p), ("labelled_slots", C.c_int64),
-                ("labelled_keys", C.c_void_p), ("labelled_root", C.c_void_p), ("labelled_voxels", C.c_int64),
+                ("labelled_keys", C.c_void_p), ("labelled_segments", C.c_void_p), ("labelled_root", C.c_void_p),
+                ("labelled_voxels", C.c_int64), ("labelled_segment_count", C.c_int64),
                 ("keys", C.c_void_p), ("ids", C.c_void_p), ("csr_points", C.c_void_p), ("occupancy", C.c_void_p)]
 
 
@@ -397,11 +398,12 @@ class Context:
             "origin": tuple(float(v.origin[a]) for a in range(3)), "voxel_size": float(v.voxel_size),
             "inv_voxel_size": float(v.inv_voxel_size), "dims": tuple(int(v.dims[a]) for a in range(3)),
             "n_voxels": V, "n_target": n, "n_stored": ns, "dilation_layers": int(v.dilation_layers),
-            "labelled_voxels": int(v.labelled_voxels),
+            "labelled_voxels": int(v.labelled_voxels), "labelled_segment_count": int(v.labelled_segment_count),
             "occupied_keys": _view(v.occupied_keys, (So,), "<u4", torch.uint32, d).clone(),
             "occupied_offsets": _view(v.occupied_offsets, (So + 1,), "<u4", torch.uint32, d).clone(),
             "labelled_keys": _view(v.labelled_keys, (Sl,), "<u4", torch.uint32, d).clone(),
-            "labelled_root": _view(v.labelled_root, (Sl,), "<i4", torch.int32, d).clone(),
+            "labelled_segments": _view(v.labelled_segments, (Sl, 2), "<u4", torch.uint32, d).clone(),
+            "labelled_root": _view(v.labelled_root, (int(v.labelled_voxels),), "<i4", torch.int32, d).clone(),
             "keys": _view(v.keys, (n,), "<i4", torch.int32, d).clone(),
             "ids": _view(v.ids, (ns,), "<i4", torch.int32, d).clone(),
             "csr_points": _view(v.csr_points, (ns, 4), "<f4", torch.float32, d).clone(),

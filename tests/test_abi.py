@@ -51,7 +51,7 @@ def test_exports_nothing_undeclared():
 
 def test_host_only_helpers(lib):
     lib.vicp_abi_version.restype = C.c_int32
-    assert lib.vicp_abi_version() == 1
+    assert lib.vicp_abi_version() == 2
     lib.vicp_status_string.restype = C.c_char_p
     lib.vicp_status_string.argtypes = [C.c_int]
     assert lib.vicp_status_string(7) == b"degenerate geometry"

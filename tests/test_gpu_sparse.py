@@ -3,8 +3,9 @@
 Its tables are mapped back to dense per-voxel arrays here and compared bit
 for bit: the occupied-voxel table's keys and counts with the oracle's
 histogram, every voxel's CSR segment with the oracle's as a set, the
-labelled-voxel table's keys, roots and rings (the Manhattan distance between
-a voxel and its root) with the oracle's dilation.  Searches and
+labelled-segment table (a label mask and a slice of the root array per 32
+voxels along x) as labelled voxels, roots and rings (the Manhattan distance
+between a voxel and its root) with the oracle's dilation.  Searches and
 registrations must equal the oracle's at the usual tolerances -- and the
 dense grid's results bit for bit, since both grids feed the same search and
 reduction the same candidates in the same order.  Also: rebuilding with
@@ -71,14 +72,31 @@ def assert_sparse_equal(g, ref, target):
     assert np.array_equal(pts[:, 3].view(np.int32), ids)
     bits = np.unpackbits(g["occupancy"].view(np.uint8), bitorder="little")[:V]
     assert np.array_equal(bits.astype(bool), counts > 0)
-    # labelled voxels: exactly the oracle's, with its roots and rings
+    # labelled voxels: exactly the oracle's, with its roots and rings.  The
+    # table holds row segments (32 voxels along x): each entry's mask names
+    # its labelled voxels and its base the first of their roots, which
+    # follow in the order of x
     lkeys = g["labelled_keys"]
     lab = np.flatnonzero(lkeys != EMPTY)
-    lv = lkeys[lab].astype(np.int64)
+    assert g["labelled_segment_count"] == lab.shape[0]
+    nx, ny = g["dims"][0], g["dims"][1]
+    nxb = (nx + 31) // 32
+    sid = lkeys[lab].astype(np.int64)
+    seg = g["labelled_segments"][lab].astype(np.int64)
+    bits = ((seg[:, :1] >> np.arange(32)) & 1).astype(bool)          # [segments, 32]
+    assert bits.any(axis=1).all()
+    s_idx, bit = np.nonzero(bits)
+    x = 32 * (sid[s_idx] % nxb) + bit
+    assert (x < nx).all()
+    lv = x + nx * (sid[s_idx] // nxb)                                 # row = y + ny z
+    rank = np.cumsum(bits, axis=1)[s_idx, bit] - 1
+    ridx = seg[s_idx, 1] + rank
     want = np.flatnonzero(ref["root"] >= 0)
     assert g["labelled_voxels"] == want.shape[0]
     assert np.array_equal(np.sort(lv), want)
-    root = g["labelled_root"][lab]
+    # the roots array is covered exactly once, segment by segment
+    assert np.array_equal(np.sort(ridx), np.arange(g["labelled_voxels"]))
+    root = g["labelled_root"][ridx]
     assert np.array_equal(root, ref["root"][lv])
     ring = np.abs(_coords(lv, g["dims"]) - _coords(root, g["dims"])).sum(axis=1)
     assert np.array_equal(ring, ref["ring"][lv].astype(np.int64))
@@ -230,7 +248,7 @@ def test_sparse_rejects_the_dense_views(pairs):
 
 
 def test_sparse_kept_grid_reports_a_cloud_that_outgrows_the_table(pairs):
-    """Under VICP_FLAG_KEEP_GRID the labelled-voxel table keeps the size the
+    """Under VICP_FLAG_KEEP_GRID the labelled-segment table keeps the size the
     first dilation found: a much larger cloud in the same grid is reported by
     the next synchronising call (VICP_ERR_STATE), and the dilation after that
     checks and grows the table again, giving the oracle's labels."""
