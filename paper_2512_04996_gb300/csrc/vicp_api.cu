@@ -653,11 +653,8 @@ vicp_status dilate_sparse(vicp_ctx *c, int L)
     const int blocks = dilate_hashed_blocks(g, L);
     unsigned *err = &ctl_of(c)->err;
     unsigned *parts_d = (unsigned *)c->lparts.p;
-    auto run = [&]() -> vicp_status {   // counts, the overflow flag and the root counter start at zero
+    auto run = [&]() -> vicp_status {   // (pass XY zeroes the counts, the overflow flag and the root counter)
         parts_d = (unsigned *)c->lparts.p;
-        cudaError_t e = cudaMemsetAsync(parts_d, 0, (size_t)(blocks + 2) * 4, c->side);
-        if (e != cudaSuccess)
-            return cuda_fail(c, e, "labelled-segment counts");
         return launch_on(c, K_DILATE, c->side, [&] {
             return launch_dilate_hashed((const unsigned *)c->occ[c->occ_cur].p, g, L, c->inter.p,
                                         (unsigned *)c->uflag.p, table_of(c->lkeys, c->cap_l), (uint2 *)c->lseg.p,

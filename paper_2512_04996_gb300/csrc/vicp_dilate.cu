@@ -50,17 +50,21 @@ namespace vicp {
 using namespace dil;
 
 // `clear` (sparse grid: the labelled-segment table's keys, which pass Z fills)
-// is set to HASH_EMPTY on the way: pass Z starts only after this kernel.
+// is set to HASH_EMPTY and `zero` (pass Z's counters) to zero on the way:
+// pass Z starts only after this kernel.
 template <class W>
 __global__ void __launch_bounds__(THREADS) k_dilate_xy(const unsigned *__restrict__ occ, long long n_words, GridGeom g,
                                                        int L, int nxb, int nyb, int units,
                                                        typename W::Stored *__restrict__ inter,
                                                        unsigned *__restrict__ rows, unsigned *__restrict__ clear,
-                                                       long long clear_words)
+                                                       long long clear_words, unsigned *__restrict__ zero,
+                                                       int zero_words)
 {
     pdl_begin();
     for (long long w = (long long)blockIdx.x * THREADS + threadIdx.x; w < clear_words; w += (long long)gridDim.x * THREADS)
         clear[w] = HASH_EMPTY;
+    for (int w = blockIdx.x * THREADS + threadIdx.x; w < zero_words; w += gridDim.x * THREADS)
+        zero[w] = 0u;
     for (int u = blockIdx.x * WARPS + (threadIdx.x >> 5); u < units; u += gridDim.x * WARPS)
         dilate_xy_unit<W>(u, occ, n_words, g, L, nxb, nyb, inter, rows);
 }
@@ -128,16 +132,17 @@ static cudaError_t run_dilate(const unsigned *occ, const GridGeom &g, int L, voi
                      zh_blocks = resident_blocks(k_dilate_z_hashed<W>);
     const int nxb = (g.nx + UX - 1) / UX, nyb = (g.ny + UY - 1) / UY, nzb = (g.nz + UZ - 1) / UZ;
     const int u_xy = nxb * nyb * g.nz;   // < V < 2^31
+    const int u_z = nxb * g.ny * nzb;    // < V < 2^31
+    const int zh_grid = min(zh_blocks, (u_z + WARPS - 1) / WARPS);
     cudaError_t e = launch_kernel(k_dilate_xy<W>, dim3(min(xy_blocks, (u_xy + WARPS - 1) / WARPS)), dim3(THREADS), 0,
                                   st, occ, occ_words(g.V), g, L, nxb, nyb, u_xy, static_cast<S *>(inter), rows,
-                                  labels ? labels->keys : nullptr, labels ? (long long)labels->mask + 1 : 0ll);
+                                  labels ? labels->keys : nullptr, labels ? (long long)labels->mask + 1 : 0ll,
+                                  labels ? counts : nullptr, labels ? zh_grid + 2 : 0);
     if (e != cudaSuccess)
         return e;
-    const int u_z = nxb * g.ny * nzb;   // < V < 2^31
     if (labels)
-        return launch_kernel(k_dilate_z_hashed<W>, dim3(min(zh_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0,
-                             st, static_cast<const S *>(inter), rows, g, L, nxb, nyb, u_z, *labels, seg, root,
-                             cap_root, counts, err);
+        return launch_kernel(k_dilate_z_hashed<W>, dim3(zh_grid), dim3(THREADS), 0, st, static_cast<const S *>(inter),
+                             rows, g, L, nxb, nyb, u_z, *labels, seg, root, cap_root, counts, err);
     return launch_kernel(k_dilate_z<W>, dim3(min(z_blocks, (u_z + WARPS - 1) / WARPS)), dim3(THREADS), 0, st,
                          static_cast<const S *>(inter), rows, dirty, g, L, nxb, nyb, u_z, root, ring);
 }

@@ -69,6 +69,11 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // voxel key; the voxel occupancy bits (`occ`, read by the dilation) are set
 // as in the dense grid.
 // ---------------------------------------------------------------------------
+// Slot tables of at most this many scan tiles keep each block's tile totals
+// in shared memory: a voxel's slot is a hash, so the keys of one warp fall
+// into many tiles, and per-warp atomics would pile onto the few tile words.
+constexpr int HIST_SMEM_TILES = 1024;
+
 template <bool AFTER_SOLVE, bool SPARSE>
 __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pts, int n, GridGeom g,
                                                    int *__restrict__ keys, unsigned *__restrict__ counts,
@@ -97,6 +102,14 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
         ctl->scan_epoch = ctl->scan_epoch + 1u;
         ctl->n_outside = 0;
         ctl->n_super = 0;
+    }
+    __shared__ unsigned s_tile[SPARSE ? HIST_SMEM_TILES : 1];
+    const int n_tiles = SPARSE ? (int)((ho.mask + 1u) / SCAN_TILE) : 0;
+    const bool block_tiles = SPARSE && n_tiles <= HIST_SMEM_TILES;
+    if (block_tiles) {
+        for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+            s_tile[t] = 0u;
+        __syncthreads();
     }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     int key = -2, bk = -2;   // lanes past the end match only each other and add nothing
@@ -166,11 +179,18 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
         if (sw >= 0 && lane == __ffs(spe) - 1)
             atomicOr(socc + sw, sbits);
     }
-    // per-tile totals for the scan (one atomicAdd per tile and warp)
+    // per-tile totals for the scan (one atomicAdd per tile and warp; for a
+    // small slot table per tile and block, through shared memory)
     const int tile = idx >= 0 ? (idx / SCAN_TILE) : -2;
     const unsigned tpeers = __match_any_sync(FULL_MASK, tile);
     if (tile >= 0 && lane == __ffs(tpeers) - 1)
-        atomicAdd(tile_sum + tile, (unsigned)__popc(tpeers));
+        atomicAdd(block_tiles ? s_tile + tile : tile_sum + tile, (unsigned)__popc(tpeers));
+    if (block_tiles) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+            if (s_tile[t])
+                atomicAdd(tile_sum + t, s_tile[t]);
+    }
 }
 
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,

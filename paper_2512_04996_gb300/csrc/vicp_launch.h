@@ -115,15 +115,15 @@ cudaError_t launch_maxcount(const unsigned *off, const GridGeom &g, DevCtl *ctl,
 cudaError_t launch_dilate(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
                           unsigned char *dirty, int *root, unsigned char *ring, cudaStream_t st);
 // The sparse grid's dilation: passes X and Y as above (the kernel also sets
-// the keys of `labels` to HASH_EMPTY first), then pass Z enters every row
+// the keys of `labels` to HASH_EMPTY and counts[0 .. B + 2) to zero), then
+// pass Z enters every row
 // segment (32 voxels along x of one row of one plane) holding labelled
 // voxels into `labels` with seg[slot] = (label mask, index of the segment's
 // first root), and the labelled voxels' root keys into root[0 .. cap_root),
 // segment by segment.  Block b of pass Z writes its segment count to
 // counts[b], b < B = dilate_hashed_blocks(g, L); if an insert gave up or the
-// roots did not fit, it sets counts[B] (zero beforehand) to 1 and
-// DEVERR_CAPACITY in *err; counts[B + 1] (zero beforehand) ends as the
-// number of labelled voxels.
+// roots did not fit, it sets counts[B] to 1 and DEVERR_CAPACITY in *err;
+// counts[B + 1] ends as the number of labelled voxels.
 cudaError_t launch_dilate_hashed(const unsigned *occ, const GridGeom &g, int L, void *inter, unsigned *rows,
                                  const HashTable &labels, uint2 *seg, int *root, unsigned cap_root, unsigned *counts,
                                  unsigned *err, cudaStream_t st);
