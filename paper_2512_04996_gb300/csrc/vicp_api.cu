@@ -669,43 +669,44 @@ vicp_status dilate_sparse(vicp_ctx *c, int L)
         c->lab_kept_dims[1] == g.ny && c->lab_kept_dims[2] == g.nz) {
         TRY(run());
     } else {
-    c->lab_kept = false;
-    for (int attempt = 0;; ++attempt) {
-        TRY(ensure_label_table(c, slots, roots, L));
-        TRY(run());
-        std::vector<unsigned> parts((size_t)blocks + 2);
-        cudaError_t e = cudaMemcpyAsync(parts.data(), parts_d, parts.size() * 4, cudaMemcpyDeviceToHost, c->side);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(c->side);
-        if (e != cudaSuccess)
-            return cuda_fail(c, e, "labelled-segment count read-back");
-        long long segs = 0;
-        for (int b = 0; b < blocks; ++b)
-            segs += parts[b];
-        const bool overflow = parts[blocks] != 0;
-        const long long count = parts[blocks + 1];   // roots handed out (all labelled voxels when they fitted)
-        if (!overflow && 2 * segs <= c->cap_l && count <= c->cap_r) {
-            c->lab_count = count;
-            c->lab_segs = segs;
-            c->lab_kept = true;
-            c->lab_L = L;
-            c->lab_kept_dims[0] = g.nx;
-            c->lab_kept_dims[1] = g.ny;
-            c->lab_kept_dims[2] = g.nz;
-            break;
-        }
-        if (overflow) {   // this dilation is run again: its capacity report is withdrawn
-            e = launch_clear_bits(err, DEVERR_CAPACITY, c->side);
+        c->lab_kept = false;
+        for (int attempt = 0;; ++attempt) {
+            TRY(ensure_label_table(c, slots, roots, L));
+            TRY(run());
+            std::vector<unsigned> parts((size_t)blocks + 2);
+            cudaError_t e = cudaMemcpyAsync(parts.data(), parts_d, parts.size() * 4, cudaMemcpyDeviceToHost, c->side);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(c->side);
             if (e != cudaSuccess)
-                return cuda_fail(c, e, "status update");
+                return cuda_fail(c, e, "labelled-segment count read-back");
+            long long segs = 0;
+            for (int b = 0; b < blocks; ++b)
+                segs += parts[b];
+            const bool overflow = parts[blocks] != 0;
+            const long long count = parts[blocks + 1];   // roots handed out (all labelled voxels when they fitted)
+            if (!overflow && 2 * segs <= c->cap_l && count <= c->cap_r) {
+                c->lab_count = count;
+                c->lab_segs = segs;
+                c->lab_kept = true;
+                c->lab_L = L;
+                c->lab_kept_dims[0] = g.nx;
+                c->lab_kept_dims[1] = g.ny;
+                c->lab_kept_dims[2] = g.nz;
+                break;
+            }
+            if (overflow) {   // this dilation is run again: its capacity report is withdrawn
+                e = launch_clear_bits(err, DEVERR_CAPACITY, c->side);
+                if (e != cudaSuccess)
+                    return cuda_fail(c, e, "status update");
+            }
+            if (attempt >= 3)
+                return fail(c, VICP_ERR_CUDA,
+                            "labelled-segment table: %lld segments / %lld voxels do not fit %lld / %lld", segs, count,
+                            c->cap_l, c->cap_r);
+            // a root count past the array is a lower bound: grow at least twofold
+            slots = pow2_at_least(2 * segs > 2 * c->cap_l ? 2 * segs : 2 * c->cap_l);
+            roots = count + count / 8 > 2 * c->cap_r ? count + count / 8 : 2 * c->cap_r;
         }
-        if (attempt >= 3)
-            return fail(c, VICP_ERR_CUDA, "labelled-segment table: %lld segments / %lld voxels do not fit %lld / %lld",
-                        segs, count, c->cap_l, c->cap_r);
-        // a root count past the array is a lower bound: grow at least twofold
-        slots = pow2_at_least(2 * segs > 2 * c->cap_l ? 2 * segs : 2 * c->cap_l);
-        roots = count + count / 8 > 2 * c->cap_r ? count + count / 8 : 2 * c->cap_r;
-    }
     }
     cudaError_t e = cudaEventRecord(c->ev_dil, c->side);
     if (e == cudaSuccess)
