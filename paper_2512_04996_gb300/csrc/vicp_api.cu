@@ -43,6 +43,7 @@ struct vicp_ctx {
     cudaEvent_t ev_hist = nullptr, ev_nns = nullptr, ev_dil = nullptr;
     cudaStream_t copy = nullptr;                          // host-input source copy, beside the build
     cudaEvent_t ev_copy_go = nullptr, ev_src = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_clr = nullptr;      // graph capture: the buffer resets beside the copy
     int device = 0;
     int sms = 152;
     std::string last_error;
@@ -897,13 +898,26 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
     vicp_status s = VICP_OK;
     cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const int first = c->occ_cur ^ 1;   // the buffers the call's first build fills
-        e = cudaMemsetAsync(c->occ[first].p, 0, c->occ[first].bytes, c->gstream);
+        // the buffers the call's first build fills are reset on the copy
+        // stream, beside the target cloud's copy (with host clouds)
+        const int first = c->occ_cur ^ 1;
+        cudaStream_t rs = key.host ? c->copy : c->gstream;
+        if (key.host) {
+            e = cudaEventRecord(c->ev_fork, c->gstream);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(c->copy, c->ev_fork, 0);
+        }
         if (e == cudaSuccess)
-            e = cudaMemsetAsync(c->boxk[first].p, 0xff, c->boxk[first].bytes, c->gstream);
+            e = cudaMemsetAsync(c->occ[first].p, 0, c->occ[first].bytes, rs);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->boxk[first].p, 0xff, c->boxk[first].bytes, rs);
         if (e == cudaSuccess && key.host) {
             const size_t sb = (size_t)key.m * 16, tb = (size_t)key.n * 16;
-            e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->gstream);
+            e = cudaEventRecord(c->ev_clr, c->copy);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->htgt.p, tgt_host, tb, cudaMemcpyHostToDevice, c->gstream);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(c->gstream, c->ev_clr, 0);
             if (e == cudaSuccess)
                 e = cudaEventRecord(c->ev_copy_go, c->gstream);
             if (e == cudaSuccess)
@@ -928,7 +942,7 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
     // an event last recorded inside the capture names a node of the graph,
     // and a later direct launch may not wait for it: every event the work
     // records is recorded again, outside the capture, on the context's stream
-    for (cudaEvent_t ev : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src})
+    for (cudaEvent_t ev : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src, c->ev_fork, c->ev_clr})
         if (cudaEventRecord(ev, saved) != cudaSuccess && e == cudaSuccess)
             e = cudaErrorUnknown;
     c->after_solve = false;
@@ -1127,7 +1141,9 @@ vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_al
         cudaEventCreateWithFlags(&c->ev_dil, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_copy_go, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_src, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_src, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_clr, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         vicp_destroy(c);
         return VICP_ERR_CUDA;
@@ -1191,7 +1207,7 @@ void vicp_destroy(vicp_ctx *c)
         cudaFreeHost(c->h_out);
     if (c->gstream)
         cudaStreamDestroy(c->gstream);
-    for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src})
+    for (cudaEvent_t e : {c->ev_hist, c->ev_nns, c->ev_dil, c->ev_copy_go, c->ev_src, c->ev_fork, c->ev_clr})
         if (e)
             cudaEventDestroy(e);
     if (c->side)
