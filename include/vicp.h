@@ -410,10 +410,10 @@ VICP_API vicp_status vicp_fixed_view(vicp_ctx *ctx, const float **slots_out, con
  * one device that overlap in time race and give wrong results, so callers
  * must serialise them.  Each call clears the parts that must start at zero.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call outside any
- * stream capture.  The address is kept for the life of the process, so the
- * library must not be used on a device after cudaDeviceReset (or any other
- * teardown of the device's primary context) in the same process.  The call
+ * device, with that device current).  The address is kept for the life of
+ * the process, so the library must not be used on a device after
+ * cudaDeviceReset (or any other teardown of the device's primary context)
+ * in the same process.  The call
  * synchronises `cuda_stream` before returning, and runs on the device that
  * is current when it is called: `cuda_stream`, the target and the outputs
  * must belong to that device.
