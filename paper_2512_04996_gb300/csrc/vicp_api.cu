@@ -77,7 +77,8 @@ struct vicp_ctx {
     Buf nn, d2, fb_list, hv_list, hv_range;
     long long cap_M = -1;
     // fixed
-    Buf partials, pose, rmse, ctl, bbox;
+    Buf partials, rmse, bbox;
+    Buf ctl;   // laid out as RegOut: the registrations' pose, then the control block
     // host-input copies (vicp_register_host)
     Buf hsrc, htgt;
     // fixed-capacity store (vicp_fixed_build): C slots per voxel
@@ -254,7 +255,13 @@ vicp_status launch(vicp_ctx *c, int kernel, F &&f)
     return launch_on(c, kernel, c->stream, std::forward<F>(f));
 }
 
-DevCtl *ctl_of(vicp_ctx *c) { return static_cast<DevCtl *>(c->ctl.p); }
+DevCtl *ctl_of(vicp_ctx *c)
+{
+    return reinterpret_cast<DevCtl *>(static_cast<char *>(c->ctl.p) + offsetof(vicp_ctx::RegOut, ctl));
+}
+// The pose a registration iterates on (16 doubles before the control block,
+// so that one copy reads both back).
+double *reg_pose_of(vicp_ctx *c) { return static_cast<double *>(c->ctl.p); }
 
 bool sparse_of(const vicp_ctx *c) { return (c->params.flags & VICP_FLAG_SPARSE_GRID) != 0; }
 
@@ -792,7 +799,7 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
 vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
                               const double *pose_in, void *out_pose, DevCtl *out_ctl, bool host_copies)
 {
-    double *pose = (double *)c->pose.p;
+    double *pose = reg_pose_of(c);
     DevCtl *d = ctl_of(c);
     cudaError_t e = cudaSuccess;
     if (!host_copies) {
@@ -820,9 +827,13 @@ vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const f
         }
         TRY(run_step(c, src, m, pose, nullptr, 1));
     }
-    e = cudaMemcpyAsync(out_pose, pose, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_ctl, d, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (reinterpret_cast<char *>(out_ctl) == static_cast<char *>(out_pose) + offsetof(vicp_ctx::RegOut, ctl)) {
+        e = cudaMemcpyAsync(out_pose, c->ctl.p, sizeof(vicp_ctx::RegOut), cudaMemcpyDeviceToHost, c->stream);
+    } else {
+        e = cudaMemcpyAsync(out_pose, pose, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_ctl, d, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    }
     if (e != cudaSuccess)
         return cuda_fail(c, e, "result read-back");
     return VICP_OK;
@@ -1152,13 +1163,11 @@ vicp_status vicp_create(vicp_ctx **out, const vicp_params *params, const vicp_al
         cudaGetLastError();
         c->sms = 152;
     }
-    s = buf_alloc(c, c->ctl, sizeof(DevCtl), "control block");
+    s = buf_alloc(c, c->ctl, sizeof(vicp_ctx::RegOut), "control block and registration pose");
     if (s == VICP_OK)
         s = buf_zero(c, c->ctl, "zero control block");
     if (s == VICP_OK)
         s = buf_alloc(c, c->partials, REDUCE_MAX_BLOCKS * REDUCE_VALUES * sizeof(float2), "partials");
-    if (s == VICP_OK)
-        s = buf_alloc(c, c->pose, 16 * sizeof(double), "pose");
     if (s == VICP_OK)
         s = buf_alloc(c, c->rmse, sizeof(double), "rmse");
     if (s == VICP_OK)
@@ -1183,7 +1192,7 @@ void vicp_destroy(vicp_ctx *c)
                   &c->bcounts, &c->boff,     &c->brick_list, &c->brick_range, &c->brick_box, &c->bslot,
                   &c->boxk[0], &c->boxk[1], &c->sb_box,     &c->sb_left,    &c->keys,
                   &c->ids,     &c->csr,      &c->bpts,       &c->outside,    &c->nn,        &c->d2,
-                  &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->pose,       &c->rmse,       &c->ctl,       &c->bbox,
+                  &c->fb_list, &c->hv_list, &c->hv_range, &c->partials, &c->rmse,       &c->ctl,       &c->bbox,
                   &c->hsrc,    &c->htgt,    &c->fslots,   &c->fcount,   &c->fover,
                   &c->okeys[0], &c->okeys[1], &c->ocount, &c->ooff, &c->socc[0], &c->socc[1], &c->stile, &c->sdesc,
                   &c->pslot,   &c->lkeys,   &c->lseg,     &c->lroot,    &c->lparts};
