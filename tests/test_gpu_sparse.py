@@ -274,3 +274,36 @@ def test_sparse_kept_grid_reports_a_cloud_that_outgrows_the_table(pairs):
     ctx.build_grid(big)                      # and kept from here on
     ctx.dilate(10)
     assert ctx.sync() == 0
+
+
+def test_sparse_histogram_with_more_slot_tiles_than_shared_memory_holds():
+    """8.5M points on a 256^3 grid: the occupied-voxel table has 2^25 slots,
+    2,048 scan tiles -- more than a block's shared-memory tile totals hold,
+    so the histogram adds its tile totals per warp.  Keys, per-voxel counts,
+    segments and the CSR store against the oracle's keys and histogram."""
+    rng = np.random.default_rng(11)
+    n = 8_500_000
+    tgt = np.zeros((n, 4), np.float32)
+    tgt[:, :3] = rng.uniform(0.0, 1.0, (n, 3))
+    ctx, g = _sparse_grid(tgt, L=1, voxel_size=1.0 / 256, origin=(0.0, 0.0, 0.0), dims=(256, 256, 256))
+    okeys = g["occupied_keys"]
+    assert okeys.shape[0] == 1 << 25
+    grid = oracle.Grid(g["origin"], g["voxel_size"], g["inv_voxel_size"], g["dims"])
+    keys = oracle.keys(grid, tgt)
+    assert np.array_equal(g["keys"], keys)
+    V = int(np.prod(g["dims"]))
+    counts = np.bincount(keys[keys >= 0], minlength=V)
+    occ_slots = np.flatnonzero(okeys != EMPTY)
+    vox = okeys[occ_slots].astype(np.int64)
+    assert np.array_equal(np.sort(vox), np.flatnonzero(counts))
+    off = g["occupied_offsets"].astype(np.int64)
+    a, b = off[occ_slots], off[occ_slots + 1]
+    assert np.array_equal(b - a, counts[vox])
+    assert int(off[-1]) == g["n_stored"] == int((keys >= 0).sum())
+    order = np.argsort(a, kind="stable")
+    a_s, b_s = a[order], b[order]
+    assert a_s[0] == 0 and np.array_equal(a_s[1:], b_s[:-1])
+    store_vox = np.repeat(vox[order], b_s - a_s)
+    ids = g["ids"]
+    assert np.array_equal(keys[ids], store_vox)
+    assert np.array_equal(np.sort(ids), np.flatnonzero(keys >= 0))
