@@ -574,7 +574,10 @@ vicp_status run_step(vicp_ctx *c, const float4 *src, int m, double *pose, double
     return VICP_OK;
 }
 
-vicp_status build(vicp_ctx *c, const float *target, int32_t n)
+// load_from (may be null): the target cloud's page-locked host copy (its
+// device-mapped address); the histogram then reads the points from there
+// and stores them to `target` (device) for the kernels after it.
+vicp_status build(vicp_ctx *c, const float *target, int32_t n, const float *load_from = nullptr)
 {
     TRY(check_cloud(c, target, n, "target"));
     const float4 *tgt = reinterpret_cast<const float4 *>(target);
@@ -608,9 +611,11 @@ vicp_status build(vicp_ctx *c, const float *target, int32_t n)
     unsigned *tiles = (unsigned *)(sparse ? c->stile.p : c->tile_sum.p);
     unsigned *socc = sparse ? (unsigned *)c->socc[c->o_cur].p : nullptr;
     TRY(launch(c, K_HISTOGRAM, [&] {
-        return launch_histogram(tgt, n, g, (int *)c->keys.p, counts, (unsigned *)c->bcounts.p, occ, tiles,
+        return launch_histogram(load_from ? reinterpret_cast<const float4 *>(load_from) : tgt, n, g,
+                                (int *)c->keys.p, counts, (unsigned *)c->bcounts.p, occ, tiles,
                                 (unsigned *)c->sb_left.p, (unsigned *)c->boxk[c->occ_cur].p, d, c->stream, after_solve,
-                                sparse ? &ho : nullptr, socc, (int *)c->pslot.p);
+                                sparse ? &ho : nullptr, socc, (int *)c->pslot.p,
+                                load_from ? const_cast<float4 *>(tgt) : nullptr);
     }));
     cudaError_t ev = cudaEventRecord(c->ev_hist, c->stream);   // the dilation may start from here
     if (ev != cudaSuccess)
@@ -795,9 +800,14 @@ vicp_status dilate(vicp_ctx *c, int32_t layers)
 // ordered after that work here), then on the context's stream build,
 // dilate, a wait for the copy stream, the iterations, and the pose and the
 // control block (loop state, status word) copied to out_pose / out_ctl
-// (host).
+// (host).  tgt_load and src_late (host_copies only; may be null): the first
+// build's histogram reads the target from its page-locked host copy
+// (device-mapped address) and stores it to tgt, and the source cloud's copy
+// from src_late is queued on the copy stream after that histogram, so that
+// the two clouds cross the host link one after the other.
 vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const float *tgt, int32_t n,
-                              const double *pose_in, void *out_pose, DevCtl *out_ctl, bool host_copies)
+                              const double *pose_in, void *out_pose, DevCtl *out_ctl, bool host_copies,
+                              const float *tgt_load = nullptr, const void *src_late = nullptr)
 {
     double *pose = reg_pose_of(c);
     DevCtl *d = ctl_of(c);
@@ -811,11 +821,20 @@ vicp_status registration_work(vicp_ctx *c, const float4 *src, int32_t m, const f
         e = cudaMemcpyAsync(pose, pose_in, 16 * sizeof(double), cudaMemcpyHostToDevice, c->copy);
     if (e == cudaSuccess)   // stop, iters, prev_rmse, last_rmse (the build's kernels use other fields)
         e = cudaMemsetAsync(&d->stop, 0, sizeof(DevCtl) - offsetof(DevCtl, stop), c->copy);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !src_late)
         e = cudaEventRecord(c->ev_src, c->copy);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "pose upload and loop state reset");
-    TRY(build(c, tgt, n));
+    TRY(build(c, tgt, n, tgt_load));
+    if (src_late) {   // ev_hist: recorded by the build right after its histogram
+        e = cudaStreamWaitEvent(c->copy, c->ev_hist, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void *)src, src_late, (size_t)m * 16, cudaMemcpyHostToDevice, c->copy);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(c->ev_src, c->copy);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "host-to-device copy of the source cloud");
+    }
     TRY(dilate(c, -1));
     e = cudaStreamWaitEvent(c->stream, c->ev_src, 0);
     if (e != cudaSuccess)
@@ -907,10 +926,21 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
     c->after_solve = false;
     cudaGraph_t g = nullptr;
     vicp_status s = VICP_OK;
+    // A page-locked host target is read by the first histogram itself (its
+    // device-mapped address); a pageable one is copied first.
+    const float *tgt_mapped = nullptr;
+    if (key.host) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, tgt_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer && (reinterpret_cast<uintptr_t>(pa.devicePointer) & 15u) == 0)
+            tgt_mapped = static_cast<const float *>(pa.devicePointer);
+        cudaGetLastError();
+    }
     cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         // the buffers the call's first build fills are reset on the copy
-        // stream, beside the target cloud's copy (with host clouds)
+        // stream (with host clouds: beside the target cloud's copy, or
+        // before the histogram that reads it from host memory)
         const int first = c->occ_cur ^ 1;
         cudaStream_t rs = key.host ? c->copy : c->gstream;
         if (key.host) {
@@ -922,7 +952,11 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
             e = cudaMemsetAsync(c->occ[first].p, 0, c->occ[first].bytes, rs);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(c->boxk[first].p, 0xff, c->boxk[first].bytes, rs);
-        if (e == cudaSuccess && key.host) {
+        if (e == cudaSuccess && key.host && tgt_mapped) {   // the source is copied after the histogram
+            e = cudaEventRecord(c->ev_clr, c->copy);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(c->gstream, c->ev_clr, 0);
+        } else if (e == cudaSuccess && key.host) {
             const size_t sb = (size_t)key.m * 16, tb = (size_t)key.n * 16;
             e = cudaEventRecord(c->ev_clr, c->copy);
             if (e == cudaSuccess)
@@ -939,7 +973,8 @@ vicp_status capture_registration(vicp_ctx *c, const vicp_ctx::RegKey &key, const
                 e = cudaEventRecord(c->ev_src, c->copy);
         }
         if (e == cudaSuccess)
-            s = registration_work(c, src, key.m, tgt, key.n, c->h_pose, c->h_out->pose, &c->h_out->ctl, key.host);
+            s = registration_work(c, src, key.m, tgt, key.n, c->h_pose, c->h_out->pose, &c->h_out->ctl, key.host,
+                                  tgt_mapped, tgt_mapped ? src_host : nullptr);
         const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
         if (e == cudaSuccess)
             e = e2;

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
                                                    unsigned *__restrict__ tile_sum, unsigned *__restrict__ sb_left,
                                                    unsigned *__restrict__ boxk, DevCtl *__restrict__ ctl,
                                                    HashTable ho, unsigned *__restrict__ socc,
-                                                   int *__restrict__ pslot)
+                                                   int *__restrict__ pslot, float4 *__restrict__ copy_out)
 {
     // In the ICP loop a build follows the previous iteration's reduction and
     // solve (AFTER_SOLVE), whose single-block tail leaves the GPU idle; the
@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
     float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (j < n) {
         q = __ldg(pts + j);
+        if (copy_out)   // pts is the caller's page-locked host cloud: keep a device copy
+            copy_out[j] = q;
         int ix, iy, iz;
         if (voxel_coords(g, q.x, q.y, q.z, ix, iy, iz)) {
             key = ix + g.nx * (iy + g.ny * iz);
@@ -196,17 +198,17 @@ __global__ void __launch_bounds__(256) k_histogram(const float4 *__restrict__ pt
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
                              unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve, const HashTable *ho,
-                             unsigned *socc, int *pslot)
+                             unsigned *socc, int *pslot, float4 *copy_out)
 {
     // occ must hold zeros: the caller clears it beforehand
     const HashTable h = ho ? *ho : HashTable{nullptr, 0u, 32};
     if (ho)
         return launch_kernel(after_solve ? k_histogram<true, true> : k_histogram<false, true>, dim3((n + 255) / 256),
                              dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ, tile_sum, sb_left, boxk, ctl, h,
-                             socc, pslot);
+                             socc, pslot, copy_out);
     return launch_kernel(after_solve ? k_histogram<true, false> : k_histogram<false, false>, dim3((n + 255) / 256),
                          dim3(256), 0, st, pts, n, g, keys, counts, bcounts, occ, tile_sum, sb_left, boxk, ctl, h,
-                         socc, pslot);
+                         socc, pslot, copy_out);
 }
 
 // ---------------------------------------------------------------------------

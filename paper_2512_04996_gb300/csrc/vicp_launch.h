@@ -75,10 +75,14 @@ cudaError_t launch_bbox(const float4 *pts, int n, unsigned *bbox6, cudaStream_t 
 // ho (the sparse grid; null: dense): counts, tile_sum and socc are indexed
 // by the voxel's slot in the occupied-voxel table ho, and pslot[j] receives
 // point j's slot (-1 outside the grid); occ is still indexed by voxel key.
+// copy_out (may be null): pts is a page-locked host cloud (its device-mapped
+// address), and every point is also stored to copy_out[j] (device memory),
+// so that the cloud crosses the host link once, inside the histogram.
 cudaError_t launch_histogram(const float4 *pts, int n, const GridGeom &g, int *keys, unsigned *counts,
                              unsigned *bcounts, unsigned *occ, unsigned *tile_sum, unsigned *sb_left,
                              unsigned *boxk, DevCtl *ctl, cudaStream_t st, bool after_solve,
-                             const HashTable *ho = nullptr, unsigned *socc = nullptr, int *pslot = nullptr);
+                             const HashTable *ho = nullptr, unsigned *socc = nullptr, int *pslot = nullptr,
+                             float4 *copy_out = nullptr);
 // dense: every off[v]; sparse: only off[v] and off[v + 1] of occupied voxels,
 // off[32 k] and off[V] (what the build and the searches read) -- the rest
 // is completed by launch_offsets_fill on the same occupancy bits.
