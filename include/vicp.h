@@ -253,7 +253,12 @@ VICP_API vicp_status vicp_register(vicp_ctx *ctx, const float *src_xyzw, int32_t
  * the grid build, the source on an internal copy stream while the grid is
  * built (ordered after all work issued earlier on the context's stream; the
  * first search waits for it).  Host buffers should be pinned for the copies
- * to run asynchronously. */
+ * to run asynchronously.  A replayed call (above) with a page-locked target
+ * (cudaHostAlloc / cudaHostRegister, 16-byte aligned) does not copy it
+ * first: the first build's histogram reads the points through their
+ * device-mapped address and stores the device copy, and the source cloud's
+ * copy follows that histogram.  Either way both buffers are read during the
+ * call only and must not change until it returns. */
 VICP_API vicp_status vicp_register_host(vicp_ctx *ctx, const float *src_xyzw_host, int32_t n_src,
                                const float *tgt_xyzw_host, int32_t n_tgt, double pose_host[16],
                                int32_t *iters_out, double *rmse_out);
